@@ -1,0 +1,485 @@
+"""FP64 CPU oracle for fast-convolution (FC) filtered CP-OFDM TX synthesis and RX analysis.
+
+TEST INFRASTRUCTURE ONLY. This module exists to check the CUDA library. Only
+``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of
+``bench.py`` may import or call it; the product path (the C-ABI library in
+``paper_2008_00672_gb300`` and its Python binding) never does, and it shares no
+code with it.
+
+What it computes, in the paper's order and notation (Yli-Kaakinen et al.,
+"Frequency-Domain Signal Processing for Spectrally-Enhanced CP-OFDM Waveforms
+in 5G New Radio"):
+
+* CP-OFDM modulation with per-symbol CP lengths (Sec. III-A, eq:TX_OFDMmod, eq:TX_CPins).
+* Continuous FC synthesis, OLA or OLS (Sec. III-B, eq:BDM, eq:tx_matrix1,
+  eq:ola_synthesis, eq:ols_synthesis, eq:ola_proc), the FC parameters of eqn:Rk.
+* Symbol-synchronized FC synthesis for one and for several symbols
+  (Sec. III-C/D, eq:padding, eq:multi-symb, eq:Gamma, eq:waveformLen) with the
+  CP extrapolation of Sec. III-E.
+* Continuous and symbol-synchronized FC analysis, OLA or OLS (Sec. IV,
+  eq:ola_analysis, eq:ols_analysis, eq:1, eq:concat2) and OFDM demodulation.
+
+Every DFT is the plain O(n^2) definition W_n[k,t] = exp(-j 2 pi k t / n) with the
+exponent reduced exactly (k*t mod n) before the FP64 exp; the independent FC
+blocks of one subband are stacked as the columns of one matrix, which is the
+block-diagonal F_m of eq:tx_matrix1 written out.
+
+Readings taken where the paper is silent, ambiguous or garbled (cited inline as Rk):
+  R2  bin map: shifted row p goes to long bin (c_m + p - floor(L/2)) mod N, so c_m is
+      the DC bin also for odd L (the printed Xi uses ceil(L/2)).
+  R3  sqrt(I_m) multiplies the TX output in both modes; RX multiplies by 1/sqrt(I_m).
+  R4  RX multiplies the gathered bins by conj(phi_r theta_n); then G = F^H exactly.
+  R5  theta_n has the positive exponent and its CP sum runs q = 1..n.
+  R6  N_L = ceil(N_O/2), N_T = floor(N_O/2), as for the low-rate split.
+  R7  RX extension removal keeps [L_L, L_L + L) of the 3L/2 concatenation buffer.
+  R8  RX segmentation is w_hat_n = Gamma_{sigma_n}^T x_hat (the stray sum over n dropped).
+  R10 symbol-synchronized mode needs lambda = 0.5, 4 | L, 4 | N, L_OFDM = L, N_CP,n <= N/4.
+  R11 L_CP,n = floor(N_CP,n L / N) in integer arithmetic.
+  R13 active subcarriers sit at signed frequencies -floor(L_act/2) .. ceil(L_act/2)-1.
+  R14 numerology groups are aligned on symbol 0's CP start and summed in time.
+  R17 OLS symbol-synchronized TX keeps [N/4 - N_CP,n, 3N/4) of block 0 and
+      [N/4, 3N/4) of block 1 (rectangular; the optional taper is unspecified).
+  R18 phase arguments are reduced exactly in integers before exp().
+  Continuous frames use R = ceil((n + 2 S_L - L)/L_S) + 1 blocks covering the padded
+  input [0_{S_L}; s; 0_{S_L}] and emit (R-1) N_S + N samples.
+
+Pins (tests/test_oracle_pins.py): printed plan numbers (Sec. III-E, Fig. Extrapol),
+DFT closed forms, delayed identity, brute-force linear convolution, exact
+adjoint between TX-OLA and RX-OLS (and TX-OLS / RX-OLA), symbol locality,
+zero-CP equivalence of symbol-synchronized and continuous processing, exact
+continuous-vs-synchronized agreement at I=1 (pins theta_n), tone and
+round-trip checks. The transition weights D_m are an input (the paper does not
+print them): parity unpinned for their values, which never enter the oracle's
+arithmetic beyond a diagonal multiply.
+"""
+from __future__ import annotations
+
+import functools
+import math
+
+import numpy as np
+
+CONTINUOUS, SYMBOL_SYNC = 0, 1
+OLA, OLS = 0, 1
+
+
+# ---------------------------------------------------------------------------
+# DFT matrices (Sec. III-B: W_L and W_N^{-1} are the DFT and IDFT matrices)
+# ---------------------------------------------------------------------------
+
+@functools.lru_cache(maxsize=8)
+def dft_matrix(n: int) -> np.ndarray:
+    """W_n[k, t] = exp(-j 2 pi k t / n), unnormalised, exponent reduced mod n exactly."""
+    k = np.arange(n, dtype=np.int64)
+    e = np.outer(k, k) % n
+    w = np.exp(-2j * np.pi * e.astype(np.float64) / n)
+    w.setflags(write=False)
+    return w
+
+
+def dft(x: np.ndarray) -> np.ndarray:
+    """W_n x along axis 0."""
+    return dft_matrix(x.shape[0]) @ x
+
+
+def idft(x: np.ndarray) -> np.ndarray:
+    """W_n^{-1} x = (1/n) conj(W_n) x along axis 0."""
+    n = x.shape[0]
+    return np.conj(dft_matrix(n)) @ x / n
+
+
+def root_of_unity(num: int, den: int) -> complex:
+    """exp(+j 2 pi num/den) with the fraction reduced exactly in integers (reading R18)."""
+    return complex(np.exp(2j * np.pi * ((num % den) / den)))
+
+
+# ---------------------------------------------------------------------------
+# FC parameters (Sec. III-B, eqn:Rk)
+# ---------------------------------------------------------------------------
+
+class Dims:
+    """FC parameters of subband m in its group.
+
+    lambda = L_O/L, L_S = L - L_O, L_L = ceil(L_O/2), L_T = floor(L_O/2);
+    N_O = lambda N, N_S = (1-lambda) N, and N_L/N_T split N_O the same way
+    (reading R6); I = N/L (eqn:Rk).
+    """
+
+    def __init__(self, group, sub):
+        self.N = N = int(group.n_long)
+        self.L = L = int(sub.l_short)
+        self.N_O = int(group.n_overlap)
+        if (self.N_O * L) % N:
+            raise ValueError("L_O = N_O*L/N is not an integer")
+        self.L_O = self.N_O * L // N
+        self.L_S = L - self.L_O
+        self.L_L = -(-self.L_O // 2)
+        self.L_T = self.L_O // 2
+        self.N_S = N - self.N_O
+        self.N_L = -(-self.N_O // 2)
+        self.N_T = self.N_O // 2
+        self.I = N / L
+        self.c = int(sub.centre_bin)
+        self.L_ofdm = int(sub.l_ofdm)
+        self.L_act = int(sub.n_active)
+        self.D = np.asarray(sub.weights, dtype=np.float64)
+        if self.D.shape != (L,):
+            raise ValueError("weights must have l_short entries")
+        self.n_cp = [int(v) for v in group.n_cp]
+        self.B = len(self.n_cp)
+
+
+def low_rate_cp(d: Dims, mode: int) -> list:
+    """L_CP,m,n.
+
+    Continuous processing needs integer low-rate CPs, N_CP,n = I L_CP,n exactly
+    (Sec. II). Symbol-synchronized processing truncates,
+    L_CP,m,n = floor(N_CP,m,n / I_m) (Sec. III-E), computed in integers (reading R11).
+    """
+    out = []
+    for ncp in d.n_cp:
+        if mode == CONTINUOUS and (ncp * d.L) % d.N:
+            raise ValueError("continuous FC needs N_CP,n*L/N to be an integer")
+        out.append(ncp * d.L // d.N)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CP-OFDM (Sec. III-A)
+# ---------------------------------------------------------------------------
+
+def active_bins(n_active: int, n_fft: int) -> np.ndarray:
+    """DFT bins of the active subcarriers, signed frequencies
+    -floor(L_act/2) .. ceil(L_act/2)-1 (reading R13)."""
+    f = np.arange(n_active) - n_active // 2
+    return f % n_fft
+
+
+def ofdm_modulate(x_act: np.ndarray, n_fft: int) -> np.ndarray:
+    """eq:TX_OFDMmod: x_OFDM = sqrt(L_OFDM) W^{-1}_{L_OFDM} x, x holding the QAM
+    symbols on the active subcarriers and zeros elsewhere."""
+    x = np.zeros(n_fft, dtype=np.complex128)
+    x[active_bins(len(x_act), n_fft)] = x_act
+    return math.sqrt(n_fft) * idft(x)
+
+
+def cp_insert(x_ofdm: np.ndarray, l_cp: int) -> np.ndarray:
+    """eq:TX_CPins: K_{L_CP} prepends the last L_CP samples."""
+    if l_cp == 0:
+        return x_ofdm.copy()
+    return np.concatenate([x_ofdm[-l_cp:], x_ofdm])
+
+
+def ofdm_demodulate(x_ofdm: np.ndarray, n_active: int) -> np.ndarray:
+    """Sec. IV: x_hat = (1/sqrt(L_OFDM)) W_{L_OFDM} x_hat_OFDM, active bins kept."""
+    n = len(x_ofdm)
+    return (dft(x_ofdm) / math.sqrt(n))[active_bins(n_active, n)]
+
+
+# ---------------------------------------------------------------------------
+# One FC block: F_{m,r} (eq:ola_synthesis / eq:ols_synthesis) and its RX
+# counterpart G_{m,r} (eq:ola_analysis / eq:ols_analysis), applied to columns.
+# ---------------------------------------------------------------------------
+
+def _shift_rows(L: int) -> np.ndarray:
+    """P^{(L/2)}: shifted row p holds original bin (p - floor(L/2)) mod L."""
+    return (np.arange(L) - L // 2) % L
+
+
+def _long_bins(d: Dims) -> np.ndarray:
+    """Xi: shifted row p maps to long bin (c_m + p - floor(L/2)) mod N (reading R2)."""
+    return (d.c + np.arange(d.L) - d.L // 2) % d.N
+
+
+def synthesis_blocks(Z: np.ndarray, d: Dims, phases: np.ndarray) -> np.ndarray:
+    """sqrt(I) W_N^{-1} M_m(phase_r) D_m P^{(L/2)} W_L applied to the columns of Z
+    (L x R, already time-windowed). Returns N x R high-rate blocks (no S window).
+    The sqrt(I) of eq:BDM is applied in both processing modes (reading R3)."""
+    U = dft(Z)                                     # W_L
+    V = U[_shift_rows(d.L), :]                     # P^{(L/2)}
+    V = V * d.D[:, None]                           # D_m
+    Y = np.zeros((d.N, Z.shape[1]), dtype=np.complex128)
+    np.add.at(Y, _long_bins(d), V * phases[None, :])   # M_m(phase)
+    return math.sqrt(d.I) * idft(Y)                # sqrt(I) W_N^{-1}
+
+
+def analysis_blocks(Wb: np.ndarray, d: Dims, phases: np.ndarray) -> np.ndarray:
+    """(1/sqrt(I)) W_L^{-1} P^{(-L/2)} D_m M_m(phase)^T W_N on the columns of Wb
+    (N x R, already time-windowed), with the conjugated phase (reading R4).
+    Returns L x R low-rate blocks (no S window)."""
+    Y = dft(Wb)                                    # W_N
+    V = Y[_long_bins(d), :] * np.conj(phases)[None, :]   # M^T with conj(phase)
+    V = V * d.D[:, None]                           # D_m
+    U = np.empty_like(V)
+    U[_shift_rows(d.L), :] = V                     # P^{(-L/2)} = (P^{(L/2)})^T
+    return idft(U) / math.sqrt(d.I)                # W_L^{-1} / sqrt(I)
+
+
+def _window(lead: int, ones: int, tail: int) -> np.ndarray:
+    return np.concatenate([np.zeros(lead), np.ones(ones), np.zeros(tail)])
+
+
+# ---------------------------------------------------------------------------
+# Continuous FC (Sec. III-B) on a low-rate stream s of one subband
+# ---------------------------------------------------------------------------
+
+def lead_pad_low(group, d: Dims) -> int:
+    """S_L (low rate). eq:BDM pads S_L zeros on both ends; the paper's typical
+    choice is S_L = L_O. The group's lead_pad is S_L*I in high-rate samples."""
+    hi = d.N_O if group.lead_pad < 0 else int(group.lead_pad)
+    if (hi * d.L) % d.N:
+        raise ValueError("lead pad is not an integer number of low-rate samples")
+    s_l = hi * d.L // d.N
+    if s_l < d.L_L:
+        raise ValueError("lead pad shorter than L_L")
+    return s_l
+
+
+def continuous_block_count(n_low: int, s_l: int, d: Dims) -> int:
+    """R_m: blocks of length L at hop L_S covering [0_{S_L}; s; 0_{S_L}]."""
+    u0 = n_low + 2 * s_l
+    if u0 <= d.L:
+        return 1
+    return -(-(u0 - d.L) // d.L_S) + 1
+
+
+def tx_continuous_subband(s: np.ndarray, group, sub, scheme: int) -> np.ndarray:
+    """w_m = sqrt(I) F_m [0_{S_L}; s; 0_{S_L}] (eq:BDM, eq:tx_matrix1) with
+    OLA (eq:ola_synthesis, A_{m,r} of eq:ola_proc) or OLS (eq:ols_synthesis,
+    S_{m,r} of eq:ola_proc). Output length (R-1) N_S + N; time 0 is the first
+    sample of the zero-padded input (times I)."""
+    d = Dims(group, sub)
+    s_l = lead_pad_low(group, d)
+    R = continuous_block_count(len(s), s_l, d)
+    u = np.zeros((R - 1) * d.L_S + d.L, dtype=np.complex128)
+    u[s_l:s_l + len(s)] = s
+    Z = np.stack([u[r * d.L_S: r * d.L_S + d.L] for r in range(R)], axis=1)
+    if scheme == OLA:
+        Z = Z * _window(d.L_L, d.L_S, d.L_T)[:, None]           # A_{m,r}
+    phases = np.array([root_of_unity(r * d.c * d.L_S, d.L) for r in range(R)])   # phi_{m,r}
+    Yb = synthesis_blocks(Z, d, phases)
+    out = np.zeros((R - 1) * d.N_S + d.N, dtype=np.complex128)
+    for r in range(R):
+        if scheme == OLA:
+            out[r * d.N_S: r * d.N_S + d.N] += Yb[:, r]
+        else:                                                    # S_{m,r}: keep [N_L, N_L+N_S)
+            out[r * d.N_S + d.N_L: r * d.N_S + d.N_L + d.N_S] += Yb[d.N_L:d.N_L + d.N_S, r]
+    return out
+
+
+def rx_continuous_subband(x: np.ndarray, group, sub, scheme: int, n_low: int) -> np.ndarray:
+    """Continuous FC analysis of the subband: blocks of N at hop N_S over x
+    (the same timing as tx_continuous_subband), G^(OLA) with the high-rate A
+    window of eq:1 or G^(OLS) with the low-rate S window of eq:1. Returns the
+    n_low low-rate samples at the positions of s."""
+    d = Dims(group, sub)
+    s_l = lead_pad_low(group, d)
+    R = continuous_block_count(n_low, s_l, d)
+    need = (R - 1) * d.N_S + d.N
+    xx = np.zeros(need, dtype=np.complex128)
+    xx[:min(need, len(x))] = x[:need]
+    Wb = np.stack([xx[r * d.N_S: r * d.N_S + d.N] for r in range(R)], axis=1)
+    if scheme == OLA:
+        Wb = Wb * _window(d.N_L, d.N_S, d.N_T)[:, None]          # A_{m,r} (high rate)
+    phases = np.array([root_of_unity(r * d.c * d.L_S, d.L) for r in range(R)])
+    Zb = analysis_blocks(Wb, d, phases)
+    u = np.zeros((R - 1) * d.L_S + d.L, dtype=np.complex128)
+    for r in range(R):
+        if scheme == OLS:                                        # S_{m,r} (low rate)
+            u[r * d.L_S + d.L_L: r * d.L_S + d.L_L + d.L_S] += Zb[d.L_L:d.L_L + d.L_S, r]
+        else:
+            u[r * d.L_S: r * d.L_S + d.L] += Zb[:, r]
+    return u[s_l:s_l + n_low]
+
+
+def continuous_symbol_offsets(d: Dims, l_cp: list) -> list:
+    """Start of each CP-OFDM symbol in the concatenated low-rate stream."""
+    off, acc = [], 0
+    for lc in l_cp:
+        off.append(acc)
+        acc += lc + d.L_ofdm
+    return off + [acc]
+
+
+# ---------------------------------------------------------------------------
+# Symbol-synchronized FC (Sec. III-C..E, Sec. IV), lambda = 0.5
+# ---------------------------------------------------------------------------
+
+def sync_check(d: Dims):
+    """The symbol-synchronized equations hard-code lambda = 0.5, 3L/2 segments and
+    L/4 shifts, and L_OFDM = L (reading R10)."""
+    if 2 * d.N_O != d.N or d.L % 4 or d.N % 4 or d.L_ofdm != d.L:
+        raise ValueError("symbol-synchronized FC needs N_O = N/2, 4 | L, 4 | N, L_OFDM = L")
+    for ncp in d.n_cp:
+        if ncp > d.N // 4:
+            raise ValueError("N_CP,n must not exceed N/4 (S_L,n >= 0)")
+
+
+def sync_sigma(d: Dims) -> list:
+    """sigma_n = n N_OFDM + sum_{q=1}^{n} N_CP,q (eq:multi-symb), N_OFDM = N."""
+    out, acc = [], 0
+    for n in range(d.B):
+        if n > 0:
+            acc += d.n_cp[n]
+        out.append(n * d.N + acc)
+    return out
+
+
+def sync_waveform_len(d: Dims) -> int:
+    """Q = N_L + N_T + B N_OFDM + sum_{n=1}^{B-1} N_CP,n (eq:waveformLen)."""
+    return d.N_L + d.N_T + d.B * d.N + sum(d.n_cp[1:])
+
+
+def sync_theta(d: Dims, n: int) -> complex:
+    """theta_n = exp(j 2 pi c_m phi_n), phi_n = (1/N) sum_{q=1}^{n} N_CP,q (Sec. III-C);
+    positive exponent, q from 1 (reading R5)."""
+    return root_of_unity(d.c * sum(d.n_cp[1:n + 1]), d.N)
+
+
+def tx_sync_subband(grid_rows: np.ndarray, group, sub, scheme: int) -> np.ndarray:
+    """Symbol-synchronized FC synthesis of one subband, all B symbols, length Q."""
+    d = Dims(group, sub)
+    sync_check(d)
+    l_cp = low_rate_cp(d, SYMBOL_SYNC)
+    sig = sync_sigma(d)
+    L, N = d.L, d.N
+    out = np.zeros(sync_waveform_len(d), dtype=np.complex128)
+    for n in range(d.B):
+        lc = l_cp[n]
+        x_cp = cp_insert(ofdm_modulate(grid_rows[n], L), lc)
+        s_ln = d.L_L - lc                                        # S_L,m,n
+        z = np.concatenate([np.zeros(s_ln), x_cp, np.zeros(d.L_T)])    # eq:padding, 3L/2
+        Z = np.stack([z[0:L], z[L // 2: L // 2 + L]], axis=1)   # (R_L^{(r)})^T z
+        if scheme == OLA:
+            Z[:, 0] *= _window(s_ln, d.L_S + lc, d.L_T)          # a_{m,0}, shortened overlap
+            Z[:, 1] *= _window(d.L_L, d.L_S, d.L_T)              # a_{m,1}
+        th = sync_theta(d, n)
+        phases = np.array([root_of_unity(r * d.c * d.L_S, L) * th for r in range(2)])  # phi_r theta_n
+        Yb = synthesis_blocks(Z, d, phases)
+        if scheme == OLS:                                        # reading R17
+            ncp = d.n_cp[n]
+            Yb[:, 0] *= _window(d.N_L - ncp, ncp + d.N_S, d.N_T)
+            Yb[:, 1] *= _window(d.N_L, d.N_S, d.N_T)
+        w = np.zeros(3 * N // 2, dtype=np.complex128)
+        w[0:N] += Yb[:, 0]                                       # R_N^{(0)}
+        w[N // 2: N // 2 + N] += Yb[:, 1]                        # R_N^{(1)}
+        out[sig[n]: sig[n] + 3 * N // 2] += w                    # Gamma_{sigma_n}
+    return out
+
+
+def rx_sync_subband(x: np.ndarray, group, sub, scheme: int) -> np.ndarray:
+    """Symbol-synchronized FC analysis + OFDM demodulation of one subband.
+    Returns [B, L_act] QAM estimates."""
+    d = Dims(group, sub)
+    sync_check(d)
+    sig = sync_sigma(d)
+    L, N = d.L, d.N
+    out = np.zeros((d.B, d.L_act), dtype=np.complex128)
+    for n in range(d.B):
+        wn = x[sig[n]: sig[n] + 3 * N // 2]                      # Gamma_{sigma_n}^T x (reading R8)
+        Wb = np.stack([wn[0:N], wn[N // 2: N // 2 + N]], axis=1)  # (R_N^{(r)})^T
+        if scheme == OLA:
+            Wb = Wb * _window(d.N_L, d.N_S, d.N_T)[:, None]      # A_{m,r}, eq:1
+        th = sync_theta(d, n)
+        phases = np.array([root_of_unity(r * d.c * d.L_S, L) * th for r in range(2)])
+        Zb = analysis_blocks(Wb, d, phases)
+        if scheme == OLS:
+            Zb = Zb * _window(d.L_L, d.L_S, d.L_T)[:, None]      # S_{m,r}, eq:1
+        zs = np.zeros(3 * L // 2, dtype=np.complex128)
+        zs[0:L] += Zb[:, 0]                                      # R_L^{(0)}
+        zs[L // 2: L // 2 + L] += Zb[:, 1]                       # R_L^{(1)}
+        x_ofdm = zs[d.L_L: d.L_L + L]                            # extension removal (reading R7)
+        out[n] = ofdm_demodulate(x_ofdm, d.L_act)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Frames: subbands of all groups summed, x = sum_m w_m (Sec. III-B)
+# ---------------------------------------------------------------------------
+
+def _group_of(geom, m):
+    return geom.groups[geom.subbands[m].group]
+
+
+def group_lead_and_len(geom, gi: int) -> tuple:
+    """(T_g, len_g): where symbol 0's CP starts in the group's own output, and
+    that output's length. Continuous: T_g = S_L I (eq:BDM padding); symbol-sync:
+    T_g = N/4 - N_CP,0 and len_g = Q (eq:waveformLen)."""
+    g = geom.groups[gi]
+    subs = [s for s in geom.subbands if s.group == gi]
+    if not subs:
+        raise ValueError("group without subbands")
+    d = Dims(g, subs[0])
+    if geom.mode == SYMBOL_SYNC:
+        return d.N // 4 - d.n_cp[0], sync_waveform_len(d)
+    s_l = lead_pad_low(g, d)
+    l_cp = low_rate_cp(d, CONTINUOUS)
+    n_low = sum(l_cp) + d.B * d.L_ofdm
+    R = continuous_block_count(n_low, s_l, d)
+    return s_l * d.N // d.L, (R - 1) * d.N_S + d.N
+
+
+def frame_layout(geom) -> tuple:
+    """Groups are placed so that symbol 0's CP starts at the same time T_s in every
+    group (reading R14). Returns (offsets per group, frame length)."""
+    ll = [group_lead_and_len(geom, gi) for gi in range(len(geom.groups))]
+    t_s = max(t for t, _ in ll)
+    offs = [t_s - t for t, _ in ll]
+    return offs, max(o + n for o, (_, n) in zip(offs, ll))
+
+
+def split_grid(geom, grid: np.ndarray) -> list:
+    """Per-subband [B, L_act] views of one stream's QAM grid (ABI layout)."""
+    out, pos = [], 0
+    for s in geom.subbands:
+        b = geom.groups[s.group].n_symbols
+        out.append(grid[pos:pos + b * s.n_active].reshape(b, s.n_active))
+        pos += b * s.n_active
+    return out
+
+
+def continuous_stream(rows: np.ndarray, d: Dims, l_cp: list) -> np.ndarray:
+    """Concatenated low-rate CP-OFDM symbols of one subband (Sec. II)."""
+    return np.concatenate([cp_insert(ofdm_modulate(rows[n], d.L_ofdm), l_cp[n]) for n in range(d.B)])
+
+
+def tx_frame(geom, grid: np.ndarray) -> np.ndarray:
+    """One stream: QAM grid -> high-rate FC-F-OFDM waveform x = sum_m w_m."""
+    offs, flen = frame_layout(geom)
+    out = np.zeros(flen, dtype=np.complex128)
+    for m, (sub, rows) in enumerate(zip(geom.subbands, split_grid(geom, np.asarray(grid)))):
+        g = geom.groups[sub.group]
+        if geom.mode == SYMBOL_SYNC:
+            w = tx_sync_subband(rows, g, sub, geom.scheme_tx)
+        else:
+            d = Dims(g, sub)
+            w = tx_continuous_subband(continuous_stream(rows, d, low_rate_cp(d, CONTINUOUS)),
+                                      g, sub, geom.scheme_tx)
+        o = offs[sub.group]
+        out[o:o + len(w)] += w
+    return out
+
+
+def rx_frame(geom, wave: np.ndarray) -> np.ndarray:
+    """One stream: received waveform -> QAM estimates in the grid layout."""
+    offs, flen = frame_layout(geom)
+    wave = np.asarray(wave, dtype=np.complex128)
+    parts = []
+    for sub in geom.subbands:
+        g = geom.groups[sub.group]
+        o = offs[sub.group]
+        d = Dims(g, sub)
+        if geom.mode == SYMBOL_SYNC:
+            est = rx_sync_subband(wave[o:], g, sub, geom.scheme_rx)
+        else:
+            l_cp = low_rate_cp(d, CONTINUOUS)
+            offs_low = continuous_symbol_offsets(d, l_cp)
+            s_hat = rx_continuous_subband(wave[o:], g, sub, geom.scheme_rx, offs_low[-1])
+            est = np.stack([ofdm_demodulate(s_hat[offs_low[n] + l_cp[n]: offs_low[n] + l_cp[n] + d.L_ofdm],
+                                            d.L_act) for n in range(d.B)])
+        parts.append(est.reshape(-1))
+    return np.concatenate(parts)
+
+
+def frame_len(geom) -> int:
+    return frame_layout(geom)[1]

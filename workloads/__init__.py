@@ -1,0 +1,223 @@
+"""Seeded synthetic 5G-NR-shaped workloads for FC-filtered CP-OFDM.
+
+This module is shared by the FP64 oracle, the tests and the benchmark. It holds
+only *descriptions* of the processing geometry (numerology, subband placement,
+CP schedules, transition weights chosen as an input) and seeded random data
+(QAM grids, AWGN). It contains none of the fast-convolution arithmetic: no
+transform, window, bin map, phase or block assembly lives here.
+
+Conventions shared with the C ABI (``include/fcofdm.h``):
+
+* ``mode``: 0 = continuous FC processing (Sec. II), 1 = symbol-synchronized
+  discontinuous FC processing (Sec. III-IV).
+* ``scheme_tx`` / ``scheme_rx``: 0 = overlap-and-add, 1 = overlap-and-save.
+* A QAM grid for one stream is the concatenation, subband by subband in the
+  order given, of ``[B_g][L_act,m]`` complex symbols, where ``B_g`` is the
+  symbol count of the subband's numerology group. Active subcarriers are stored
+  in ascending signed frequency ``f = -floor(L_act/2) ... ceil(L_act/2)-1``.
+* Weights ``D_m`` are real, one per short-transform bin, in fftshifted order
+  (index ``p`` holds signed bin ``p - floor(L_m/2)``).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+
+CONTINUOUS, SYMBOL_SYNC = 0, 1
+OLA, OLS = 0, 1
+
+
+@dataclass(frozen=True)
+class Group:
+    """One numerology group: shares the long transform size and symbol timing."""
+    n_long: int                 # N, long (high-rate) transform size
+    n_overlap: int              # N_O = lambda*N high-rate overlap samples
+    n_cp: tuple                 # N_CP,n per symbol, high-rate samples (len = B)
+    lead_pad: int = -1          # continuous mode: S_L*I_m in high-rate samples; -1 -> N_O
+
+    @property
+    def n_symbols(self) -> int:
+        return len(self.n_cp)
+
+
+@dataclass(frozen=True)
+class Subband:
+    """One FC subband (Sec. II-B); ``weights`` is D_m in fftshifted order."""
+    l_short: int                # L_m
+    l_ofdm: int                 # L_OFDM,m
+    n_active: int               # L_act,m
+    centre_bin: int             # c_m on the long grid (may be negative)
+    group: int                  # index into Geometry.groups
+    weights: np.ndarray = field(compare=False, repr=False)
+
+
+@dataclass(frozen=True)
+class Geometry:
+    mode: int
+    scheme_tx: int
+    scheme_rx: int
+    groups: tuple
+    subbands: tuple
+    name: str = ""
+    qam_order: int = 4
+
+    def grid_len(self) -> int:
+        """Complex QAM symbols per stream (sum over subbands of B_g * L_act,m)."""
+        return sum(self.groups[s.group].n_symbols * s.n_active for s in self.subbands)
+
+    def nominal_samples(self) -> int:
+        """High-rate samples of the nominal signal duration (symbols + CPs) per stream."""
+        g = self.groups[0]
+        per_sym = g.n_long if self.mode == SYMBOL_SYNC else None
+        if per_sym is None:
+            sb = next(s for s in self.subbands if s.group == 0)
+            per_sym = sb.l_ofdm * g.n_long // sb.l_short
+        return sum(per_sym + c for c in g.n_cp)
+
+
+# ---------------------------------------------------------------------------
+# 5G NR numerology helpers (3GPP normal CP): the first symbol of every 0.5 ms
+# carries a longer CP. These are signal-format constants, not FC arithmetic.
+# ---------------------------------------------------------------------------
+
+def nr_normal_cp(n_fft: int, scs_khz: int, n_symbols: int) -> tuple:
+    """Normal-CP lengths at a sampling rate of ``n_fft * scs``.
+
+    The base CP is 144/2048 of the useful symbol; the first symbol of each
+    half subframe gets an extra 16/2048 of the 15 kHz symbol (i.e. 16*64*Tc).
+    """
+    base = 144 * n_fft // 2048
+    # the half-subframe extension is 16 samples at 30.72 Msps, scaled to fs = n_fft*scs
+    if (16 * n_fft * scs_khz) % 30720:
+        raise ValueError("CP extension is not an integer number of samples at this rate")
+    ext = 16 * n_fft * scs_khz // 30720
+    syms_per_half = 7 * (scs_khz // 15)
+    return tuple(base + (ext if (n % syms_per_half) == 0 else 0) for n in range(n_symbols))
+
+
+def rc_transition_weights(l_short: int, n_active: int, n_tb: int) -> np.ndarray:
+    """Frequency window D_m: ones on the active bins, raised-cosine transition bins.
+
+    Transition bin j = 1..n_tb counted outward from the passband edge gets
+    0.5*(1 + cos(pi*j/(n_tb+1))); all other bins are zero. Returned in fftshifted
+    order (index p <-> signed bin p - floor(L/2)). The paper leaves the weight
+    values to the designer, so these are an input choice, not part of the method.
+    """
+    w = np.zeros(l_short, dtype=np.float64)
+    lo = -(n_active // 2)
+    hi = lo + n_active            # exclusive
+    half = l_short // 2
+    if hi - lo + 2 * n_tb > l_short:
+        raise ValueError("passband plus transition bands exceed the short transform")
+    w[lo + half: hi + half] = 1.0
+    for j in range(1, n_tb + 1):
+        v = 0.5 * (1.0 + math.cos(math.pi * j / (n_tb + 1)))
+        w[hi - 1 + j + half] = v
+        w[lo - j + half] = v
+    return w
+
+
+def full_band_weights(l_short: int) -> np.ndarray:
+    return np.ones(l_short, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Named workloads
+# ---------------------------------------------------------------------------
+
+def config_single_5mhz() -> Geometry:
+    """5 MHz NR, 15 kHz SCS, 24 PRB (288 SC), N=512 at 7.68 Msps, L=384,
+    50% overlap-save on TX and RX, 14 symbols (one slot), QPSK, 8 RC bins."""
+    n_cp = nr_normal_cp(512, 15, 14)                      # 40, 36 x6, 40, 36 x6
+    g = Group(n_long=512, n_overlap=256, n_cp=n_cp)
+    sb = Subband(l_short=384, l_ofdm=384, n_active=288, centre_bin=0, group=0,
+                 weights=rc_transition_weights(384, 288, 8))
+    return Geometry(CONTINUOUS, OLS, OLS, (g,), (sb,), name="nr5mhz_15khz_24prb_L384_N512_ols", qam_order=4)
+
+
+def config_mixed_20mhz() -> Geometry:
+    """20 MHz at 30.72 Msps, 1 ms subframe, symbol-synchronized FC.
+
+    Group A: 15 kHz SCS, N=2048, 51 PRB (612 SC), L=1024, 14 symbols.
+    Group B: 30 kHz SCS, N=1024, 24 PRB (288 SC), L=512, 28 symbols.
+    A occupies 15 kHz bins [-606, 6), B occupies [30, 606) (B's own 30 kHz grid:
+    [15, 303)), a 24-bin (2 PRB) guard between them. OLA TX, OLS RX, 16-QAM.
+    """
+    ga = Group(n_long=2048, n_overlap=1024, n_cp=nr_normal_cp(2048, 15, 14))
+    gb = Group(n_long=1024, n_overlap=512, n_cp=nr_normal_cp(1024, 30, 28))
+    sa = Subband(l_short=1024, l_ofdm=1024, n_active=612, centre_bin=-300, group=0,
+                 weights=rc_transition_weights(1024, 612, 8))
+    sbb = Subband(l_short=512, l_ofdm=512, n_active=288, centre_bin=159, group=1,
+                  weights=rc_transition_weights(512, 288, 8))
+    return Geometry(SYMBOL_SYNC, OLA, OLS, (ga, gb), (sa, sbb),
+                    name="nr20mhz_mixed_15k51prb_30k24prb_symsync", qam_order=16)
+
+
+def config_100mhz(n_slots: int = 10) -> Geometry:
+    """100 MHz NR, 30 kHz SCS, 273 PRB (3276 SC), N=L=4096 at 122.88 Msps,
+    50% overlap (OLA TX, OLS RX), ``n_slots`` slots of 14 symbols, 64-QAM."""
+    g = Group(n_long=4096, n_overlap=2048, n_cp=nr_normal_cp(4096, 30, 14 * n_slots))
+    sb = Subband(l_short=4096, l_ofdm=4096, n_active=3276, centre_bin=0, group=0,
+                 weights=rc_transition_weights(4096, 3276, 8))
+    return Geometry(CONTINUOUS, OLA, OLS, (g,), (sb,), name=f"nr100mhz_30khz_273prb_N4096_{n_slots}slots",
+                    qam_order=64)
+
+
+NAMED = {
+    "single5": config_single_5mhz,
+    "mixed20": config_mixed_20mhz,
+    "nr100": config_100mhz,
+}
+
+
+# ---------------------------------------------------------------------------
+# Seeded data
+# ---------------------------------------------------------------------------
+
+def _qam_levels(order: int) -> np.ndarray:
+    m = int(round(math.sqrt(order)))
+    if m * m != order:
+        raise ValueError("square QAM only")
+    lv = np.arange(-(m - 1), m, 2, dtype=np.float64)
+    norm = math.sqrt(2.0 * np.mean(lv ** 2))
+    return lv / norm
+
+
+def qam_grid(geom: Geometry, n_streams: int, seed: int) -> np.ndarray:
+    """Uniform random square-QAM symbols at unit average power.
+
+    Returns complex128 ``[n_streams, grid_len]``; stream ``s`` uses
+    ``Generator(PCG64(seed + s))`` so any stream can be regenerated alone.
+    """
+    lv = _qam_levels(geom.qam_order)
+    out = np.empty((n_streams, geom.grid_len()), dtype=np.complex128)
+    for s in range(n_streams):
+        rng = np.random.Generator(np.random.PCG64(seed + s))
+        i = rng.integers(0, len(lv), size=(2, out.shape[1]))
+        out[s] = lv[i[0]] + 1j * lv[i[1]]
+    return out
+
+
+def gaussian_vector(n: int, seed: int) -> np.ndarray:
+    """Circular complex Gaussian vector, unit variance per complex sample."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return (rng.standard_normal(n) + 1j * rng.standard_normal(n)) / math.sqrt(2.0)
+
+
+def awgn(wave: np.ndarray, snr_db: float, seed: int) -> np.ndarray:
+    """Complex AWGN with variance set from the mean power of ``wave`` (per row)."""
+    wave = np.asarray(wave)
+    flat = wave.reshape(-1, wave.shape[-1])
+    out = np.empty_like(flat, dtype=np.complex128)
+    for i in range(flat.shape[0]):
+        p = float(np.mean(np.abs(flat[i]) ** 2))
+        sigma = math.sqrt(p / (10.0 ** (snr_db / 10.0)))
+        out[i] = flat[i] + sigma * gaussian_vector(flat.shape[1], seed + i)
+    return out.reshape(wave.shape)
+
+
+def default_seed(config_index: int) -> int:
+    """Seed convention: 1000 + 100*config; stream s adds s."""
+    return 1000 + 100 * config_index
