@@ -1,0 +1,166 @@
+/*
+ * fcofdm.h -- C ABI of the GB300 fast-convolution (FC) filtered CP-OFDM library.
+ *
+ * The library implements the TX subband synthesis and RX subband analysis of
+ * Yli-Kaakinen et al., "Frequency-Domain Signal Processing for Spectrally-
+ * Enhanced CP-OFDM Waveforms in 5G New Radio":
+ *   - continuous FC processing with overlap-and-add (OLA) or overlap-and-save
+ *     (OLS) blocks (Sec. II and III-B, eq:BDM, eq:ola_synthesis, eq:ols_synthesis);
+ *   - symbol-synchronized discontinuous FC processing with dynamic first-block
+ *     overlap, CP-phase compensation theta_n, CP extrapolation and symbol-wise
+ *     OLA (Sec. III-C..E, eq:padding, eq:multi-symb, eq:waveformLen);
+ *   - the RX counterparts (Sec. IV, eq:ola_analysis, eq:ols_analysis, eq:concat2),
+ *   - CP-OFDM modulation/demodulation of every subband (eq:TX_OFDMmod, eq:TX_CPins).
+ *
+ * Every compute step runs in CUDA kernels for sm_103a. Nothing here falls back
+ * to the CPU. All functions return an FC_* status; none throws.
+ *
+ * Data layout (all device buffers, caller-owned, complex64 = interleaved
+ * {float re, float im}, 8-byte aligned; 16-byte alignment recommended):
+ *   grid  [n_streams][grid_len]: per stream, subband after subband (in the
+ *         order given at plan creation), [B_g][L_act,m] QAM symbols with the
+ *         active subcarriers in ascending signed frequency
+ *         f = -floor(L_act/2) .. ceil(L_act/2)-1 (long bin c_m + f).
+ *   wave  [n_streams][wave_len]: one frame of the high-rate waveform per stream.
+ *         All numerology groups are aligned so that symbol 0's cyclic prefix
+ *         starts at the same sample; continuous groups start their zero-padded
+ *         input S_L*I samples before that point, symbol-synchronized groups start
+ *         sigma_0 = 0 at N/4 - N_CP,0 before it (eq:waveformLen).
+ */
+#ifndef FCOFDM_H
+#define FCOFDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FC_OK 0
+#define FC_ERR_INVALID 1      /* geometry or argument violates a documented constraint */
+#define FC_ERR_UNSUPPORTED 2  /* valid for the paper, but a size this build has no kernel for */
+#define FC_ERR_NOMEM 3        /* device allocation failed (plan creation only) */
+#define FC_ERR_CUDA 4         /* a CUDA runtime call or kernel launch failed */
+#define FC_ERR_TIMEOUT 5      /* a bounded device-side wait gave up */
+
+/* processing modes (Sec. II vs Sec. III) */
+#define FC_CONTINUOUS 0
+#define FC_SYMBOL_SYNC 1
+
+/* block schemes */
+#define FC_OLA 0
+#define FC_OLS 1
+
+/*
+ * One numerology group: subbands that share the long transform W_N and the
+ * symbol timing (Sec. III: "overall symbol durations of all subband signals
+ * ... have equal lengths"). Different groups get their own long transform and
+ * are summed in time, x = sum_m w_m (Sec. III-B).
+ */
+typedef struct fc_group {
+  int32_t n_long;          /* N: long (high-rate) transform size                      */
+  int32_t n_overlap;       /* N_O = lambda*N high-rate overlap; symbol-sync needs N/2  */
+  int32_t lead_pad;        /* continuous only: S_L*I_m in high-rate samples, -1 = N_O  */
+  int32_t n_symbols;       /* B: CP-OFDM symbols per frame                             */
+  const int32_t* n_cp;     /* N_CP,n, n = 0..B-1, high-rate samples (host, copied)     */
+} fc_group;
+
+/* One FC subband (Sec. II-B, Sec. III-A). */
+typedef struct fc_subband {
+  int32_t l_short;         /* L_m: short transform size, I_m = N/L_m (eqn:Rk)          */
+  int32_t l_ofdm;          /* L_OFDM,m: OFDM (I)DFT size; symbol-sync needs L_OFDM = L */
+  int32_t n_active;        /* L_act,m: active subcarriers                              */
+  int32_t centre_bin;      /* c_m: centre bin on the long grid (may be negative)       */
+  int32_t group;           /* index of the subband's numerology group                  */
+  const double* weights;   /* D_m: l_short real weights, fftshifted order (index p is
+                              signed bin p - floor(L/2)); host, copied at creation     */
+} fc_subband;
+
+typedef struct fc_geometry {
+  int32_t mode;            /* FC_CONTINUOUS or FC_SYMBOL_SYNC                          */
+  int32_t scheme_tx;       /* FC_OLA or FC_OLS                                         */
+  int32_t scheme_rx;       /* FC_OLA or FC_OLS                                         */
+  int32_t n_groups;        /* 1..FC_MAX_GROUPS                                         */
+  const fc_group* groups;
+  int32_t n_subbands;      /* 1..FC_MAX_SUBBANDS                                       */
+  const fc_subband* subbands;
+} fc_geometry;
+
+#define FC_MAX_GROUPS 4
+#define FC_MAX_SUBBANDS 16
+#define FC_MAX_TRANSFORM 4096  /* largest N, L_m or L_OFDM,m this build has kernels for */
+
+typedef struct fc_sizes {
+  int64_t grid_len;        /* complex QAM symbols per stream                           */
+  int64_t wave_len;        /* complex high-rate samples per stream (one frame)         */
+  int64_t nominal_len;     /* high-rate samples of the nominal duration (group 0)      */
+  int64_t workspace_per_stream; /* device workspace bytes per stream for TX and RX     */
+  int32_t tx_kernels;      /* kernel launches per fc_tx_synthesize                     */
+  int32_t rx_kernels;      /* kernel launches per fc_rx_analyze                        */
+} fc_sizes;
+
+typedef struct fc_plan fc_plan;
+
+/*
+ * Build an immutable plan: validates the geometry, derives the FC parameters
+ * (eqn:Rk; L_CP,n = floor(N_CP,n L/N), Sec. III-E; sigma_n and Q,
+ * eq:multi-symb / eq:waveformLen; the block map), generates twiddle, weight
+ * and phase tables in FP64 on the host, rounds them once to FP32 and uploads
+ * them to `device`. Allocates device memory (cudaMalloc); execute calls never
+ * allocate. Returns FC_ERR_INVALID for geometry the paper's equations do not
+ * define (e.g. L_O not integer, symbol-sync with lambda != 0.5 or N_CP,n > N/4,
+ * continuous with a fractional low-rate CP), FC_ERR_UNSUPPORTED for transform
+ * sizes outside 2^a 3^b <= FC_MAX_TRANSFORM. On error *out is NULL.
+ * A plan may be used from several host threads and CUDA streams at once.
+ */
+int fc_plan_create(fc_plan** out, const fc_geometry* geometry, int32_t device);
+
+/*
+ * Host-only validation: runs every check of fc_plan_create and fills `out`
+ * (may be NULL) without touching a GPU or allocating device memory.
+ */
+int fc_geometry_check(const fc_geometry* geometry, fc_sizes* out);
+
+/* Per-stream sizes of the buffers an execute call reads and writes. */
+int fc_query(const fc_plan* plan, fc_sizes* out);
+
+/*
+ * TX subband synthesis (Sec. III): grid [n_streams][grid_len] -> wave
+ * [n_streams][wave_len]. CP-OFDM modulation, FC blocks (short DFT, fftshift,
+ * D_m, bin map with phi_r theta_n, sqrt(I_m)-scaled long IDFT), OLA/OLS and
+ * symbol-wise assembly, sum over subbands and groups. Every wave sample is
+ * written (no pre-zeroing needed). `workspace` (device, >= n_streams *
+ * workspace_per_stream bytes, may be NULL when that is 0) holds the low-rate
+ * CP-OFDM stream of continuous mode. Asynchronous on `stream` (a cudaStream_t,
+ * NULL = default stream); buffers must stay valid until the stream reaches it.
+ * n_streams == 0 is a no-op.
+ */
+int fc_tx_synthesize(const fc_plan* plan, int32_t n_streams, const void* grid_in, void* wave_out,
+                     void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * RX subband analysis (Sec. IV): wave [n_streams][wave_len] -> grid
+ * [n_streams][grid_len] (QAM estimates on the active subcarriers): long DFT,
+ * bin gather with conj(phi_r theta_n), D_m, inverse shift, 1/sqrt(I_m)-scaled
+ * short IDFT, OLS discard or OLA accumulate, concatenation / CP removal
+ * (eq:concat2) and OFDM demodulation. Same buffer rules as fc_tx_synthesize.
+ */
+int fc_rx_analyze(const fc_plan* plan, int32_t n_streams, const void* wave_in, void* grid_out,
+                  void* workspace, size_t workspace_bytes, void* stream);
+
+/* Frees the plan's device tables. Safe on NULL. Must not race with running calls. */
+void fc_plan_destroy(fc_plan* plan);
+
+/* Human-readable text for a status code (static storage). */
+const char* fc_status_string(int status);
+
+/* Text of the last error recorded on this host thread (static per thread). */
+const char* fc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCOFDM_H */

@@ -1,0 +1,8 @@
+"""GB300-native fast-convolution filtered CP-OFDM (TX synthesis / RX analysis).
+
+The compute path is the CUDA library built from ``csrc/`` (see ``build.py``);
+``fc`` is its thin ctypes binding.
+"""
+from .fc import (FC_CONTINUOUS, FC_OLA, FC_OLS, FC_SYMBOL_SYNC, FcError, Plan, fc_geometry_check,  # noqa: F401
+                 fc_plan_create, fc_plan_destroy, fc_query, fc_rx_analyze, fc_status_string, fc_tx_synthesize,
+                 load_library)

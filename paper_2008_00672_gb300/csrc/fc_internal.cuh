@@ -1,0 +1,92 @@
+// Internal plan layout shared by the host planner (fc_plan.cu) and the kernels
+// (fc_kernels.cu). Everything a kernel needs arrives in one FcPlanDev passed by
+// value; per-symbol and per-bin tables live in one device allocation.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fcofdm.h"
+
+#define FC_THREADS 512
+#define FC_MAX_SIZES 12       // distinct transform sizes in one plan
+#define FC_MAX_PASSES 8
+#define FC_MAX_ELEMS_PER_THREAD 16   // in-place FFT: batch*n <= FC_THREADS*16
+
+struct FcSize {
+  int n;
+  int npass;
+  int radix[FC_MAX_PASSES];
+  const float2* tw;   // tw[m] = exp(-j 2 pi m / n), m in [0, n), FP64-rounded
+};
+
+struct FcGroupDev {
+  int N, N_O, N_S, N_L, N_T;
+  int B;              // symbols
+  int offset;         // placement of the group's output in the frame
+  int len;            // group output length (Q or (R-1) N_S + N)
+  int R;              // continuous: block count
+  int size_N;         // index into FcPlanDev::sz
+  int first_sub, n_sub;
+  const int* sigma;   // [B] sync: sigma_n in group time
+  const int* ncp;     // [B] N_CP,n
+  const int* cps;     // [B] (sum_{q=1}^{n} N_CP,q) mod N
+};
+
+struct FcSubDev {
+  int L, Lofdm, Lact, c, group;
+  int L_S, L_L, L_T;
+  int S_L;            // continuous lead pad (low rate)
+  int n_low;          // continuous: low-rate stream length
+  int p_lo, p_hi;     // nonzero range of D_m (shifted order)
+  int size_L, size_O; // indices into sz for L and L_OFDM
+  long long grid_off; // complex offset of the subband inside one stream's grid
+  long long ws_off;   // complex offset inside one stream's workspace
+  const float* dtx;   // [L] D_m * sqrt(I)/(sqrt(L_OFDM) N)
+  const float* drx;   // [L] D_m / (sqrt(I) L sqrt(L_OFDM))
+  const int* lcp;     // [B] L_CP,m,n
+  const int* soff;    // [B] continuous: symbol start in the low-rate stream
+};
+
+struct FcJob {
+  int group;
+  int index;          // sync: symbol n; continuous: first block r0
+  int nblk;           // blocks in the job (1 or 2)
+  int start;          // frame time of the job's first output sample (TX) / input sample (RX)
+};
+
+struct FcChunk {
+  int j0, j1;         // job range
+  int t0, t1;         // TX: owned output range [t0, t1)
+};
+
+struct FcPlanDev {
+  int mode, scheme_tx, scheme_rx;
+  int n_groups, n_subs, n_sizes;
+  int frame_len;
+  long long grid_len;
+  long long ws_len;   // workspace complex elements per stream
+  int ring;           // TX ring length (power of two)
+  int ybuf;           // spectrum buffer length (complex)
+  int wbuf;           // low-rate buffer length (complex)
+  int max_span;       // longest job output span
+  FcGroupDev g[FC_MAX_GROUPS];
+  FcSubDev s[FC_MAX_SUBBANDS];
+  FcSize sz[FC_MAX_SIZES];
+};
+
+// kernel launchers (defined in fc_kernels.cu); dP is the plan's device copy
+cudaError_t fc_launch_tx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+                              int n_streams, const float2* grid, float2* wave, size_t smem, cudaStream_t st);
+cudaError_t fc_launch_rx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+                              int n_streams, const float2* wave, float2* grid, size_t smem, cudaStream_t st);
+cudaError_t fc_launch_ofdm_mod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const float2* grid,
+                               float2* ws, size_t smem, cudaStream_t st);
+cudaError_t fc_launch_tx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+                              int n_streams, const float2* ws, float2* wave, size_t smem, cudaStream_t st);
+cudaError_t fc_launch_rx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+                              int n_streams, const float2* wave, float2* ws, size_t smem, cudaStream_t st);
+cudaError_t fc_launch_ofdm_demod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const float2* ws,
+                                 float2* grid, size_t smem, cudaStream_t st);
+// raise the dynamic shared-memory limit of every kernel on the current device
+cudaError_t fc_set_smem_limits(size_t max_dynamic_smem);

@@ -1,0 +1,775 @@
+// CUDA kernels (sm_103a) of FC-filtered CP-OFDM TX synthesis and RX analysis.
+//
+// Structure (plain FP32 path):
+//   * every transform (OFDM IDFT/DFT L_OFDM, short DFT/IDFT L_m, long IDFT/DFT N)
+//     is an in-place mixed-radix Stockham FFT in shared memory, one CTA per job,
+//     radix-2/3/4/8/16 butterflies in registers, FP32 twiddles generated in FP64
+//     on the host and rounded once;
+//   * the spectra of a block never leave shared memory: the short-DFT output is
+//     weighted by D_m and scattered through the bin map Xi straight into the
+//     long spectrum (TX), or gathered from it (RX);
+//   * TX output assembly (OLA accumulate, OLS discard, symbol-wise OLA with the
+//     Gamma_sigma placement of eq:multi-symb, and the sum over subbands and
+//     numerology groups) happens in a shared-memory ring that each CTA owns for
+//     a contiguous range of output time; a range is written to HBM exactly once,
+//     when no later job can touch it.
+//
+// Symbol-synchronized jobs are (group, symbol) pairs and process the two FC
+// blocks of a symbol as a batch of two (Sec. III-C); continuous jobs are pairs
+// of consecutive FC blocks (Sec. III-B).
+#include "fc_internal.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// multiply by -i (forward transform) or +i (inverse transform)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// cos(2 pi m / 16), m in [0, 16)
+__host__ __device__ constexpr float c16(int m) {
+  return m == 0 ? 1.0f
+       : m == 1 ? 0.92387953251128674f
+       : m == 2 ? 0.70710678118654752f
+       : m == 3 ? 0.38268343236508977f
+       : m == 4 ? 0.0f
+       : m == 5 ? -0.38268343236508977f
+       : m == 6 ? -0.70710678118654752f
+       : m == 7 ? -0.92387953251128674f
+       : m == 8 ? -1.0f
+       : m == 9 ? -0.92387953251128674f
+       : m == 10 ? -0.70710678118654752f
+       : m == 11 ? -0.38268343236508977f
+       : m == 12 ? 0.0f
+       : m == 13 ? 0.38268343236508977f
+       : m == 14 ? 0.70710678118654752f
+                 : 0.92387953251128674f;
+}
+
+// a * exp(-+ j 2 pi M / 16): minus sign for the forward DFT, plus for the inverse
+template <int M, bool INV>
+__device__ __forceinline__ float2 tw16(float2 a) {
+  constexpr int m = M & 15;
+  if constexpr (m == 0) {
+    return a;
+  } else if constexpr (m == 4) {
+    return mul_mi<INV>(a);
+  } else if constexpr (m == 8) {
+    return make_float2(-a.x, -a.y);
+  } else if constexpr (m == 12) {
+    return mul_mi<!INV>(a);
+  } else {
+    constexpr float c = c16(m);
+    constexpr float s = c16((m + 12) & 15);   // sin(2 pi m/16)
+    if constexpr (INV) return make_float2(a.x * c - a.y * s, a.y * c + a.x * s);
+    else return make_float2(a.x * c + a.y * s, a.y * c - a.x * s);
+  }
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  const float2 s13 = cadd(a1, a3), d13 = mul_mi<INV>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+
+// In-register DFT of size R (X[k] = sum_t x[t] exp(-+ j 2 pi k t / R)), natural order.
+template <int R, bool INV>
+struct Dft;
+
+template <bool INV>
+struct Dft<2, INV> {
+  static __device__ __forceinline__ void run(float2 (&v)[2]) {
+    const float2 a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+  }
+};
+
+template <bool INV>
+struct Dft<3, INV> {
+  static __device__ __forceinline__ void run(float2 (&v)[3]) {
+    const float s = 0.86602540378443865f;   // sin(2 pi/3); cos(2 pi/3) = -1/2
+    const float2 s12 = cadd(v[1], v[2]), d12 = csub(v[1], v[2]);
+    const float2 m = make_float2(fmaf(-0.5f, s12.x, v[0].x), fmaf(-0.5f, s12.y, v[0].y));
+    const float2 isd = make_float2(-s * d12.y, s * d12.x);   // j s (x1 - x2)
+    v[0] = cadd(v[0], s12);
+    if (INV) {
+      v[1] = cadd(m, isd);
+      v[2] = csub(m, isd);
+    } else {
+      v[1] = csub(m, isd);
+      v[2] = cadd(m, isd);
+    }
+  }
+};
+
+template <bool INV>
+struct Dft<4, INV> {
+  static __device__ __forceinline__ void run(float2 (&v)[4]) { dft4<INV>(v[0], v[1], v[2], v[3]); }
+};
+
+// 8 = 2 x 4: inner 2-point DFTs over t1 (stride 4), twiddle W_8^{t2 k1}, outer 4-point DFTs.
+template <bool INV>
+struct Dft<8, INV> {
+  static __device__ __forceinline__ void run(float2 (&v)[8]) {
+#pragma unroll
+    for (int t2 = 0; t2 < 4; ++t2) {
+      const float2 a = v[t2];
+      v[t2] = cadd(a, v[t2 + 4]);
+      v[t2 + 4] = csub(a, v[t2 + 4]);
+    }
+    v[5] = tw16<2, INV>(v[5]);
+    v[6] = tw16<4, INV>(v[6]);
+    v[7] = tw16<6, INV>(v[7]);
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+    dft4<INV>(v[4], v[5], v[6], v[7]);
+    // v[4 k1 + k2] holds X[k1 + 2 k2]
+    float2 t[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t[i] = v[i];
+#pragma unroll
+    for (int k1 = 0; k1 < 2; ++k1)
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 2 * k2] = t[4 * k1 + k2];
+  }
+};
+
+// 16 = 4 x 4: inner 4-point DFTs over t1 (stride 4), twiddle W_16^{t2 k1}, outer 4-point DFTs.
+template <bool INV>
+struct Dft<16, INV> {
+  static __device__ __forceinline__ void run(float2 (&v)[16]) {
+#pragma unroll
+    for (int t2 = 0; t2 < 4; ++t2) dft4<INV>(v[t2], v[t2 + 4], v[t2 + 8], v[t2 + 12]);
+    v[5] = tw16<1, INV>(v[5]);
+    v[6] = tw16<2, INV>(v[6]);
+    v[7] = tw16<3, INV>(v[7]);
+    v[9] = tw16<2, INV>(v[9]);
+    v[10] = tw16<4, INV>(v[10]);
+    v[11] = tw16<6, INV>(v[11]);
+    v[13] = tw16<3, INV>(v[13]);
+    v[14] = tw16<6, INV>(v[14]);
+    v[15] = tw16<9, INV>(v[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    float2 t[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[4 * k1 + k2];
+  }
+};
+
+// One register file v[] serves every radix: butterfly u of a thread occupies
+// v[u R .. u R + R). The radix-specific phases contain no barrier, so the
+// register allocator sees a single live array across the pass.
+template <int R, bool INV>
+__device__ __forceinline__ void pass_load(float2 (&v)[FC_MAX_ELEMS_PER_THREAD], const float2* a, int n, int batch,
+                                          int p, const float2* __restrict__ tw) {
+  constexpr int MAXB = FC_MAX_ELEMS_PER_THREAD / R;
+  const int nb = n / R;
+  const int total = nb * batch;
+  const int twstep = n / (p * R);
+#pragma unroll
+  for (int u = 0; u < MAXB; ++u) {
+    const int idx = threadIdx.x + u * FC_THREADS;
+    if (idx < total) {
+      const int b = idx / nb;
+      const int i = idx - b * nb;
+      const int k = i % p;
+      const float2* s = a + b * n + i;
+      float2 w[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) w[j] = s[j * nb];
+      if (p > 1) {
+#pragma unroll
+        for (int j = 1; j < R; ++j) {
+          float2 t = __ldg(tw + j * k * twstep);
+          if (INV) t.y = -t.y;
+          w[j] = cmul(w[j], t);
+        }
+      }
+      Dft<R, INV>::run(w);
+#pragma unroll
+      for (int j = 0; j < R; ++j) v[u * R + j] = w[j];
+    }
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void pass_store(const float2 (&v)[FC_MAX_ELEMS_PER_THREAD], float2* a, int n, int batch,
+                                           int p) {
+  constexpr int MAXB = FC_MAX_ELEMS_PER_THREAD / R;
+  const int nb = n / R;
+  const int total = nb * batch;
+#pragma unroll
+  for (int u = 0; u < MAXB; ++u) {
+    const int idx = threadIdx.x + u * FC_THREADS;
+    if (idx < total) {
+      const int b = idx / nb;
+      const int i = idx - b * nb;
+      const int k = i % p;
+      float2* d = a + b * n + (i - k) * R + k;
+#pragma unroll
+      for (int j = 0; j < R; ++j) d[j * p] = v[u * R + j];
+    }
+  }
+}
+
+// In-place Stockham FFT over `batch` contiguous transforms of size n in shared
+// memory. Pass s with radix R and p = product of the previous radices:
+//   butterfly i (0 <= i < n/R), k = i mod p, inputs a[i + j n/R] * W_{pR}^{j k},
+//   DFT_R, outputs to a[(i - k) R + k + j p]. All threads read their butterflies
+//   into registers, synchronise, then write back, so one buffer suffices.
+//   Requires batch * n <= FC_THREADS * FC_MAX_ELEMS_PER_THREAD (radix 3:
+//   batch * n / 3 <= FC_THREADS * floor(FC_MAX_ELEMS_PER_THREAD / 3)).
+// Unnormalised DFT (INV=false, exp(-j...)) or inverse DFT without 1/n (INV=true).
+template <bool INV>
+__device__ __forceinline__ void fft_inplace(float2* a, int batch, const FcSize& z) {
+  float2 v[FC_MAX_ELEMS_PER_THREAD];
+  int p = 1;
+#pragma unroll 1
+  for (int s = 0; s < z.npass; ++s) {
+    const int R = z.radix[s];
+    if (R == 16) pass_load<16, INV>(v, a, z.n, batch, p, z.tw);
+    else if (R == 8) pass_load<8, INV>(v, a, z.n, batch, p, z.tw);
+    else if (R == 4) pass_load<4, INV>(v, a, z.n, batch, p, z.tw);
+    else if (R == 2) pass_load<2, INV>(v, a, z.n, batch, p, z.tw);
+    else pass_load<3, INV>(v, a, z.n, batch, p, z.tw);
+    __syncthreads();
+    if (R == 16) pass_store<16>(v, a, z.n, batch, p);
+    else if (R == 8) pass_store<8>(v, a, z.n, batch, p);
+    else if (R == 4) pass_store<4>(v, a, z.n, batch, p);
+    else if (R == 2) pass_store<2>(v, a, z.n, batch, p);
+    else pass_store<3>(v, a, z.n, batch, p);
+    __syncthreads();
+    p *= R;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// shared helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_plan(FcPlanDev& P, const FcPlanDev* __restrict__ gP) {
+  const int words = (int)(sizeof(FcPlanDev) / 4);
+  const int* src = reinterpret_cast<const int*>(gP);
+  int* dst = reinterpret_cast<int*>(&P);
+  for (int i = threadIdx.x; i < words; i += FC_THREADS) dst[i] = __ldg(src + i);
+  __syncthreads();
+}
+
+__device__ __forceinline__ void zero_buf(float2* a, int n) {
+  for (int i = threadIdx.x; i < n; i += FC_THREADS) a[i] = make_float2(0.f, 0.f);
+}
+
+// exp(+j 2 pi e / N) from the forward twiddle table of size N, e reduced exactly.
+__device__ __forceinline__ float2 pos_root(const FcSize& z, long long e) {
+  long long m = e % z.n;
+  if (m < 0) m += z.n;
+  float2 w = __ldg(z.tw + m);
+  return make_float2(w.x, -w.y);
+}
+
+// bin i of an n-point DFT -> index of the active subcarrier (or -1)
+__device__ __forceinline__ int active_index(int i, int n, int n_act) {
+  const int f = (i < (n + 1) / 2) ? i : i - n;
+  const int lo = n_act / 2;
+  return (f >= -lo && f < n_act - lo) ? f + lo : -1;
+}
+
+// Copy ring[from, to) to dst and clear it, in segments no longer than the ring.
+__device__ __forceinline__ void ring_flush(float2* ring, int mask, float2* __restrict__ dst, int from, int to) {
+  while (from < to) {
+    const int seg = min(to - from, mask + 1);
+    for (int i = threadIdx.x; i < seg; i += FC_THREADS) {
+      const int T = from + i;
+      dst[T] = ring[T & mask];
+      ring[T & mask] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    from += seg;
+  }
+}
+
+// OFDM modulation of one symbol into buf[0, Lofdm): active bins, inverse DFT (unscaled).
+__device__ __forceinline__ void ofdm_symbol_to_time(const FcPlanDev& P, const FcSubDev& S, const float2* __restrict__ row,
+                                                    float2* buf) {
+  const int L = S.Lofdm;
+  for (int i = threadIdx.x; i < L; i += FC_THREADS) {
+    const int a = active_index(i, L, S.Lact);
+    buf[i] = a >= 0 ? __ldg(row + a) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  fft_inplace<true>(buf, 1, P.sz[S.size_O]);
+}
+
+// TX map: Y[r][(c + p - floor(L/2)) mod N] += Z[r][(p - floor(L/2)) mod L] * D[p] * ph_r
+__device__ __forceinline__ void tx_map(const FcSubDev& S, int N, const float2* Z, float2* Y, float2 ph0, float2 ph1,
+                                       int nblk) {
+  const int L = S.L, h = L / 2, cnt = S.p_hi - S.p_lo;
+  for (int idx = threadIdx.x; idx < nblk * cnt; idx += FC_THREADS) {
+    const int r = idx >= cnt;
+    const int p = S.p_lo + idx - r * cnt;
+    int k = p - h;
+    if (k < 0) k += L;
+    int q = (S.c + p - h) % N;
+    if (q < 0) q += N;
+    const float w = __ldg(S.dtx + p);
+    const float2 v = cmul(Z[r * L + k], r ? ph1 : ph0);
+    float2& y = Y[r * N + q];
+    y.x = fmaf(v.x, w, y.x);
+    y.y = fmaf(v.y, w, y.y);
+  }
+  __syncthreads();
+}
+
+// RX gather: V[r][k] = Y[r][(c + p - floor(L/2)) mod N] * conj(ph_r) * Drx[p], p = (k + floor(L/2)) mod L
+__device__ __forceinline__ void rx_gather(const FcSubDev& S, int N, const float2* Y, float2* V, float2 ph0, float2 ph1,
+                                          int nblk) {
+  const int L = S.L, h = L / 2;
+  for (int idx = threadIdx.x; idx < 2 * L; idx += FC_THREADS) {
+    const int r = idx >= L;
+    const int k = idx - r * L;
+    int p = k + h;
+    if (p >= L) p -= L;
+    float2 v = make_float2(0.f, 0.f);
+    if (r < nblk && p >= S.p_lo && p < S.p_hi) {
+      int q = (S.c + p - h) % N;
+      if (q < 0) q += N;
+      const float2 ph = r ? ph1 : ph0;
+      const float2 y = Y[r * N + q];
+      const float w = __ldg(S.drx + p);
+      // y * conj(ph) * w
+      v = make_float2((y.x * ph.x + y.y * ph.y) * w, (y.y * ph.x - y.x * ph.y) * w);
+    }
+    V[idx] = v;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Symbol-synchronized TX (Sec. III-C..E)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(FC_THREADS, 1)
+k_tx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
+          int n_chunks, const float2* __restrict__ grid, float2* __restrict__ wave) {
+  __shared__ FcPlanDev P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  load_plan(P, gP);
+  float2* ring = reinterpret_cast<float2*>(smem_raw);
+  float2* Y = ring + P.ring;
+  float2* W = Y + P.ybuf;
+  const int stream = blockIdx.x / n_chunks;
+  const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
+  const float2* gsrc = grid + (size_t)stream * P.grid_len;
+  float2* wdst = wave + (size_t)stream * P.frame_len;
+  const int mask = P.ring - 1;
+  zero_buf(ring, P.ring);
+  int flushed = ch.t0;
+  __syncthreads();
+
+  for (int j = ch.j0; j < ch.j1; ++j) {
+    const FcJob jb = jobs[j];
+    const FcGroupDev& G = P.g[jb.group];
+    const int N = G.N, n = jb.index;
+    zero_buf(Y, 2 * N);
+    __syncthreads();
+    for (int m = G.first_sub; m < G.first_sub + G.n_sub; ++m) {
+      const FcSubDev& S = P.s[m];
+      const int L = S.L, q4 = L / 4;
+      const int lcp = S.lcp[n];
+      // T1: OFDM symbol (eq:TX_OFDMmod, scaling folded into D)
+      ofdm_symbol_to_time(P, S, gsrc + S.grid_off + (long long)n * S.Lact, W);
+      // T2-T3: CP insertion, zero padding to 3L/2 (eq:padding), two segments with the
+      // dynamic-overlap analysis windows a_{m,0}, a_{m,1} (OLA) or none (OLS)
+      float2* Z = W + L;
+      for (int idx = threadIdx.x; idx < 2 * L; idx += FC_THREADS) {
+        const int r = idx >= L;
+        const int zi = r * (L / 2) + idx - r * L;     // index in the padded symbol z_n
+        bool in = zi >= q4 - lcp && zi < q4 + L;
+        if (P.scheme_tx == FC_OLA) in = in && (r == 0 ? zi < 3 * q4 : zi >= 3 * q4);
+        int bi = zi - q4;
+        if (bi < 0) bi += L;
+        Z[idx] = in ? W[bi] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      // T4: short DFTs of both blocks
+      fft_inplace<false>(Z, 2, P.sz[S.size_L]);
+      // T5: fftshift, D_m, bin map with phi_r theta_n (phi_r theta_n = exp(j2pi c (r N_S + S_n)/N))
+      const FcSize& zN = P.sz[G.size_N];
+      const float2 ph0 = pos_root(zN, (long long)S.c * G.cps[n]);
+      const float2 ph1 = pos_root(zN, (long long)S.c * (G.cps[n] + G.N_S));
+      tx_map(S, N, Z, Y, ph0, ph1, 2);
+    }
+    // T6: long IDFTs (1/N and sqrt(I) folded into D)
+    fft_inplace<true>(Y, 2, P.sz[G.size_N]);
+    // T7: R_N^{(r)} combination (OLS windows s_{m,0}, s_{m,1}), Gamma_sigma placement into the ring
+    const int h = N / 2, ncp = G.ncp[n];
+    const bool ols = P.scheme_tx == FC_OLS;
+    for (int tau = threadIdx.x; tau < 3 * h; tau += FC_THREADS) {
+      float2 v = make_float2(0.f, 0.f);
+      if (tau < N && (!ols || (tau >= G.N_L - ncp && tau < G.N_L + G.N_S))) v = cadd(v, Y[tau]);
+      if (tau >= h) {
+        const int t = tau - h;
+        if (!ols || (t >= G.N_L && t < G.N_L + G.N_S)) v = cadd(v, Y[N + t]);
+      }
+      const int T = jb.start + tau;
+      if (T >= flushed && T < ch.t1) {
+        float2& rr = ring[T & mask];
+        rr = cadd(rr, v);
+      }
+    }
+    __syncthreads();
+    const int upto = (j + 1 < ch.j1) ? min(jobs[j + 1].start, ch.t1) : ch.t1;
+    if (upto > flushed) {
+      ring_flush(ring, mask, wdst, flushed, upto);
+      flushed = upto;
+    }
+  }
+  if (ch.t1 > flushed) ring_flush(ring, mask, wdst, flushed, ch.t1);
+}
+
+// ---------------------------------------------------------------------------
+// Symbol-synchronized RX (Sec. IV)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(FC_THREADS, 1)
+k_rx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
+          int n_chunks, const float2* __restrict__ wave, float2* __restrict__ grid) {
+  __shared__ FcPlanDev P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  load_plan(P, gP);
+  float2* Y = reinterpret_cast<float2*>(smem_raw);
+  float2* W = Y + P.ybuf;
+  const int stream = blockIdx.x / n_chunks;
+  const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
+  const float2* src = wave + (size_t)stream * P.frame_len;
+  float2* gdst = grid + (size_t)stream * P.grid_len;
+  const bool ola = P.scheme_rx == FC_OLA;
+
+  for (int j = ch.j0; j < ch.j1; ++j) {
+    const FcJob jb = jobs[j];
+    const FcGroupDev& G = P.g[jb.group];
+    const int N = G.N, n = jb.index, h = N / 2;
+    // R1: segmentation w_hat^{(r)} = (R_N^{(r)})^T Gamma_sigma^T x_hat, high-rate A window for OLA (eq:1)
+    for (int idx = threadIdx.x; idx < 2 * N; idx += FC_THREADS) {
+      const int r = idx >= N;
+      const int t = idx - r * N;
+      float2 v = __ldg(src + jb.start + r * h + t);
+      if (ola && !(t >= G.N_L && t < G.N_L + G.N_S)) v = make_float2(0.f, 0.f);
+      Y[idx] = v;
+    }
+    __syncthreads();
+    // R2: long DFTs
+    fft_inplace<false>(Y, 2, P.sz[G.size_N]);
+    for (int m = G.first_sub; m < G.first_sub + G.n_sub; ++m) {
+      const FcSubDev& S = P.s[m];
+      const int L = S.L, q4 = L / 4;
+      const FcSize& zN = P.sz[G.size_N];
+      const float2 ph0 = pos_root(zN, (long long)S.c * G.cps[n]);
+      const float2 ph1 = pos_root(zN, (long long)S.c * (G.cps[n] + G.N_S));
+      // R3: gather with conj(phi_r theta_n), D_m, inverse shift
+      rx_gather(S, N, Y, W, ph0, ph1, 2);
+      // R4: short IDFTs (1/(sqrt(I) L) folded into D)
+      fft_inplace<true>(W, 2, P.sz[S.size_L]);
+      // R5: S window and concatenation (eq:concat2), or OLA of the two blocks
+      float2* X = W + 2 * L;
+      for (int t = threadIdx.x; t < L; t += FC_THREADS) {
+        float2 v;
+        if (!ola) {
+          v = t < L / 2 ? W[q4 + t] : W[L + t - q4];
+        } else {
+          const int u = q4 + t;
+          v = make_float2(0.f, 0.f);
+          if (u < L) v = cadd(v, W[u]);
+          if (u >= L / 2) v = cadd(v, W[L + u - L / 2]);
+        }
+        X[t] = v;
+      }
+      __syncthreads();
+      // R6: OFDM demodulation, active bins out
+      fft_inplace<false>(X, 1, P.sz[S.size_O]);
+      float2* row = gdst + S.grid_off + (long long)n * S.Lact;
+      for (int a = threadIdx.x; a < S.Lact; a += FC_THREADS) {
+        int bin = a - S.Lact / 2;
+        if (bin < 0) bin += L;
+        row[a] = X[bin];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Continuous mode, stage 1 (TX): CP-OFDM symbols -> low-rate stream s_m (workspace)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool locate_symbol(const FcPlanDev& P, int& m, int& n, int per_stream_idx) {
+  int acc = 0;
+  for (m = 0; m < P.n_subs; ++m) {
+    const int B = P.g[P.s[m].group].B;
+    if (per_stream_idx < acc + B) {
+      n = per_stream_idx - acc;
+      return true;
+    }
+    acc += B;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(FC_THREADS, 1)
+k_ofdm_mod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2* __restrict__ grid,
+           float2* __restrict__ ws) {
+  __shared__ FcPlanDev P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  load_plan(P, gP);
+  float2* buf = reinterpret_cast<float2*>(smem_raw);
+  const int stream = blockIdx.x / syms_per_stream;
+  int m, n;
+  if (!locate_symbol(P, m, n, blockIdx.x - stream * syms_per_stream)) return;
+  const FcSubDev& S = P.s[m];
+  ofdm_symbol_to_time(P, S, grid + (size_t)stream * P.grid_len + S.grid_off + (long long)n * S.Lact, buf);
+  const int L = S.Lofdm, lcp = S.lcp[n];
+  float2* dst = ws + (size_t)stream * P.ws_len + S.ws_off + S.soff[n];
+  for (int i = threadIdx.x; i < lcp + L; i += FC_THREADS) {   // K_{L_CP} (eq:TX_CPins)
+    int bi = i - lcp;
+    if (bi < 0) bi += L;
+    dst[i] = buf[bi];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Continuous mode, stage 2 (TX): FC blocks over [0_{S_L}; s; 0_{S_L}] (eq:BDM)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(FC_THREADS, 1)
+k_tx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
+          int n_chunks, const float2* __restrict__ ws, float2* __restrict__ wave) {
+  __shared__ FcPlanDev P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  load_plan(P, gP);
+  float2* ring = reinterpret_cast<float2*>(smem_raw);
+  float2* Y = ring + P.ring;
+  float2* Z = Y + P.ybuf;
+  const int stream = blockIdx.x / n_chunks;
+  const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
+  const float2* wsrc = ws + (size_t)stream * P.ws_len;
+  float2* wdst = wave + (size_t)stream * P.frame_len;
+  const int mask = P.ring - 1;
+  const bool ols = P.scheme_tx == FC_OLS;
+  zero_buf(ring, P.ring);
+  int flushed = ch.t0;
+  __syncthreads();
+
+  for (int j = ch.j0; j < ch.j1; ++j) {
+    const FcJob jb = jobs[j];
+    const FcGroupDev& G = P.g[jb.group];
+    const int N = G.N, r0 = jb.index, nb = jb.nblk;
+    zero_buf(Y, 2 * N);
+    __syncthreads();
+    for (int m = G.first_sub; m < G.first_sub + G.n_sub; ++m) {
+      const FcSubDev& S = P.s[m];
+      const int L = S.L;
+      const float2* s = wsrc + S.ws_off;
+      // segmentation, A_{m,r} for OLA (eq:ola_proc)
+      for (int idx = threadIdx.x; idx < 2 * L; idx += FC_THREADS) {
+        const int b = idx >= L;
+        const int t = idx - b * L;
+        const int pos = (r0 + b) * S.L_S + t - S.S_L;
+        float2 v = make_float2(0.f, 0.f);
+        if (b < nb && pos >= 0 && pos < S.n_low && (ols || (t >= S.L_L && t < S.L_L + S.L_S))) v = __ldg(s + pos);
+        Z[idx] = v;
+      }
+      __syncthreads();
+      fft_inplace<false>(Z, 2, P.sz[S.size_L]);
+      const FcSize& zN = P.sz[G.size_N];
+      const float2 ph0 = pos_root(zN, (long long)S.c * r0 * G.N_S);         // phi_{m,r}
+      const float2 ph1 = pos_root(zN, (long long)S.c * (r0 + 1) * G.N_S);
+      tx_map(S, N, Z, Y, ph0, ph1, nb);
+    }
+    fft_inplace<true>(Y, 2, P.sz[G.size_N]);
+    // OLA accumulate / OLS discard (S_{m,r}) into the ring
+    const int span = G.N_S + N;
+    for (int tau = threadIdx.x; tau < span; tau += FC_THREADS) {
+      float2 v = make_float2(0.f, 0.f);
+      if (tau < N && (!ols || (tau >= G.N_L && tau < G.N_L + G.N_S))) v = cadd(v, Y[tau]);
+      if (nb > 1 && tau >= G.N_S) {
+        const int t = tau - G.N_S;
+        if (!ols || (t >= G.N_L && t < G.N_L + G.N_S)) v = cadd(v, Y[N + t]);
+      }
+      const int T = jb.start + tau;
+      if (T >= flushed && T < ch.t1) {
+        float2& rr = ring[T & mask];
+        rr = cadd(rr, v);
+      }
+    }
+    __syncthreads();
+    const int upto = (j + 1 < ch.j1) ? min(jobs[j + 1].start, ch.t1) : ch.t1;
+    if (upto > flushed) {
+      ring_flush(ring, mask, wdst, flushed, upto);
+      flushed = upto;
+    }
+  }
+  if (ch.t1 > flushed) ring_flush(ring, mask, wdst, flushed, ch.t1);
+}
+
+// ---------------------------------------------------------------------------
+// Continuous mode, stage 1 (RX): FC analysis blocks -> low-rate stream (OLS,
+// disjoint kept parts) or per-block outputs (OLA, summed by the demodulator)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(FC_THREADS, 1)
+k_rx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
+          int n_chunks, const float2* __restrict__ wave, float2* __restrict__ ws) {
+  __shared__ FcPlanDev P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  load_plan(P, gP);
+  float2* Y = reinterpret_cast<float2*>(smem_raw);
+  float2* V = Y + P.ybuf;
+  const int stream = blockIdx.x / n_chunks;
+  const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
+  const float2* src = wave + (size_t)stream * P.frame_len;
+  float2* wdst = ws + (size_t)stream * P.ws_len;
+  const bool ola = P.scheme_rx == FC_OLA;
+
+  for (int j = ch.j0; j < ch.j1; ++j) {
+    const FcJob jb = jobs[j];
+    const FcGroupDev& G = P.g[jb.group];
+    const int N = G.N, r0 = jb.index, nb = jb.nblk;
+    for (int idx = threadIdx.x; idx < 2 * N; idx += FC_THREADS) {
+      const int b = idx >= N;
+      const int t = idx - b * N;
+      float2 v = make_float2(0.f, 0.f);
+      if (b < nb && (!ola || (t >= G.N_L && t < G.N_L + G.N_S))) v = __ldg(src + jb.start + b * G.N_S + t);
+      Y[idx] = v;
+    }
+    __syncthreads();
+    fft_inplace<false>(Y, 2, P.sz[G.size_N]);
+    for (int m = G.first_sub; m < G.first_sub + G.n_sub; ++m) {
+      const FcSubDev& S = P.s[m];
+      const int L = S.L;
+      const FcSize& zN = P.sz[G.size_N];
+      const float2 ph0 = pos_root(zN, (long long)S.c * r0 * G.N_S);
+      const float2 ph1 = pos_root(zN, (long long)S.c * (r0 + 1) * G.N_S);
+      rx_gather(S, N, Y, V, ph0, ph1, nb);
+      fft_inplace<true>(V, 2, P.sz[S.size_L]);
+      float2* d = wdst + S.ws_off;
+      if (!ola) {   // S_{m,r}: keep [L_L, L_L + L_S) at low-rate position r L_S + L_L
+        for (int idx = threadIdx.x; idx < nb * S.L_S; idx += FC_THREADS) {
+          const int b = idx >= S.L_S;
+          const int t = S.L_L + idx - b * S.L_S;
+          const int pos = (r0 + b) * S.L_S + t - S.S_L;
+          if (pos >= 0 && pos < S.n_low) d[pos] = V[b * L + t];
+        }
+      } else {      // keep whole blocks; overlapping parts are added by the demodulator
+        for (int idx = threadIdx.x; idx < nb * L; idx += FC_THREADS) {
+          const int b = idx >= L;
+          d[(long long)(r0 + b) * L + idx - b * L] = V[idx];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Continuous mode, stage 2 (RX): CP removal and OFDM demodulation
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(FC_THREADS, 1)
+k_ofdm_demod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2* __restrict__ ws,
+             float2* __restrict__ grid) {
+  __shared__ FcPlanDev P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  load_plan(P, gP);
+  float2* buf = reinterpret_cast<float2*>(smem_raw);
+  const int stream = blockIdx.x / syms_per_stream;
+  int m, n;
+  if (!locate_symbol(P, m, n, blockIdx.x - stream * syms_per_stream)) return;
+  const FcSubDev& S = P.s[m];
+  const FcGroupDev& G = P.g[S.group];
+  const float2* s = ws + (size_t)stream * P.ws_len + S.ws_off;
+  const int Lo = S.Lofdm, base = S.soff[n] + S.lcp[n];
+  const bool ola = P.scheme_rx == FC_OLA;
+  for (int t = threadIdx.x; t < Lo; t += FC_THREADS) {
+    float2 v = make_float2(0.f, 0.f);
+    if (!ola) {
+      v = __ldg(s + base + t);
+    } else {
+      const int Pu = S.S_L + base + t;                       // position in the padded stream
+      int r_hi = Pu / S.L_S;
+      if (r_hi > G.R - 1) r_hi = G.R - 1;
+      for (int r = r_hi; r >= 0 && Pu - r * S.L_S < S.L; --r) v = cadd(v, __ldg(s + (long long)r * S.L + Pu - r * S.L_S));
+    }
+    buf[t] = v;
+  }
+  __syncthreads();
+  fft_inplace<false>(buf, 1, P.sz[S.size_O]);
+  float2* row = grid + (size_t)stream * P.grid_len + S.grid_off + (long long)n * S.Lact;
+  for (int a = threadIdx.x; a < S.Lact; a += FC_THREADS) {
+    int bin = a - S.Lact / 2;
+    if (bin < 0) bin += Lo;
+    row[a] = buf[bin];
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t fc_launch_tx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+                              int n_streams, const float2* grid, float2* wave, size_t smem, cudaStream_t st) {
+  k_tx_sync<<<dim3((unsigned)(n_streams * n_chunks)), FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, grid, wave);
+  return cudaGetLastError();
+}
+
+cudaError_t fc_launch_rx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+                              int n_streams, const float2* wave, float2* grid, size_t smem, cudaStream_t st) {
+  k_rx_sync<<<dim3((unsigned)(n_streams * n_chunks)), FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, wave, grid);
+  return cudaGetLastError();
+}
+
+cudaError_t fc_launch_ofdm_mod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const float2* grid,
+                               float2* ws, size_t smem, cudaStream_t st) {
+  k_ofdm_mod<<<dim3((unsigned)(n_streams * syms_per_stream)), FC_THREADS, smem, st>>>(dP, syms_per_stream, grid, ws);
+  return cudaGetLastError();
+}
+
+cudaError_t fc_launch_tx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+                              int n_streams, const float2* ws, float2* wave, size_t smem, cudaStream_t st) {
+  k_tx_cont<<<dim3((unsigned)(n_streams * n_chunks)), FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, ws, wave);
+  return cudaGetLastError();
+}
+
+cudaError_t fc_launch_rx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+                              int n_streams, const float2* wave, float2* ws, size_t smem, cudaStream_t st) {
+  k_rx_cont<<<dim3((unsigned)(n_streams * n_chunks)), FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, wave, ws);
+  return cudaGetLastError();
+}
+
+cudaError_t fc_launch_ofdm_demod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const float2* ws,
+                                 float2* grid, size_t smem, cudaStream_t st) {
+  k_ofdm_demod<<<dim3((unsigned)(n_streams * syms_per_stream)), FC_THREADS, smem, st>>>(dP, syms_per_stream, ws, grid);
+  return cudaGetLastError();
+}
+
+cudaError_t fc_set_smem_limits(size_t max_smem) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_tx_sync, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_rx_sync, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_tx_cont, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_rx_cont, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_ofdm_mod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_ofdm_demod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
+  return cudaSuccess;
+}

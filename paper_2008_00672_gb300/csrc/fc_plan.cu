@@ -1,0 +1,656 @@
+// Host side of the C ABI: geometry validation, FC parameters, frame layout,
+// FP64 table generation (rounded once to FP32), job/chunk schedule, launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fc_internal.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return FC_ERR_CUDA;
+}
+
+constexpr size_t kSmemPerBlockMax = 232448;   // 227 KB opt-in dynamic + static limit on sm_10x
+
+// ---------------------------------------------------------------------------
+// host staging of all device tables in one allocation
+// ---------------------------------------------------------------------------
+struct Blob {
+  std::vector<unsigned char> bytes;
+  size_t add(const void* p, size_t n, size_t align = 16) {
+    size_t off = (bytes.size() + align - 1) / align * align;
+    bytes.resize(off + n);
+    if (n) std::memcpy(bytes.data() + off, p, n);
+    return off;
+  }
+  template <class T>
+  size_t add_vec(const std::vector<T>& v) { return add(v.data(), v.size() * sizeof(T)); }
+};
+
+bool is_2a3b(int n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+// Radix schedule: all factors 3 as radix-3 passes; the power of two split into
+// ceil(a/4) passes of 2^(<=4), balanced, avoiding radix 2 where possible.
+void radix_plan(int n, int* radix, int* npass) {
+  int a = 0, b = 0, m = n;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  while (m % 3 == 0) { m /= 3; ++b; }
+  int k = 0;
+  if (a > 0) {
+    int passes = (a + 3) / 4;
+    int base = a / passes, extra = a % passes;
+    for (int i = 0; i < passes; ++i) radix[k++] = 1 << (base + (i < extra ? 1 : 0));
+  }
+  for (int i = 0; i < b; ++i) radix[k++] = 3;
+  *npass = k;
+}
+
+struct SubHost {
+  int L = 0, Lo = 0, Lact = 0, c = 0, g = 0;
+  int L_O = 0, L_S = 0, L_L = 0, L_T = 0, S_L = 0, n_low = 0, R = 0;
+  std::vector<double> D;
+  std::vector<int> lcp, soff;
+};
+
+struct GroupHost {
+  int N = 0, N_O = 0, N_S = 0, N_L = 0, N_T = 0, B = 0, lead_hi = 0, T_lead = 0, len = 0, R = 0, offset = 0;
+  std::vector<int> ncp, sigma, cps;
+  std::vector<int> subs;
+};
+
+}  // namespace
+
+struct fc_plan {
+  int device = 0;
+  int num_sms = 0;
+  FcPlanDev h{};
+  FcPlanDev* d_plan = nullptr;
+  unsigned char* d_mem = nullptr;
+  FcJob* d_jobs = nullptr;
+  int n_jobs = 0;
+  std::vector<int> splits;                  // chunk counts per stream available
+  std::vector<const FcChunk*> tx_chunks, rx_chunks;
+  std::vector<int> tx_nchunks, rx_nchunks;
+  size_t smem_tx = 0, smem_rx = 0, smem_ofdm = 0;
+  int syms_per_stream = 0;
+  fc_sizes sizes{};
+};
+
+namespace {
+
+int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
+  if (!geo) return fail(FC_ERR_INVALID, "geometry is NULL");
+  if (geo->mode != FC_CONTINUOUS && geo->mode != FC_SYMBOL_SYNC) return fail(FC_ERR_INVALID, "unknown mode");
+  if ((geo->scheme_tx != FC_OLA && geo->scheme_tx != FC_OLS) || (geo->scheme_rx != FC_OLA && geo->scheme_rx != FC_OLS))
+    return fail(FC_ERR_INVALID, "unknown OLA/OLS scheme");
+  if (geo->n_groups < 1 || geo->n_groups > FC_MAX_GROUPS || !geo->groups)
+    return fail(FC_ERR_INVALID, "n_groups out of range");
+  if (geo->n_subbands < 1 || geo->n_subbands > FC_MAX_SUBBANDS || !geo->subbands)
+    return fail(FC_ERR_INVALID, "n_subbands out of range");
+  const bool sync = geo->mode == FC_SYMBOL_SYNC;
+  const int G = geo->n_groups, M = geo->n_subbands;
+
+  // ---- groups --------------------------------------------------------------
+  std::vector<GroupHost> gh(G);
+  for (int g = 0; g < G; ++g) {
+    const fc_group& in = geo->groups[g];
+    GroupHost& o = gh[g];
+    o.N = in.n_long;
+    o.N_O = in.n_overlap;
+    o.B = in.n_symbols;
+    if (o.N < 2 || o.N_O < 0 || o.N_O >= o.N) return fail(FC_ERR_INVALID, "need 0 <= N_O < N");
+    if (o.B < 1 || !in.n_cp) return fail(FC_ERR_INVALID, "need n_symbols >= 1 and n_cp");
+    if (!is_2a3b(o.N) || o.N > FC_MAX_TRANSFORM) return fail(FC_ERR_UNSUPPORTED, "N must be 2^a 3^b <= 4096");
+    o.N_S = o.N - o.N_O;
+    o.N_L = (o.N_O + 1) / 2;   // ceil(N_O/2)
+    o.N_T = o.N_O / 2;
+    o.ncp.assign(in.n_cp, in.n_cp + o.B);
+    for (int v : o.ncp)
+      if (v < 0) return fail(FC_ERR_INVALID, "negative N_CP");
+    if (sync) {
+      if (2 * o.N_O != o.N || o.N % 4) return fail(FC_ERR_INVALID, "symbol-sync needs N_O = N/2 and 4 | N");
+      for (int v : o.ncp)
+        if (v > o.N / 4) return fail(FC_ERR_INVALID, "symbol-sync needs N_CP,n <= N/4");
+    }
+    o.lead_hi = (in.lead_pad < 0) ? o.N_O : in.lead_pad;
+  }
+
+  // ---- subbands ------------------------------------------------------------
+  std::vector<SubHost> sh(M);
+  for (int m = 0; m < M; ++m) {
+    const fc_subband& in = geo->subbands[m];
+    SubHost& o = sh[m];
+    o.L = in.l_short; o.Lo = in.l_ofdm; o.Lact = in.n_active; o.c = in.centre_bin; o.g = in.group;
+    if (o.g < 0 || o.g >= G) return fail(FC_ERR_INVALID, "subband group out of range");
+    const GroupHost& g = gh[o.g];
+    if (!in.weights) return fail(FC_ERR_INVALID, "weights is NULL");
+    if (o.L < 1 || o.L > g.N) return fail(FC_ERR_INVALID, "need 1 <= L <= N");
+    if (!is_2a3b(o.L) || !is_2a3b(o.Lo) || o.Lo > FC_MAX_TRANSFORM)
+      return fail(FC_ERR_UNSUPPORTED, "L and L_OFDM must be 2^a 3^b <= 4096");
+    if (o.Lact < 1 || o.Lact > o.Lo) return fail(FC_ERR_INVALID, "need 1 <= L_act <= L_OFDM");
+    if ((long long)g.N_O * o.L % g.N) return fail(FC_ERR_INVALID, "L_O = N_O L / N is not an integer");
+    o.L_O = (int)((long long)g.N_O * o.L / g.N);
+    o.L_S = o.L - o.L_O;
+    o.L_L = (o.L_O + 1) / 2;
+    o.L_T = o.L_O / 2;
+    o.D.assign(in.weights, in.weights + o.L);
+    o.lcp.resize(g.B);
+    for (int n = 0; n < g.B; ++n) {
+      const long long num = (long long)g.ncp[n] * o.L;
+      if (!sync && num % g.N) return fail(FC_ERR_INVALID, "continuous FC needs integer low-rate CPs (N_CP L / N)");
+      o.lcp[n] = (int)(num / g.N);   // floor, Sec. III-E
+    }
+    if (sync) {
+      if (o.L % 4) return fail(FC_ERR_INVALID, "symbol-sync needs 4 | L");
+      if (o.Lo != o.L) return fail(FC_ERR_INVALID, "symbol-sync needs L_OFDM = L");
+    } else {
+      if ((long long)o.Lo * g.N % o.L) return fail(FC_ERR_INVALID, "N_OFDM = L_OFDM N / L is not an integer");
+      if ((long long)g.lead_hi * o.L % g.N) return fail(FC_ERR_INVALID, "lead pad is not an integer at low rate");
+      o.S_L = (int)((long long)g.lead_hi * o.L / g.N);
+      if (o.S_L < o.L_L) return fail(FC_ERR_INVALID, "lead pad shorter than L_L");
+      o.soff.resize(g.B);
+      int acc = 0;
+      for (int n = 0; n < g.B; ++n) {
+        o.soff[n] = acc;
+        acc += o.lcp[n] + o.Lo;
+      }
+      o.n_low = acc;
+      const long long u0 = (long long)o.n_low + 2LL * o.S_L;
+      o.R = (u0 <= o.L) ? 1 : (int)((u0 - o.L + o.L_S - 1) / o.L_S) + 1;
+    }
+  }
+  for (int g = 0; g < G; ++g) {
+    for (int m = 0; m < M; ++m)
+      if (sh[m].g == g) gh[g].subs.push_back(m);
+    if (gh[g].subs.empty()) return fail(FC_ERR_INVALID, "a group has no subband");
+  }
+  // subbands must be stored grouped for the kernels; keep the caller's grid
+  // order through grid_off, and sort the processing order by group
+  std::vector<int> order;
+  for (int g = 0; g < G; ++g)
+    for (int m : gh[g].subs) order.push_back(m);
+
+  // ---- frame layout --------------------------------------------------------
+  for (int g = 0; g < G; ++g) {
+    GroupHost& o = gh[g];
+    if (sync) {
+      o.T_lead = o.N / 4 - o.ncp[0];
+      long long q = (long long)o.N / 2 + (long long)o.B * o.N;
+      for (int n = 1; n < o.B; ++n) q += o.ncp[n];
+      o.len = (int)q;                                         // eq:waveformLen
+      o.sigma.resize(o.B);
+      long long acc = 0;
+      for (int n = 0; n < o.B; ++n) {
+        if (n > 0) acc += o.ncp[n];
+        o.sigma[n] = (int)((long long)n * o.N + acc);        // eq:multi-symb
+      }
+    } else {
+      const SubHost& s0 = sh[o.subs[0]];
+      for (int m : o.subs) {
+        const long long dur_hi = (long long)sh[m].n_low * o.N / sh[m].L;
+        const long long dur0 = (long long)s0.n_low * o.N / s0.L;
+        if (dur_hi != dur0 || sh[m].R != s0.R)
+          return fail(FC_ERR_INVALID, "continuous subbands of one group need equal high-rate durations");
+      }
+      o.R = s0.R;
+      o.T_lead = o.lead_hi;
+      o.len = (o.R - 1) * o.N_S + o.N;
+    }
+    o.cps.resize(o.B);
+    long long acc = 0;
+    for (int n = 0; n < o.B; ++n) {
+      if (n > 0) acc += o.ncp[n];
+      o.cps[n] = (int)(acc % o.N);
+    }
+  }
+  int t_s = 0;
+  for (auto& o : gh) t_s = std::max(t_s, o.T_lead);
+  long long frame_len = 0;
+  for (auto& o : gh) {
+    o.offset = t_s - o.T_lead;
+    frame_len = std::max(frame_len, (long long)o.offset + o.len);
+  }
+  if (frame_len > (1LL << 30)) return fail(FC_ERR_UNSUPPORTED, "frame too long");
+
+  // ---- transform sizes, twiddles ------------------------------------------
+  std::vector<int> sizes;
+  auto size_index = [&](int n) {
+    for (size_t i = 0; i < sizes.size(); ++i)
+      if (sizes[i] == n) return (int)i;
+    sizes.push_back(n);
+    return (int)sizes.size() - 1;
+  };
+  std::vector<int> g_sizeN(G), s_sizeL(M), s_sizeO(M);
+  for (int g = 0; g < G; ++g) g_sizeN[g] = size_index(gh[g].N);
+  for (int m = 0; m < M; ++m) {
+    s_sizeL[m] = size_index(sh[m].L);
+    s_sizeO[m] = size_index(sh[m].Lo);
+  }
+  if ((int)sizes.size() > FC_MAX_SIZES) return fail(FC_ERR_UNSUPPORTED, "too many distinct transform sizes");
+
+  Blob blob;
+  std::vector<size_t> tw_off(sizes.size());
+  for (size_t i = 0; i < sizes.size(); ++i) {
+    const int n = sizes[i];
+    std::vector<float2> tw(n);
+    for (int mm = 0; mm < n; ++mm) {
+      const double ang = 2.0 * M_PI * (double)mm / (double)n;   // exact reduction: mm < n
+      tw[mm] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    }
+    tw_off[i] = blob.add_vec(tw);
+  }
+
+  // ---- per-subband tables --------------------------------------------------
+  std::vector<size_t> off_dtx(M), off_drx(M), off_lcp(M), off_soff(M);
+  std::vector<int> plo(M), phi(M);
+  for (int m = 0; m < M; ++m) {
+    const SubHost& o = sh[m];
+    const GroupHost& g = gh[o.g];
+    const double I = (double)g.N / (double)o.L;
+    const double stx = std::sqrt(I) / (std::sqrt((double)o.Lo) * (double)g.N);
+    const double srx = 1.0 / (std::sqrt(I) * (double)o.L * std::sqrt((double)o.Lo));
+    std::vector<float> dtx(o.L), drx(o.L);
+    int lo = o.L, hi = 0;
+    for (int p = 0; p < o.L; ++p) {
+      dtx[p] = (float)(o.D[p] * stx);
+      drx[p] = (float)(o.D[p] * srx);
+      if (o.D[p] != 0.0) {
+        lo = std::min(lo, p);
+        hi = std::max(hi, p + 1);
+      }
+    }
+    if (lo >= hi) lo = hi = 0;
+    plo[m] = lo;
+    phi[m] = hi;
+    off_dtx[m] = blob.add_vec(dtx);
+    off_drx[m] = blob.add_vec(drx);
+    off_lcp[m] = blob.add_vec(o.lcp);
+    std::vector<int> so = o.soff;
+    if (so.empty()) so.assign(1, 0);
+    off_soff[m] = blob.add_vec(so);
+  }
+  std::vector<size_t> off_sigma(G), off_ncp(G), off_cps(G);
+  for (int g = 0; g < G; ++g) {
+    std::vector<int> sg = gh[g].sigma;
+    if (sg.empty()) sg.assign(1, 0);
+    off_sigma[g] = blob.add_vec(sg);
+    off_ncp[g] = blob.add_vec(gh[g].ncp);
+    off_cps[g] = blob.add_vec(gh[g].cps);
+  }
+
+  // ---- jobs ----------------------------------------------------------------
+  std::vector<FcJob> jobs;
+  std::vector<int> span;
+  for (int g = 0; g < G; ++g) {
+    const GroupHost& o = gh[g];
+    if (sync) {
+      for (int n = 0; n < o.B; ++n) jobs.push_back(FcJob{g, n, 2, o.offset + o.sigma[n]});
+    } else {
+      for (int r0 = 0; r0 < o.R; r0 += 2) jobs.push_back(FcJob{g, r0, std::min(2, o.R - r0), o.offset + r0 * o.N_S});
+    }
+  }
+  std::stable_sort(jobs.begin(), jobs.end(), [](const FcJob& a, const FcJob& b) { return a.start < b.start; });
+  int max_span = 0;
+  for (const FcJob& jb : jobs) {
+    const GroupHost& o = gh[jb.group];
+    const int sp = sync ? 3 * o.N / 2 : (jb.nblk - 1) * o.N_S + o.N;
+    span.push_back(sp);
+    max_span = std::max(max_span, sp);
+  }
+  const int n_jobs = (int)jobs.size();
+  const size_t off_jobs = blob.add_vec(jobs);
+
+  // chunk tables for several splits per stream
+  std::vector<int> splits;
+  for (int k = 1; k <= 64 && k <= n_jobs; k *= 2) splits.push_back(k);
+  std::vector<size_t> off_txc, off_rxc;
+  std::vector<int> ntx, nrx;
+  for (int K : splits) {
+    std::vector<int> bidx;   // job index boundaries
+    for (int c = 0; c <= K; ++c) bidx.push_back((int)((long long)c * n_jobs / K));
+    // TX: owned time ranges start at the first job of each chunk
+    std::vector<int> tb;
+    tb.push_back(0);
+    for (int c = 1; c < K; ++c) {
+      const int t = jobs[bidx[c]].start;
+      if (t > tb.back()) tb.push_back(t);
+    }
+    tb.push_back((int)frame_len);
+    std::vector<FcChunk> tx;
+    for (size_t c = 0; c + 1 < tb.size(); ++c) {
+      const int t0 = tb[c], t1 = tb[c + 1];
+      int j0 = 0;
+      while (j0 < n_jobs && (long long)jobs[j0].start + max_span <= t0) ++j0;
+      int j1 = j0;
+      while (j1 < n_jobs && jobs[j1].start < t1) ++j1;
+      tx.push_back(FcChunk{j0, j1, t0, t1});
+    }
+    std::vector<FcChunk> rx;
+    for (int c = 0; c < K; ++c)
+      if (bidx[c + 1] > bidx[c]) rx.push_back(FcChunk{bidx[c], bidx[c + 1], 0, 0});
+    off_txc.push_back(blob.add_vec(tx));
+    off_rxc.push_back(blob.add_vec(rx));
+    ntx.push_back((int)tx.size());
+    nrx.push_back((int)rx.size());
+  }
+
+  // ---- buffers and shared memory -------------------------------------------
+  int n_max = 0, l_max = 0, lo_max = 0;
+  for (auto& o : gh) n_max = std::max(n_max, o.N);
+  for (auto& o : sh) {
+    l_max = std::max(l_max, o.L);
+    lo_max = std::max(lo_max, o.Lo);
+  }
+  // in-place FFT capacity: batch 2 of N and L
+  for (size_t i = 0; i < sizes.size(); ++i) {
+    const int n = sizes[i];
+    const int cap = (n % 3 == 0) ? FC_THREADS * (FC_MAX_ELEMS_PER_THREAD / 3) * 3 : FC_THREADS * FC_MAX_ELEMS_PER_THREAD;
+    if (2 * n > cap) return fail(FC_ERR_UNSUPPORTED, "transform too large for the in-place FFT");
+  }
+  int ring = 1;
+  while (ring < max_span) ring <<= 1;
+  const int ybuf = 2 * n_max;
+  const int wbuf = sync ? 3 * l_max : 2 * l_max;
+  pl->smem_tx = (size_t)(ring + ybuf + wbuf) * sizeof(float2);
+  pl->smem_rx = (size_t)(ybuf + wbuf) * sizeof(float2);
+  pl->smem_ofdm = (size_t)lo_max * sizeof(float2);
+  const size_t smem_cap = kSmemPerBlockMax - sizeof(FcPlanDev) - 256;
+  if (pl->smem_tx > smem_cap || pl->smem_rx > smem_cap)
+    return fail(FC_ERR_UNSUPPORTED, "geometry needs more shared memory than one SM has");
+
+  // workspace (continuous): low-rate stream per subband, or R*L per subband for RX OLA
+  long long ws_len = 0;
+  std::vector<long long> ws_off(M, 0);
+  if (!sync) {
+    for (int m : order) {
+      ws_off[m] = ws_len;
+      long long need = sh[m].n_low;
+      if (geo->scheme_rx == FC_OLA) need = std::max(need, (long long)sh[m].R * sh[m].L);
+      ws_len += (need + 1) / 2 * 2;   // keep 16-byte alignment per slot
+    }
+  }
+
+  // grid offsets in the caller's subband order
+  std::vector<long long> grid_off(M);
+  long long grid_len = 0;
+  for (int m = 0; m < M; ++m) {
+    grid_off[m] = grid_len;
+    grid_len += (long long)gh[sh[m].g].B * sh[m].Lact;
+  }
+
+  int syms = 0;
+  for (int m = 0; m < M; ++m) syms += gh[sh[m].g].B;
+  pl->syms_per_stream = syms;
+
+  fc_sizes& z = pl->sizes;
+  z.grid_len = grid_len;
+  z.wave_len = frame_len;
+  {
+    const GroupHost& o = gh[0];
+    const SubHost& s0 = sh[o.subs[0]];
+    long long nom = 0;
+    const long long n_ofdm = sync ? o.N : (long long)s0.Lo * o.N / s0.L;
+    for (int n = 0; n < o.B; ++n) nom += n_ofdm + o.ncp[n];
+    z.nominal_len = nom;
+  }
+  z.workspace_per_stream = ws_len * (long long)sizeof(float2);
+  z.tx_kernels = sync ? 1 : 2;
+  z.rx_kernels = sync ? 1 : 2;
+  if (!upload) return FC_OK;
+
+  // ---- device upload ---------------------------------------------------------
+  const size_t off_plan = blob.add(nullptr, sizeof(FcPlanDev));
+  cudaError_t e = cudaMalloc(&pl->d_mem, blob.bytes.size());
+  if (e != cudaSuccess) {
+    pl->d_mem = nullptr;
+    return e == cudaErrorMemoryAllocation ? fail(FC_ERR_NOMEM, "cudaMalloc of plan tables failed")
+                                          : cuda_fail(e, "cudaMalloc");
+  }
+  unsigned char* base = pl->d_mem;
+  FcPlanDev& P = pl->h;
+  std::memset(&P, 0, sizeof(P));
+  P.mode = geo->mode;
+  P.scheme_tx = geo->scheme_tx;
+  P.scheme_rx = geo->scheme_rx;
+  P.n_groups = G;
+  P.n_subs = M;
+  P.n_sizes = (int)sizes.size();
+  P.frame_len = (int)frame_len;
+  P.grid_len = grid_len;
+  P.ws_len = ws_len;
+  P.ring = ring;
+  P.ybuf = ybuf;
+  P.wbuf = wbuf;
+  P.max_span = max_span;
+  for (size_t i = 0; i < sizes.size(); ++i) {
+    FcSize& z = P.sz[i];
+    z.n = sizes[i];
+    radix_plan(z.n, z.radix, &z.npass);
+    z.tw = reinterpret_cast<const float2*>(base + tw_off[i]);
+  }
+  // kernels walk subbands of a group contiguously: store them in group order
+  std::vector<int> slot_of(M);
+  for (int i = 0; i < M; ++i) slot_of[order[i]] = i;
+  int first = 0;
+  for (int g = 0; g < G; ++g) {
+    const GroupHost& o = gh[g];
+    FcGroupDev& d = P.g[g];
+    d.N = o.N; d.N_O = o.N_O; d.N_S = o.N_S; d.N_L = o.N_L; d.N_T = o.N_T;
+    d.B = o.B; d.offset = o.offset; d.len = o.len; d.R = o.R;
+    d.size_N = g_sizeN[g];
+    d.first_sub = first;
+    d.n_sub = (int)o.subs.size();
+    first += d.n_sub;
+    d.sigma = reinterpret_cast<const int*>(base + off_sigma[g]);
+    d.ncp = reinterpret_cast<const int*>(base + off_ncp[g]);
+    d.cps = reinterpret_cast<const int*>(base + off_cps[g]);
+  }
+  for (int m = 0; m < M; ++m) {
+    const SubHost& o = sh[m];
+    FcSubDev& d = P.s[slot_of[m]];
+    d.L = o.L; d.Lofdm = o.Lo; d.Lact = o.Lact; d.c = o.c; d.group = o.g;
+    d.L_S = o.L_S; d.L_L = o.L_L; d.L_T = o.L_T; d.S_L = o.S_L; d.n_low = o.n_low;
+    d.p_lo = plo[m]; d.p_hi = phi[m];
+    d.size_L = s_sizeL[m]; d.size_O = s_sizeO[m];
+    d.grid_off = grid_off[m];
+    d.ws_off = ws_off[m];
+    d.dtx = reinterpret_cast<const float*>(base + off_dtx[m]);
+    d.drx = reinterpret_cast<const float*>(base + off_drx[m]);
+    d.lcp = reinterpret_cast<const int*>(base + off_lcp[m]);
+    d.soff = reinterpret_cast<const int*>(base + off_soff[m]);
+  }
+  std::memcpy(blob.bytes.data() + off_plan, &P, sizeof(P));
+  e = cudaMemcpy(base, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy of plan tables");
+
+  pl->d_plan = reinterpret_cast<FcPlanDev*>(base + off_plan);
+  pl->d_jobs = reinterpret_cast<FcJob*>(base + off_jobs);
+  pl->n_jobs = n_jobs;
+  pl->splits = splits;
+  for (size_t i = 0; i < splits.size(); ++i) {
+    pl->tx_chunks.push_back(reinterpret_cast<const FcChunk*>(base + off_txc[i]));
+    pl->rx_chunks.push_back(reinterpret_cast<const FcChunk*>(base + off_rxc[i]));
+  }
+  pl->tx_nchunks = ntx;
+  pl->rx_nchunks = nrx;
+  return FC_OK;
+}
+
+std::once_flag g_smem_once[64];
+
+size_t pick_split(const fc_plan* pl, int n_streams) {
+  const long long want = 2LL * pl->num_sms;
+  size_t k = 0;
+  while (k + 1 < pl->splits.size() && (long long)n_streams * pl->splits[k] < want) ++k;
+  return k;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int check_io(const fc_plan* plan, int32_t n_streams, const void* in, const void* out, const void* ws,
+             size_t ws_bytes) {
+  if (!plan) return fail(FC_ERR_INVALID, "plan is NULL");
+  if (n_streams < 0) return fail(FC_ERR_INVALID, "n_streams < 0");
+  if (n_streams == 0) return FC_OK;
+  if (!in || !out) return fail(FC_ERR_INVALID, "input or output pointer is NULL");
+  if (((uintptr_t)in | (uintptr_t)out) & 7) return fail(FC_ERR_INVALID, "buffers must be 8-byte aligned");
+  const long long need = (long long)n_streams * plan->sizes.workspace_per_stream;
+  if (need > 0) {
+    if (!ws || ws_bytes < (size_t)need) return fail(FC_ERR_INVALID, "workspace missing or too small");
+    if ((uintptr_t)ws & 15) return fail(FC_ERR_INVALID, "workspace must be 16-byte aligned");
+  }
+  if ((long long)n_streams * plan->tx_nchunks.back() > 0x7fffffffLL) return fail(FC_ERR_INVALID, "too many streams");
+  return FC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fc_plan_create(fc_plan** out, const fc_geometry* geometry, int32_t device) {
+  if (!out) return fail(FC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev || device >= 64) return fail(FC_ERR_INVALID, "device out of range");
+  DeviceGuard dg(device);
+  if (!dg.ok) return fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  fc_plan* pl = new fc_plan();
+  pl->device = device;
+  e = cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete pl;
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  cudaError_t se = cudaSuccess;
+  std::call_once(g_smem_once[device], [&] { se = fc_set_smem_limits(kSmemPerBlockMax - sizeof(FcPlanDev) - 256); });
+  if (se != cudaSuccess) {
+    delete pl;
+    return cuda_fail(se, "cudaFuncSetAttribute");
+  }
+  const int rc = build_plan(pl, geometry, true);
+  if (rc != FC_OK) {
+    if (pl->d_mem) cudaFree(pl->d_mem);
+    delete pl;
+    return rc;
+  }
+  *out = pl;
+  return FC_OK;
+}
+
+int fc_geometry_check(const fc_geometry* geometry, fc_sizes* out) {
+  fc_plan tmp;
+  const int rc = build_plan(&tmp, geometry, false);
+  if (rc == FC_OK && out) *out = tmp.sizes;
+  return rc;
+}
+
+int fc_query(const fc_plan* plan, fc_sizes* out) {
+  if (!plan || !out) return fail(FC_ERR_INVALID, "NULL argument");
+  *out = plan->sizes;
+  return FC_OK;
+}
+
+int fc_tx_synthesize(const fc_plan* plan, int32_t n_streams, const void* grid_in, void* wave_out, void* workspace,
+                     size_t workspace_bytes, void* stream) {
+  int rc = check_io(plan, n_streams, grid_in, wave_out, workspace, workspace_bytes);
+  if (rc != FC_OK || n_streams == 0) return rc;
+  DeviceGuard dg(plan->device);
+  if (!dg.ok) return fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t k = pick_split(plan, n_streams);
+  const float2* grid = (const float2*)grid_in;
+  float2* wave = (float2*)wave_out;
+  cudaError_t e;
+  if (plan->h.mode == FC_SYMBOL_SYNC) {
+    e = fc_launch_tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, grid, wave,
+                          plan->smem_tx, st);
+  } else {
+    e = fc_launch_ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid, (float2*)workspace, plan->smem_ofdm,
+                           st);
+    if (e == cudaSuccess)
+      e = fc_launch_tx_cont(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams,
+                            (const float2*)workspace, wave, plan->smem_tx, st);
+  }
+  return e == cudaSuccess ? FC_OK : cuda_fail(e, "TX kernel launch");
+}
+
+int fc_rx_analyze(const fc_plan* plan, int32_t n_streams, const void* wave_in, void* grid_out, void* workspace,
+                  size_t workspace_bytes, void* stream) {
+  int rc = check_io(plan, n_streams, wave_in, grid_out, workspace, workspace_bytes);
+  if (rc != FC_OK || n_streams == 0) return rc;
+  DeviceGuard dg(plan->device);
+  if (!dg.ok) return fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t k = pick_split(plan, n_streams);
+  const float2* wave = (const float2*)wave_in;
+  float2* grid = (float2*)grid_out;
+  cudaError_t e;
+  if (plan->h.mode == FC_SYMBOL_SYNC) {
+    e = fc_launch_rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, wave, grid,
+                          plan->smem_rx, st);
+  } else {
+    e = fc_launch_rx_cont(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, wave,
+                          (float2*)workspace, plan->smem_rx, st);
+    if (e == cudaSuccess)
+      e = fc_launch_ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, (const float2*)workspace, grid,
+                               plan->smem_ofdm, st);
+  }
+  return e == cudaSuccess ? FC_OK : cuda_fail(e, "RX kernel launch");
+}
+
+void fc_plan_destroy(fc_plan* plan) {
+  if (!plan) return;
+  {
+    DeviceGuard dg(plan->device);
+    if (plan->d_mem) cudaFree(plan->d_mem);
+  }
+  delete plan;
+}
+
+const char* fc_status_string(int status) {
+  switch (status) {
+    case FC_OK: return "FC_OK";
+    case FC_ERR_INVALID: return "FC_ERR_INVALID: invalid geometry or argument";
+    case FC_ERR_UNSUPPORTED: return "FC_ERR_UNSUPPORTED: size or layout this build has no kernel for";
+    case FC_ERR_NOMEM: return "FC_ERR_NOMEM: device allocation failed";
+    case FC_ERR_CUDA: return "FC_ERR_CUDA: CUDA runtime error";
+    case FC_ERR_TIMEOUT: return "FC_ERR_TIMEOUT: bounded device wait expired";
+    default: return "unknown status";
+  }
+}
+
+const char* fc_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+"""Thin ctypes binding of the C ABI in ``include/fcofdm.h``.
+
+Argument marshalling only: every step of FC synthesis/analysis runs in the CUDA
+library ``_build/libfcofdm.so``. There is no CPU fallback; if the library has
+not been built the first call raises ``RuntimeError``.
+
+The functions keep the C names (``fc_plan_create``, ``fc_query``,
+``fc_tx_synthesize``, ``fc_rx_analyze``, ``fc_plan_destroy``,
+``fc_status_string``). ``Plan`` is a small owner object around them that takes
+torch device tensors (complex64) and the current torch CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfcofdm.so")
+
+FC_OK, FC_ERR_INVALID, FC_ERR_UNSUPPORTED, FC_ERR_NOMEM, FC_ERR_CUDA, FC_ERR_TIMEOUT = range(6)
+FC_CONTINUOUS, FC_SYMBOL_SYNC = 0, 1
+FC_OLA, FC_OLS = 0, 1
+
+EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize", "fc_rx_analyze", "fc_plan_destroy",
+            "fc_status_string", "fc_last_error")
+
+
+class FcGroup(ctypes.Structure):
+    _fields_ = [("n_long", ctypes.c_int32), ("n_overlap", ctypes.c_int32), ("lead_pad", ctypes.c_int32),
+                ("n_symbols", ctypes.c_int32), ("n_cp", ctypes.POINTER(ctypes.c_int32))]
+
+
+class FcSubband(ctypes.Structure):
+    _fields_ = [("l_short", ctypes.c_int32), ("l_ofdm", ctypes.c_int32), ("n_active", ctypes.c_int32),
+                ("centre_bin", ctypes.c_int32), ("group", ctypes.c_int32),
+                ("weights", ctypes.POINTER(ctypes.c_double))]
+
+
+class FcGeometry(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("scheme_tx", ctypes.c_int32), ("scheme_rx", ctypes.c_int32),
+                ("n_groups", ctypes.c_int32), ("groups", ctypes.POINTER(FcGroup)),
+                ("n_subbands", ctypes.c_int32), ("subbands", ctypes.POINTER(FcSubband))]
+
+
+class FcSizes(ctypes.Structure):
+    _fields_ = [("grid_len", ctypes.c_int64), ("wave_len", ctypes.c_int64), ("nominal_len", ctypes.c_int64),
+                ("workspace_per_stream", ctypes.c_int64), ("tx_kernels", ctypes.c_int32),
+                ("rx_kernels", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libfcofdm.so (raises RuntimeError when it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"FC CUDA library not built: {path} is missing "
+                               "(run `python -m paper_2008_00672_gb300.build`)")
+        lib = ctypes.CDLL(path)
+        vp, i32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+        lib.fc_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(FcGeometry), i32]
+        lib.fc_plan_create.restype = ctypes.c_int
+        lib.fc_geometry_check.argtypes = [ctypes.POINTER(FcGeometry), ctypes.POINTER(FcSizes)]
+        lib.fc_geometry_check.restype = ctypes.c_int
+        lib.fc_query.argtypes = [vp, ctypes.POINTER(FcSizes)]
+        lib.fc_query.restype = ctypes.c_int
+        lib.fc_tx_synthesize.argtypes = [vp, i32, vp, vp, vp, sz, vp]
+        lib.fc_tx_synthesize.restype = ctypes.c_int
+        lib.fc_rx_analyze.argtypes = [vp, i32, vp, vp, vp, sz, vp]
+        lib.fc_rx_analyze.restype = ctypes.c_int
+        lib.fc_plan_destroy.argtypes = [vp]
+        lib.fc_plan_destroy.restype = None
+        lib.fc_status_string.argtypes = [ctypes.c_int]
+        lib.fc_status_string.restype = ctypes.c_char_p
+        lib.fc_last_error.argtypes = []
+        lib.fc_last_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+class FcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = load_library()
+        super().__init__(f"{where}: {lib.fc_status_string(status).decode()} ({lib.fc_last_error().decode()})")
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != FC_OK:
+        raise FcError(status, where)
+
+
+def _marshal_geometry(geom):
+    """Build the C structs from any object with the Geometry attributes; keeps the
+    backing arrays alive in the returned tuple."""
+    keep = []
+    groups = (FcGroup * len(geom.groups))()
+    for i, g in enumerate(geom.groups):
+        cps = (ctypes.c_int32 * len(g.n_cp))(*[int(v) for v in g.n_cp])
+        keep.append(cps)
+        groups[i] = FcGroup(int(g.n_long), int(g.n_overlap), int(getattr(g, "lead_pad", -1)), len(g.n_cp), cps)
+    subs = (FcSubband * len(geom.subbands))()
+    for i, s in enumerate(geom.subbands):
+        w = (ctypes.c_double * int(s.l_short))(*[float(v) for v in s.weights])
+        keep.append(w)
+        subs[i] = FcSubband(int(s.l_short), int(s.l_ofdm), int(s.n_active), int(s.centre_bin), int(s.group), w)
+    geo = FcGeometry(int(geom.mode), int(geom.scheme_tx), int(geom.scheme_rx), len(geom.groups), groups,
+                     len(geom.subbands), subs)
+    return geo, (groups, subs, keep)
+
+
+# --------------------------------------------------------------------------
+# C-named functions
+# --------------------------------------------------------------------------
+
+def fc_plan_create(geom, device: int = 0) -> ctypes.c_void_p:
+    lib = load_library()
+    geo, _keep = _marshal_geometry(geom)
+    h = ctypes.c_void_p()
+    _check(lib.fc_plan_create(ctypes.byref(h), ctypes.byref(geo), int(device)), "fc_plan_create")
+    return h
+
+
+def fc_geometry_check(geom) -> FcSizes:
+    """Host-only validation of a geometry; returns the per-stream sizes."""
+    lib = load_library()
+    geo, _keep = _marshal_geometry(geom)
+    out = FcSizes()
+    _check(lib.fc_geometry_check(ctypes.byref(geo), ctypes.byref(out)), "fc_geometry_check")
+    return out
+
+
+def fc_query(plan) -> FcSizes:
+    out = FcSizes()
+    _check(load_library().fc_query(plan, ctypes.byref(out)), "fc_query")
+    return out
+
+
+def fc_tx_synthesize(plan, n_streams: int, grid_in: int, wave_out: int, workspace: int = 0,
+                     workspace_bytes: int = 0, stream: int = 0):
+    _check(load_library().fc_tx_synthesize(plan, int(n_streams), grid_in, wave_out, workspace or None,
+                                           int(workspace_bytes), stream or None), "fc_tx_synthesize")
+
+
+def fc_rx_analyze(plan, n_streams: int, wave_in: int, grid_out: int, workspace: int = 0,
+                  workspace_bytes: int = 0, stream: int = 0):
+    _check(load_library().fc_rx_analyze(plan, int(n_streams), wave_in, grid_out, workspace or None,
+                                        int(workspace_bytes), stream or None), "fc_rx_analyze")
+
+
+def fc_plan_destroy(plan):
+    if plan:
+        load_library().fc_plan_destroy(plan)
+
+
+def fc_status_string(status: int) -> str:
+    return load_library().fc_status_string(int(status)).decode()
+
+
+# --------------------------------------------------------------------------
+# torch convenience owner
+# --------------------------------------------------------------------------
+
+class Plan:
+    """Owns one fc_plan; execute calls take complex64 CUDA tensors."""
+
+    def __init__(self, geom, device: int = 0):
+        self.device = int(device)
+        self.handle = fc_plan_create(geom, self.device)
+        s = fc_query(self.handle)
+        self.grid_len = int(s.grid_len)
+        self.wave_len = int(s.wave_len)
+        self.nominal_len = int(s.nominal_len)
+        self.workspace_per_stream = int(s.workspace_per_stream)
+        self.tx_kernels = int(s.tx_kernels)
+        self.rx_kernels = int(s.rx_kernels)
+        self._ws = None
+
+    def close(self):
+        if self.handle:
+            fc_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace(self, n_streams: int):
+        """A device workspace large enough for n_streams (allocated by torch, reused)."""
+        import torch
+        need = self.workspace_per_stream * int(n_streams)
+        if need == 0:
+            return None
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
+        return self._ws
+
+    @staticmethod
+    def _stream_handle(stream):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        return int(stream.cuda_stream)
+
+    def tx_synthesize(self, grid, wave_out, workspace=None, stream=None):
+        n = self._streams(grid, self.grid_len, wave_out, self.wave_len)
+        ws = workspace if workspace is not None else self.workspace(n)
+        fc_tx_synthesize(self.handle, n, grid.data_ptr(), wave_out.data_ptr(),
+                         ws.data_ptr() if ws is not None else 0,
+                         ws.numel() * ws.element_size() if ws is not None else 0, self._stream_handle(stream))
+        return wave_out
+
+    def rx_analyze(self, wave, grid_out, workspace=None, stream=None):
+        n = self._streams(wave, self.wave_len, grid_out, self.grid_len)
+        ws = workspace if workspace is not None else self.workspace(n)
+        fc_rx_analyze(self.handle, n, wave.data_ptr(), grid_out.data_ptr(),
+                      ws.data_ptr() if ws is not None else 0,
+                      ws.numel() * ws.element_size() if ws is not None else 0, self._stream_handle(stream))
+        return grid_out
+
+    @staticmethod
+    def _streams(a, la, b, lb) -> int:
+        import torch
+        for t in (a, b):
+            if t.dtype != torch.complex64 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("expected contiguous complex64 CUDA tensors")
+        if a.numel() % la or b.numel() % lb or a.numel() // la != b.numel() // lb:
+            raise ValueError("input and output sizes do not match the plan")
+        return a.numel() // la

@@ -1,0 +1,113 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every function the
+header declares, and its host-only geometry validation agrees with the oracle's
+frame arithmetic and rejects what the paper's equations do not define."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import fc_oracle as fo
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fcofdm.h")
+
+
+@pytest.fixture(scope="module")
+def fc():
+    from paper_2008_00672_gb300 import build
+    build.build()
+    from paper_2008_00672_gb300 import fc as fcmod
+    fcmod.load_library()
+    return fcmod
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(fc_\w+)\s*\(", txt, flags=re.M)))
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for n in ["fc_plan_create", "fc_tx_synthesize", "fc_rx_analyze", "fc_plan_destroy", "fc_query",
+              "fc_geometry_check", "fc_status_string", "fc_last_error"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(fc):
+    lib = fc.load_library()
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    out = subprocess.run(["nm", "-D", "--defined-only", fc.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (fc_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_status_strings(fc):
+    for code in range(6):
+        assert fc.fc_status_string(code).startswith("FC_")
+
+
+def _sizes_match(fc, geom):
+    s = fc.fc_geometry_check(geom)
+    assert s.wave_len == fo.frame_len(geom)
+    assert s.grid_len == geom.grid_len()
+    return s
+
+
+@pytest.mark.parametrize("name", ["single5", "mixed20"])
+def test_sizes_match_oracle_named(fc, name):
+    geom = wl.NAMED[name]()
+    s = _sizes_match(fc, geom)
+    assert s.nominal_len == geom.nominal_samples()
+    if geom.mode == wl.SYMBOL_SYNC:
+        assert s.workspace_per_stream == 0
+
+
+def test_sizes_match_oracle_100mhz(fc):
+    geom = wl.config_100mhz(10)
+    s = _sizes_match(fc, geom)
+    assert s.nominal_len == 614400
+    assert s.workspace_per_stream > 0
+
+
+def test_nominal_samples_printed_configs(fc):
+    """One slot at 7.68 Msps = 7680 samples; 1 ms at 30.72 Msps = 30720."""
+    assert fc.fc_geometry_check(wl.config_single_5mhz()).nominal_len == 7680
+    assert fc.fc_geometry_check(wl.config_mixed_20mhz()).nominal_len == 30720
+
+
+def _g(mode, N, N_O, L, Lo, act, c, ncp, lead=-1, stx=0, srx=1):
+    g = wl.Group(N, N_O, tuple(ncp), lead)
+    s = wl.Subband(L, Lo, act, c, 0, np.ones(L))
+    return wl.Geometry(mode, stx, srx, (g,), (s,))
+
+
+@pytest.mark.parametrize("geom,code", [
+    (_g(1, 32, 8, 16, 16, 8, 0, (2,)), 1),            # symbol-sync needs lambda = 0.5
+    (_g(1, 32, 16, 16, 16, 8, 0, (9,)), 1),           # N_CP > N/4
+    (_g(1, 32, 16, 18, 18, 8, 0, (2,)), 1),           # 4 does not divide L
+    (_g(1, 32, 16, 16, 32, 8, 0, (2,)), 1),           # L_OFDM != L in symbol-sync mode
+    (_g(0, 32, 16, 16, 16, 8, 0, (3,)), 1),           # fractional low-rate CP in continuous mode
+    (_g(0, 32, 10, 24, 24, 8, 0, (0,)), 1),           # L_O = N_O L/N not an integer
+    (_g(0, 32, 16, 16, 16, 20, 0, (4,)), 1),          # L_act > L_OFDM
+    (_g(0, 32, 16, 16, 16, 8, 0, (4,), lead=4), 1),   # lead pad shorter than L_L
+    (_g(0, 8192, 4096, 8192, 8192, 8, 0, (0,)), 2),   # beyond the largest built transform
+    (_g(0, 40, 20, 40, 40, 8, 0, (0,)), 2),           # 5 is not a built radix
+])
+def test_invalid_geometry_rejected(fc, geom, code):
+    with pytest.raises(fc.FcError) as ei:
+        fc.fc_geometry_check(geom)
+    assert ei.value.status == code
+
+
+def test_oracle_rejects_the_same_invalid_geometry():
+    """The oracle refuses the geometries the paper leaves undefined, as the library does."""
+    for geom in [_g(1, 32, 8, 16, 16, 8, 0, (2,)), _g(1, 32, 16, 16, 16, 8, 0, (9,)),
+                 _g(0, 32, 16, 16, 16, 8, 0, (3,))]:
+        with pytest.raises(ValueError):
+            fo.tx_frame(geom, np.zeros(geom.grid_len(), complex))

@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Both sides get the same seeded inputs, rounded once to complex64 (the ABI's
+type), so the comparison measures the FP32 computation only. The bar is the
+RMS-normalised error ||gpu - oracle|| / ||oracle|| <= 1e-5, per stream, on the
+TX waveform and on the RX QAM estimates.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import fc_oracle as fo
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2008_00672_gb300 import build
+    build.build()
+    return torch
+
+
+def c64(a):
+    return np.asarray(a).astype(np.complex64)
+
+
+def rel(a, b):
+    b = np.asarray(b)
+    return float(np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_tx_rx(torch, geom, grid, wave_rx):
+    from paper_2008_00672_gb300 import Plan
+    plan = Plan(geom)
+    g = torch.from_numpy(c64(grid)).cuda()
+    w = torch.empty((grid.shape[0], plan.wave_len), dtype=torch.complex64, device="cuda")
+    plan.tx_synthesize(g, w)
+    wr = torch.from_numpy(c64(wave_rx)).cuda()
+    est = torch.empty_like(g)
+    plan.rx_analyze(wr, est)
+    torch.cuda.synchronize()
+    out = w.cpu().numpy(), est.cpu().numpy()
+    plan.close()
+    return out
+
+
+def check_geometry(torch, geom, n_streams, seed, snr_db=30.0, streams_to_check=None):
+    grid = c64(wl.qam_grid(geom, n_streams, seed)).astype(np.complex128)
+    idx = list(range(n_streams)) if streams_to_check is None else streams_to_check
+    ref_tx = {s: fo.tx_frame(geom, grid[s]) for s in idx}
+    # RX input: the oracle waveform plus AWGN, rounded to complex64 (same for both sides)
+    flen = fo.frame_len(geom)
+    wave_rx = np.zeros((n_streams, flen), dtype=np.complex128)
+    for s in idx:
+        wave_rx[s] = wl.awgn(ref_tx[s], snr_db, seed + 7919 * (s + 1))
+    wave_rx = c64(wave_rx).astype(np.complex128)
+    w, e = gpu_tx_rx(torch, geom, grid, wave_rx)
+    worst = (0.0, 0.0)
+    for s in idx:
+        et = rel(w[s], ref_tx[s])
+        er = rel(e[s], fo.rx_frame(geom, wave_rx[s]))
+        worst = (max(worst[0], et), max(worst[1], er))
+    assert worst[0] <= TOL and worst[1] <= TOL, worst
+    return w, e
+
+
+def geom1(mode, stx, srx, N, N_O, L, Lo, act, c, n_cp, D=None, lead=-1):
+    D = wl.rc_transition_weights(L, act if Lo == L else min(act, L - 8), 3) if D is None else D
+    g = wl.Group(N, N_O, tuple(n_cp), lead)
+    s = wl.Subband(L, Lo, act, c, 0, D)
+    return wl.Geometry(mode, stx, srx, (g,), (s,))
+
+
+# ---------------------------------------------------------------------------
+# small geometries spanning the schemes, radices and edge cases
+# ---------------------------------------------------------------------------
+
+SYNC_SMALL = [
+    # N, L, c, n_cp  (OLA/OLS TX x OLA/OLS RX)
+    (32, 16, 3, (6, 4, 4, 5)),
+    (64, 16, -5, (16, 0, 3, 16, 9)),             # L_CP = N_CP/4 floors, CP = N/4 and 0
+    (48, 24, 7, (12, 9, 9)),                      # radix 3
+    (128, 64, 60, (10, 9, 9, 9, 9, 9, 9)),        # subband wraps past the Nyquist bin
+]
+
+
+@pytest.mark.parametrize("stx", [fo.OLA, fo.OLS])
+@pytest.mark.parametrize("srx", [fo.OLA, fo.OLS])
+@pytest.mark.parametrize("case", SYNC_SMALL)
+def test_sync_small(torch_cuda, stx, srx, case):
+    N, L, c, n_cp = case
+    geom = geom1(fo.SYMBOL_SYNC, stx, srx, N, N // 2, L, L, L - 8, c, n_cp)
+    check_geometry(torch_cuda, geom, 3, 11)
+
+
+CONT_SMALL = [
+    # N, N_O, L, L_OFDM, act, c, n_cp, lead
+    (64, 32, 48, 48, 36, -7, (8, 4, 4, 8), -1),          # I = 4/3, radix 3
+    (64, 16, 32, 32, 24, 9, (6, 2, 2, 2), -1),            # lambda = 0.25
+    (64, 32, 64, 64, 40, 0, (16, 8, 8), -1),              # I = 1
+    (128, 64, 64, 32, 20, -20, (8, 4, 4, 4, 8), -1),      # L_OFDM < L
+    (64, 32, 32, 32, 20, 5, (4, 2, 2, 2), 32),            # longer lead pad
+]
+
+
+@pytest.mark.parametrize("stx", [fo.OLA, fo.OLS])
+@pytest.mark.parametrize("srx", [fo.OLA, fo.OLS])
+@pytest.mark.parametrize("case", CONT_SMALL)
+def test_continuous_small(torch_cuda, stx, srx, case):
+    N, N_O, L, Lo, act, c, n_cp, lead = case
+    D = wl.rc_transition_weights(L, min(act * L // Lo, L - 8), 3)
+    geom = geom1(fo.CONTINUOUS, stx, srx, N, N_O, L, Lo, act, c, n_cp, D=D, lead=lead)
+    check_geometry(torch_cuda, geom, 2, 13)
+
+
+def test_sync_two_subbands_one_group_overlapping_transitions(torch_cuda):
+    """Two subbands of different L share the long IDFT; their transition bins overlap and add."""
+    g = wl.Group(128, 64, (12, 8, 8, 8))
+    s1 = wl.Subband(64, 64, 36, -24, 0, wl.rc_transition_weights(64, 36, 6))
+    s2 = wl.Subband(32, 32, 16, 20, 0, wl.rc_transition_weights(32, 16, 4))
+    geom = wl.Geometry(fo.SYMBOL_SYNC, fo.OLA, fo.OLS, (g,), (s1, s2))
+    check_geometry(torch_cuda, geom, 2, 17)
+
+
+def test_continuous_two_subbands_one_group(torch_cuda):
+    g = wl.Group(128, 64, (16, 8, 8, 8))
+    s1 = wl.Subband(64, 64, 40, -30, 0, wl.rc_transition_weights(64, 40, 6))
+    s2 = wl.Subband(32, 32, 16, 40, 0, wl.rc_transition_weights(32, 16, 4))
+    geom = wl.Geometry(fo.CONTINUOUS, fo.OLS, fo.OLA, (g,), (s1, s2))
+    check_geometry(torch_cuda, geom, 2, 19)
+
+
+def test_sync_three_groups_subband_order(torch_cuda):
+    """Groups given out of order, subbands listed against the group order."""
+    ga = wl.Group(64, 32, (12, 8, 8))
+    gb = wl.Group(32, 16, (6, 4, 4, 4, 4, 4))
+    gc = wl.Group(128, 64, (20, 16))
+    sb = wl.Subband(16, 16, 10, 5, 1, wl.rc_transition_weights(16, 10, 2))
+    sa = wl.Subband(32, 32, 20, -12, 0, wl.rc_transition_weights(32, 20, 3))
+    sc = wl.Subband(64, 64, 30, 33, 2, wl.rc_transition_weights(64, 30, 4))
+    geom = wl.Geometry(fo.SYMBOL_SYNC, fo.OLA, fo.OLS, (ga, gb, gc), (sb, sc, sa))
+    check_geometry(torch_cuda, geom, 3, 23)
+
+
+def test_single_symbol_and_full_band(torch_cuda):
+    geom = geom1(fo.SYMBOL_SYNC, fo.OLA, fo.OLS, 32, 16, 32, 32, 32, 0, (8,), D=np.ones(32))
+    check_geometry(torch_cuda, geom, 1, 29)
+
+
+# ---------------------------------------------------------------------------
+# the named 5G NR workloads
+# ---------------------------------------------------------------------------
+
+def test_nr5mhz_single_subband_ols(torch_cuda):
+    check_geometry(torch_cuda, wl.config_single_5mhz(), 3, wl.default_seed(1))
+
+
+def test_nr20mhz_mixed_numerology_symbol_sync(torch_cuda):
+    check_geometry(torch_cuda, wl.config_mixed_20mhz(), 2, wl.default_seed(2))
+
+
+def test_nr100mhz_two_slots(torch_cuda):
+    check_geometry(torch_cuda, wl.config_100mhz(2), 1, wl.default_seed(3))
+
+
+# ---------------------------------------------------------------------------
+# batching: a stream's result does not depend on the batch it runs in
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["mixed20", "single5"])
+def test_batch_invariance_bitwise(torch_cuda, name):
+    """Alone (many chunks per stream) and inside a large batch (one chunk per
+    stream) the same stream gives bit-identical TX and RX output."""
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import Plan
+    geom = wl.NAMED[name]()
+    plan = Plan(geom)
+    big = 333
+    grid = c64(wl.qam_grid(geom, 4, 5)).astype(np.complex64)
+    gbig = np.tile(grid, (big // 4 + 1, 1))[:big]
+    g1 = torch.from_numpy(grid[2:3].copy()).cuda()
+    gb = torch.from_numpy(gbig).cuda()
+    w1 = torch.empty((1, plan.wave_len), dtype=torch.complex64, device="cuda")
+    wb = torch.empty((big, plan.wave_len), dtype=torch.complex64, device="cuda")
+    plan.tx_synthesize(g1, w1)
+    plan.tx_synthesize(gb, wb)
+    e1 = torch.empty_like(g1)
+    eb = torch.empty_like(gb)
+    plan.rx_analyze(w1, e1)
+    plan.rx_analyze(wb, eb)
+    torch.cuda.synchronize()
+    for k in range(2, big, 4):
+        assert torch.equal(wb[k], w1[0])
+        assert torch.equal(eb[k], e1[0])
+
+
+# ---------------------------------------------------------------------------
+# full benchmark size: sampled streams against the oracle
+# ---------------------------------------------------------------------------
+
+def test_bench_size_sampled_streams(torch_cuda):
+    """The benchmark's batch of 1 ms subframes (2048 streams): three sampled
+    streams, including the last, against the oracle."""
+    geom = wl.config_mixed_20mhz()
+    check_geometry(torch_cuda, geom, 2048, wl.default_seed(2), streams_to_check=[0, 1025, 2047])
+
+
+# ---------------------------------------------------------------------------
+# ABI argument handling on a device
+# ---------------------------------------------------------------------------
+
+def test_abi_errors_and_noop(torch_cuda):
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import fc
+    geom = wl.config_single_5mhz()
+    p = fc.Plan(geom)
+    # zero streams: no-op, even with NULL buffers
+    fc.fc_tx_synthesize(p.handle, 0, None, None)
+    g = torch.zeros((1, p.grid_len), dtype=torch.complex64, device="cuda")
+    w = torch.zeros((1, p.wave_len), dtype=torch.complex64, device="cuda")
+    with pytest.raises(fc.FcError) as ei:     # workspace missing (continuous mode needs one)
+        fc.fc_tx_synthesize(p.handle, 1, g.data_ptr(), w.data_ptr(), 0, 0)
+    assert ei.value.status == fc.FC_ERR_INVALID
+    with pytest.raises(fc.FcError):
+        fc.fc_rx_analyze(p.handle, -1, w.data_ptr(), g.data_ptr())
+    with pytest.raises(fc.FcError):
+        fc.fc_tx_synthesize(p.handle, 1, None, w.data_ptr())
+    p.close()
