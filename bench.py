@@ -1,0 +1,438 @@
+"""Benchmark: FC TX synthesis + RX analysis throughput on GB300.
+
+Workload (one step): the 20 MHz mixed-numerology subframe at 30.72 Msps
+(15 kHz / 51 PRB with N=2048, L=1024 and 30 kHz / 24 PRB with N=1024, L=512,
+symbol-synchronized FC, OLA TX, OLS RX, 16-QAM, 1 ms), batched over
+independent streams (carriers x antennas): TX turns every stream's QAM grid
+into its waveform, RX turns a received (TX + 30 dB AWGN) waveform into QAM
+estimates. Inputs are resident in HBM and larger than L2.
+
+value = (TX + RX) nominal high-rate samples of all streams on all GPUs / time,
+in Msamples/s. One JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--streams S] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FC TX+RX Msamples/s on 1 GB300 at stated EVM vs FP64 oracle; % HBM peak; p99 slot ms"
+WORKLOAD = "nr20mhz_mixed_15k51prb_30k24prb_symsync_1ms"
+SNR_DB = 30.0
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz: float, n_sms: int = 152) -> float:
+    """FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
+    return n_sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def transform_flops(geom) -> float:
+    """Conventional 5 n log2 n flops per complex transform, summed over one stream
+    and one direction (TX: OFDM IDFT, 2 short DFTs, 2 long IDFTs per symbol; RX the
+    mirror image)."""
+    total = 0.0
+    for s in geom.subbands:
+        g = geom.groups[s.group]
+        per_sym = 5 * s.l_ofdm * math.log2(s.l_ofdm) + 2 * 5 * s.l_short * math.log2(s.l_short)
+        total += g.n_symbols * per_sym
+    for g in geom.groups:
+        total += g.n_symbols * 2 * 5 * g.n_long * math.log2(g.n_long)
+    return total
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("fc_kernels.cu", "fc_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2008_00672_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(kernel: str):
+    """DRAM bytes per launch recorded from an ncu capture of the current kernel source, else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 7:
+                    self.samples.append(parts)
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        rows = []
+        for p in self.samples:
+            try:
+                rows.append((float(p[0]), float(p[1]), p[3:7]))
+            except ValueError:
+                pass
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, v in enumerate(flags) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm and CPU baseline: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def _oracle_worker(args):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import workloads as wl
+    from oracle import fc_oracle as fo
+    seed, n_frames = args
+    geom = wl.config_mixed_20mhz()
+    grid = wl.qam_grid(geom, n_frames, seed)
+    t0 = time.perf_counter()
+    for s in range(n_frames):
+        w = fo.tx_frame(geom, grid[s])
+        fo.rx_frame(geom, w)
+    return time.perf_counter() - t0, n_frames
+
+
+def oracle_pool(cores: int):
+    """A spawn pool of single-threaded oracle workers (imports and DFT matrices warmed)."""
+    import multiprocessing as mp
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    pool = mp.get_context("spawn").Pool(cores)
+    pool.map(_oracle_worker, [(4242, 1)] * cores)
+    return pool
+
+
+def oracle_throughput(pool, frames_per_core: int, cores: int, seed: int = 4242):
+    """Time the oracle (TX + RX of whole 1 ms subframes) on the pool's `cores`
+    workers. Returns (Msamples/s, seconds, frames)."""
+    import workloads as wl
+    nominal = wl.config_mixed_20mhz().nominal_samples()
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_worker, [(seed + i, frames_per_core) for i in range(cores)])
+    wall = time.perf_counter() - t0
+    frames = sum(r[1] for r in res)
+    return 2 * nominal * frames / wall / 1e6, wall, frames
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    vals, times = [], []
+    pool = oracle_pool(cores)
+    try:
+        for i in range(args.warmup + args.steps):
+            v, wall, frames = oracle_throughput(pool, 1, cores, seed=5000 + i)
+            if i >= args.warmup:
+                vals.append(v)
+                times.append(wall)
+    finally:
+        pool.close()
+    value = statistics.median(vals)
+    sample = f"{cores} frames (1 per core) of the 1 ms subframe, TX+RX, per step"
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Msamples/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * statistics.median(times), 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "streams_per_step": cores, "oracle": "FP64 numpy, O(n^2) DFTs"},
+           "cpu_baseline": {"value": round(value, 4), "unit": "Msamples/s", "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": "Msamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+    import workloads as wl
+    from paper_2008_00672_gb300 import Plan, build
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    build.build()
+    geom = wl.config_mixed_20mhz()
+    plan = Plan(geom, device=local_rank)
+    S = args.streams
+    seed = wl.default_seed(2) + 100000 * rank
+
+    # inputs: seeded QAM grid; RX input = TX output + 30 dB AWGN (made once, on the device)
+    grid_np = wl.qam_grid(geom, min(S, 64), seed).astype(np.complex64)
+    reps = -(-S // grid_np.shape[0])
+    grid = torch.from_numpy(grid_np).to(dev).repeat(reps, 1)[:S].contiguous()
+    wave = torch.empty((S, plan.wave_len), dtype=torch.complex64, device=dev)
+    est = torch.empty_like(grid)
+    plan.tx_synthesize(grid, wave)
+    torch.cuda.synchronize(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    p = wave.abs().pow(2).mean(dim=1, keepdim=True)
+    sigma = torch.sqrt(p / (10 ** (SNR_DB / 10)) / 2)
+    noise = torch.complex(torch.randn(wave.shape, generator=gen, device=dev),
+                          torch.randn(wave.shape, generator=gen, device=dev))
+    rx_in = (wave + noise * sigma).to(torch.complex64).contiguous()
+    del noise
+    torch.cuda.synchronize(dev)
+
+    st = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(st)
+        plan.tx_synthesize(grid, wave)
+        if ev is not None:
+            ev[1].record(st)
+        plan.rx_analyze(rx_in, est)
+        if ev is not None:
+            ev[2].record(st)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    t_start.record(st)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(st)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    ms_total = t_start.elapsed_time(t_end)
+    tx_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    rx_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    if world > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+
+    nominal = plan.nominal_len
+    samples_step = 2 * nominal * S * world
+    value = samples_step * args.steps / (ms_total * 1e-3) / 1e6
+
+    # ---- end to end through the public API: pinned host in, host out ----------
+    h_grid = grid.cpu().pin_memory()
+    h_rx = rx_in.cpu().pin_memory()
+    h_wave = torch.empty(wave.shape, dtype=wave.dtype).pin_memory()
+    h_est = torch.empty(est.shape, dtype=est.dtype).pin_memory()
+    d_grid = torch.empty_like(grid)
+    d_rx = torch.empty_like(rx_in)
+
+    def e2e_step():
+        d_grid.copy_(h_grid, non_blocking=True)
+        d_rx.copy_(h_rx, non_blocking=True)
+        plan.tx_synthesize(d_grid, wave)
+        plan.rx_analyze(d_rx, est)
+        h_wave.copy_(wave, non_blocking=True)
+        h_est.copy_(est, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 10))
+    e0.record(st)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = samples_step * e2e_steps / (e2e_ms * 1e-3) / 1e6
+    h2d = (grid.numel() + rx_in.numel()) * 8
+    d2h = (wave.numel() + est.numel()) * 8
+
+    if rank != 0:
+        return
+
+    # ---- slot latency: one stream, TX + RX, p50/p99 ---------------------------
+    g1, w1, e1_, r1 = grid[:1].clone(), wave[:1].clone(), est[:1].clone(), rx_in[:1].clone()
+    lat = []
+    for i in range(220):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        plan.tx_synthesize(g1, w1)
+        plan.rx_analyze(r1, e1_)
+        b.record(st)
+        b.synchronize()
+        if i >= 20:
+            lat.append(a.elapsed_time(b))
+    lat.sort()
+
+    # ---- accuracy of the timed path against the FP64 oracle (one sampled stream) ----
+    from oracle import fc_oracle as fo
+    s_chk = S - 1
+    gref = grid[s_chk].cpu().numpy().astype(np.complex128)
+    w_ref = fo.tx_frame(geom, gref)
+    plan.tx_synthesize(grid, wave)
+    plan.rx_analyze(rx_in, est)
+    torch.cuda.synchronize(dev)
+    w_gpu = wave[s_chk].cpu().numpy()
+    r_in = rx_in[s_chk].cpu().numpy().astype(np.complex128)
+    e_ref = fo.rx_frame(geom, r_in)
+    e_gpu = est[s_chk].cpu().numpy()
+    tx_err = float(np.linalg.norm(w_gpu - w_ref) / np.linalg.norm(w_ref))
+    rx_err = float(np.linalg.norm(e_gpu - e_ref) / np.linalg.norm(e_ref))
+    evm_db = float(10 * np.log10(np.sum(np.abs(e_gpu - gref) ** 2) / np.sum(np.abs(gref) ** 2)))
+
+    # ---- roofline of the dominant kernel --------------------------------------
+    peaks, peak_kind = load_peaks()
+    flops_frame = transform_flops(geom)
+    dom = "k_tx_sync" if tx_ms >= rx_ms else "k_rx_sync"
+    dom_ms = max(tx_ms, rx_ms)
+    achieved_tflops = flops_frame * S / (dom_ms * 1e-3) / 1e12
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = fp32_alu_peak_tflops(sm_mhz)
+    bytes_frame = 8 * (nominal + plan.grid_len)
+    hbm_gbs = bytes_frame * S / (dom_ms * 1e-3) / 1e9
+    traffic = traffic_from_profile(dom)
+    roofline = {"bound": "alu", "kernel": dom, "achieved": round(achieved_tflops, 3),
+                "peak": round(alu_peak, 2), "unit": "TFLOP/s", "frac": round(achieved_tflops / alu_peak, 4),
+                "traffic": traffic,
+                "flops_per_launch": flops_frame * S,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (sm_max_mhz of {peak_kind} peaks)",
+                "hbm_context": {"achieved_gbs": round(hbm_gbs, 1), "peak_gbs": peaks.get("hbm_gbs"),
+                                "frac": round(hbm_gbs / float(peaks.get("hbm_gbs", 6800.0)), 4),
+                                "algorithmic_bytes_per_launch": bytes_frame * S, "peak_kind": peak_kind},
+                "tx_ms": round(tx_ms, 4), "rx_ms": round(rx_ms, 4)}
+
+    # ---- CPU baseline (oracle on the host cores, bounded sample) ---------------
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        pool = oracle_pool(cores)
+        try:
+            v, wall, frames = oracle_throughput(pool, 2, cores)
+        finally:
+            pool.close()
+        cpu = {"value": round(v, 4), "unit": "Msamples/s", "cores": cores, "kind": "oracle",
+               "sample": f"{frames} subframes (1 per core), TX+RX, {wall:.1f} s wall"}
+
+    out = {"metric": METRIC, "value": round(value, 2), "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "streams_per_gpu": S, "nominal_samples_per_stream": nominal,
+                      "wave_len": plan.wave_len, "grid_len": plan.grid_len, "parallelism": f"replicas x{world}",
+                      "l2": "inputs larger than L2 (grid %.0f MB, waveforms 2 x %.0f MB per GPU)"
+                            % (grid.numel() * 8 / 1e6, wave.numel() * 8 / 1e6)},
+           "roofline": roofline, "cpu_baseline": cpu,
+           "e2e": {"value": round(e2e_value, 2), "unit": "Msamples/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h},
+           "latency_1stream_ms": {"p50": round(lat[len(lat) // 2], 4), "p99": round(lat[int(0.99 * len(lat))], 4),
+                                  "slot_budget_ms": 1.0},
+           "accuracy": {"tx_rel_rms_vs_oracle": tx_err, "rx_rel_rms_vs_oracle": rx_err, "evm_db_awgn30": evm_db},
+           "clocks": clk, "gpu_launches": args.steps * (plan.tx_kernels + plan.rx_kernels)}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--streams", type=int, default=2048)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

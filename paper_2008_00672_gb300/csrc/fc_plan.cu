@@ -33,8 +33,8 @@ struct Blob {
   std::vector<unsigned char> bytes;
   size_t add(const void* p, size_t n, size_t align = 16) {
     size_t off = (bytes.size() + align - 1) / align * align;
-    bytes.resize(off + n);
-    if (n) std::memcpy(bytes.data() + off, p, n);
+    bytes.resize(off + n, 0);
+    if (n && p) std::memcpy(bytes.data() + off, p, n);
     return off;
   }
   template <class T>
@@ -82,6 +82,7 @@ struct GroupHost {
 struct fc_plan {
   int device = 0;
   int num_sms = 0;
+  size_t smem_cap = kSmemPerBlockMax - sizeof(FcPlanDev) - 256;   // dynamic shared memory per CTA
   FcPlanDev h{};
   FcPlanDev* d_plan = nullptr;
   unsigned char* d_mem = nullptr;
@@ -373,7 +374,7 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   pl->smem_tx = (size_t)(ring + ybuf + wbuf) * sizeof(float2);
   pl->smem_rx = (size_t)(ybuf + wbuf) * sizeof(float2);
   pl->smem_ofdm = (size_t)lo_max * sizeof(float2);
-  const size_t smem_cap = kSmemPerBlockMax - sizeof(FcPlanDev) - 256;
+  const size_t smem_cap = pl->smem_cap;
   if (pl->smem_tx > smem_cap || pl->smem_rx > smem_cap)
     return fail(FC_ERR_UNSUPPORTED, "geometry needs more shared memory than one SM has");
 
@@ -415,15 +416,17 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   z.workspace_per_stream = ws_len * (long long)sizeof(float2);
   z.tx_kernels = sync ? 1 : 2;
   z.rx_kernels = sync ? 1 : 2;
-  if (!upload) return FC_OK;
-
   // ---- device upload ---------------------------------------------------------
   const size_t off_plan = blob.add(nullptr, sizeof(FcPlanDev));
-  cudaError_t e = cudaMalloc(&pl->d_mem, blob.bytes.size());
-  if (e != cudaSuccess) {
-    pl->d_mem = nullptr;
-    return e == cudaErrorMemoryAllocation ? fail(FC_ERR_NOMEM, "cudaMalloc of plan tables failed")
-                                          : cuda_fail(e, "cudaMalloc");
+  // Without upload (host-only check) every table pointer is laid out against a
+  // null base, so the whole host path runs and only the two CUDA calls are skipped.
+  if (upload) {
+    cudaError_t e = cudaMalloc(&pl->d_mem, blob.bytes.size());
+    if (e != cudaSuccess) {
+      pl->d_mem = nullptr;
+      return e == cudaErrorMemoryAllocation ? fail(FC_ERR_NOMEM, "cudaMalloc of plan tables failed")
+                                            : cuda_fail(e, "cudaMalloc");
+    }
   }
   unsigned char* base = pl->d_mem;
   FcPlanDev& P = pl->h;
@@ -479,8 +482,10 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     d.soff = reinterpret_cast<const int*>(base + off_soff[m]);
   }
   std::memcpy(blob.bytes.data() + off_plan, &P, sizeof(P));
-  e = cudaMemcpy(base, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy of plan tables");
+  if (upload) {
+    cudaError_t e = cudaMemcpy(base, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy of plan tables");
+  }
 
   pl->d_plan = reinterpret_cast<FcPlanDev*>(base + off_plan);
   pl->d_jobs = reinterpret_cast<FcJob*>(base + off_jobs);
@@ -553,8 +558,16 @@ int fc_plan_create(fc_plan** out, const fc_geometry* geometry, int32_t device) {
     delete pl;
     return cuda_fail(e, "cudaDeviceGetAttribute");
   }
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (e != cudaSuccess) {
+    delete pl;
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  const size_t reserve = sizeof(FcPlanDev) + 256;   // static shared memory of the kernels
+  pl->smem_cap = (size_t)optin > reserve ? (size_t)optin - reserve : 0;
   cudaError_t se = cudaSuccess;
-  std::call_once(g_smem_once[device], [&] { se = fc_set_smem_limits(kSmemPerBlockMax - sizeof(FcPlanDev) - 256); });
+  std::call_once(g_smem_once[device], [&] { se = fc_set_smem_limits(pl->smem_cap); });
   if (se != cudaSuccess) {
     delete pl;
     return cuda_fail(se, "cudaFuncSetAttribute");
