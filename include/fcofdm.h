@@ -86,7 +86,12 @@ typedef struct fc_geometry {
   const fc_group* groups;
   int32_t n_subbands;      /* 1..FC_MAX_SUBBANDS                                       */
   const fc_subband* subbands;
+  int32_t flags;           /* 0, or FC_FLAG_GENERIC_KERNELS                            */
 } fc_geometry;
+
+/* Use the generic shared-memory kernels even where a specialised kernel exists
+   (both compute the same result; this exists to test one against the other). */
+#define FC_FLAG_GENERIC_KERNELS 1
 
 #define FC_MAX_GROUPS 4
 #define FC_MAX_SUBBANDS 16

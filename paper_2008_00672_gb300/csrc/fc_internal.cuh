@@ -9,6 +9,7 @@
 #include "../../include/fcofdm.h"
 
 #define FC_THREADS 512
+#define FC_WARP_THREADS 128      // warp-specialised kernels: 4 warps, one symbol job per warp
 #define FC_MAX_SIZES 12       // distinct transform sizes in one plan
 #define FC_MAX_PASSES 8
 #define FC_MAX_ELEMS_PER_THREAD 16   // in-place FFT: batch*n <= FC_THREADS*16
@@ -90,3 +91,10 @@ cudaError_t fc_launch_ofdm_demod(const FcPlanDev* dP, int syms_per_stream, int n
                                  float2* grid, size_t smem, cudaStream_t st);
 // raise the dynamic shared-memory limit of every kernel on the current device
 cudaError_t fc_set_smem_limits(size_t max_dynamic_smem);
+
+// warp-specialised symbol-synchronized kernels (fc_warp.cu); jobs are grouped per chunk
+cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+                                   int n_streams, int frame_len, const float2* grid, float2* wave, cudaStream_t st);
+cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+                                   int n_streams, const float2* wave, float2* grid, cudaStream_t st);
+cudaError_t fc_set_warp_smem_limits();

@@ -91,6 +91,10 @@ struct fc_plan {
   std::vector<int> splits;                  // chunk counts per stream available
   std::vector<const FcChunk*> tx_chunks, rx_chunks;
   std::vector<int> tx_nchunks, rx_nchunks;
+  bool warp_path = false;                   // warp-specialised symbol-sync kernels apply
+  FcJob* d_wjobs = nullptr;                 // jobs regrouped per chunk for the warp kernels
+  std::vector<const FcChunk*> w_chunks;
+  std::vector<int> w_nchunks;
   size_t smem_tx = 0, smem_rx = 0, smem_ofdm = 0;
   int syms_per_stream = 0;
   fc_sizes sizes{};
@@ -354,6 +358,34 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     nrx.push_back((int)rx.size());
   }
 
+  // warp-specialised path: symbol-sync, one subband per group, I = 2, L in {512, 1024}
+  bool warp_ok = sync && !(geo->flags & FC_FLAG_GENERIC_KERNELS) && (frame_len % 2 == 0);
+  for (int g = 0; g < G && warp_ok; ++g) {
+    if (gh[g].subs.size() != 1) { warp_ok = false; break; }
+    const SubHost& o = sh[gh[g].subs[0]];
+    const bool shape = (o.L == 1024 && gh[g].N == 2048) || (o.L == 512 && gh[g].N == 1024);
+    if (!shape) warp_ok = false;
+  }
+  std::vector<size_t> off_wjobs_k, off_wch;
+  size_t off_wjobs = 0;
+  if (warp_ok) {
+    // most expensive jobs first (N = 2048 before N = 1024), dealt round-robin to the chunks
+    std::vector<FcJob> by_cost = jobs;
+    std::stable_sort(by_cost.begin(), by_cost.end(),
+                     [&](const FcJob& a, const FcJob& b) { return gh[a.group].N > gh[b.group].N; });
+    std::vector<FcJob> wj;
+    for (int K : splits) {
+      std::vector<FcChunk> ch;
+      for (int c = 0; c < K; ++c) {
+        const int j0 = (int)wj.size();
+        for (int j = c; j < n_jobs; j += K) wj.push_back(by_cost[j]);
+        ch.push_back(FcChunk{j0, (int)wj.size(), 0, 0});
+      }
+      off_wch.push_back(blob.add_vec(ch));
+    }
+    off_wjobs = blob.add_vec(wj);
+  }
+
   // ---- buffers and shared memory -------------------------------------------
   int n_max = 0, l_max = 0, lo_max = 0;
   for (auto& o : gh) n_max = std::max(n_max, o.N);
@@ -497,6 +529,14 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   }
   pl->tx_nchunks = ntx;
   pl->rx_nchunks = nrx;
+  pl->warp_path = warp_ok;
+  if (warp_ok) {
+    pl->d_wjobs = reinterpret_cast<FcJob*>(base + off_wjobs);
+    for (size_t i = 0; i < splits.size(); ++i) {
+      pl->w_chunks.push_back(reinterpret_cast<const FcChunk*>(base + off_wch[i]));
+      pl->w_nchunks.push_back(splits[i]);
+    }
+  }
   return FC_OK;
 }
 
@@ -567,7 +607,10 @@ int fc_plan_create(fc_plan** out, const fc_geometry* geometry, int32_t device) {
   const size_t reserve = sizeof(FcPlanDev) + 256;   // static shared memory of the kernels
   pl->smem_cap = (size_t)optin > reserve ? (size_t)optin - reserve : 0;
   cudaError_t se = cudaSuccess;
-  std::call_once(g_smem_once[device], [&] { se = fc_set_smem_limits(pl->smem_cap); });
+  std::call_once(g_smem_once[device], [&] {
+    se = fc_set_smem_limits(pl->smem_cap);
+    if (se == cudaSuccess) se = fc_set_warp_smem_limits();
+  });
   if (se != cudaSuccess) {
     delete pl;
     return cuda_fail(se, "cudaFuncSetAttribute");
@@ -606,7 +649,10 @@ int fc_tx_synthesize(const fc_plan* plan, int32_t n_streams, const void* grid_in
   const float2* grid = (const float2*)grid_in;
   float2* wave = (float2*)wave_out;
   cudaError_t e;
-  if (plan->h.mode == FC_SYMBOL_SYNC) {
+  if (plan->warp_path && ((uintptr_t)wave_out & 15) == 0) {   // float4 reductions need 16-byte alignment
+    e = fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams,
+                               plan->h.frame_len, grid, wave, st);
+  } else if (plan->h.mode == FC_SYMBOL_SYNC) {
     e = fc_launch_tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, grid, wave,
                           plan->smem_tx, st);
   } else {
@@ -630,7 +676,10 @@ int fc_rx_analyze(const fc_plan* plan, int32_t n_streams, const void* wave_in, v
   const float2* wave = (const float2*)wave_in;
   float2* grid = (float2*)grid_out;
   cudaError_t e;
-  if (plan->h.mode == FC_SYMBOL_SYNC) {
+  if (plan->warp_path) {
+    e = fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams, wave,
+                               grid, st);
+  } else if (plan->h.mode == FC_SYMBOL_SYNC) {
     e = fc_launch_rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, wave, grid,
                           plan->smem_rx, st);
   } else {

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfcofdm.so")
 
 FC_OK, FC_ERR_INVALID, FC_ERR_UNSUPPORTED, FC_ERR_NOMEM, FC_ERR_CUDA, FC_ERR_TIMEOUT = range(6)
 FC_CONTINUOUS, FC_SYMBOL_SYNC = 0, 1
+FC_FLAG_GENERIC_KERNELS = 1
 FC_OLA, FC_OLS = 0, 1
 
 EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize", "fc_rx_analyze", "fc_plan_destroy",
@@ -40,7 +41,8 @@ class FcSubband(ctypes.Structure):
 class FcGeometry(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("scheme_tx", ctypes.c_int32), ("scheme_rx", ctypes.c_int32),
                 ("n_groups", ctypes.c_int32), ("groups", ctypes.POINTER(FcGroup)),
-                ("n_subbands", ctypes.c_int32), ("subbands", ctypes.POINTER(FcSubband))]
+                ("n_subbands", ctypes.c_int32), ("subbands", ctypes.POINTER(FcSubband)),
+                ("flags", ctypes.c_int32)]
 
 
 class FcSizes(ctypes.Structure):
@@ -111,7 +113,7 @@ def _marshal_geometry(geom):
         keep.append(w)
         subs[i] = FcSubband(int(s.l_short), int(s.l_ofdm), int(s.n_active), int(s.centre_bin), int(s.group), w)
     geo = FcGeometry(int(geom.mode), int(geom.scheme_tx), int(geom.scheme_rx), len(geom.groups), groups,
-                     len(geom.subbands), subs)
+                     len(geom.subbands), subs, int(getattr(geom, "flags", 0)))
     return geo, (groups, subs, keep)
 
 

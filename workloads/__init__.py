@@ -62,6 +62,7 @@ class Geometry:
     subbands: tuple
     name: str = ""
     qam_order: int = 4
+    flags: int = 0               # ABI flags (e.g. force the generic kernels); no effect on the result
 
     def grid_len(self) -> int:
         """Complex QAM symbols per stream (sum over subbands of B_g * L_act,m)."""
