@@ -440,13 +440,14 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
   load_plan_w(P, gP);
   const int stream = blockIdx.x / n_chunks;
   const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
+  if (threadIdx.x == 0) next_job = ch.j0;
+  __syncthreads();                                  // the plan copy is complete before any use
   const float2* gsrc = grid + (size_t)stream * P.grid_len;
   float2* wdst = wave + (size_t)stream * P.frame_len;
   if (zero_output) {   // the CTA owns the whole stream: clear it before the reductions
     for (int i = threadIdx.x; i < P.frame_len; i += blockDim.x) wdst[i] = czero();
+    __syncthreads();
   }
-  if (threadIdx.x == 0) next_job = ch.j0;
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   float2* scr = wscr + (threadIdx.x >> 5) * kScratch;
   float2* map = scr + kTrans;
@@ -472,10 +473,10 @@ k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
   load_plan_w(P, gP);
   const int stream = blockIdx.x / n_chunks;
   const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
+  if (threadIdx.x == 0) next_job = ch.j0;
+  __syncthreads();                                  // the plan copy is complete before any use
   const float2* src = wave + (size_t)stream * P.frame_len;
   float2* gdst = grid + (size_t)stream * P.grid_len;
-  if (threadIdx.x == 0) next_job = ch.j0;
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   float2* scr = wscr + (threadIdx.x >> 5) * kScratch;
   float2* map = scr + kTrans;
