@@ -155,6 +155,29 @@ int fc_tx_synthesize(const fc_plan* plan, int32_t n_streams, const void* grid_in
 int fc_rx_analyze(const fc_plan* plan, int32_t n_streams, const void* wave_in, void* grid_out,
                   void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * Allocation-free TX (no counterpart in the paper; it is a deployment option).
+ * Same computation and buffer rules as fc_tx_synthesize, but the workspace is a
+ * device array built into the library (FC_STATIC_WORKSPACE_BYTES per GPU, held
+ * from library load until process exit) instead of a caller buffer, for callers
+ * that cannot allocate device memory at run time (fixed-budget real-time loops,
+ * hosts whose allocator belongs to another framework). The call never calls
+ * cudaMalloc/cudaFree or any allocating routine.
+ *  - Returns FC_ERR_INVALID (see fc_last_error) if n_streams * workspace_per_stream
+ *    exceeds FC_STATIC_WORKSPACE_BYTES; plans with no workspace need (symbol-sync
+ *    mode) are not limited.
+ *  - The first call on a device looks up the array's device address once (with
+ *    the plan's device made current for that lookup); make that first call
+ *    before capturing the stream into a CUDA graph.
+ *  - All calls on one device share the one array: calls that overlap on the GPU
+ *    (different CUDA streams, or several host threads) race and corrupt each
+ *    other's output. Serialise them. Nothing in the array needs clearing between
+ *    calls; each call writes every element it reads.
+ */
+#define FC_STATIC_WORKSPACE_BYTES (32u << 20)
+int fc_tx_synthesize_static(const fc_plan* plan, int32_t n_streams, const void* grid_in, void* wave_out,
+                            void* stream);
+
 /* Frees the plan's device tables. Safe on NULL. Must not race with running calls. */
 void fc_plan_destroy(fc_plan* plan);
 

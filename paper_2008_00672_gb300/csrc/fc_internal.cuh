@@ -98,3 +98,7 @@ cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, const
 cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
                                    int n_streams, const float2* wave, float2* grid, cudaStream_t st);
 cudaError_t fc_set_warp_smem_limits();
+
+// helpers for entry points defined outside fc_plan.cu
+int fc_internal_fail(int code, const char* msg);     // records fc_last_error() and returns code
+int fc_internal_plan_device(const fc_plan* plan);    // the device a plan was created on

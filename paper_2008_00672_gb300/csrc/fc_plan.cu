@@ -580,6 +580,10 @@ int check_io(const fc_plan* plan, int32_t n_streams, const void* in, const void*
 
 }  // namespace
 
+int fc_internal_fail(int code, const char* msg) { return fail(code, msg); }
+
+int fc_internal_plan_device(const fc_plan* plan) { return plan ? plan->device : -1; }
+
 extern "C" {
 
 int fc_plan_create(fc_plan** out, const fc_geometry* geometry, int32_t device) {

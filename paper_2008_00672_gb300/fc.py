@@ -24,7 +24,7 @@ FC_FLAG_GENERIC_KERNELS = 1
 FC_OLA, FC_OLS = 0, 1
 
 EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize", "fc_rx_analyze", "fc_plan_destroy",
-            "fc_status_string", "fc_last_error")
+            "fc_status_string", "fc_last_error", "fc_tx_synthesize_static")
 
 
 class FcGroup(ctypes.Structure):
@@ -76,6 +76,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fc_tx_synthesize.restype = ctypes.c_int
         lib.fc_rx_analyze.argtypes = [vp, i32, vp, vp, vp, sz, vp]
         lib.fc_rx_analyze.restype = ctypes.c_int
+        lib.fc_tx_synthesize_static.argtypes = [vp, i32, vp, vp, vp]
+        lib.fc_tx_synthesize_static.restype = ctypes.c_int
         lib.fc_plan_destroy.argtypes = [vp]
         lib.fc_plan_destroy.restype = None
         lib.fc_status_string.argtypes = [ctypes.c_int]
@@ -154,6 +156,13 @@ def fc_rx_analyze(plan, n_streams: int, wave_in: int, grid_out: int, workspace: 
                   workspace_bytes: int = 0, stream: int = 0):
     _check(load_library().fc_rx_analyze(plan, int(n_streams), wave_in, grid_out, workspace or None,
                                         int(workspace_bytes), stream or None), "fc_rx_analyze")
+
+
+def fc_tx_synthesize_static(plan, n_streams: int, grid_in: int, wave_out: int, stream: int = 0):
+    """TX with the library's built-in device workspace instead of a caller buffer
+    (for callers that cannot allocate device memory at run time)."""
+    _check(load_library().fc_tx_synthesize_static(plan, int(n_streams), grid_in, wave_out, stream or None),
+           "fc_tx_synthesize_static")
 
 
 def fc_plan_destroy(plan):
