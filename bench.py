@@ -83,6 +83,27 @@ def traffic_from_profile(kernel: str):
     return e.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(ms: float, device=None) -> float:
+    """Slowest rank's time (all ranks run the same step count; value is whole-job)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(ms)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_msps(samples_per_rank_step: int, world: int, steps: int, ms: float) -> float:
+    """Replicas: every rank processes its own streams, so the job's samples are world x per-rank."""
+    return samples_per_rank_step * world * steps / (ms * 1e-3) / 1e6
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Each replica draws its own streams."""
+    return base + 100000 * rank
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -223,7 +244,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     geom = wl.config_mixed_20mhz()
     plan = Plan(geom, device=local_rank)
     S = args.streams
-    seed = wl.default_seed(2) + 100000 * rank
+    seed = rank_seed(wl.default_seed(2), rank)
 
     # inputs: seeded QAM grid; RX input = TX output + 30 dB AWGN (made once, on the device)
     grid_np = wl.qam_grid(geom, min(S, 64), seed).astype(np.complex64)
@@ -278,14 +299,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     ms_total = t_start.elapsed_time(t_end)
     tx_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     rx_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
-    if world > 1:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dev)
 
     nominal = plan.nominal_len
     samples_step = 2 * nominal * S * world
-    value = samples_step * args.steps / (ms_total * 1e-3) / 1e6
+    value = whole_job_msps(2 * nominal * S, world, args.steps, ms_total)
 
     # ---- end to end through the public API: pinned host in, host out ----------
     h_grid = grid.cpu().pin_memory()
@@ -315,11 +333,8 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     e1.record(st)
     torch.cuda.synchronize(dev)
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = samples_step * e2e_steps / (e2e_ms * 1e-3) / 1e6
+    e2e_ms = max_over_ranks(e2e_ms, dev)
+    e2e_value = whole_job_msps(2 * nominal * S, world, e2e_steps, e2e_ms)
     h2d = (grid.numel() + rx_in.numel()) * 8
     d2h = (wave.numel() + est.numel()) * 8
 

@@ -10,6 +10,12 @@
 
 #define FC_THREADS 512
 #define FC_WARP_THREADS 128      // warp-specialised kernels: 4 warps, one symbol job per warp
+#ifndef FC_WARP_TX_MIN_BLOCKS
+#define FC_WARP_TX_MIN_BLOCKS 2  // resident CTAs per SM the warp TX kernel is compiled for
+#endif
+#ifndef FC_WARP_RX_MIN_BLOCKS
+#define FC_WARP_RX_MIN_BLOCKS 3  // resident CTAs per SM the warp RX kernel is compiled for
+#endif
 #define FC_MAX_SIZES 12       // distinct transform sizes in one plan
 #define FC_MAX_PASSES 8
 #define FC_MAX_ELEMS_PER_THREAD 16   // in-place FFT: batch*n <= FC_THREADS*16

@@ -3,18 +3,21 @@
 //
 // One warp processes one symbol job (Sec. III-C for TX, Sec. IV for RX) end to
 // end with no CTA-wide barrier:
-//   * 1024-point transforms are four-step 32 x 32 FFTs held in registers
-//     (32 values per lane) with one shared-memory transpose; two 512-point
-//     transforms run together as 16 x 32 four-step FFTs;
+//   * transforms are four-step FFTs held in registers (32 values per lane): one
+//     1024-point transform (32 x 32) or two 512-point transforms (16 x 32), with
+//     one shared-memory transpose each;
 //   * the long N = 2048 transform is split by one radix-2 step into two
-//     1024-point transforms (even and odd output samples for the TX IDFT,
-//     even and odd bins for the RX DFT);
+//     1024-point transforms (even and odd output samples for the TX IDFT, even
+//     and odd bins for the RX DFT);
 //   * the segmentation of the zero-padded symbol into the two FC blocks
 //     (eq:padding, R_L^{(r)}) is a register renaming, because L/4 and L/2 are
 //     multiples of the 32-sample stride of the register layout;
 //   * TX overlap-add (blocks of a symbol, neighbouring symbols, numerology
 //     groups; eq:multi-symb) is done with vector reductions into the zeroed
 //     output waveform, so warps never wait for each other.
+// Every job is a short program of stages "prepare -> forward FFT -> consume";
+// inverse transforms are conj(FFT(conj(x))). The whole kernel therefore holds a
+// single copy of the unrolled FFT, which keeps the hot code in the instruction cache.
 #include "fc_device.cuh"
 #include "fc_internal.cuh"
 
@@ -40,10 +43,285 @@ __device__ __forceinline__ float2 root_pos(const float2* __restrict__ tw, int n,
   return make_float2(w.x, -w.y);
 }
 
-// v[k] *= W_n^{+-lane k} for k = 1..K-1, with W^{lane k} = W^{4 m lane} W^{j lane} (k = 4 m + j):
-// K/4 + 3 table loads and one complex multiply per twiddle (one rounding away from the table).
+// Compiler-only fence: keeps the scheduler from hoisting every load of a stage
+// ahead of its first use (which would need twice the registers of the data).
+__device__ __forceinline__ void sched_fence() { asm volatile("" ::: "memory"); }
+
+// v[k] *= W^{lane e(k)} for k = 1..31 with e(k) = 4 (m & mmask) + j, k = 4 m + j.
+// One 1024-point transform: tw = W_1024 table, mmask = 7 (e = k). Two 512-point
+// transforms: tw = W_512 table, mmask = 3 (e = k mod 16, the same twiddles for both).
+// W^{lane e} = W^{4 (m & mmask) lane} W^{j lane}: 11 table loads and one complex
+// multiply per twiddle (one rounding away from the FP64-generated table; the
+// table's entry 0 is exactly 1).
+__device__ __forceinline__ void step_twiddles(float2 (&v)[32], const float2* __restrict__ tw, int lane, int mmask) {
+  float2 tj[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) tj[j] = __ldg(tw + lane * j);
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    sched_fence();
+    const float2 tm = __ldg(tw + lane * 4 * (m & mmask));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * m + j;
+      if (k == 0) continue;
+      v[k] = cmul(v[k], j ? cmul(tm, tj[j]) : tm);
+    }
+  }
+}
+
+// Forward four-step FFT of one warp.
+//  two512 = false: one 1024-point transform; in: lane b holds x[32 a + b] in v[a];
+//                  out: lane k1 holds X[k1 + 32 k2] in v[k2].
+//  two512 = true:  two 512-point transforms; in: lane b holds x_T[32 a + b] in
+//                  v[16 T + a] (a < 16); out: lane k1 + 16 T holds X_T[k1 + 16 k2] in v[k2].
+__device__ __forceinline__ void warp_fft(float2 (&v)[32], float2* scr, const float2* __restrict__ tw1024,
+                                         const float2* __restrict__ tw512, int lane, bool two512) {
+  if (!two512) {
+    Dft<32, false>::run(v);
+  } else {
+    Dft<16, false>::run(v);
+    Dft<16, false>::run(v + 16);
+  }
+  step_twiddles(v, two512 ? tw512 : tw1024, lane, two512 ? 3 : 7);
+#pragma unroll
+  for (int k = 0; k < 32; ++k) scr[k * kPad + lane] = v[k];
+  __syncwarp();
+#pragma unroll
+  for (int b = 0; b < 32; ++b) v[b] = scr[lane * kPad + b];
+  __syncwarp();
+  Dft<32, false>::run(v);
+}
+
+__device__ __forceinline__ void conj32(float2 (&v)[32]) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k].y = -v[k].y;
+}
+
+__device__ __forceinline__ float weight(const FcSubDev& S, const float* __restrict__ d, int p) {
+  return (p >= S.p_lo && p < S.p_hi) ? __ldg(d + p) : 0.f;
+}
+
+// signed short-transform frequency of natural bin k (even L)
+__device__ __forceinline__ int signed_bin(int k, int L) { return k < L / 2 ? k : k - L; }
+
+// Twiddle tables of a job: 1024-point, and 512-point (L = 512) or 2048-point (N = 2048).
+struct JobTables {
+  const float2* t1024;
+  const float2* t512;
+  const float2* t2048;
+};
+
+__device__ __forceinline__ JobTables job_tables(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S) {
+  JobTables t;
+  if (S.L == 1024) {
+    t.t1024 = P.sz[S.size_L].tw;
+    t.t2048 = P.sz[G.size_N].tw;
+    t.t512 = nullptr;
+  } else {
+    t.t512 = P.sz[S.size_L].tw;
+    t.t1024 = P.sz[G.size_N].tw;
+    t.t2048 = nullptr;
+  }
+  return t;
+}
+
+// ---------------------------------------------------------------------------
+// TX job. L = 1024 (N = 2048), stages:
+//   0   OFDM IDFT of the grid row -> body (kept in registers)
+//   1/4 block r = 0/1: segment + window from the body, short DFT, map into the folded spectrum
+//   2/5 even output samples of block r (IDFT of the folded spectrum), kept in registers
+//   3/6 odd output samples (IDFT of the spectrum times exp(+j 2 pi q / 2048)); both
+//       parities reduced into the waveform as float4
+// L = 512 (N = 1024), stages:
+//   0   OFDM IDFT -> body to the map buffer
+//   1   both blocks segmented from the body, two 512-point DFTs (kept in registers)
+//   2/3 block r = 0/1: map into the 1024-bin spectrum, IDFT, reduce into the waveform
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
+                                       const float2* __restrict__ gsrc, float2* __restrict__ wdst, float2* scr,
+                                       float2* map, int lane) {
+  const bool big = S.L == 1024;
+  const JobTables tb = job_tables(P, G, S);
+  const int n = jb.index;
+  const int hl = S.Lact / 2, hu = S.Lact - hl;
+  const float2* __restrict__ row = gsrc + S.grid_off + (long long)n * S.Lact;
+  const int lcp = S.lcp[n], ncp = G.ncp[n];
+  const bool ols = P.scheme_tx == FC_OLS;
+  const bool v4 = ((jb.start & 1) == 0);
+  const float2* __restrict__ twN = big ? tb.t2048 : tb.t1024;
+  const int nN = big ? 2048 : 1024;
+  const float2 ph0 = root_pos(twN, nN, (long long)S.c * G.cps[n]);                  // phi_0 theta_n
+  const float2 ph1 = root_pos(twN, nN, (long long)S.c * (G.cps[n] + G.N_S));       // phi_1 theta_n
+  const int nst = big ? 7 : 4;
+  float2 v[32], keep[32];
+#pragma unroll 1
+  for (int st = 0; st < nst; ++st) {
+    // ---------------- prepare ----------------
+    bool inv, two512;
+    if (big) {
+      two512 = false;
+      if (st == 0) {                                    // T1: active bins of the row
+#pragma unroll
+        for (int a = 0; a < 32; ++a) {
+          const int f = signed_bin(32 * a + lane, 1024);
+          v[a] = (f >= -hl && f < hu) ? __ldg(row + f + hl) : czero();
+        }
+        inv = true;
+      } else if (st == 1 || st == 4) {                  // T2-T3: block r from the body
+        const bool r1 = st == 4;
+#pragma unroll
+        for (int a = 0; a < 32; ++a) {
+          const int t = 32 * a + lane;
+          bool k;
+          if (!ols) k = r1 ? (t >= 256 && t < 768) : (t >= 256 - lcp && t < 768);
+          else k = r1 ? (t < 768) : (t >= 256 - lcp);
+          const float2 b = r1 ? keep[(a + 8) & 31] : keep[(a + 24) & 31];
+          v[a] = k ? b : czero();
+        }
+        inv = false;
+      } else if (st == 2 || st == 5) {                  // T6: even samples from the folded spectrum;
+#pragma unroll                                          //     the odd-sample input replaces it in place
+        for (int a = 0; a < 32; ++a) {
+          const int qp = 32 * a + lane;
+          const float2 y = map[qp];
+          int kt = (qp - S.c) & 1023;
+          if (kt >= 512) kt -= 1024;
+          v[a] = y;
+          map[qp] = cmulc(y, __ldg(tb.t2048 + ((S.c + kt) & 2047)));   // y exp(+j 2 pi q / 2048)
+        }
+        inv = true;
+      } else {                                          // T6: odd samples; the even outputs move from
+#pragma unroll                                          //     the transpose buffer into their map slots
+        for (int a = 0; a < 32; ++a) {
+          const int qp = 32 * a + lane;
+          const float2 t = map[qp];
+          map[qp] = scr[a * kPad + lane];
+          v[a] = t;
+        }
+        inv = true;
+      }
+    } else {
+      if (st == 0) {
+#pragma unroll
+        for (int a = 0; a < 16; ++a) {
+          const int f = signed_bin(32 * a + lane, 512);
+          v[a] = (f >= -hl && f < hu) ? __ldg(row + f + hl) : czero();
+          v[16 + a] = czero();
+        }
+        inv = true;
+        two512 = true;
+      } else if (st == 1) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+#pragma unroll
+          for (int a = 0; a < 16; ++a) {
+            const int t = 32 * a + lane;
+            bool k;
+            if (!ols) k = (r == 0) ? (t >= 128 - lcp && t < 384) : (t >= 128 && t < 384);
+            else k = (r == 0) ? (t >= 128 - lcp) : (t < 384);
+            v[16 * r + a] = k ? map[(t - 128 + 256 * r) & 511] : czero();
+          }
+        }
+        __syncwarp();
+        inv = false;
+        two512 = true;
+      } else {                                          // block r = st - 2 into the 1024-bin spectrum
+        const int r = st - 2;
+#pragma unroll
+        for (int a = 0; a < 32; ++a) map[32 * a + lane] = czero();
+        __syncwarp();
+        if ((lane >> 4) == r) {
+          const float2 ph = r ? ph1 : ph0;
+#pragma unroll
+          for (int k2 = 0; k2 < 32; ++k2) {
+            const int kt = signed_bin((lane & 15) + 16 * k2, 512);
+            map[(S.c + kt) & 1023] = cscale(cmul(keep[k2], ph), weight(S, S.dtx, kt + 256));
+            if ((k2 & 7) == 7) sched_fence();
+          }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int a = 0; a < 32; ++a) v[a] = map[32 * a + lane];
+        __syncwarp();
+        inv = true;
+        two512 = false;
+      }
+    }
+    // ---------------- transform ----------------
+    if (inv) conj32(v);
+    warp_fft(v, scr, tb.t1024, tb.t512, lane, two512);
+    if (inv) conj32(v);
+    // ---------------- consume ----------------
+    if (big) {
+      if (st == 0) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) keep[k] = v[k];   // body[k1 + 32 k2]
+      } else if (st == 1 || st == 4) {                  // T5: shift, D_m, bin map with phi_r theta_n
+        const float2 ph = (st == 4) ? ph1 : ph0;
+#pragma unroll
+        for (int k2 = 0; k2 < 32; ++k2) {
+          const int kt = signed_bin(lane + 32 * k2, 1024);
+          map[(S.c + kt) & 1023] = cscale(cmul(v[k2], ph), weight(S, S.dtx, kt + 512));
+          if ((k2 & 7) == 7) sched_fence();
+        }
+        __syncwarp();
+      } else if (st == 2 || st == 5) {                  // park the even outputs in this lane's
+#pragma unroll                                          // column of the transpose buffer
+        for (int k = 0; k < 32; ++k) scr[k * kPad + lane] = v[k];
+      } else {                                          // T7: OLS window, R_N^{(r)}, Gamma_sigma
+        const int r = (st == 6);
+        const int lo = r ? G.N_L : G.N_L - ncp, hi = G.N_L + G.N_S;
+#pragma unroll
+        for (int k2 = 0; k2 < 32; ++k2) {
+          const int tau = 2 * (lane + 32 * k2);
+          float2 a0 = map[32 * k2 + lane], a1 = v[k2];
+          if (ols) {
+            if (!(tau >= lo && tau < hi)) a0 = czero();
+            if (!(tau + 1 >= lo && tau + 1 < hi)) a1 = czero();
+          }
+          float2* dst = wdst + jb.start + r * 1024 + tau;
+          if (v4) {
+            atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a0.x, a0.y, a1.x, a1.y));
+          } else {
+            atomicAdd(dst, a0);
+            atomicAdd(dst + 1, a1);
+          }
+        }
+        __syncwarp();
+      }
+    } else {
+      if (st == 0) {                                    // body[k1 + 16 k2] in lanes 0..15
+        if (lane < 16) {
+#pragma unroll
+          for (int k2 = 0; k2 < 32; ++k2) map[lane + 16 * k2] = v[k2];
+        }
+        __syncwarp();
+      } else if (st == 1) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) keep[k] = v[k];   // U_r[k1 + 16 k2], r = lane >> 4
+      } else {
+        const int r = st - 2;
+        const int lo = r ? G.N_L : G.N_L - ncp, hi = G.N_L + G.N_S;
+#pragma unroll
+        for (int k2 = 0; k2 < 32; ++k2) {
+          const int tau = lane + 32 * k2;
+          float2 a0 = v[k2];
+          if (ols && !(tau >= lo && tau < hi)) a0 = czero();
+          atomicAdd(wdst + jb.start + r * 512 + tau, a0);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// RX jobs: one function per numerology, each with its transforms specialised for
+// their direction (the RX kernel holds few enough job shapes for its instruction
+// working set, and the specialised transforms execute fewer instructions).
+// ---------------------------------------------------------------------------
 template <int K, bool INV>
-__device__ __forceinline__ void step_twiddles(float2* v, const float2* __restrict__ tw, int lane) {
+__device__ __forceinline__ void step_twiddles_k(float2* v, const float2* __restrict__ tw, int lane) {
   float2 tj[4];
   tj[0] = make_float2(1.f, 0.f);
 #pragma unroll
@@ -65,9 +343,9 @@ __device__ __forceinline__ void step_twiddles(float2* v, const float2* __restric
 // Four-step 1024-point FFT. In: lane b holds x[32 a + b] in v[a].
 // Out: lane k1 holds X[k1 + 32 k2] in v[k2]. tw = forward table of size 1024.
 template <bool INV>
-__device__ __forceinline__ void warp_fft1024(float2 (&v)[32], float2* scr, const float2* __restrict__ tw, int lane) {
+__device__ __forceinline__ void warp_fft1024_d(float2 (&v)[32], float2* scr, const float2* __restrict__ tw, int lane) {
   Dft<32, INV>::run(v);
-  step_twiddles<32, INV>(v, tw, lane);
+  step_twiddles_k<32, INV>(v, tw, lane);
 #pragma unroll
   for (int k = 0; k < 32; ++k) scr[k * kPad + lane] = v[k];
   __syncwarp();
@@ -81,14 +359,14 @@ __device__ __forceinline__ void warp_fft1024(float2 (&v)[32], float2* scr, const
 // v[16 T + a], a < 16. Out: lane L = k1 + 16 T holds X_T[k1 + 16 k2] in v[k2].
 // tw = forward table of size 512.
 template <bool INV>
-__device__ __forceinline__ void warp_fft512x2(float2 (&v)[32], float2* scr, const float2* __restrict__ tw, int lane) {
+__device__ __forceinline__ void warp_fft512x2_d(float2 (&v)[32], float2* scr, const float2* __restrict__ tw, int lane) {
   Dft<16, INV>::run(v);
   Dft<16, INV>::run(v + 16);
   {
     float2 t[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) t[k] = make_float2(1.f, 0.f);
-    step_twiddles<16, INV>(t, tw, lane);       // t[k] = W_512^{+-lane k}
+    step_twiddles_k<16, INV>(t, tw, lane);       // t[k] = W_512^{+-lane k}
 #pragma unroll
     for (int k = 1; k < 16; ++k) {
       v[k] = cmul(v[k], t[k]);
@@ -102,171 +380,6 @@ __device__ __forceinline__ void warp_fft512x2(float2 (&v)[32], float2* scr, cons
   for (int b = 0; b < 32; ++b) v[b] = scr[lane * kPad + b];
   __syncwarp();
   Dft<32, INV>::run(v);
-}
-
-__device__ __forceinline__ float weight(const FcSubDev& S, const float* __restrict__ d, int p) {
-  return (p >= S.p_lo && p < S.p_hi) ? __ldg(d + p) : 0.f;
-}
-
-// ---------------------------------------------------------------------------
-// TX, L = 1024, N = 2048
-// ---------------------------------------------------------------------------
-__device__ __noinline__ void tx_job_1024(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
-                                            const float2* __restrict__ gsrc, float2* __restrict__ wdst, float2* scr,
-                                            float2* map, int lane) {
-  constexpr int L = 1024;
-  const float2* __restrict__ twL = P.sz[S.size_L].tw;
-  const float2* __restrict__ twN = P.sz[G.size_N].tw;
-  const int n = jb.index;
-  const int hl = S.Lact / 2, hu = S.Lact - hl;
-  const float2* __restrict__ row = gsrc + S.grid_off + (long long)n * S.Lact;
-  float2 v[32];
-  // T1: active subcarriers into the inverse-transform layout (bin 32 a + lane)
-#pragma unroll
-  for (int a = 0; a < 32; ++a) {
-    const int i = 32 * a + lane;
-    const int f = i < L / 2 ? i : i - L;
-    v[a] = (f >= -hl && f < hu) ? __ldg(row + f + hl) : czero();
-  }
-  warp_fft1024<true>(v, scr, twL, lane);          // body[k1 + 32 k2] in lane k1, v[k2]
-  float2 bd[32];
-#pragma unroll
-  for (int k = 0; k < 32; ++k) bd[k] = v[k];
-  const int lcp = S.lcp[n], ncp = G.ncp[n];
-  const bool ols = P.scheme_tx == FC_OLS;
-  const bool v4 = ((jb.start & 1) == 0);
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    // T2-T3: block r of the padded symbol: position t = 32 a + lane holds body[(t - L/4 + r L/2) mod L]
-#pragma unroll
-    for (int a = 0; a < 32; ++a) {
-      const int t = 32 * a + lane;
-      bool keep;
-      if (!ols) keep = (r == 0) ? (t >= L / 4 - lcp && t < 3 * L / 4) : (t >= L / 4 && t < 3 * L / 4);
-      else keep = (r == 0) ? (t >= L / 4 - lcp) : (t < 3 * L / 4);
-      v[a] = keep ? bd[(a + 24 + 16 * r) & 31] : czero();
-    }
-    // T4: short DFT
-    warp_fft1024<false>(v, scr, twL, lane);       // U[k1 + 32 k2]
-    // T5: shift, D_m, bin map with phi_r theta_n; the 1024-bin band folds one-to-one onto q mod 1024
-    const float2 ph = root_pos(twN, 2048, (long long)S.c * (G.cps[n] + r * G.N_S));
-#pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) {
-      const int k = lane + 32 * k2;
-      const int kt = k < L / 2 ? k : k - L;
-      const float w = weight(S, S.dtx, kt + L / 2);
-      map[(S.c + kt) & 1023] = cscale(cmul(v[k2], ph), w);
-    }
-    __syncwarp();
-    // T6: long IDFT as two 1024-point IDFTs of the folded spectrum (even / odd output samples)
-    float2 u[32], x[32];
-#pragma unroll
-    for (int a = 0; a < 32; ++a) {
-      const int qp = 32 * a + lane;
-      int kt = (qp - S.c) & 1023;
-      if (kt >= 512) kt -= 1024;
-      const float2 y = map[qp];
-      u[a] = y;
-      x[a] = cmulc(y, __ldg(twN + ((S.c + kt) & 2047)));    // y * exp(+j 2 pi q / 2048)
-    }
-    __syncwarp();
-    warp_fft1024<true>(u, scr, twL, lane);        // output sample 2 (k1 + 32 k2)
-    warp_fft1024<true>(x, scr, twL, lane);        // output sample 2 (k1 + 32 k2) + 1
-    // T7: OLS window, R_N^{(r)} and Gamma_sigma placement by reduction into the waveform
-#pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) {
-      const int tau = 2 * (lane + 32 * k2);
-      float2 a0 = u[k2], a1 = x[k2];
-      if (ols) {
-        const int lo = (r == 0) ? G.N_L - ncp : G.N_L, hi = G.N_L + G.N_S;
-        if (!(tau >= lo && tau < hi)) a0 = czero();
-        if (!(tau + 1 >= lo && tau + 1 < hi)) a1 = czero();
-      }
-      float2* dst = wdst + jb.start + r * (2048 / 2) + tau;
-      if (v4) {
-        atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a0.x, a0.y, a1.x, a1.y));
-      } else {
-        atomicAdd(dst, a0);
-        atomicAdd(dst + 1, a1);
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// TX, L = 512, N = 1024
-// ---------------------------------------------------------------------------
-__device__ __noinline__ void tx_job_512(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
-                                           const float2* __restrict__ gsrc, float2* __restrict__ wdst, float2* scr,
-                                           float2* map, int lane) {
-  constexpr int L = 512;
-  const float2* __restrict__ twL = P.sz[S.size_L].tw;
-  const float2* __restrict__ twN = P.sz[G.size_N].tw;
-  const int n = jb.index;
-  const int hl = S.Lact / 2, hu = S.Lact - hl;
-  const float2* __restrict__ row = gsrc + S.grid_off + (long long)n * S.Lact;
-  float2 v[32];
-#pragma unroll
-  for (int a = 0; a < 16; ++a) {
-    const int i = 32 * a + lane;
-    const int f = i < L / 2 ? i : i - L;
-    v[a] = (f >= -hl && f < hu) ? __ldg(row + f + hl) : czero();
-    v[16 + a] = czero();
-  }
-  warp_fft512x2<true>(v, scr, twL, lane);         // lanes 0..15: body[k1 + 16 k2] in v[k2]
-  if (lane < 16) {
-#pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) map[lane + 16 * k2] = v[k2];
-  }
-  __syncwarp();
-  const int lcp = S.lcp[n], ncp = G.ncp[n];
-  const bool ols = P.scheme_tx == FC_OLS;
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-#pragma unroll
-    for (int a = 0; a < 16; ++a) {
-      const int t = 32 * a + lane;
-      bool keep;
-      if (!ols) keep = (r == 0) ? (t >= L / 4 - lcp && t < 3 * L / 4) : (t >= L / 4 && t < 3 * L / 4);
-      else keep = (r == 0) ? (t >= L / 4 - lcp) : (t < 3 * L / 4);
-      v[16 * r + a] = keep ? map[(t - L / 4 + r * (L / 2)) & (L - 1)] : czero();
-    }
-  }
-  __syncwarp();
-  warp_fft512x2<false>(v, scr, twL, lane);        // lane k1 + 16 r: U_r[k1 + 16 k2] in v[k2]
-  const int myr = lane >> 4, k1 = lane & 15;
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-#pragma unroll
-    for (int a = 0; a < 32; ++a) map[32 * a + lane] = czero();
-    __syncwarp();
-    if (myr == r) {
-      const float2 ph = root_pos(twN, 1024, (long long)S.c * (G.cps[n] + r * G.N_S));
-#pragma unroll
-      for (int k2 = 0; k2 < 32; ++k2) {
-        const int k = k1 + 16 * k2;
-        const int kt = k < L / 2 ? k : k - L;
-        const float w = weight(S, S.dtx, kt + L / 2);
-        map[(S.c + kt) & 1023] = cscale(cmul(v[k2], ph), w);
-      }
-    }
-    __syncwarp();
-    float2 u[32];
-#pragma unroll
-    for (int a = 0; a < 32; ++a) u[a] = map[32 * a + lane];
-    __syncwarp();
-    warp_fft1024<true>(u, scr, twN, lane);        // sample k1' + 32 k2 of block r
-#pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) {
-      const int tau = lane + 32 * k2;
-      float2 a0 = u[k2];
-      if (ols) {
-        const int lo = (r == 0) ? G.N_L - ncp : G.N_L, hi = G.N_L + G.N_S;
-        if (!(tau >= lo && tau < hi)) a0 = czero();
-      }
-      atomicAdd(wdst + jb.start + r * (1024 / 2) + tau, a0);
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
@@ -303,7 +416,7 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
         }
         X[a] = s ? cmul(csub(x0, x1), __ldg(twN + tp)) : cadd(x0, x1);
       }
-      warp_fft1024<false>(X, scr, twL, lane);     // bin 2 (k1 + 32 k2) + s
+      warp_fft1024_d<false>(X, scr, twL, lane);     // bin 2 (k1 + 32 k2) + s
 #pragma unroll
       for (int k2 = 0; k2 < 32; ++k2) {
         const int q = 2 * (lane + 32 * k2) + s;
@@ -320,7 +433,7 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
     for (int a = 0; a < 32; ++a) u[a] = map[32 * a + lane];
     __syncwarp();
     // R4: short IDFT
-    warp_fft1024<true>(u, scr, twL, lane);        // z_r[k1 + 32 k2] in u[k2]
+    warp_fft1024_d<true>(u, scr, twL, lane);        // z_r[k1 + 32 k2] in u[k2]
     // R5: S window + concatenation (eq:concat2), or OLA of both blocks; x_ofdm[t], t = lane + 32 k2
     if (!ola) {
 #pragma unroll
@@ -334,7 +447,7 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
     }
   }
   // R6: OFDM demodulation and active-bin output
-  warp_fft1024<false>(h, scr, twL, lane);
+  warp_fft1024_d<false>(h, scr, twL, lane);
   const int hl = S.Lact / 2, hu = S.Lact - hl;
   float2* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
 #pragma unroll
@@ -368,7 +481,7 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
       if (ola && !(t >= G.N_L && t < G.N_L + G.N_S)) xv = czero();
       u[a] = xv;
     }
-    warp_fft1024<false>(u, scr, twN, lane);       // bin k1 + 32 k2
+    warp_fft1024_d<false>(u, scr, twN, lane);       // bin k1 + 32 k2
   }
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
@@ -393,7 +506,7 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
     v[16 + a] = map[L + 32 * a + lane];
   }
   __syncwarp();
-  warp_fft512x2<true>(v, scr, twL, lane);         // lane k1 + 16 r: z_r[k1 + 16 k2]
+  warp_fft512x2_d<true>(v, scr, twL, lane);         // lane k1 + 16 r: z_r[k1 + 16 k2]
   {
     const int r = lane >> 4, k1 = lane & 15;
 #pragma unroll
@@ -415,7 +528,7 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
     v[16 + a] = czero();
   }
   __syncwarp();
-  warp_fft512x2<false>(v, scr, twL, lane);        // lanes 0..15: X[k1 + 16 k2]
+  warp_fft512x2_d<false>(v, scr, twL, lane);        // lanes 0..15: X[k1 + 16 k2]
   if (lane < 16) {
     const int hl = S.Lact / 2, hu = S.Lact - hl;
     float2* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
@@ -428,10 +541,11 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
   }
 }
 
+
 // ---------------------------------------------------------------------------
 // kernels: one CTA per (stream, chunk), warps take jobs from a shared counter
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(FC_WARP_THREADS, 3)
+__global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_TX_MIN_BLOCKS)
 k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
                int n_chunks, int zero_output, const float2* __restrict__ grid, float2* __restrict__ wave) {
   __shared__ FcPlanDev P;
@@ -458,13 +572,11 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     if (j >= ch.j1) break;
     const FcJob jb = jobs[j];
     const FcGroupDev& G = P.g[jb.group];
-    const FcSubDev& S = P.s[G.first_sub];
-    if (S.L == 1024) tx_job_1024(P, G, S, jb, gsrc, wdst, scr, map, lane);
-    else tx_job_512(P, G, S, jb, gsrc, wdst, scr, map, lane);
+    tx_job(P, G, P.s[G.first_sub], jb, gsrc, wdst, scr, map, lane);
   }
 }
 
-__global__ void __launch_bounds__(FC_WARP_THREADS, 3)
+__global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_RX_MIN_BLOCKS)
 k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
                int n_chunks, const float2* __restrict__ wave, float2* __restrict__ grid) {
   __shared__ FcPlanDev P;
@@ -492,6 +604,7 @@ k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     else rx_job_512(P, G, S, jb, src, gdst, scr, map, lane);
   }
 }
+
 
 __global__ void k_zero(float4* __restrict__ p, size_t n4) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
