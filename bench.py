@@ -15,6 +15,7 @@ in Msamples/s. One JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -236,7 +237,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     import numpy as np
     import torch
     import workloads as wl
-    from paper_2008_00672_gb300 import Plan, build
+    from paper_2008_00672_gb300 import FC_FLAG_REDUCED_RX, Plan, build
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -356,6 +357,22 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
             lat.append(a.elapsed_time(b))
     lat.sort()
 
+    # ---- RX variant: the joint IDFT/DFT form of eq:reduc (FC_FLAG_REDUCED_RX), same input ----
+    plan_red = Plan(dataclasses.replace(geom, flags=FC_FLAG_REDUCED_RX), device=local_rank)
+    for _ in range(3):
+        plan_red.rx_analyze(rx_in, est)
+    red = []
+    for _ in range(max(3, min(args.steps, 20))):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        plan_red.rx_analyze(rx_in, est)
+        b.record(st)
+        b.synchronize()
+        red.append(a.elapsed_time(b))
+    plan_red.close()
+    rx_variants = {"direct_ms": round(rx_ms, 4), "eq_reduc_ms": round(statistics.mean(red), 4)}
+
     # ---- accuracy of the timed path against the FP64 oracle (one sampled stream) ----
     from oracle import fc_oracle as fo
     s_chk = S - 1
@@ -418,6 +435,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
            "latency_1stream_ms": {"p50": round(lat[len(lat) // 2], 4), "p99": round(lat[int(0.99 * len(lat))], 4),
                                   "slot_budget_ms": 1.0},
            "accuracy": {"tx_rel_rms_vs_oracle": tx_err, "rx_rel_rms_vs_oracle": rx_err, "evm_db_awgn30": evm_db},
+           "rx_variants": rx_variants,
            "clocks": clk, "gpu_launches": args.steps * (plan.tx_kernels + plan.rx_kernels)}
     print(json.dumps(out), flush=True)
 

@@ -86,12 +86,18 @@ typedef struct fc_geometry {
   const fc_group* groups;
   int32_t n_subbands;      /* 1..FC_MAX_SUBBANDS                                       */
   const fc_subband* subbands;
-  int32_t flags;           /* 0, or FC_FLAG_GENERIC_KERNELS                            */
+  int32_t flags;           /* 0, or an OR of the FC_FLAG_* bits below                  */
 } fc_geometry;
 
 /* Use the generic shared-memory kernels even where a specialised kernel exists
    (both compute the same result; this exists to test one against the other). */
 #define FC_FLAG_GENERIC_KERNELS 1
+/* Overlap-save symbol-synchronised RX of a subband with L_m = 1024, N_m = 2048 in the
+   joint form of eq:reduc (Sec. III-C): x_hat = C Omega(g_0 - Omega g_1) + Omega Omega g_1
+   with C = W S_hat W^-1, instead of the two block IDFTs, the S window, eq:concat2 and
+   the OFDM DFT. Same result up to rounding. It applies to the specialised one-warp-per-
+   symbol kernels only; other RX work (OLA, other sizes, FC_FLAG_GENERIC_KERNELS) ignores it. */
+#define FC_FLAG_REDUCED_RX 2
 
 #define FC_MAX_GROUPS 4
 #define FC_MAX_SUBBANDS 16

@@ -33,6 +33,7 @@ Readings taken where the paper is silent, ambiguous or garbled (cited inline as 
   R6  N_L = ceil(N_O/2), N_T = floor(N_O/2), as for the low-rate split.
   R7  RX extension removal keeps [L_L, L_L + L) of the 3L/2 concatenation buffer.
   R8  RX segmentation is w_hat_n = Gamma_{sigma_n}^T x_hat (the stray sum over n dropped).
+  R9  in the simplified RX, P^(+-L/4) act as circular shifts (S_hat = S shifted by L/4).
   R10 symbol-synchronized mode needs lambda = 0.5, 4 | L, 4 | N, L_OFDM = L, N_CP,n <= N/4.
   R11 L_CP,n = floor(N_CP,n L / N) in integer arithmetic.
   R13 active subcarriers sit at signed frequencies -floor(L_act/2) .. ceil(L_act/2)-1.
@@ -394,6 +395,47 @@ def rx_sync_subband(x: np.ndarray, group, sub, scheme: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# Simplified symbol-synchronized RX (Sec. V, "Simplified Implementation"; eq:FCcomb, eq:reduc)
+# ---------------------------------------------------------------------------
+
+def omega(L: int, phi: int) -> np.ndarray:
+    """Omega_phi = diag(W_L^{0}, W_L^{phi}, ..., W_L^{phi (L-1)}), W_L = exp(-j 2 pi / L)."""
+    k = np.arange(L, dtype=np.int64)
+    return np.exp(-2j * np.pi * ((phi * k) % L) / L)
+
+
+def halfband_C(L: int) -> np.ndarray:
+    """C = W_L S_hat W_L^{-1} (eq:halfband), S_hat = the OLS window [0_{L/4}; 1_{L/2}; 0_{L/4}]
+    circularly shifted left/up by L/4 (reading R9): ones on [0, L/2)."""
+    s_hat = np.zeros(L)
+    s_hat[:L // 2] = 1.0
+    return dft_matrix(L) @ np.diag(s_hat) @ (np.conj(dft_matrix(L)) / L)
+
+
+def rx_sync_subband_simplified(x: np.ndarray, group, sub) -> np.ndarray:
+    """Symbol-synchronized OLS RX with the joint IFFT/FFT of eq:reduc:
+    x_hat = Omega_{-L/4} [F (g_{2n} - Omega_{L/2} g_{2n+1}) + Omega_{L/2} g_{2n+1}],
+    F = Omega_{L/4} C Omega_{-L/4}, with g the FC output blocks in the frequency
+    domain (the inputs of W_L^{-1} in eq:FCcomb). Then 1/sqrt(L) and the active bins."""
+    d = Dims(group, sub)
+    sync_check(d)
+    sig = sync_sigma(d)
+    L, N = d.L, d.N
+    F = np.diag(omega(L, L // 4)) @ halfband_C(L) @ np.diag(omega(L, -L // 4))
+    out = np.zeros((d.B, d.L_act), dtype=np.complex128)
+    for n in range(d.B):
+        wn = x[sig[n]: sig[n] + 3 * N // 2]
+        Wb = np.stack([wn[0:N], wn[N // 2: N // 2 + N]], axis=1)
+        th = sync_theta(d, n)
+        phases = np.array([root_of_unity(r * d.c * d.L_S, L) * th for r in range(2)])
+        g = dft(analysis_blocks(Wb, d, phases))       # frequency-domain FC outputs: W_L z
+        g0, g1 = g[:, 0], g[:, 1]
+        xh = omega(L, -L // 4) * (F @ (g0 - omega(L, L // 2) * g1) + omega(L, L // 2) * g1)
+        out[n] = (xh / math.sqrt(L))[active_bins(d.L_act, L)]
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Frames: subbands of all groups summed, x = sum_m w_m (Sec. III-B)
 # ---------------------------------------------------------------------------
 
@@ -460,8 +502,9 @@ def tx_frame(geom, grid: np.ndarray) -> np.ndarray:
     return out
 
 
-def rx_frame(geom, wave: np.ndarray) -> np.ndarray:
-    """One stream: received waveform -> QAM estimates in the grid layout."""
+def rx_frame(geom, wave: np.ndarray, simplified: bool = False) -> np.ndarray:
+    """One stream: received waveform -> QAM estimates in the grid layout.
+    simplified=True uses eq:reduc for symbol-synchronized OLS RX."""
     offs, flen = frame_layout(geom)
     wave = np.asarray(wave, dtype=np.complex128)
     parts = []
@@ -469,7 +512,11 @@ def rx_frame(geom, wave: np.ndarray) -> np.ndarray:
         g = geom.groups[sub.group]
         o = offs[sub.group]
         d = Dims(g, sub)
-        if geom.mode == SYMBOL_SYNC:
+        if geom.mode == SYMBOL_SYNC and simplified:
+            if geom.scheme_rx != OLS:
+                raise ValueError("eq:reduc is the overlap-save RX")
+            est = rx_sync_subband_simplified(wave[o:], g, sub)
+        elif geom.mode == SYMBOL_SYNC:
             est = rx_sync_subband(wave[o:], g, sub, geom.scheme_rx)
         else:
             l_cp = low_rate_cp(d, CONTINUOUS)

@@ -3,6 +3,6 @@
 The compute path is the CUDA library built from ``csrc/`` (see ``build.py``);
 ``fc`` is its thin ctypes binding.
 """
-from .fc import (FC_CONTINUOUS, FC_OLA, FC_OLS, FC_SYMBOL_SYNC, FcError, Plan, fc_geometry_check,  # noqa: F401
+from .fc import (FC_CONTINUOUS, FC_FLAG_GENERIC_KERNELS, FC_FLAG_REDUCED_RX, FC_OLA, FC_OLS, FC_SYMBOL_SYNC, FcError, Plan, fc_geometry_check,  # noqa: F401
                  fc_plan_create, fc_plan_destroy, fc_query, fc_rx_analyze, fc_status_string, fc_tx_synthesize,
                  load_library)

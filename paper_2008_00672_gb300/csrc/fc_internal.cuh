@@ -69,6 +69,7 @@ struct FcChunk {
 
 struct FcPlanDev {
   int mode, scheme_tx, scheme_rx;
+  int flags;          // fc_geometry.flags
   int n_groups, n_subs, n_sizes;
   int frame_len;
   long long grid_len;

@@ -466,6 +466,7 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   P.mode = geo->mode;
   P.scheme_tx = geo->scheme_tx;
   P.scheme_rx = geo->scheme_rx;
+  P.flags = geo->flags;
   P.n_groups = G;
   P.n_subs = M;
   P.n_sizes = (int)sizes.size();

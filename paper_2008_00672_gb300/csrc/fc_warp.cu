@@ -385,6 +385,100 @@ __device__ __forceinline__ void warp_fft512x2_d(float2 (&v)[32], float2* scr, co
 // ---------------------------------------------------------------------------
 // RX, N = 2048, L = 1024
 // ---------------------------------------------------------------------------
+// j^e x for e mod 4 (multiplication by a power of +j)
+__device__ __forceinline__ float2 mul_jpow(float2 x, int e) {
+  switch (e & 3) {
+    case 0: return x;
+    case 1: return make_float2(-x.y, x.x);
+    case 2: return make_float2(-x.x, -x.y);
+    default: return make_float2(x.y, -x.x);
+  }
+}
+
+// R1-R3 for block r: the 2048-point DFT as two 1024-point halves (even / odd bins),
+// then the subband's 1024 bins gathered with conj(phi_r theta_n) and D_m into map
+// at their natural short-transform index k. combine: instead of storing g_r[k],
+// store j^k (g_r[k] - (-1)^k map[k]) (the bracket of eq:reduc, map holding g_1).
+__device__ __forceinline__ void rx_block_gather_1024(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S,
+                                                     const FcJob& jb, const float2* __restrict__ src, float2* scr,
+                                                     float2* map, int lane, int r, bool combine) {
+  constexpr int L = 1024;
+  const float2* __restrict__ twL = P.sz[S.size_L].tw;
+  const float2* __restrict__ twN = P.sz[G.size_N].tw;
+  const float2* __restrict__ x = src + jb.start + r * (2048 / 2);
+  const float2 ph = root_pos(twN, 2048, (long long)S.c * (G.cps[jb.index] + r * G.N_S));
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    float2 X[32];
+    // even bins: DFT of x0 + x1; odd bins: DFT of (x0 - x1) exp(-j 2 pi tp / 2048)
+#pragma unroll
+    for (int a = 0; a < 32; ++a) {
+      const int tp = 32 * a + lane;
+      const float2 x0 = __ldg(x + tp), x1 = __ldg(x + tp + 1024);
+      X[a] = s ? cmul(csub(x0, x1), __ldg(twN + tp)) : cadd(x0, x1);
+    }
+    warp_fft1024_d<false>(X, scr, twL, lane);     // bin 2 (k1 + 32 k2) + s
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) {
+      const int q = 2 * (lane + 32 * k2) + s;
+      int kt = (q - S.c) & 2047;
+      if (kt >= 1024) kt -= 2048;
+      if (kt >= -L / 2 && kt < L / 2) {
+        const int k = kt & (L - 1);
+        const float2 g = cscale(cmulc(X[k2], ph), weight(S, S.drx, kt + L / 2));
+        if (!combine) {
+          map[k] = g;
+        } else {
+          const float2 g1 = map[k];
+          map[k] = mul_jpow((k & 1) ? cadd(g, g1) : csub(g, g1), k);
+        }
+      }
+    }
+  }
+}
+
+// Overlap-save RX in the joint form of eq:reduc (opt-in, FC_FLAG_REDUCED_RX):
+//   x_hat = W_L S_hat W_L^{-1} [j^k (g_0 - (-1)^k g_1)] + (-j)^k g_1   (scaled by L),
+// where g_r are the gathered block spectra and S_hat keeps time samples [0, L/2).
+// One IDFT and one DFT replace the two block IDFTs and the OFDM DFT (6 transforms of
+// 1024 points per symbol instead of 7), at the cost of a second pass over the output row.
+__device__ __noinline__ void rx_job_1024_reduced(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
+                                            const float2* __restrict__ src, float2* __restrict__ gdst, float2* scr,
+                                            float2* map, int lane) {
+  constexpr int L = 1024;
+  const float2* __restrict__ twL = P.sz[S.size_L].tw;
+  const int n = jb.index;
+  const int hl = S.Lact / 2, hu = S.Lact - hl;
+  float2* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
+  float2 u[32];
+  rx_block_gather_1024(P, G, S, jb, src, scr, map, lane, 1, false);    // map = g_1
+  __syncwarp();
+  // L (-j)^k g_1[k] goes straight to the output row; the same thread adds the
+  // transform result to it at the end (no register copy across the next stages)
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) {
+    const int k = lane + 32 * k2;
+    const int f = k < L / 2 ? k : k - L;
+    if (f >= -hl && f < hu) row[f + hl] = cscale(mul_jpow(map[k], 3 * k), (float)L);
+  }
+  __syncwarp();
+  rx_block_gather_1024(P, G, S, jb, src, scr, map, lane, 0, true);     // map = j^k (g_0 - (-1)^k g_1)
+  __syncwarp();
+#pragma unroll
+  for (int a = 0; a < 32; ++a) u[a] = map[32 * a + lane];
+  __syncwarp();
+  warp_fft1024_d<true>(u, scr, twL, lane);        // time k1 + 32 k2
+#pragma unroll
+  for (int k2 = 16; k2 < 32; ++k2) u[k2] = czero();   // S_hat
+  warp_fft1024_d<false>(u, scr, twL, lane);       // bin k1 + 32 k2
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) {
+    const int bin = lane + 32 * k2;
+    const int f = bin < L / 2 ? bin : bin - L;
+    if (f >= -hl && f < hu) row[f + hl] = cadd(u[k2], row[f + hl]);
+  }
+}
+
 __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                             const float2* __restrict__ src, float2* __restrict__ gdst, float2* scr,
                                             float2* map, int lane) {
@@ -600,7 +694,9 @@ k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     const FcJob jb = jobs[j];
     const FcGroupDev& G = P.g[jb.group];
     const FcSubDev& S = P.s[G.first_sub];
-    if (S.L == 1024) rx_job_1024(P, G, S, jb, src, gdst, scr, map, lane);
+    if (S.L == 1024 && (P.flags & FC_FLAG_REDUCED_RX) && P.scheme_rx == FC_OLS)
+      rx_job_1024_reduced(P, G, S, jb, src, gdst, scr, map, lane);
+    else if (S.L == 1024) rx_job_1024(P, G, S, jb, src, gdst, scr, map, lane);
     else rx_job_512(P, G, S, jb, src, gdst, scr, map, lane);
   }
 }

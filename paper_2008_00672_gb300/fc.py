@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfcofdm.so")
 FC_OK, FC_ERR_INVALID, FC_ERR_UNSUPPORTED, FC_ERR_NOMEM, FC_ERR_CUDA, FC_ERR_TIMEOUT = range(6)
 FC_CONTINUOUS, FC_SYMBOL_SYNC = 0, 1
 FC_FLAG_GENERIC_KERNELS = 1
+FC_FLAG_REDUCED_RX = 2
 FC_OLA, FC_OLS = 0, 1
 
 EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize", "fc_rx_analyze", "fc_plan_destroy",

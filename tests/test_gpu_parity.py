@@ -61,10 +61,12 @@ def check_geometry(torch, geom, n_streams, seed, snr_db=30.0, streams_to_check=N
         wave_rx[s] = wl.awgn(ref_tx[s], snr_db, seed + 7919 * (s + 1))
     wave_rx = c64(wave_rx).astype(np.complex128)
     w, e = gpu_tx_rx(torch, geom, grid, wave_rx)
+    # FC_FLAG_REDUCED_RX: compare with the oracle's own eq:reduc form
+    reduced = bool(geom.flags & 2) and geom.mode == wl.SYMBOL_SYNC and geom.scheme_rx == fo.OLS
     worst = (0.0, 0.0)
     for s in idx:
         et = rel(w[s], ref_tx[s])
-        er = rel(e[s], fo.rx_frame(geom, wave_rx[s]))
+        er = rel(e[s], fo.rx_frame(geom, wave_rx[s], simplified=reduced))
         worst = (max(worst[0], et), max(worst[1], er))
     assert worst[0] <= TOL and worst[1] <= TOL, worst
     return w, e
@@ -161,9 +163,10 @@ def test_nr5mhz_single_subband_ols(torch_cuda):
     check_geometry(torch_cuda, wl.config_single_5mhz(), 3, wl.default_seed(1))
 
 
-@pytest.mark.parametrize("flags", [0, 1])
+@pytest.mark.parametrize("flags", [0, 1, 2])
 def test_nr20mhz_mixed_numerology_symbol_sync(torch_cuda, flags):
-    """flags=0: warp-specialised kernels; flags=1: generic shared-memory kernels."""
+    """flags=0: warp-specialised kernels; flags=1: generic shared-memory kernels;
+    flags=2: warp kernels with the eq:reduc RX for the L = 1024 subband."""
     geom = dataclasses.replace(wl.config_mixed_20mhz(), flags=flags)
     check_geometry(torch_cuda, geom, 2, wl.default_seed(2))
 
@@ -186,13 +189,24 @@ def test_warp_path_single_group(torch_cuda, case):
     check_geometry(torch_cuda, geom, 3, 31)
 
 
-def test_warp_path_two_groups_odd_offsets(torch_cuda):
+@pytest.mark.parametrize("case", [c for c in WARP_CASES if c[6] == fo.OLS])
+def test_reduced_rx_single_group(torch_cuda, case):
+    """eq:reduc RX (FC_FLAG_REDUCED_RX) against the oracle's eq:reduc form; for L = 512
+    the flag is ignored and the direct kernel runs (same result up to rounding)."""
+    N, L, act, c, n_cp, stx, srx = case
+    D = wl.rc_transition_weights(L, act, min(8, (L - act) // 2))
+    geom = dataclasses.replace(geom1(fo.SYMBOL_SYNC, stx, srx, N, N // 2, L, L, act, c, n_cp, D=D), flags=2)
+    check_geometry(torch_cuda, geom, 3, 41)
+
+
+@pytest.mark.parametrize("flags", [0, 2])
+def test_warp_path_two_groups_odd_offsets(torch_cuda, flags):
     """Two numerology groups whose alignment puts group B at an odd sample offset."""
     ga = wl.Group(2048, 1024, (161, 144, 144))
     gb = wl.Group(1024, 512, (88, 72, 72, 72, 72, 72))
     sa = wl.Subband(1024, 1024, 600, -310, 0, wl.rc_transition_weights(1024, 600, 8))
     sb = wl.Subband(512, 512, 280, 160, 1, wl.rc_transition_weights(512, 280, 8))
-    geom = wl.Geometry(fo.SYMBOL_SYNC, fo.OLA, fo.OLS, (ga, gb), (sa, sb))
+    geom = wl.Geometry(fo.SYMBOL_SYNC, fo.OLA, fo.OLS, (ga, gb), (sa, sb), flags=flags)
     check_geometry(torch_cuda, geom, 2, 37)
 
 

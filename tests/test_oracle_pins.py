@@ -440,3 +440,30 @@ def test_invalid_sync_geometry_rejected():
     with pytest.raises(ValueError):
         g = geom1(fo.SYMBOL_SYNC, fo.OLA, fo.OLS, 32, 8, 16, 16, 10, 0, (2,), np.ones(16))
         fo.tx_frame(g, np.zeros(10))                              # lambda != 0.5
+
+
+# ---------------------------------------------------------------------------
+# Simplified RX (eq:reduc)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", [16, 32, 64])
+def test_halfband_complement(L):
+    """C + Omega_{L/2} C Omega_{L/2} = I: the two half windows add to the identity
+    (the lowpass/highpass pair behind eq:reduc)."""
+    C = fo.halfband_C(L)
+    O = np.diag(fo.omega(L, L // 2))
+    assert np.allclose(C + O @ C @ O, np.eye(L), atol=1e-12)
+
+
+@pytest.mark.parametrize("N,L,c,n_cp", [(32, 16, 3, (6, 4, 4, 5)), (64, 32, -9, (16, 8, 0, 13)),
+                                        (2048, 1024, -300, (160, 144)), (48, 24, 5, (12, 3))])
+def test_simplified_rx_equals_direct(N, L, c, n_cp):
+    """eq:reduc == eq:FCcomb (direct RX: two short IDFTs, concatenation, OFDM DFT)
+    exactly, for arbitrary received waveforms (reading R9: circular P^(+-L/4))."""
+    rng = np.random.default_rng(N + L)
+    D = rng.uniform(0, 1, L)
+    gm = geom1(fo.SYMBOL_SYNC, fo.OLA, fo.OLS, N, N // 2, L, L, L - 4, c, n_cp, D)
+    w = crand(rng, fo.frame_len(gm))
+    a = fo.rx_frame(gm, w)
+    b = fo.rx_frame(gm, w, simplified=True)
+    assert np.allclose(a, b, atol=1e-10 * np.max(np.abs(a)))
