@@ -110,6 +110,9 @@ typedef struct fc_sizes {
   int64_t workspace_per_stream; /* device workspace bytes per stream for TX and RX     */
   int32_t tx_kernels;      /* kernel launches per fc_tx_synthesize                     */
   int32_t rx_kernels;      /* kernel launches per fc_rx_analyze                        */
+  int64_t slot_len;        /* T: samples one stream call emits (TX) or takes (RX);
+                              0 if the geometry cannot stream (see fc_state_create)    */
+  int64_t stream_delay;    /* D = wave_len - slot_len: TX tail / RX look-behind length */
 } fc_sizes;
 
 typedef struct fc_plan fc_plan;
@@ -160,6 +163,63 @@ int fc_tx_synthesize(const fc_plan* plan, int32_t n_streams, const void* grid_in
  */
 int fc_rx_analyze(const fc_plan* plan, int32_t n_streams, const void* wave_in, void* grid_out,
                   void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Stream calls: a stream is an endless sequence of slots of this geometry (a slot =
+ * the CP lists of all groups, duration T = fc_sizes.slot_len samples). The paper
+ * processes one frame with zero history (Sec. III-B pads both ends, eq:waveformLen
+ * sizes the symbol-synchronized frame); a stream call instead continues the previous
+ * call, so that K calls give exactly what one frame of the K-slot geometry (every
+ * CP list repeated K times, slot grids stacked per subband) gives:
+ *   TX: the concatenated outputs of calls 0..K-1 are samples [0, K T) of the K-slot
+ *       frame (its last D = fc_sizes.stream_delay samples stay in the state and come
+ *       out at the start of call K).
+ *   RX: call k decodes slot k from the D samples before its input (the "look-behind",
+ *       kept in the state) followed by its T input samples, i.e. from samples
+ *       [k T, k T + Q) of the stream [look-behind at reset; input 0; input 1; ...].
+ *       The K-slot frame x (length K T + D) is decoded by a priming call whose input
+ *       ends with x[0, D) (its output discarded) and then calls on x[D + k T, D + (k+1) T).
+ * This holds exactly (up to rounding) when every group lasts the same T, every
+ * c_m T / N_m is an integer (theta_n and phi_r then repeat every slot; true for the
+ * 5G NR numerologies, where the CPs of a slot add up to whole symbols) and, in
+ * continuous mode, T L_m / N_m is a whole number of hops L_S with S_L >= L_O; and
+ * D <= T. Otherwise slot_len is 0 and fc_state_create returns FC_ERR_UNSUPPORTED.
+ *
+ * fc_state holds, per stream, the TX tail and the RX look-behind (D samples each,
+ * zero at creation) and one frame buffer per direction. It is created for a fixed
+ * n_streams and may be used with any plan of the same device whose fc_sizes give the
+ * same wave_len, slot_len and stream_delay. TX calls of one state must be ordered
+ * (same CUDA stream, or synchronised), and so must its RX calls; a TX and an RX call
+ * of one state may overlap (they touch disjoint buffers).
+ */
+typedef struct fc_state fc_state;
+
+/* Allocates the state on the plan's device (cudaMalloc; the stream calls never
+   allocate). FC_ERR_UNSUPPORTED if the plan's geometry cannot stream. */
+int fc_state_create(const fc_plan* plan, int32_t n_streams, fc_state** out);
+
+/* Zeroes the TX tail and the RX look-behind, asynchronously on `stream`. */
+int fc_state_reset(fc_state* state, void* stream);
+
+/* Frees the state (after its calls have finished). Safe on NULL. */
+void fc_state_destroy(fc_state* state);
+
+/*
+ * One TX stream call: grid [n_streams][grid_len] -> slot_out [n_streams][slot_len].
+ * Runs fc_tx_synthesize into the state's frame buffer, then adds the carried tail to
+ * the first D samples and keeps samples [T, T + D) as the next tail. Workspace and
+ * stream rules as fc_tx_synthesize; n_streams is the state's.
+ */
+int fc_tx_synthesize_stream(const fc_plan* plan, fc_state* state, const void* grid_in, void* slot_out,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * One RX stream call: slot_in [n_streams][slot_len] -> grid [n_streams][grid_len].
+ * Assembles [look-behind; slot_in] in the state's frame buffer, keeps the last D
+ * input samples as the next look-behind and runs fc_rx_analyze on the frame.
+ */
+int fc_rx_analyze_stream(const fc_plan* plan, fc_state* state, const void* slot_in, void* grid_out,
+                         void* workspace, size_t workspace_bytes, void* stream);
 
 /*
  * Allocation-free TX (no counterpart in the paper; it is a deployment option).

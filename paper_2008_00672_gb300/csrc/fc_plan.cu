@@ -236,6 +236,26 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   }
   if (frame_len > (1LL << 30)) return fail(FC_ERR_UNSUPPORTED, "frame too long");
 
+  // ---- stream calls (fc_state): a slot is the whole CP list of every group ----
+  // The K-slot frame is the one-slot frame repeated at period T (so a stream call can
+  // run the one-slot frame and carry D = Q - T samples) when every group lasts the
+  // same T, c_m T / N is an integer (theta_n and phi_r repeat every slot) and, in
+  // continuous mode, a slot is a whole number of hops L_S with S_L >= L_O (the one-
+  // slot frame then holds every block that touches its symbols).
+  long long slot_len = -1;
+  bool streamable = true;
+  for (int m = 0; m < M; ++m) {
+    const GroupHost& g = gh[sh[m].g];
+    long long t = 0;
+    for (int n = 0; n < g.B; ++n) t += g.ncp[n];
+    t += sync ? (long long)g.B * g.N : (long long)g.B * sh[m].Lo * g.N / sh[m].L;
+    if (slot_len < 0) slot_len = t;
+    if (t != slot_len || ((long long)sh[m].c * t) % g.N) streamable = false;
+    if (!sync && (sh[m].n_low % sh[m].L_S || sh[m].S_L < sh[m].L_O)) streamable = false;
+  }
+  const long long stream_delay = frame_len - slot_len;
+  if (stream_delay < 0 || stream_delay > slot_len) streamable = false;
+
   // ---- transform sizes, twiddles ------------------------------------------
   std::vector<int> sizes;
   auto size_index = [&](int n) {
@@ -446,6 +466,8 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     z.nominal_len = nom;
   }
   z.workspace_per_stream = ws_len * (long long)sizeof(float2);
+  z.slot_len = streamable ? slot_len : 0;
+  z.stream_delay = streamable ? stream_delay : 0;
   z.tx_kernels = sync ? 1 : 2;
   z.rx_kernels = sync ? 1 : 2;
   // ---- device upload ---------------------------------------------------------

@@ -1,0 +1,211 @@
+// Stream calls (fc_state): consecutive slots of one geometry processed call by call
+// so that the concatenated results equal one frame of the repeated geometry.
+//
+// A frame of one slot is Q = T + D samples long: its last D samples overlap the next
+// slot (the FC filter tails of Sec. III-B and the symbol-wise OLA of eq:multi-symb).
+// When the geometry repeats with period T (same slot duration in every group, c_m T / N
+// an integer so that theta_n and phi_r repeat), the K-slot frame is the sum of one-slot
+// frames at offsets k T (TX), and slot k of the K-slot analysis only reads samples
+// [k T, k T + Q) (RX). So a TX call runs the one-slot frame and carries D samples; an RX
+// call prepends the D samples it kept from the previous input.
+#include <cstdio>
+
+#include "fc_internal.cuh"
+
+struct fc_state {
+  int device = 0;
+  int n_streams = 0;
+  long long wave_len = 0, slot_len = 0, delay = 0;
+  float2* d_mem = nullptr;
+  float2* tx_frame = nullptr;   // [n_streams][wave_len]
+  float2* rx_frame = nullptr;   // [n_streams][wave_len]
+  float2* tail = nullptr;       // [n_streams][delay]   TX samples [T, T + D) of the previous call
+  float2* look = nullptr;       // [n_streams][delay]   last D RX input samples of the previous call
+};
+
+namespace {
+
+struct DevGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DevGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DevGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int cuda_err(cudaError_t e, const char* where) {
+  char msg[200];
+  snprintf(msg, sizeof msg, "%s: %s", where, cudaGetErrorString(e));
+  return fc_internal_fail(e == cudaErrorMemoryAllocation ? FC_ERR_NOMEM : FC_ERR_CUDA, msg);
+}
+
+// out[s][t] = frame[s][t] + tail[s][t] (t < D);  tail[s][t] = frame[s][T + t] (t < D).
+// Each (s, t < D) is read and rewritten by the same thread.
+__global__ void k_stream_tx(const float2* __restrict__ frame, float2* __restrict__ tail, float2* __restrict__ out,
+                            long long total, long long Q, long long T, long long D) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long s = i / T, t = i - s * T;
+    const float2* f = frame + s * Q;
+    float2 v = f[t];
+    if (t < D) {
+      float2* tl = tail + s * D + t;
+      const float2 c = *tl;
+      v.x += c.x;
+      v.y += c.y;
+      *tl = f[T + t];
+    }
+    out[i] = v;
+  }
+}
+
+// frame[s][t] = look[s][t] (t < D) or in[s][t - D];  look[s][t] = in[s][T - D + t] (t < D).
+__global__ void k_stream_rx(const float2* __restrict__ in, float2* __restrict__ look, float2* __restrict__ frame,
+                            long long total, long long Q, long long T, long long D) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long s = i / Q, t = i - s * Q;
+    const float2* x = in + s * T;
+    if (t < D) {
+      float2* lk = look + s * D + t;
+      frame[i] = *lk;
+      *lk = x[T - D + t];
+    } else {
+      frame[i] = x[t - D];
+    }
+  }
+}
+
+int grid_for(long long total) {
+  long long b = (total + 255) / 256;
+  const long long cap = 152LL * 16;   // grid-stride beyond this
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+int check_state(const fc_plan* plan, const fc_state* st, const void* in, const void* out, fc_sizes* sz) {
+  if (!plan || !st) return fc_internal_fail(FC_ERR_INVALID, "plan or state is NULL");
+  int rc = fc_query(plan, sz);
+  if (rc != FC_OK) return rc;
+  if (sz->slot_len == 0) return fc_internal_fail(FC_ERR_UNSUPPORTED, "the plan's geometry cannot stream");
+  if (sz->wave_len != st->wave_len || sz->slot_len != st->slot_len || sz->stream_delay != st->delay)
+    return fc_internal_fail(FC_ERR_INVALID, "state was created for a plan with other frame sizes");
+  if (fc_internal_plan_device(plan) != st->device)
+    return fc_internal_fail(FC_ERR_INVALID, "state and plan are on different devices");
+  if (st->n_streams == 0) return FC_OK;
+  if (!in || !out) return fc_internal_fail(FC_ERR_INVALID, "input or output pointer is NULL");
+  if (((uintptr_t)in | (uintptr_t)out) & 7) return fc_internal_fail(FC_ERR_INVALID, "buffers must be 8-byte aligned");
+  return FC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fc_state_create(const fc_plan* plan, int32_t n_streams, fc_state** out) {
+  if (!out) return fc_internal_fail(FC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!plan) return fc_internal_fail(FC_ERR_INVALID, "plan is NULL");
+  if (n_streams < 0) return fc_internal_fail(FC_ERR_INVALID, "n_streams < 0");
+  fc_sizes sz;
+  int rc = fc_query(plan, &sz);
+  if (rc != FC_OK) return rc;
+  if (sz.slot_len == 0)
+    return fc_internal_fail(FC_ERR_UNSUPPORTED,
+                            "geometry cannot stream: groups differ in slot duration, some c_m T / N is not an "
+                            "integer, a continuous slot is not whole hops with S_L >= L_O, or D > T");
+  const int dev = fc_internal_plan_device(plan);
+  DevGuard dg(dev);
+  if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  fc_state* st = new fc_state();
+  st->device = dev;
+  st->n_streams = n_streams;
+  st->wave_len = sz.wave_len;
+  st->slot_len = sz.slot_len;
+  st->delay = sz.stream_delay;
+  const long long S = n_streams;
+  // frames first, each starting 16-byte aligned (the TX kernels reduce with float4 into
+  // rows of pitch wave_len), then tail and look-behind
+  const long long frame_elems = (S * sz.wave_len + 1) / 2 * 2;
+  const long long elems = 2 * frame_elems + 2 * S * st->delay;
+  if (elems > 0) {
+    cudaError_t e = cudaMalloc(&st->d_mem, (size_t)elems * sizeof(float2));
+    if (e != cudaSuccess) {
+      delete st;
+      return cuda_err(e, "cudaMalloc of the stream state");
+    }
+    e = cudaMemset(st->d_mem, 0, (size_t)elems * sizeof(float2));
+    if (e != cudaSuccess) {
+      cudaFree(st->d_mem);
+      delete st;
+      return cuda_err(e, "cudaMemset of the stream state");
+    }
+  }
+  st->tx_frame = st->d_mem;
+  st->rx_frame = st->d_mem + frame_elems;
+  st->tail = st->d_mem + 2 * frame_elems;
+  st->look = st->tail + S * st->delay;
+  *out = st;
+  return FC_OK;
+}
+
+int fc_state_reset(fc_state* state, void* stream) {
+  if (!state) return fc_internal_fail(FC_ERR_INVALID, "state is NULL");
+  const size_t bytes = (size_t)(2 * (long long)state->n_streams * state->delay) * sizeof(float2);
+  if (bytes == 0) return FC_OK;
+  DevGuard dg(state->device);
+  if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  const cudaError_t e = cudaMemsetAsync(state->tail, 0, bytes, (cudaStream_t)stream);
+  return e == cudaSuccess ? FC_OK : cuda_err(e, "cudaMemsetAsync");
+}
+
+void fc_state_destroy(fc_state* state) {
+  if (!state) return;
+  {
+    DevGuard dg(state->device);
+    if (state->d_mem) cudaFree(state->d_mem);
+  }
+  delete state;
+}
+
+int fc_tx_synthesize_stream(const fc_plan* plan, fc_state* state, const void* grid_in, void* slot_out,
+                            void* workspace, size_t workspace_bytes, void* stream) {
+  fc_sizes sz;
+  int rc = check_state(plan, state, grid_in, slot_out, &sz);
+  if (rc != FC_OK || state->n_streams == 0) return rc;
+  rc = fc_tx_synthesize(plan, state->n_streams, grid_in, state->tx_frame, workspace, workspace_bytes, stream);
+  if (rc != FC_OK) return rc;
+  DevGuard dg(state->device);
+  if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  const long long total = (long long)state->n_streams * state->slot_len;
+  const long long Q = sz.wave_len;
+  k_stream_tx<<<grid_for(total), 256, 0, (cudaStream_t)stream>>>(state->tx_frame, state->tail, (float2*)slot_out,
+                                                                  total, Q, state->slot_len, state->delay);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? FC_OK : cuda_err(e, "stream TX epilogue launch");
+}
+
+int fc_rx_analyze_stream(const fc_plan* plan, fc_state* state, const void* slot_in, void* grid_out,
+                         void* workspace, size_t workspace_bytes, void* stream) {
+  fc_sizes sz;
+  int rc = check_state(plan, state, slot_in, grid_out, &sz);
+  if (rc != FC_OK || state->n_streams == 0) return rc;
+  {
+    DevGuard dg(state->device);
+    if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
+    const long long Q = sz.wave_len;
+    const long long total = (long long)state->n_streams * Q;
+    k_stream_rx<<<grid_for(total), 256, 0, (cudaStream_t)stream>>>((const float2*)slot_in, state->look,
+                                                                    state->rx_frame, total, Q, state->slot_len,
+                                                                    state->delay);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(e, "stream RX prologue launch");
+  }
+  return fc_rx_analyze(plan, state->n_streams, state->rx_frame, grid_out, workspace, workspace_bytes, stream);
+}
+
+}  // extern "C"

@@ -25,7 +25,8 @@ FC_FLAG_REDUCED_RX = 2
 FC_OLA, FC_OLS = 0, 1
 
 EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize", "fc_rx_analyze", "fc_plan_destroy",
-            "fc_status_string", "fc_last_error", "fc_tx_synthesize_static")
+            "fc_status_string", "fc_last_error", "fc_tx_synthesize_static", "fc_state_create", "fc_state_reset",
+            "fc_state_destroy", "fc_tx_synthesize_stream", "fc_rx_analyze_stream")
 
 
 class FcGroup(ctypes.Structure):
@@ -49,7 +50,7 @@ class FcGeometry(ctypes.Structure):
 class FcSizes(ctypes.Structure):
     _fields_ = [("grid_len", ctypes.c_int64), ("wave_len", ctypes.c_int64), ("nominal_len", ctypes.c_int64),
                 ("workspace_per_stream", ctypes.c_int64), ("tx_kernels", ctypes.c_int32),
-                ("rx_kernels", ctypes.c_int32)]
+                ("rx_kernels", ctypes.c_int32), ("slot_len", ctypes.c_int64), ("stream_delay", ctypes.c_int64)]
 
 
 _lib = None
@@ -79,6 +80,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fc_rx_analyze.restype = ctypes.c_int
         lib.fc_tx_synthesize_static.argtypes = [vp, i32, vp, vp, vp]
         lib.fc_tx_synthesize_static.restype = ctypes.c_int
+        lib.fc_state_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
+        lib.fc_state_create.restype = ctypes.c_int
+        lib.fc_state_reset.argtypes = [vp, vp]
+        lib.fc_state_reset.restype = ctypes.c_int
+        lib.fc_state_destroy.argtypes = [vp]
+        lib.fc_state_destroy.restype = None
+        lib.fc_tx_synthesize_stream.argtypes = [vp, vp, vp, vp, vp, sz, vp]
+        lib.fc_tx_synthesize_stream.restype = ctypes.c_int
+        lib.fc_rx_analyze_stream.argtypes = [vp, vp, vp, vp, vp, sz, vp]
+        lib.fc_rx_analyze_stream.restype = ctypes.c_int
         lib.fc_plan_destroy.argtypes = [vp]
         lib.fc_plan_destroy.restype = None
         lib.fc_status_string.argtypes = [ctypes.c_int]
@@ -166,6 +177,33 @@ def fc_tx_synthesize_static(plan, n_streams: int, grid_in: int, wave_out: int, s
            "fc_tx_synthesize_static")
 
 
+def fc_state_create(plan, n_streams: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().fc_state_create(plan, int(n_streams), ctypes.byref(h)), "fc_state_create")
+    return h
+
+
+def fc_state_reset(state, stream: int = 0):
+    _check(load_library().fc_state_reset(state, stream or None), "fc_state_reset")
+
+
+def fc_state_destroy(state):
+    if state:
+        load_library().fc_state_destroy(state)
+
+
+def fc_tx_synthesize_stream(plan, state, grid_in: int, slot_out: int, workspace: int = 0, workspace_bytes: int = 0,
+                            stream: int = 0):
+    _check(load_library().fc_tx_synthesize_stream(plan, state, grid_in, slot_out, workspace or None,
+                                                  int(workspace_bytes), stream or None), "fc_tx_synthesize_stream")
+
+
+def fc_rx_analyze_stream(plan, state, slot_in: int, grid_out: int, workspace: int = 0, workspace_bytes: int = 0,
+                         stream: int = 0):
+    _check(load_library().fc_rx_analyze_stream(plan, state, slot_in, grid_out, workspace or None,
+                                               int(workspace_bytes), stream or None), "fc_rx_analyze_stream")
+
+
 def fc_plan_destroy(plan):
     if plan:
         load_library().fc_plan_destroy(plan)
@@ -192,6 +230,8 @@ class Plan:
         self.workspace_per_stream = int(s.workspace_per_stream)
         self.tx_kernels = int(s.tx_kernels)
         self.rx_kernels = int(s.rx_kernels)
+        self.slot_len = int(s.slot_len)
+        self.stream_delay = int(s.stream_delay)
         self._ws = None
 
     def close(self):
@@ -247,3 +287,50 @@ class Plan:
         if a.numel() % la or b.numel() % lb or a.numel() // la != b.numel() // lb:
             raise ValueError("input and output sizes do not match the plan")
         return a.numel() // la
+
+
+class State:
+    """Owns one fc_state: per-stream TX tail and RX look-behind for stream calls
+    (consecutive slots whose concatenated results equal one frame of the repeated
+    geometry)."""
+
+    def __init__(self, plan: Plan, n_streams: int):
+        self.plan = plan
+        self.n_streams = int(n_streams)
+        self.handle = fc_state_create(plan.handle, self.n_streams)
+
+    def close(self):
+        if self.handle:
+            fc_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, stream=None):
+        fc_state_reset(self.handle, Plan._stream_handle(stream))
+
+    def tx(self, grid, slot_out, workspace=None, stream=None):
+        p = self.plan
+        n = Plan._streams(grid, p.grid_len, slot_out, p.slot_len)
+        if n != self.n_streams:
+            raise ValueError("the state was created for another number of streams")
+        ws = workspace if workspace is not None else p.workspace(n)
+        fc_tx_synthesize_stream(p.handle, self.handle, grid.data_ptr(), slot_out.data_ptr(),
+                                ws.data_ptr() if ws is not None else 0,
+                                ws.numel() * ws.element_size() if ws is not None else 0, Plan._stream_handle(stream))
+        return slot_out
+
+    def rx(self, slot_in, grid_out, workspace=None, stream=None):
+        p = self.plan
+        n = Plan._streams(slot_in, p.slot_len, grid_out, p.grid_len)
+        if n != self.n_streams:
+            raise ValueError("the state was created for another number of streams")
+        ws = workspace if workspace is not None else p.workspace(n)
+        fc_rx_analyze_stream(p.handle, self.handle, slot_in.data_ptr(), grid_out.data_ptr(),
+                             ws.data_ptr() if ws is not None else 0,
+                             ws.numel() * ws.element_size() if ws is not None else 0, Plan._stream_handle(stream))
+        return grid_out

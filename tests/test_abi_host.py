@@ -111,3 +111,31 @@ def test_oracle_rejects_the_same_invalid_geometry():
                  _g(0, 32, 16, 16, 16, 8, 0, (3,))]:
         with pytest.raises(ValueError):
             fo.tx_frame(geom, np.zeros(geom.grid_len(), complex))
+
+
+def _stream_cases():
+    from tests.test_stream_semantics import STREAMABLE, small_sync
+    named = [(n, wl.NAMED[n]()) for n in ("single5", "mixed20")]
+    return named + list(STREAMABLE), small_sync(5, (16, 8, 8, 9))
+
+
+def test_stream_sizes_match_the_slot_identities(fc):
+    """slot_len / stream_delay from the planner agree with the slot duration and the
+    one-slot frame of the oracle for every geometry whose stream identities hold."""
+    from tests.test_stream_semantics import slot_len
+    good, bad = _stream_cases()
+    for name, geom in good:
+        s = fc.fc_geometry_check(geom)
+        assert s.slot_len == slot_len(geom), name
+        assert s.stream_delay == fo.frame_len(geom) - slot_len(geom), name
+    assert fc.fc_geometry_check(bad).slot_len == 0      # c_m T / N not an integer
+
+
+def test_stream_sizes_refuse_unequal_group_slots(fc):
+    """Two groups whose CP lists last different times cannot share a stream slot."""
+    ga = wl.Group(64, 32, (16, 16, 16, 16))
+    gb = wl.Group(32, 16, (8,) * 6)
+    sa = wl.Subband(32, 32, 20, 6, 0, wl.rc_transition_weights(32, 20, 3))
+    sb = wl.Subband(16, 16, 10, -4, 1, wl.rc_transition_weights(16, 10, 2))
+    geom = wl.Geometry(fo.SYMBOL_SYNC, fo.OLA, fo.OLS, (ga, gb), (sa, sb))
+    assert fc.fc_geometry_check(geom).slot_len == 0
