@@ -244,6 +244,59 @@ int fc_rx_analyze_stream(const fc_plan* plan, fc_state* state, const void* slot_
 int fc_tx_synthesize_static(const fc_plan* plan, int32_t n_streams, const void* grid_in, void* wave_out,
                             void* stream);
 
+/* Directions, for the autotuner and the batch executor. */
+#define FC_TX 0
+#define FC_RX 1
+
+/*
+ * Autotuner (no counterpart in the paper; launch-shape selection on this GPU). For
+ * n_streams streams, times every launch shape the plan has for TX and for RX — the
+ * number of CTAs each stream's symbol jobs are spread over (1, 2, 4, ... chunks per
+ * stream) and, where the one-warp-per-symbol kernels apply, those kernels and the
+ * generic shared-memory kernels — `reps` times each on `stream`, and records the
+ * fastest per direction in the plan. Later execute calls with exactly n_streams
+ * streams use it; other counts keep the built-in occupancy rule. Results do not
+ * depend on the choice beyond rounding. Allocates and frees temporary device buffers
+ * and synchronises `stream`: call it at set-up, not inside a stream capture.
+ */
+int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* stream);
+
+/* The launch shape an execute call with n_streams streams will use in `direction`. */
+int fc_plan_choice(const fc_plan* plan, int32_t n_streams, int32_t direction, int32_t* chunks_per_stream,
+                   int32_t* generic_kernels);
+
+/*
+ * Batch executor (no counterpart in the paper). Runs a fixed list of execute calls on
+ * plans of different geometries (carriers with their own bandwidth, numerology and
+ * subbands) as one unit: the calls are spread over `n_lanes` internal CUDA streams
+ * that fork from and join back into the caller's stream, so small carriers run side
+ * by side instead of one after another. With use_graph != 0 the first fc_batch_launch
+ * captures the whole fork/join into a CUDA graph and later launches replay it (one
+ * host call for every kernel of every item); the items' pointers are then fixed, so
+ * refill the same buffers between launches. Items with a state are stream calls
+ * (fc_tx_synthesize_stream / fc_rx_analyze_stream), others frame calls. Items must
+ * not share output buffers, workspaces or states. Every item's result equals that of
+ * its own call.
+ */
+typedef struct fc_batch_item {
+  const fc_plan* plan;
+  fc_state* state;           /* NULL: frame call                                        */
+  int32_t direction;         /* FC_TX or FC_RX                                          */
+  int32_t n_streams;         /* must be the state's n_streams when state != NULL        */
+  const void* in;            /* device: grid (TX) or waveform / slot (RX)               */
+  void* out;                 /* device: waveform / slot (TX) or grid (RX)               */
+  void* workspace;           /* device, or NULL: the batch allocates what the plan needs */
+  size_t workspace_bytes;
+} fc_batch_item;
+
+typedef struct fc_batch fc_batch;
+
+/* Copies the item list; allocates the lanes, events and missing workspaces. */
+int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes, int32_t use_graph,
+                    fc_batch** out);
+int fc_batch_launch(fc_batch* batch, void* stream);
+void fc_batch_destroy(fc_batch* batch);
+
 /* Frees the plan's device tables. Safe on NULL. Must not race with running calls. */
 void fc_plan_destroy(fc_plan* plan);
 

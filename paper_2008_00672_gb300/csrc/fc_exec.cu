@@ -1,0 +1,195 @@
+// Batch executor: a fixed list of execute calls on plans of different geometries,
+// spread over internal CUDA streams ("lanes") that fork from and join into the
+// caller's stream, optionally captured once into a CUDA graph and replayed.
+//
+// Uneven carriers (one 5 MHz carrier next to a 100 MHz one) give kernels of very
+// different grid sizes; one after another, the small ones leave most of the 152 SMs
+// idle and every call pays its launch latency. Side by side on lanes they fill the
+// GPU together, and a graph replay issues all of them with one host call.
+#include <cstdio>
+#include <vector>
+
+#include "fc_internal.cuh"
+
+struct fc_batch {
+  int device = 0;
+  std::vector<fc_batch_item> items;
+  std::vector<cudaStream_t> lanes;
+  std::vector<cudaEvent_t> lane_done;
+  cudaStream_t origin = nullptr;                  // the stream the graph is captured on / replayed on
+  cudaEvent_t ev_fork = nullptr, ev_enter = nullptr, ev_exit = nullptr;
+  bool use_graph = false;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<void*> owned;                       // workspaces the batch allocated
+};
+
+namespace {
+
+struct DevGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DevGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = prev == dev || cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DevGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int cuda_err(cudaError_t e, const char* where) {
+  char msg[200];
+  snprintf(msg, sizeof msg, "%s: %s", where, cudaGetErrorString(e));
+  return fc_internal_fail(e == cudaErrorMemoryAllocation ? FC_ERR_NOMEM : FC_ERR_CUDA, msg);
+}
+
+int run_item(const fc_batch_item& it, cudaStream_t st) {
+  void* s = (void*)st;
+  if (it.state) {
+    return it.direction == FC_TX
+               ? fc_tx_synthesize_stream(it.plan, it.state, it.in, it.out, it.workspace, it.workspace_bytes, s)
+               : fc_rx_analyze_stream(it.plan, it.state, it.in, it.out, it.workspace, it.workspace_bytes, s);
+  }
+  return it.direction == FC_TX
+             ? fc_tx_synthesize(it.plan, it.n_streams, it.in, it.out, it.workspace, it.workspace_bytes, s)
+             : fc_rx_analyze(it.plan, it.n_streams, it.in, it.out, it.workspace, it.workspace_bytes, s);
+}
+
+// fork from origin, item i on lane i mod n_lanes, join back into origin
+int issue(fc_batch* b) {
+  cudaError_t e = cudaEventRecord(b->ev_fork, b->origin);
+  for (size_t l = 0; l < b->lanes.size() && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(b->lanes[l], b->ev_fork, 0);
+  if (e != cudaSuccess) return cuda_err(e, "batch fork");
+  for (size_t i = 0; i < b->items.size(); ++i) {
+    const int rc = run_item(b->items[i], b->lanes[i % b->lanes.size()]);
+    if (rc != FC_OK) return rc;
+  }
+  for (size_t l = 0; l < b->lanes.size() && e == cudaSuccess; ++l) {
+    e = cudaEventRecord(b->lane_done[l], b->lanes[l]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->lane_done[l], 0);
+  }
+  return e == cudaSuccess ? FC_OK : cuda_err(e, "batch join");
+}
+
+void release(fc_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (cudaEvent_t ev : b->lane_done) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : {b->ev_fork, b->ev_enter, b->ev_exit})
+    if (ev) cudaEventDestroy(ev);
+  for (cudaStream_t s : b->lanes) cudaStreamDestroy(s);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  for (void* p : b->owned) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes, int32_t use_graph,
+                    fc_batch** out) {
+  if (!out) return fc_internal_fail(FC_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!items || n_items < 1) return fc_internal_fail(FC_ERR_INVALID, "need at least one item");
+  if (n_lanes < 1 || n_lanes > 64) return fc_internal_fail(FC_ERR_INVALID, "n_lanes must be 1..64");
+  const int dev = fc_internal_plan_device(items[0].plan);
+  for (int i = 0; i < n_items; ++i) {
+    const fc_batch_item& it = items[i];
+    if (!it.plan) return fc_internal_fail(FC_ERR_INVALID, "item without a plan");
+    if (fc_internal_plan_device(it.plan) != dev) return fc_internal_fail(FC_ERR_INVALID, "items on different devices");
+    if (it.direction != FC_TX && it.direction != FC_RX) return fc_internal_fail(FC_ERR_INVALID, "bad direction");
+    if (it.n_streams < 0) return fc_internal_fail(FC_ERR_INVALID, "n_streams < 0");
+  }
+  DevGuard dg(dev);
+  if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  fc_batch* b = new fc_batch();
+  b->device = dev;
+  b->items.assign(items, items + n_items);
+  b->use_graph = use_graph != 0;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  for (int l = 0; l < n_lanes && e == cudaSuccess; ++l) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->lanes.push_back(s);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->lane_done.push_back(ev);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_enter, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_exit, cudaEventDisableTiming);
+  // workspaces the caller left to the batch (continuous-mode plans need one per item)
+  for (auto& it : b->items) {
+    if (e != cudaSuccess || it.workspace) continue;
+    fc_sizes sz;
+    const int rc = fc_query(it.plan, &sz);
+    if (rc != FC_OK) {
+      release(b);
+      delete b;
+      return rc;
+    }
+    const size_t need = (size_t)it.n_streams * (size_t)sz.workspace_per_stream;
+    if (need == 0) continue;
+    void* p = nullptr;
+    e = cudaMalloc(&p, need);
+    if (e == cudaSuccess) {
+      b->owned.push_back(p);
+      it.workspace = p;
+      it.workspace_bytes = need;
+    }
+  }
+  if (e != cudaSuccess) {
+    release(b);
+    delete b;
+    return cuda_err(e, "fc_batch_create");
+  }
+  *out = b;
+  return FC_OK;
+}
+
+int fc_batch_launch(fc_batch* b, void* stream) {
+  if (!b) return fc_internal_fail(FC_ERR_INVALID, "batch is NULL");
+  DevGuard dg(b->device);
+  if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t caller = (cudaStream_t)stream;
+  cudaError_t e = cudaEventRecord(b->ev_enter, caller);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->ev_enter, 0);
+  if (e != cudaSuccess) return cuda_err(e, "batch enter");
+  int rc = FC_OK;
+  if (!b->use_graph) {
+    rc = issue(b);
+  } else {
+    if (!b->exec) {
+      e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_err(e, "cudaStreamBeginCapture");
+      rc = issue(b);
+      cudaGraph_t g = nullptr;
+      e = cudaStreamEndCapture(b->origin, &g);
+      if (rc == FC_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (rc != FC_OK) return rc;
+      if (e != cudaSuccess) {
+        b->exec = nullptr;
+        return cuda_err(e, "batch graph capture");
+      }
+    }
+    e = cudaGraphLaunch(b->exec, b->origin);
+    if (e != cudaSuccess) return cuda_err(e, "cudaGraphLaunch");
+  }
+  if (rc != FC_OK) return rc;
+  e = cudaEventRecord(b->ev_exit, b->origin);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, b->ev_exit, 0);
+  return e == cudaSuccess ? FC_OK : cuda_err(e, "batch exit");
+}
+
+void fc_batch_destroy(fc_batch* b) {
+  if (!b) return;
+  {
+    DevGuard dg(b->device);
+    if (b->origin) cudaStreamSynchronize(b->origin);
+    release(b);
+  }
+  delete b;
+}
+
+}  // extern "C"

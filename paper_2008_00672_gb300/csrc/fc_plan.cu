@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -98,6 +99,10 @@ struct fc_plan {
   size_t smem_tx = 0, smem_rx = 0, smem_ofdm = 0;
   int syms_per_stream = 0;
   fc_sizes sizes{};
+  // launch choices measured by fc_plan_autotune, per (n_streams, direction); execute
+  // calls without an entry use the occupancy heuristic pick_split
+  mutable std::mutex tune_mu;
+  std::map<std::pair<int, int>, std::pair<int, int>> tuned;   // -> (split index, generic kernels)
 };
 
 namespace {
@@ -601,6 +606,50 @@ int check_io(const fc_plan* plan, int32_t n_streams, const void* in, const void*
   return FC_OK;
 }
 
+// (split index, generic) for this call: the autotuned choice if there is one
+std::pair<int, int> choose(const fc_plan* pl, int n_streams, int dir) {
+  {
+    std::lock_guard<std::mutex> lock(pl->tune_mu);
+    auto it = pl->tuned.find({n_streams, dir});
+    if (it != pl->tuned.end()) return it->second;
+  }
+  return {(int)pick_split(pl, n_streams), 0};
+}
+
+cudaError_t launch_tx(const fc_plan* plan, int n_streams, const float2* grid, float2* wave, float2* workspace,
+                      cudaStream_t st, std::pair<int, int> c) {
+  const size_t k = (size_t)c.first;
+  // float4 reductions of the warp kernel need a 16-byte aligned waveform
+  if (plan->warp_path && !c.second && ((uintptr_t)wave & 15) == 0)
+    return fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams,
+                                  plan->h.frame_len, grid, wave, st);
+  if (plan->h.mode == FC_SYMBOL_SYNC)
+    return fc_launch_tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, grid,
+                             wave, plan->smem_tx, st);
+  cudaError_t e = fc_launch_ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid, workspace,
+                                     plan->smem_ofdm, st);
+  if (e == cudaSuccess)
+    e = fc_launch_tx_cont(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, workspace,
+                          wave, plan->smem_tx, st);
+  return e;
+}
+
+cudaError_t launch_rx(const fc_plan* plan, int n_streams, const float2* wave, float2* grid, float2* workspace,
+                      cudaStream_t st, std::pair<int, int> c) {
+  const size_t k = (size_t)c.first;
+  if (plan->warp_path && !c.second)
+    return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams,
+                                  wave, grid, st);
+  if (plan->h.mode == FC_SYMBOL_SYNC)
+    return fc_launch_rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, wave,
+                             grid, plan->smem_rx, st);
+  cudaError_t e = fc_launch_rx_cont(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams,
+                                    wave, workspace, plan->smem_rx, st);
+  if (e == cudaSuccess)
+    e = fc_launch_ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, grid, plan->smem_ofdm, st);
+  return e;
+}
+
 }  // namespace
 
 int fc_internal_fail(int code, const char* msg) { return fail(code, msg); }
@@ -671,24 +720,8 @@ int fc_tx_synthesize(const fc_plan* plan, int32_t n_streams, const void* grid_in
   if (rc != FC_OK || n_streams == 0) return rc;
   DeviceGuard dg(plan->device);
   if (!dg.ok) return fail(FC_ERR_CUDA, "cudaSetDevice failed");
-  cudaStream_t st = (cudaStream_t)stream;
-  const size_t k = pick_split(plan, n_streams);
-  const float2* grid = (const float2*)grid_in;
-  float2* wave = (float2*)wave_out;
-  cudaError_t e;
-  if (plan->warp_path && ((uintptr_t)wave_out & 15) == 0) {   // float4 reductions need 16-byte alignment
-    e = fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams,
-                               plan->h.frame_len, grid, wave, st);
-  } else if (plan->h.mode == FC_SYMBOL_SYNC) {
-    e = fc_launch_tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, grid, wave,
-                          plan->smem_tx, st);
-  } else {
-    e = fc_launch_ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid, (float2*)workspace, plan->smem_ofdm,
-                           st);
-    if (e == cudaSuccess)
-      e = fc_launch_tx_cont(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams,
-                            (const float2*)workspace, wave, plan->smem_tx, st);
-  }
+  const cudaError_t e = launch_tx(plan, n_streams, (const float2*)grid_in, (float2*)wave_out, (float2*)workspace,
+                                  (cudaStream_t)stream, choose(plan, n_streams, FC_TX));
   return e == cudaSuccess ? FC_OK : cuda_fail(e, "TX kernel launch");
 }
 
@@ -698,25 +731,76 @@ int fc_rx_analyze(const fc_plan* plan, int32_t n_streams, const void* wave_in, v
   if (rc != FC_OK || n_streams == 0) return rc;
   DeviceGuard dg(plan->device);
   if (!dg.ok) return fail(FC_ERR_CUDA, "cudaSetDevice failed");
-  cudaStream_t st = (cudaStream_t)stream;
-  const size_t k = pick_split(plan, n_streams);
-  const float2* wave = (const float2*)wave_in;
-  float2* grid = (float2*)grid_out;
-  cudaError_t e;
-  if (plan->warp_path) {
-    e = fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams, wave,
-                               grid, st);
-  } else if (plan->h.mode == FC_SYMBOL_SYNC) {
-    e = fc_launch_rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, wave, grid,
-                          plan->smem_rx, st);
-  } else {
-    e = fc_launch_rx_cont(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, wave,
-                          (float2*)workspace, plan->smem_rx, st);
-    if (e == cudaSuccess)
-      e = fc_launch_ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, (const float2*)workspace, grid,
-                               plan->smem_ofdm, st);
-  }
+  const cudaError_t e = launch_rx(plan, n_streams, (const float2*)wave_in, (float2*)grid_out, (float2*)workspace,
+                                  (cudaStream_t)stream, choose(plan, n_streams, FC_RX));
   return e == cudaSuccess ? FC_OK : cuda_fail(e, "RX kernel launch");
+}
+
+int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* stream) {
+  if (!plan) return fail(FC_ERR_INVALID, "plan is NULL");
+  if (n_streams < 1 || reps < 1) return fail(FC_ERR_INVALID, "need n_streams >= 1 and reps >= 1");
+  DeviceGuard dg(plan->device);
+  if (!dg.ok) return fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  const fc_sizes& z = plan->sizes;
+  const size_t n_grid = (size_t)n_streams * z.grid_len, n_wave = (size_t)n_streams * z.wave_len;
+  const size_t ws_bytes = (size_t)n_streams * z.workspace_per_stream;
+  // tuning buffers (zeros: the kernels' time does not depend on the values)
+  unsigned char* mem = nullptr;
+  const size_t bytes = (n_grid + n_wave) * sizeof(float2) + ws_bytes + 256;
+  cudaError_t e = cudaMalloc(&mem, bytes);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? fail(FC_ERR_NOMEM, "autotune buffers")
+                                                              : cuda_fail(e, "cudaMalloc");
+  e = cudaMemsetAsync(mem, 0, bytes, st);
+  float2* grid = (float2*)mem;
+  float2* wave = grid + n_grid;
+  float2* ws = (float2*)(((uintptr_t)(wave + n_wave) + 255) & ~(uintptr_t)255);
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  std::pair<int, int> best[2] = {{0, 0}, {0, 0}};
+  for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir) {
+    float best_ms = 1e30f;
+    for (int generic = 0; generic <= (plan->warp_path ? 1 : 0) && e == cudaSuccess; ++generic) {
+      for (int k = 0; k < (int)plan->splits.size() && e == cudaSuccess; ++k) {
+        const std::pair<int, int> c{k, generic};
+        auto run = [&]() {
+          return dir == FC_TX ? launch_tx(plan, n_streams, grid, wave, ws, st, c)
+                              : launch_rx(plan, n_streams, wave, grid, ws, st, c);
+        };
+        for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = run();
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = run();
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e == cudaSuccess && ms < best_ms) {
+          best_ms = ms;
+          best[dir] = c;
+        }
+      }
+    }
+  }
+  for (cudaEvent_t x : ev)
+    if (x) cudaEventDestroy(x);
+  cudaStreamSynchronize(st);
+  cudaFree(mem);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  std::lock_guard<std::mutex> lock(plan->tune_mu);
+  plan->tuned[{n_streams, FC_TX}] = best[FC_TX];
+  plan->tuned[{n_streams, FC_RX}] = best[FC_RX];
+  return FC_OK;
+}
+
+int fc_plan_choice(const fc_plan* plan, int32_t n_streams, int32_t direction, int32_t* chunks_per_stream,
+                   int32_t* generic_kernels) {
+  if (!plan || (direction != FC_TX && direction != FC_RX) || n_streams < 1)
+    return fail(FC_ERR_INVALID, "bad plan, direction or n_streams");
+  const std::pair<int, int> c = choose(plan, n_streams, direction);
+  if (chunks_per_stream) *chunks_per_stream = plan->splits[c.first];
+  if (generic_kernels) *generic_kernels = (plan->warp_path && !c.second) ? 0 : 1;
+  return FC_OK;
 }
 
 void fc_plan_destroy(fc_plan* plan) {

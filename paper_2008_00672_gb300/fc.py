@@ -23,10 +23,12 @@ FC_CONTINUOUS, FC_SYMBOL_SYNC = 0, 1
 FC_FLAG_GENERIC_KERNELS = 1
 FC_FLAG_REDUCED_RX = 2
 FC_OLA, FC_OLS = 0, 1
+FC_TX, FC_RX = 0, 1
 
 EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize", "fc_rx_analyze", "fc_plan_destroy",
             "fc_status_string", "fc_last_error", "fc_tx_synthesize_static", "fc_state_create", "fc_state_reset",
-            "fc_state_destroy", "fc_tx_synthesize_stream", "fc_rx_analyze_stream")
+            "fc_state_destroy", "fc_tx_synthesize_stream", "fc_rx_analyze_stream", "fc_plan_autotune",
+            "fc_plan_choice", "fc_batch_create", "fc_batch_launch", "fc_batch_destroy")
 
 
 class FcGroup(ctypes.Structure):
@@ -51,6 +53,12 @@ class FcSizes(ctypes.Structure):
     _fields_ = [("grid_len", ctypes.c_int64), ("wave_len", ctypes.c_int64), ("nominal_len", ctypes.c_int64),
                 ("workspace_per_stream", ctypes.c_int64), ("tx_kernels", ctypes.c_int32),
                 ("rx_kernels", ctypes.c_int32), ("slot_len", ctypes.c_int64), ("stream_delay", ctypes.c_int64)]
+
+
+class FcBatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("state", ctypes.c_void_p), ("direction", ctypes.c_int32),
+                ("n_streams", ctypes.c_int32), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
 _lib = None
@@ -90,6 +98,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fc_tx_synthesize_stream.restype = ctypes.c_int
         lib.fc_rx_analyze_stream.argtypes = [vp, vp, vp, vp, vp, sz, vp]
         lib.fc_rx_analyze_stream.restype = ctypes.c_int
+        lib.fc_plan_autotune.argtypes = [vp, i32, i32, vp]
+        lib.fc_plan_autotune.restype = ctypes.c_int
+        lib.fc_plan_choice.argtypes = [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.fc_plan_choice.restype = ctypes.c_int
+        lib.fc_batch_create.argtypes = [ctypes.POINTER(FcBatchItem), i32, i32, i32, ctypes.POINTER(vp)]
+        lib.fc_batch_create.restype = ctypes.c_int
+        lib.fc_batch_launch.argtypes = [vp, vp]
+        lib.fc_batch_launch.restype = ctypes.c_int
+        lib.fc_batch_destroy.argtypes = [vp]
+        lib.fc_batch_destroy.restype = None
         lib.fc_plan_destroy.argtypes = [vp]
         lib.fc_plan_destroy.restype = None
         lib.fc_status_string.argtypes = [ctypes.c_int]
@@ -204,6 +222,35 @@ def fc_rx_analyze_stream(plan, state, slot_in: int, grid_out: int, workspace: in
                                                int(workspace_bytes), stream or None), "fc_rx_analyze_stream")
 
 
+def fc_plan_autotune(plan, n_streams: int, reps: int = 5, stream: int = 0):
+    _check(load_library().fc_plan_autotune(plan, int(n_streams), int(reps), stream or None), "fc_plan_autotune")
+
+
+def fc_plan_choice(plan, n_streams: int, direction: int):
+    """(chunks per stream, generic kernels) an execute call with n_streams will use."""
+    k, g = ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().fc_plan_choice(plan, int(n_streams), int(direction), ctypes.byref(k), ctypes.byref(g)),
+           "fc_plan_choice")
+    return int(k.value), int(g.value)
+
+
+def fc_batch_create(items, n_lanes: int = 8, use_graph: bool = True) -> ctypes.c_void_p:
+    arr = (FcBatchItem * len(items))(*items)
+    h = ctypes.c_void_p()
+    _check(load_library().fc_batch_create(arr, len(items), int(n_lanes), int(bool(use_graph)), ctypes.byref(h)),
+           "fc_batch_create")
+    return h
+
+
+def fc_batch_launch(batch, stream: int = 0):
+    _check(load_library().fc_batch_launch(batch, stream or None), "fc_batch_launch")
+
+
+def fc_batch_destroy(batch):
+    if batch:
+        load_library().fc_batch_destroy(batch)
+
+
 def fc_plan_destroy(plan):
     if plan:
         load_library().fc_plan_destroy(plan)
@@ -244,6 +291,13 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def autotune(self, n_streams: int, reps: int = 5, stream=None):
+        """Measure every launch shape for n_streams streams and keep the fastest."""
+        fc_plan_autotune(self.handle, n_streams, reps, self._stream_handle(stream))
+
+    def choice(self, n_streams: int, direction: int):
+        return fc_plan_choice(self.handle, n_streams, direction)
 
     def workspace(self, n_streams: int):
         """A device workspace large enough for n_streams (allocated by torch, reused)."""
@@ -334,3 +388,38 @@ class State:
                              ws.data_ptr() if ws is not None else 0,
                              ws.numel() * ws.element_size() if ws is not None else 0, Plan._stream_handle(stream))
         return grid_out
+
+
+class Batch:
+    """Owns one fc_batch over (plan, direction, input tensor, output tensor[, state])
+    items; launch() runs them all (forked over lanes, replayed as a CUDA graph)."""
+
+    def __init__(self, items, n_lanes: int = 8, use_graph: bool = True):
+        self._keep = []
+        c_items = []
+        for it in items:
+            plan, direction, src, dst = it[:4]
+            state = it[4] if len(it) > 4 else None
+            if state is not None:
+                ls, ld = (plan.grid_len, plan.slot_len) if direction == FC_TX else (plan.slot_len, plan.grid_len)
+            else:
+                ls, ld = (plan.grid_len, plan.wave_len) if direction == FC_TX else (plan.wave_len, plan.grid_len)
+            n = Plan._streams(src, ls, dst, ld)
+            self._keep.append((plan, src, dst, state))
+            c_items.append(FcBatchItem(plan.handle.value, state.handle.value if state is not None else None,
+                                       int(direction), n, src.data_ptr(), dst.data_ptr(), None, 0))
+        self.handle = fc_batch_create(c_items, n_lanes, use_graph)
+
+    def launch(self, stream=None):
+        fc_batch_launch(self.handle, Plan._stream_handle(stream))
+
+    def close(self):
+        if self.handle:
+            fc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

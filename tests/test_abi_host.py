@@ -139,3 +139,21 @@ def test_stream_sizes_refuse_unequal_group_slots(fc):
     sb = wl.Subband(16, 16, 10, -4, 1, wl.rc_transition_weights(16, 10, 2))
     geom = wl.Geometry(fo.SYMBOL_SYNC, fo.OLA, fo.OLS, (ga, gb), (sa, sb))
     assert fc.fc_geometry_check(geom).slot_len == 0
+
+
+def test_uneven_carriers_plan_on_the_host(fc):
+    """Every carrier of the uneven multi-carrier workload is a valid geometry with the
+    oracle's frame and grid sizes, and the draw covers every bandwidth and SCS."""
+    carriers = wl.config_uneven_carriers()
+    assert len(carriers) == 64
+    seen_bw, seen_scs = set(), set()
+    for c in carriers:
+        s = fc.fc_geometry_check(c)
+        assert s.wave_len == fo.frame_len(c) and s.grid_len == c.grid_len(), c.name
+        _, bw, scs, _ = c.name.split("_")
+        seen_bw.add(bw)
+        seen_scs.add(scs)
+        n = c.groups[0].n_long
+        assert n & (n - 1) == 0 and 128 <= n <= 4096
+    assert seen_bw == {"5MHz", "10MHz", "20MHz", "50MHz", "100MHz"}
+    assert seen_scs == {"15kHz", "30kHz", "60kHz"}

@@ -1,0 +1,124 @@
+"""GPU: batch executor (uneven carriers side by side, CUDA graph replay) and the
+autotuner. Every batched result must equal the item's own call (same kernels, so up
+to the order of floating-point reductions) and the FP64 oracle (<= 1e-5)."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import fc_oracle as fo
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2008_00672_gb300 import build
+    build.build()
+    return torch
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def c64(a):
+    return np.asarray(a).astype(np.complex64)
+
+
+def setup(torch, carriers, n_streams, seed):
+    from paper_2008_00672_gb300 import Plan
+    out = []
+    for i, geom in enumerate(carriers):
+        plan = Plan(geom)
+        grid = c64(wl.qam_grid(geom, n_streams, seed + 31 * i))
+        out.append(dict(geom=geom, plan=plan, grid_np=grid.astype(np.complex128),
+                        grid=torch.from_numpy(grid).cuda(),
+                        wave=torch.zeros((n_streams, plan.wave_len), dtype=torch.complex64, device="cuda"),
+                        rx_in=None, est=torch.zeros((n_streams, plan.grid_len), dtype=torch.complex64,
+                                                    device="cuda")))
+    return out
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_uneven_carriers_match_oracle(torch_cuda, use_graph):
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import FC_RX, FC_TX, Batch
+    carriers = wl.config_uneven_carriers(seed=1400, n_carriers=8, n_slots=1)
+    S = 2
+    cs = setup(torch, carriers, S, 500)
+    # RX inputs: the oracle waveform of each carrier plus 30 dB AWGN
+    for j, c in enumerate(cs):
+        ref = [fo.tx_frame(c["geom"], c["grid_np"][s]) for s in range(S)]
+        c["ref_tx"] = ref
+        x = np.stack([c64(wl.awgn(ref[s], 30.0, 77 + 13 * j + s)).astype(np.complex128) for s in range(S)])
+        c["rx_np"] = x
+        c["rx_in"] = torch.from_numpy(c64(x)).cuda()
+    items = [(c["plan"], FC_TX, c["grid"], c["wave"]) for c in cs] + \
+            [(c["plan"], FC_RX, c["rx_in"], c["est"]) for c in cs]
+    b = Batch(items, n_lanes=4, use_graph=use_graph)
+    for _ in range(2):                       # second launch replays the graph
+        for c in cs:
+            c["wave"].zero_()
+            c["est"].zero_()
+        b.launch()
+        torch.cuda.synchronize()
+        for c in cs:
+            w, e = c["wave"].cpu().numpy(), c["est"].cpu().numpy()
+            for s in range(S):
+                assert rel(w[s], c["ref_tx"][s]) <= TOL, c["geom"].name
+                assert rel(e[s], fo.rx_frame(c["geom"], c["rx_np"][s])) <= TOL, c["geom"].name
+    # new inputs in the same buffers: the replayed graph reads them
+    for i, c in enumerate(cs):
+        g2 = c64(wl.qam_grid(c["geom"], S, 900 + i))
+        c["grid"].copy_(torch.from_numpy(g2))
+        c["ref_tx"] = [fo.tx_frame(c["geom"], g2[s].astype(np.complex128)) for s in range(S)]
+    b.launch()
+    torch.cuda.synchronize()
+    for c in cs:
+        w = c["wave"].cpu().numpy()
+        for s in range(S):
+            assert rel(w[s], c["ref_tx"][s]) <= TOL, c["geom"].name
+    b.close()
+    for c in cs:
+        c["plan"].close()
+
+
+def test_batch_equals_single_calls(torch_cuda):
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import FC_TX, Batch
+    carriers = wl.config_uneven_carriers(seed=1401, n_carriers=12, n_slots=1)
+    cs = setup(torch, carriers, 3, 600)
+    b = Batch([(c["plan"], FC_TX, c["grid"], c["wave"]) for c in cs], n_lanes=6, use_graph=True)
+    b.launch()
+    torch.cuda.synchronize()
+    for c in cs:
+        single = torch.empty_like(c["wave"])
+        c["plan"].tx_synthesize(c["grid"], single)
+        torch.cuda.synchronize()
+        assert rel(c["wave"].cpu().numpy(), single.cpu().numpy()) < 1e-6, c["geom"].name
+    b.close()
+
+
+def test_autotune_keeps_results_and_records_a_choice(torch_cuda):
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import FC_RX, FC_TX, Plan
+    geom = wl.config_mixed_20mhz()
+    plan = Plan(geom)
+    S = 40
+    grid = torch.from_numpy(c64(wl.qam_grid(geom, S, 3))).cuda()
+    before = torch.empty((S, plan.wave_len), dtype=torch.complex64, device="cuda")
+    plan.tx_synthesize(grid, before)
+    plan.autotune(S, reps=3)
+    for d in (FC_TX, FC_RX):
+        k, generic = plan.choice(S, d)
+        assert k in (1, 2, 4, 8, 16, 32, 64) and generic in (0, 1)
+    after = torch.empty_like(before)
+    plan.tx_synthesize(grid, after)
+    torch.cuda.synchronize()
+    ref = fo.tx_frame(geom, c64(wl.qam_grid(geom, S, 3))[S - 1].astype(np.complex128))
+    assert rel(after[S - 1].cpu().numpy(), ref) <= TOL
+    assert rel(after.cpu().numpy(), before.cpu().numpy()) < 1e-6
+    plan.close()

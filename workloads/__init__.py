@@ -166,6 +166,61 @@ def config_100mhz(n_slots: int = 10) -> Geometry:
                     qam_order=64)
 
 
+# NR sampling rates with power-of-two FFT sizes per channel bandwidth (MHz -> Msps)
+NR_RATE_MSPS = {5: 7.68, 10: 15.36, 20: 30.72, 50: 61.44, 100: 122.88}
+# (bandwidth MHz, SCS kHz) pairs NR defines: no 100 MHz at 15 kHz, no 5 MHz at 60 kHz
+NR_BW_SCS = tuple((bw, scs) for bw in (5, 10, 20, 50, 100) for scs in (15, 30, 60)
+                  if (bw, scs) not in ((100, 15), (5, 60)))
+
+
+def _short_len(n_active: int, n_long: int, n_tb: int = 8) -> int:
+    """Smallest power of two holding the active bins plus both transition bands."""
+    L = 16
+    while L < n_active + 2 * n_tb:
+        L *= 2
+    return min(L, n_long)
+
+
+def config_uneven_carriers(seed: int = 1400, n_carriers: int = 64, n_slots: int = 4) -> list:
+    """Independent carriers of uneven shape, one geometry each.
+
+    Per carrier (seeded PCG64): a (bandwidth, SCS) pair NR defines, drawn uniformly;
+    the NR sampling rate of that bandwidth, so N = f_s / SCS is a power of two
+    (128 .. 4096); 1-8 subbands of 1-273 PRB each, drawn one after another while
+    the total, with a 2-PRB guard between neighbours, stays within 90 % of the
+    bandwidth; each subband's short transform is the smallest power of two holding
+    its active subcarriers and 8 raised-cosine transition bins per side. Subbands sit
+    side by side from the low band edge, centred on DC as a whole. Symbol-synchronized
+    FC (OLA TX, OLS RX), n_slots slots of 14 symbols with NR normal CP, QPSK/16/64-QAM.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n_carriers):
+        bw, scs = NR_BW_SCS[int(rng.integers(len(NR_BW_SCS)))]
+        n_long = int(round(NR_RATE_MSPS[bw] * 1000 / scs))
+        budget = int(0.9 * bw * 1000 // (12 * scs))
+        prbs = []
+        for _ in range(int(rng.integers(1, 9))):
+            left = budget - sum(prbs) - 2 * len(prbs)
+            if left < 1:
+                break
+            prbs.append(int(rng.integers(1, min(273, left) + 1)))
+        width = 12 * (sum(prbs) + 2 * (len(prbs) - 1))
+        lo = -(width // 2)
+        subs = []
+        for prb in prbs:
+            n_act = 12 * prb
+            L = _short_len(n_act, n_long)
+            subs.append(Subband(l_short=L, l_ofdm=L, n_active=n_act, centre_bin=lo + n_act // 2, group=0,
+                                weights=rc_transition_weights(L, n_act, 8)))
+            lo += n_act + 24
+        g = Group(n_long=n_long, n_overlap=n_long // 2, n_cp=nr_normal_cp(n_long, scs, 14 * n_slots))
+        qam = (4, 16, 64)[int(rng.integers(3))]
+        out.append(Geometry(SYMBOL_SYNC, OLA, OLS, (g,), tuple(subs),
+                            name=f"carrier{i}_{bw}MHz_{scs}kHz_{len(subs)}sb", qam_order=qam))
+    return out
+
+
 NAMED = {
     "single5": config_single_5mhz,
     "mixed20": config_mixed_20mhz,
