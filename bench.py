@@ -295,6 +295,45 @@ def uneven_carriers_bench(torch, dev, st, steps: int) -> dict:
                                "batch_graph_autotuned": round(samples / ms_tuned / 1e3, 1)}}
 
 
+def serving_bench(torch, dev, n_requests: int) -> dict:
+    """Serving loop: Poisson slot requests at 2000/s with per-carrier TDD patterns,
+    replayed in real time by the native server; latency p50/p99 against the 0.5 ms
+    budget. Two carrier sets: 16 carriers drawn like the uneven workload, and the
+    fixed 100 MHz / 273 PRB carrier alone."""
+    import numpy as np
+    import workloads as wl
+    from paper_2008_00672_gb300 import Server
+
+    def one(carriers, n_req, seed):
+        srv = Server(device=dev.index or 0, n_lanes=8, hbm_reserve_bytes=4 << 30)
+        bufs = []
+        rng = np.random.default_rng(seed)
+        for g in carriers:
+            cid = srv.add_carrier(g)
+            z = srv.sizes[cid]
+            grid = torch.from_numpy(((rng.choice([-1.0, 1.0], z.grid_len) + 1j * rng.choice([-1.0, 1.0], z.grid_len))
+                                     / np.sqrt(2)).astype(np.complex64)).pin_memory()
+            slot = torch.zeros(z.slot_len, dtype=torch.complex64).pin_memory()
+            slot_in = torch.from_numpy((0.01 * rng.standard_normal(2 * z.slot_len)).astype(np.float32)
+                                       ).view(torch.complex64).pin_memory()
+            est = torch.zeros(z.grid_len, dtype=torch.complex64).pin_memory()
+            bufs.append(((grid, slot), (slot_in, est)))
+        trace = wl.serving_trace(len(carriers), n_req, 2000.0, seed)
+        reqs = [(t, c, d, bufs[c][d][0], bufs[c][d][1]) for t, c, d in trace]
+        lat = np.asarray(srv.run(reqs)) * 1e3
+        srv.close()
+        lat.sort()
+        return {"requests": n_req, "rate_per_s": 2000, "carriers": len(carriers),
+                "p50_ms": round(float(lat[len(lat) // 2]), 4), "p99_ms": round(float(lat[int(0.99 * len(lat))]), 4),
+                "max_ms": round(float(lat[-1]), 4), "within_budget": round(float(np.mean(lat <= 0.5)), 4)}
+
+    mix = wl.config_uneven_carriers(seed=wl.default_seed(5), n_carriers=16, n_slots=1, whole_cp_period=True)
+    return {"budget_ms": 0.5,
+            "uneven_16_carriers": one(mix, n_requests, wl.default_seed(5)),
+            "nr100mhz_carrier": one([wl.config_100mhz(1)], max(1000, n_requests // 4), wl.default_seed(5) + 1),
+            "latency": "arrival to completion of H2D copy + stream call + D2H copy, host clock"}
+
+
 def run_gpu(args, rank: int, world: int, local_rank: int):
     import numpy as np
     import torch
@@ -437,6 +476,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
 
     # ---- uneven carriers: 64 independent geometries in one batch (graph + lanes) ----
     uneven = uneven_carriers_bench(torch, dev, st, args.steps)
+    serving = serving_bench(torch, dev, args.serve_requests) if args.serve_requests > 0 else None
 
     # ---- accuracy of the timed path against the FP64 oracle (one sampled stream) ----
     from oracle import fc_oracle as fo
@@ -500,7 +540,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
            "latency_1stream_ms": {"p50": round(lat[len(lat) // 2], 4), "p99": round(lat[int(0.99 * len(lat))], 4),
                                   "slot_budget_ms": 1.0},
            "accuracy": {"tx_rel_rms_vs_oracle": tx_err, "rx_rel_rms_vs_oracle": rx_err, "evm_db_awgn30": evm_db},
-           "rx_variants": rx_variants, "uneven_carriers": uneven,
+           "rx_variants": rx_variants, "uneven_carriers": uneven, "serving": serving,
            "clocks": clk, "gpu_launches": args.steps * (plan.tx_kernels + plan.rx_kernels)}
     print(json.dumps(out), flush=True)
 
@@ -513,6 +553,8 @@ def main():
     ap.add_argument("--streams", type=int, default=2048)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=20000,
+                    help="slot requests of the serving-loop measurement (0 skips it)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

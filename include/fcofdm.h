@@ -297,6 +297,45 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
 int fc_batch_launch(fc_batch* batch, void* stream);
 void fc_batch_destroy(fc_batch* batch);
 
+/*
+ * Serving loop (no counterpart in the paper; the deployment around the FC path).
+ * A server holds admitted carriers, each with a device-resident plan, a one-stream
+ * fc_state and one slot of device input/output, and serves slot requests of those
+ * carriers as they arrive. fc_server_run replays a request list in real time: each
+ * request is issued at its arrival time on its carrier's lane (host-to-device copy of
+ * the input, the stream call, device-to-host copy of the output), with no batch
+ * boundary, and its latency (arrival to observed completion, host clock) is returned.
+ * Requests of one carrier run in order, so each carrier's results equal its own stream
+ * calls whatever else the server is doing.
+ */
+typedef struct fc_server fc_server;
+
+typedef struct fc_serve_request {
+  double arrival_s;        /* seconds after the start of fc_server_run; non-decreasing  */
+  int32_t carrier;         /* id from fc_server_add_carrier                             */
+  int32_t direction;       /* FC_TX: grid in, slot_len samples out; FC_RX: the reverse  */
+  const void* host_in;     /* host complex64 (page-locked memory for asynchronous copies) */
+  void* host_out;
+} fc_serve_request;
+
+/* n_lanes CUDA streams; admission keeps hbm_reserve_bytes of device memory free. */
+int fc_server_create(int32_t device, int32_t n_lanes, uint64_t hbm_reserve_bytes, fc_server** out);
+
+/* Admits a carrier (its geometry must stream: fc_sizes.slot_len > 0). FC_ERR_NOMEM,
+   with nothing allocated, when its plan, state and buffers would not fit in the free
+   device memory above the reserve. */
+int fc_server_add_carrier(fc_server* server, const fc_geometry* geometry, int32_t* carrier_id);
+
+/* The sizes of an admitted carrier (grid_len, slot_len, ...). */
+int fc_server_carrier_sizes(const fc_server* server, int32_t carrier, fc_sizes* out);
+
+/* Replays `requests` (sorted by arrival) in real time; latency_s[i] gets request i's
+   latency in seconds. Returns when every request has completed. */
+int fc_server_run(fc_server* server, const fc_serve_request* requests, int32_t n_requests, double* latency_s);
+
+/* Frees every carrier and the lanes (after synchronising them). Safe on NULL. */
+void fc_server_destroy(fc_server* server);
+
 /* Frees the plan's device tables. Safe on NULL. Must not race with running calls. */
 void fc_plan_destroy(fc_plan* plan);
 

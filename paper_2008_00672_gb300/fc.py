@@ -28,7 +28,8 @@ FC_TX, FC_RX = 0, 1
 EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize", "fc_rx_analyze", "fc_plan_destroy",
             "fc_status_string", "fc_last_error", "fc_tx_synthesize_static", "fc_state_create", "fc_state_reset",
             "fc_state_destroy", "fc_tx_synthesize_stream", "fc_rx_analyze_stream", "fc_plan_autotune",
-            "fc_plan_choice", "fc_batch_create", "fc_batch_launch", "fc_batch_destroy")
+            "fc_plan_choice", "fc_batch_create", "fc_batch_launch", "fc_batch_destroy", "fc_server_create",
+            "fc_server_add_carrier", "fc_server_carrier_sizes", "fc_server_run", "fc_server_destroy")
 
 
 class FcGroup(ctypes.Structure):
@@ -59,6 +60,11 @@ class FcBatchItem(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("state", ctypes.c_void_p), ("direction", ctypes.c_int32),
                 ("n_streams", ctypes.c_int32), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class FcServeRequest(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("carrier", ctypes.c_int32), ("direction", ctypes.c_int32),
+                ("host_in", ctypes.c_void_p), ("host_out", ctypes.c_void_p)]
 
 
 _lib = None
@@ -108,6 +114,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fc_batch_launch.restype = ctypes.c_int
         lib.fc_batch_destroy.argtypes = [vp]
         lib.fc_batch_destroy.restype = None
+        lib.fc_server_create.argtypes = [i32, i32, ctypes.c_uint64, ctypes.POINTER(vp)]
+        lib.fc_server_create.restype = ctypes.c_int
+        lib.fc_server_add_carrier.argtypes = [vp, ctypes.POINTER(FcGeometry), ctypes.POINTER(i32)]
+        lib.fc_server_add_carrier.restype = ctypes.c_int
+        lib.fc_server_carrier_sizes.argtypes = [vp, i32, ctypes.POINTER(FcSizes)]
+        lib.fc_server_carrier_sizes.restype = ctypes.c_int
+        lib.fc_server_run.argtypes = [vp, ctypes.POINTER(FcServeRequest), i32, ctypes.POINTER(ctypes.c_double)]
+        lib.fc_server_run.restype = ctypes.c_int
+        lib.fc_server_destroy.argtypes = [vp]
+        lib.fc_server_destroy.restype = None
         lib.fc_plan_destroy.argtypes = [vp]
         lib.fc_plan_destroy.restype = None
         lib.fc_status_string.argtypes = [ctypes.c_int]
@@ -249,6 +265,39 @@ def fc_batch_launch(batch, stream: int = 0):
 def fc_batch_destroy(batch):
     if batch:
         load_library().fc_batch_destroy(batch)
+
+
+def fc_server_create(device: int = 0, n_lanes: int = 8, hbm_reserve_bytes: int = 0) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().fc_server_create(int(device), int(n_lanes), int(hbm_reserve_bytes), ctypes.byref(h)),
+           "fc_server_create")
+    return h
+
+
+def fc_server_add_carrier(server, geom) -> int:
+    geo, _keep = _marshal_geometry(geom)
+    cid = ctypes.c_int32(-1)
+    _check(load_library().fc_server_add_carrier(server, ctypes.byref(geo), ctypes.byref(cid)), "fc_server_add_carrier")
+    return int(cid.value)
+
+
+def fc_server_carrier_sizes(server, carrier: int) -> FcSizes:
+    out = FcSizes()
+    _check(load_library().fc_server_carrier_sizes(server, int(carrier), ctypes.byref(out)), "fc_server_carrier_sizes")
+    return out
+
+
+def fc_server_run(server, requests) -> list:
+    """requests: sequence of FcServeRequest; returns the latencies in seconds."""
+    arr = (FcServeRequest * len(requests))(*requests)
+    lat = (ctypes.c_double * len(requests))()
+    _check(load_library().fc_server_run(server, arr, len(requests), lat), "fc_server_run")
+    return list(lat)
+
+
+def fc_server_destroy(server):
+    if server:
+        load_library().fc_server_destroy(server)
 
 
 def fc_plan_destroy(plan):
@@ -416,6 +465,44 @@ class Batch:
     def close(self):
         if self.handle:
             fc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owns one fc_server. add_carrier(geom) -> id; run(requests) replays
+    (arrival_s, carrier, direction, host_in, host_out) requests in real time with
+    page-locked CPU tensors and returns the latencies (seconds)."""
+
+    def __init__(self, device: int = 0, n_lanes: int = 8, hbm_reserve_bytes: int = 0):
+        self.handle = fc_server_create(device, n_lanes, hbm_reserve_bytes)
+        self.sizes = []
+
+    def add_carrier(self, geom) -> int:
+        cid = fc_server_add_carrier(self.handle, geom)
+        self.sizes.append(fc_server_carrier_sizes(self.handle, cid))
+        return cid
+
+    def run(self, requests):
+        import torch
+        reqs = []
+        for t, cid, direction, h_in, h_out in requests:
+            z = self.sizes[cid]
+            n_in, n_out = (z.grid_len, z.slot_len) if direction == FC_TX else (z.slot_len, z.grid_len)
+            for x, n in ((h_in, n_in), (h_out, n_out)):
+                if x.dtype != torch.complex64 or x.is_cuda or not x.is_contiguous() or x.numel() != n:
+                    raise ValueError("expected contiguous complex64 host tensors of the carrier's sizes")
+            reqs.append(FcServeRequest(float(t), int(cid), int(direction), h_in.data_ptr(), h_out.data_ptr()))
+        return fc_server_run(self.handle, reqs)
+
+    def close(self):
+        if self.handle:
+            fc_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

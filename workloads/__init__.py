@@ -181,7 +181,8 @@ def _short_len(n_active: int, n_long: int, n_tb: int = 8) -> int:
     return min(L, n_long)
 
 
-def config_uneven_carriers(seed: int = 1400, n_carriers: int = 64, n_slots: int = 4) -> list:
+def config_uneven_carriers(seed: int = 1400, n_carriers: int = 64, n_slots: int = 4,
+                           whole_cp_period: bool = False) -> list:
     """Independent carriers of uneven shape, one geometry each.
 
     Per carrier (seeded PCG64): a (bandwidth, SCS) pair NR defines, drawn uniformly;
@@ -192,6 +193,8 @@ def config_uneven_carriers(seed: int = 1400, n_carriers: int = 64, n_slots: int 
     its active subcarriers and 8 raised-cosine transition bins per side. Subbands sit
     side by side from the low band edge, centred on DC as a whole. Symbol-synchronized
     FC (OLA TX, OLS RX), n_slots slots of 14 symbols with NR normal CP, QPSK/16/64-QAM.
+    whole_cp_period: a 60 kHz carrier gets 2 n_slots slots, so that every frame holds
+    whole 0.5 ms CP periods (the long CP every 28 symbols) and repeats slot after slot.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
@@ -214,10 +217,33 @@ def config_uneven_carriers(seed: int = 1400, n_carriers: int = 64, n_slots: int 
             subs.append(Subband(l_short=L, l_ofdm=L, n_active=n_act, centre_bin=lo + n_act // 2, group=0,
                                 weights=rc_transition_weights(L, n_act, 8)))
             lo += n_act + 24
-        g = Group(n_long=n_long, n_overlap=n_long // 2, n_cp=nr_normal_cp(n_long, scs, 14 * n_slots))
+        slots = n_slots * (2 if whole_cp_period and scs == 60 else 1)
+        g = Group(n_long=n_long, n_overlap=n_long // 2, n_cp=nr_normal_cp(n_long, scs, 14 * slots))
         qam = (4, 16, 64)[int(rng.integers(3))]
         out.append(Geometry(SYMBOL_SYNC, OLA, OLS, (g,), tuple(subs),
                             name=f"carrier{i}_{bw}MHz_{scs}kHz_{len(subs)}sb", qam_order=qam))
+    return out
+
+
+TDD_PATTERNS = ("DDDSU", "DDSUU", "DDDDDDDSUU", "DSUUU")
+
+
+def serving_trace(n_carriers: int, n_requests: int, rate_hz: float, seed: int) -> list:
+    """Slot requests for a serving run: Poisson arrivals at rate_hz over all carriers,
+    each arrival for a carrier drawn uniformly; a carrier's k-th request is its slot k,
+    whose direction follows the carrier's seeded TDD pattern (D and S slots -> TX,
+    U -> RX). Returns sorted (arrival_s, carrier, direction 0=TX / 1=RX) tuples."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pattern = [TDD_PATTERNS[int(rng.integers(len(TDD_PATTERNS)))] for _ in range(n_carriers)]
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n_requests))
+    who = rng.integers(0, n_carriers, n_requests)
+    count = [0] * n_carriers
+    out = []
+    for ti, c in zip(t, who):
+        c = int(c)
+        p = pattern[c]
+        out.append((float(ti), c, 1 if p[count[c] % len(p)] == "U" else 0))
+        count[c] += 1
     return out
 
 
