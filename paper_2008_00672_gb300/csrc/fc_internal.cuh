@@ -74,6 +74,7 @@ struct FcPlanDev {
   int frame_len;
   long long grid_len;
   long long ws_len;   // workspace complex elements per stream
+  long long tc_off;   // tensor-core path: workspace offset of the R x 4096 spectrum rows
   int ring;           // TX ring length (power of two)
   int ybuf;           // spectrum buffer length (complex)
   int wbuf;           // low-rate buffer length (complex)
@@ -100,6 +101,16 @@ cudaError_t fc_launch_ofdm_demod(const FcPlanDev* dP, int syms_per_stream, int n
 cudaError_t fc_set_smem_limits(size_t max_dynamic_smem);
 
 // warp-specialised symbol-synchronized kernels (fc_warp.cu); jobs are grouped per chunk
+// tensor-core FC passes (continuous, one subband, L = N = 4096)
+#define FC_TC_TX_FFT 0
+#define FC_TC_TX_IFFT 1
+#define FC_TC_RX_FFT 2
+#define FC_TC_RX_IFFT 3
+cudaError_t fc_launch_tc(const FcPlanDev* dP, const unsigned char* dft64, int pass, int n_streams, int n_blocks,
+                         const float2* in, float2* out, float2* ws, int* err, int num_sms, cudaStream_t st);
+cudaError_t fc_set_tc_smem_limits();
+void fc_tc_dft64_image(unsigned char* out);
+size_t fc_tc_dft64_image_bytes();
 cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
                                    int n_streams, int frame_len, const float2* grid, float2* wave, cudaStream_t st);
 cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,

@@ -93,6 +93,9 @@ struct fc_plan {
   std::vector<const FcChunk*> tx_chunks, rx_chunks;
   std::vector<int> tx_nchunks, rx_nchunks;
   bool warp_path = false;                   // warp-specialised symbol-sync kernels apply
+  bool tc_tx = false, tc_rx = false;        // tensor-core FC passes apply (FC_FLAG_TENSOR_DFT)
+  const unsigned char* d_dft64 = nullptr;   // DFT-64 B operand images (hi, lo)
+  int* d_err = nullptr;                     // device error word of the tensor-core kernels
   FcJob* d_wjobs = nullptr;                 // jobs regrouped per chunk for the warp kernels
   std::vector<const FcChunk*> w_chunks;
   std::vector<int> w_nchunks;
@@ -435,7 +438,14 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   if (pl->smem_tx > smem_cap || pl->smem_rx > smem_cap)
     return fail(FC_ERR_UNSUPPORTED, "geometry needs more shared memory than one SM has");
 
-  // workspace (continuous): low-rate stream per subband, or R*L per subband for RX OLA
+  // tensor-core FC passes: continuous, one group, one subband, L = N = 4096; RX only
+  // for overlap-save (the OLA analysis keeps the FP32 kernels)
+  const bool tc_tx = (geo->flags & FC_FLAG_TENSOR_DFT) && !sync && G == 1 && M == 1 && sh[0].L == 4096 &&
+                     gh[0].N == 4096;
+  const bool tc_rx = tc_tx && geo->scheme_rx == FC_OLS;
+
+  // workspace (continuous): low-rate stream per subband, or R*L per subband for RX OLA;
+  // the tensor-core passes add R rows of 4096 bins between their two transforms
   long long ws_len = 0;
   std::vector<long long> ws_off(M, 0);
   if (!sync) {
@@ -445,6 +455,11 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
       if (geo->scheme_rx == FC_OLA) need = std::max(need, (long long)sh[m].R * sh[m].L);
       ws_len += (need + 1) / 2 * 2;   // keep 16-byte alignment per slot
     }
+  }
+  long long tc_off = 0;
+  if (tc_tx) {
+    tc_off = ws_len;
+    ws_len += (long long)sh[0].R * 4096;
   }
 
   // grid offsets in the caller's subband order
@@ -473,8 +488,16 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   z.workspace_per_stream = ws_len * (long long)sizeof(float2);
   z.slot_len = streamable ? slot_len : 0;
   z.stream_delay = streamable ? stream_delay : 0;
-  z.tx_kernels = sync ? 1 : 2;
-  z.rx_kernels = sync ? 1 : 2;
+  z.tx_kernels = sync ? 1 : (tc_tx ? 3 : 2);
+  z.rx_kernels = sync ? 1 : (tc_rx ? 3 : 2);
+  size_t off_dft = 0, off_err = 0;
+  if (tc_tx) {
+    std::vector<unsigned char> img(fc_tc_dft64_image_bytes());
+    fc_tc_dft64_image(img.data());
+    off_dft = blob.add(img.data(), img.size(), 256);
+    const int zero = 0;
+    off_err = blob.add(&zero, sizeof(int));
+  }
   // ---- device upload ---------------------------------------------------------
   const size_t off_plan = blob.add(nullptr, sizeof(FcPlanDev));
   // Without upload (host-only check) every table pointer is laid out against a
@@ -500,6 +523,7 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   P.frame_len = (int)frame_len;
   P.grid_len = grid_len;
   P.ws_len = ws_len;
+  P.tc_off = tc_off;
   P.ring = ring;
   P.ybuf = ybuf;
   P.wbuf = wbuf;
@@ -558,6 +582,12 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   pl->tx_nchunks = ntx;
   pl->rx_nchunks = nrx;
   pl->warp_path = warp_ok;
+  pl->tc_tx = tc_tx;
+  pl->tc_rx = tc_rx;
+  if (tc_tx) {
+    pl->d_dft64 = base + off_dft;
+    pl->d_err = reinterpret_cast<int*>(base + off_err);
+  }
   if (warp_ok) {
     pl->d_wjobs = reinterpret_cast<FcJob*>(base + off_wjobs);
     for (size_t i = 0; i < splits.size(); ++i) {
@@ -628,6 +658,18 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const float2* grid, fl
                              wave, plan->smem_tx, st);
   cudaError_t e = fc_launch_ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid, workspace,
                                      plan->smem_ofdm, st);
+  if (plan->tc_tx && !c.second) {
+    const int R = plan->h.g[0].R;
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(wave, 0, (size_t)n_streams * plan->h.frame_len * sizeof(float2), st);
+    if (e == cudaSuccess)
+      e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_TX_FFT, n_streams, R, nullptr, nullptr, workspace,
+                       plan->d_err, plan->num_sms, st);
+    if (e == cudaSuccess)
+      e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_TX_IFFT, n_streams, R, nullptr, wave, workspace,
+                       plan->d_err, plan->num_sms, st);
+    return e;
+  }
   if (e == cudaSuccess)
     e = fc_launch_tx_cont(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, workspace,
                           wave, plan->smem_tx, st);
@@ -643,6 +685,17 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const float2* wave, fl
   if (plan->h.mode == FC_SYMBOL_SYNC)
     return fc_launch_rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, wave,
                              grid, plan->smem_rx, st);
+  if (plan->tc_rx && !c.second) {
+    const int R = plan->h.g[0].R;
+    cudaError_t e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_RX_FFT, n_streams, R, wave, nullptr, workspace,
+                                 plan->d_err, plan->num_sms, st);
+    if (e == cudaSuccess)
+      e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_RX_IFFT, n_streams, R, nullptr, nullptr, workspace,
+                       plan->d_err, plan->num_sms, st);
+    if (e == cudaSuccess)
+      e = fc_launch_ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, grid, plan->smem_ofdm, st);
+    return e;
+  }
   cudaError_t e = fc_launch_rx_cont(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams,
                                     wave, workspace, plan->smem_rx, st);
   if (e == cudaSuccess)
@@ -686,6 +739,7 @@ int fc_plan_create(fc_plan** out, const fc_geometry* geometry, int32_t device) {
   std::call_once(g_smem_once[device], [&] {
     se = fc_set_smem_limits(pl->smem_cap);
     if (se == cudaSuccess) se = fc_set_warp_smem_limits();
+    if (se == cudaSuccess) se = fc_set_tc_smem_limits();
   });
   if (se != cudaSuccess) {
     delete pl;
@@ -761,7 +815,8 @@ int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* strea
   std::pair<int, int> best[2] = {{0, 0}, {0, 0}};
   for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir) {
     float best_ms = 1e30f;
-    for (int generic = 0; generic <= (plan->warp_path ? 1 : 0) && e == cudaSuccess; ++generic) {
+    const bool special = dir == FC_TX ? (plan->warp_path || plan->tc_tx) : (plan->warp_path || plan->tc_rx);
+    for (int generic = 0; generic <= (special ? 1 : 0) && e == cudaSuccess; ++generic) {
       for (int k = 0; k < (int)plan->splits.size() && e == cudaSuccess; ++k) {
         const std::pair<int, int> c{k, generic};
         auto run = [&]() {
@@ -799,8 +854,21 @@ int fc_plan_choice(const fc_plan* plan, int32_t n_streams, int32_t direction, in
     return fail(FC_ERR_INVALID, "bad plan, direction or n_streams");
   const std::pair<int, int> c = choose(plan, n_streams, direction);
   if (chunks_per_stream) *chunks_per_stream = plan->splits[c.first];
-  if (generic_kernels) *generic_kernels = (plan->warp_path && !c.second) ? 0 : 1;
+  const bool special = direction == FC_TX ? (plan->warp_path || plan->tc_tx) : (plan->warp_path || plan->tc_rx);
+  if (generic_kernels) *generic_kernels = (special && !c.second) ? 0 : 1;
   return FC_OK;
+}
+
+int fc_plan_device_status(const fc_plan* plan) {
+  if (!plan) return fail(FC_ERR_INVALID, "plan is NULL");
+  if (!plan->d_err) return FC_OK;
+  DeviceGuard dg(plan->device);
+  if (!dg.ok) return fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  int v = 0;
+  cudaError_t e = cudaMemcpy(&v, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && v) e = cudaMemset(plan->d_err, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+  return v ? fail(FC_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs") : FC_OK;
 }
 
 void fc_plan_destroy(fc_plan* plan) {

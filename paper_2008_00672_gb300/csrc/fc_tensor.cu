@@ -1,0 +1,334 @@
+// FC blocks on the 5th-generation tensor cores (tcgen05): the 4096-point short and
+// long DFTs of continuous FC with L = N = 4096 (Sec. III-B, eq:BDM; the 100 MHz NR
+// carrier) as a four-step GEMM-DFT, 4096 = 64 x 64.
+//
+//   X[k1 + 64 k2] = sum_n2 W64^(n2 k2) W4096^(n2 k1) sum_n1 W64^(n1 k1) x[64 n1 + n2]
+//
+// Stage 1 multiplies the 64 x 64 data matrix by the DFT-64 matrix, the twiddles
+// W4096^(n2 k1) are applied in registers, stage 3 multiplies by the DFT-64 matrix
+// again. Complex numbers ride along K and N as interleaved (re, im) pairs: the data
+// rows are the M side (A, K-major, (re, im) of 64 inputs = K 128), the DFT-64 matrix
+// is the B side (N 128 = (re, im) of 64 outputs), so D = A B^T gives each TMEM lane
+// (one data row) its 64 complex outputs side by side.
+//
+// Precision: BF16 operands split as x = hi + lo (hi = bf16(x), lo = bf16(x - hi)) and
+// three products hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM: about 16 bits of
+// each operand reach the product (relative error ~1e-5 per transform), far below the
+// -60 dB budget of the reduced-precision path.
+//
+// One CTA (256 threads, 8 warps) per SM works through tiles of two transforms
+// (M = 128 rows): every thread stages operands into shared memory (128-byte swizzle,
+// the layout the MMA descriptors name), one thread issues the MMAs, warps read the
+// accumulator back with tcgen05.ld. The FC steps around the transforms are fused into
+// the operand staging (prologue: segmentation, A window, conjugation) and the
+// accumulator read-back (epilogue: shift, D_m, phi_r, bin map, OLA / OLS assembly).
+// The transform between two passes goes through the workspace.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <cuda_bf16.h>
+
+#include "fc_device.cuh"
+#include "fc_internal.cuh"
+#include "fc_tc.cuh"
+
+namespace {
+
+using namespace fcdev;
+using namespace fctc;
+
+constexpr int kN = 4096;
+constexpr int kThreads = 256;
+constexpr int kChunk = 128 * 128;          // bytes of one 64-element K chunk of a 128-row operand
+constexpr int kOp = 2 * kChunk;            // one 128 x 128 BF16 operand (K = 128): 32 KB
+constexpr int kSmem = 4 * kOp + 1024;      // B hi, B lo, A hi, A lo, plus alignment slack
+constexpr uint32_t kIdesc =                // kind::f16, BF16 x BF16 -> FP32, K-major, M = N = 128
+    (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+
+// Byte offset of BF16 element k of row `row` in a 128-row, K = 128 operand: two
+// 64-element chunks, rows of 128 bytes, 16-byte units XOR-swizzled by row % 8.
+__host__ __device__ __forceinline__ uint32_t op_off(int row, int k) {
+  const int j = k >> 6, byte = (k & 63) * 2;
+  return (uint32_t)(j * kChunk + row * 128 + ((((byte >> 4) ^ (row & 7))) << 4) + (byte & 15));
+}
+
+__device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, uint32_t off, float2 v) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+  *reinterpret_cast<__nv_bfloat162*>(hi + off) = h;
+  *reinterpret_cast<__nv_bfloat162*>(lo + off) = l;
+}
+
+// exp(+j 2 pi e / n) from the table W_n^m = exp(-j 2 pi m / n), n a power of two
+__device__ __forceinline__ float2 root_pos_tc(const float2* __restrict__ tw, int n, long long e) {
+  const float2 w = __ldg(tw + (int)(e & (long long)(n - 1)));
+  return make_float2(w.x, -w.y);
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+struct TcArgs {
+  const FcPlanDev* P;
+  const unsigned char* dft64;   // B operand images: hi then lo (kOp bytes each)
+  int pass;                     // FC_TC_TX_FFT, FC_TC_TX_IFFT, FC_TC_RX_FFT, FC_TC_RX_IFFT
+  int n_streams;
+  const float2* in;             // wave (RX_FFT) or workspace
+  float2* out;                  // wave (TX_IFFT) or workspace
+  float2* ws;                   // workspace base
+  int* err;                     // set to 1 when a bounded wait gives up
+};
+
+// ---- prologue: element i of transform g (the block r of stream s), already conjugated
+// for the inverse passes --------------------------------------------------------------
+__device__ __forceinline__ float2 tc_in(const TcArgs& a, const FcGroupDev& G, const FcSubDev& S, int g, int i) {
+  const int s = g / G.R, r = g - s * G.R;
+  const FcPlanDev& P = *a.P;
+  switch (a.pass) {
+    case FC_TC_TX_FFT: {                      // padded low-rate stream, A window for OLA
+      if (P.scheme_tx == FC_OLA && (i < S.L_L || i >= S.L_L + S.L_S)) return czero();
+      const long long idx = (long long)r * S.L_S + i - S.S_L;
+      if (idx < 0 || idx >= S.n_low) return czero();
+      return __ldg(a.ws + (long long)s * P.ws_len + S.ws_off + idx);
+    }
+    case FC_TC_TX_IFFT:
+    case FC_TC_RX_IFFT: {                     // spectrum row, conjugated: IDFT = conj DFT conj
+      const float2 v = __ldg(a.ws + (long long)s * P.ws_len + P.tc_off + (long long)r * kN + i);
+      return make_float2(v.x, -v.y);
+    }
+    default: {                                // RX_FFT: block r of the received frame
+      return __ldg(a.in + (long long)s * P.frame_len + G.offset + (long long)r * G.N_S + i);
+    }
+  }
+}
+
+// ---- epilogue: bin (or time) k of transform g --------------------------------------------
+__device__ __forceinline__ void tc_out(const TcArgs& a, const FcGroupDev& G, const FcSubDev& S, float2 ph, int g,
+                                       int k, float2 X) {
+  const int s = g / G.R, r = g - s * G.R;
+  const FcPlanDev& P = *a.P;
+  switch (a.pass) {
+    case FC_TC_TX_FFT: {                      // shift, D_m (with the scalings), phi_r, bin map (I = 1)
+      const int p = (k + kN / 2) & (kN - 1);
+      const float w = __ldg(S.dtx + p);
+      const int q = (k + S.c) & (kN - 1);
+      a.ws[(long long)s * P.ws_len + P.tc_off + (long long)r * kN + q] = cscale(cmul(ph, X), w);
+      break;
+    }
+    case FC_TC_TX_IFFT: {                     // y = conj(X); OLA add or OLS S window
+      const float2 y = make_float2(X.x, -X.y);
+      float2* o = a.out + (long long)s * P.frame_len + G.offset + (long long)r * G.N_S + k;
+      if (P.scheme_tx == FC_OLA) {
+        atomicAdd(&o->x, y.x);
+        atomicAdd(&o->y, y.y);
+      } else if (k >= G.N_L && k < G.N_L + G.N_S) {
+        *o = y;
+      }
+      break;
+    }
+    case FC_TC_RX_FFT: {                      // gather with conj(phi_r), D_m, inverse shift
+      const int kk = (k - S.c) & (kN - 1);
+      const int p = (kk + kN / 2) & (kN - 1);
+      const float w = __ldg(S.drx + p);
+      a.ws[(long long)s * P.ws_len + P.tc_off + (long long)r * kN + kk] = cscale(cmulc(X, ph), w);
+      break;
+    }
+    default: {                                // RX_IFFT: OLS keeps [L_L, L_L + L_S) of each block
+      if (k < S.L_L || k >= S.L_L + S.L_S) break;
+      const long long idx = (long long)r * S.L_S + k - S.S_L;
+      if (idx >= 0 && idx < S.n_low)
+        a.ws[(long long)s * P.ws_len + S.ws_off + idx] = make_float2(X.x, -X.y);
+      break;
+    }
+  }
+}
+
+__device__ __forceinline__ void issue_mmas(uint32_t tcol, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi, uint32_t b_lo) {
+#pragma unroll
+  for (int prod = 0; prod < 3; ++prod) {      // hi*hi + hi*lo + lo*hi
+    const uint32_t a = prod == 2 ? a_lo : a_hi;
+    const uint32_t b = prod == 1 ? b_lo : b_hi;
+#pragma unroll
+    for (int st = 0; st < 8; ++st) {          // K = 128 in steps of 16 (32 bytes)
+      const uint32_t ko = (uint32_t)((st >> 2) * kChunk + (st & 3) * 32);
+      mma_f16(tcol, sdesc_kmajor_sw128(a + ko), sdesc_kmajor_sw128(b + ko), kIdesc, prod > 0 || st > 0);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* b_hi = sm;
+  unsigned char* b_lo = sm + kOp;
+  unsigned char* a_hi = sm + 2 * kOp;
+  unsigned char* a_lo = sm + 3 * kOp;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const FcPlanDev& P = *args.P;
+  const FcGroupDev& G = P.g[0];
+  const FcSubDev& S = P.s[0];
+  const float2* __restrict__ tw = P.sz[G.size_N].tw;        // W_4096^m
+
+  // DFT-64 operand images into shared memory (already swizzled on the host)
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(args.dft64);
+    uint4* dst = reinterpret_cast<uint4*>(b_hi);
+    for (int i = tid; i < 2 * kOp / 16; i += kThreads) dst[i] = __ldg(src + i);
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, 256);
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    abort_flag = 0;
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo), sb_hi = smem_u32(b_hi), sb_lo = smem_u32(b_lo);
+
+  const int total = args.n_streams * G.R;
+  const int n_tiles = (total + 1) / 2;
+  const int q = warp & 3, h = warp >> 2;          // TMEM lane quadrant, column half
+  const int row = 32 * q + lane;                   // this thread's accumulator row
+  const int rt = row >> 6, rlo = row & 63;         // transform in the tile, row within it
+  uint32_t phase = 0;
+
+  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    // ---- prologue: A1[64 t + n2][(n1, re/im)] = x_t[64 n1 + n2] -----------------------
+    for (int e = tid; e < 2 * kN; e += kThreads) {
+      const int t = e >> 12, i = e & (kN - 1);
+      const int g = 2 * tile + t;
+      const float2 v = g < total ? tc_in(args, G, S, g, i) : czero();
+      split_store(a_hi, a_lo, op_off(64 * t + (i & 63), 2 * (i >> 6)), v);
+    }
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      issue_mmas(tbase, sa_hi, sa_lo, sb_hi, sb_lo);
+      mma_commit(&bar);
+    }
+    if (!mbar_wait(&bar, phase)) {
+      atomicExch(args.err, 1);
+      abort_flag = 1;
+    }
+    phase ^= 1;
+    tc_fence_after();
+    __syncthreads();
+    if (abort_flag) break;
+    // ---- twiddles; A3[64 t + k1][(n2, re/im)] = A1'[64 t + n2][k1] W4096^(n2 k1) ----------
+    // thread: row (t = rt, n2 = rlo), columns of k1 in [32 h, 32 h + 32)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float d[32];
+      tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h + 32 * c), d);
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int k1 = 32 * h + 16 * c + m;
+        const float2 w = __ldg(tw + ((rlo * k1) & (kN - 1)));
+        split_store(a_hi, a_lo, op_off(64 * rt + k1, 2 * rlo), cmul(make_float2(d[2 * m], d[2 * m + 1]), w));
+      }
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      issue_mmas(tbase + 128, sa_hi, sa_lo, sb_hi, sb_lo);
+      mma_commit(&bar);
+    }
+    if (!mbar_wait(&bar, phase)) {
+      atomicExch(args.err, 1);
+      abort_flag = 1;
+    }
+    phase ^= 1;
+    tc_fence_after();
+    __syncthreads();
+    if (abort_flag) break;
+    // ---- epilogue: thread row (t = rt, k1 = rlo), k2 in [32 h, 32 h + 32) ----------------
+    const int g = 2 * tile + rt;
+    if (g < total) {
+      const int s = g / G.R, r = g - s * G.R;
+      (void)s;
+      const float2 ph = root_pos_tc(P.sz[S.size_L].tw, S.L, (long long)r * S.c * S.L_S);   // phi_r
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        float d[32];
+        tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 + 64 * h + 32 * c), d);
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+          const int k2 = 32 * h + 16 * c + m;
+          tc_out(args, G, S, ph, g, rlo + 64 * k2, make_float2(d[2 * m], d[2 * m + 1]));
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();                       // A and the TMEM columns are free for the next tile
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, 256);
+}
+
+}  // namespace
+
+cudaError_t fc_launch_tc(const FcPlanDev* dP, const unsigned char* dft64, int pass, int n_streams, int n_blocks,
+                         const float2* in, float2* out, float2* ws, int* err, int num_sms, cudaStream_t st) {
+  TcArgs a{dP, dft64, pass, n_streams, in, out, ws, err};
+  const int tiles = (n_streams * n_blocks + 1) / 2;
+  const int grid = tiles < num_sms ? tiles : num_sms;
+  if (grid < 1) return cudaSuccess;
+  k_tc_fc<<<grid, kThreads, kSmem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t fc_set_tc_smem_limits() {
+  return cudaFuncSetAttribute(k_tc_fc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+}
+
+// Host image of the DFT-64 B operand (N 128 = (re, im) of output k, K 128 = (re, im) of
+// input n): D[row][2k + 0] = Re X[k], D[row][2k + 1] = Im X[k]. Entries from FP64
+// cos/sin of 2 pi (n k mod 64) / 64, split into BF16 hi and lo (round to nearest even).
+namespace {
+uint16_t bf16_rne(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  return (uint16_t)(u >> 16);
+}
+float bf16_to_float(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+}  // namespace
+
+void fc_tc_dft64_image(unsigned char* out /* 2 * kOp bytes */) {
+  std::memset(out, 0, 2 * kOp);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int kk = 0; kk < 64; ++kk)
+    for (int nn = 0; nn < 64; ++nn) {
+      const double ang = two_pi * (double)((kk * nn) & 63) / 64.0;
+      const double cr = std::cos(ang), ci = -std::sin(ang);   // W64^(n k)
+      // out re: x_re cr - x_im ci ; out im: x_re ci + x_im cr
+      const double v[2][2] = {{cr, -ci}, {ci, cr}};
+      for (int co = 0; co < 2; ++co)
+        for (int cin = 0; cin < 2; ++cin) {
+          const float f = (float)v[co][cin];
+          const uint16_t hb = bf16_rne(f);
+          const uint16_t lb = bf16_rne((float)((double)v[co][cin] - (double)bf16_to_float(hb)));
+          const uint32_t off = op_off(2 * kk + co, 2 * nn + cin);
+          std::memcpy(out + off, &hb, 2);
+          std::memcpy(out + kOp + off, &lb, 2);
+        }
+    }
+}
+
+size_t fc_tc_dft64_image_bytes() { return 2 * (size_t)kOp; }

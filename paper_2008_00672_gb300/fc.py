@@ -22,6 +22,7 @@ FC_OK, FC_ERR_INVALID, FC_ERR_UNSUPPORTED, FC_ERR_NOMEM, FC_ERR_CUDA, FC_ERR_TIM
 FC_CONTINUOUS, FC_SYMBOL_SYNC = 0, 1
 FC_FLAG_GENERIC_KERNELS = 1
 FC_FLAG_REDUCED_RX = 2
+FC_FLAG_TENSOR_DFT = 4
 FC_OLA, FC_OLS = 0, 1
 FC_TX, FC_RX = 0, 1
 
@@ -29,7 +30,8 @@ EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize
             "fc_status_string", "fc_last_error", "fc_tx_synthesize_static", "fc_state_create", "fc_state_reset",
             "fc_state_destroy", "fc_tx_synthesize_stream", "fc_rx_analyze_stream", "fc_plan_autotune",
             "fc_plan_choice", "fc_batch_create", "fc_batch_launch", "fc_batch_destroy", "fc_server_create",
-            "fc_server_add_carrier", "fc_server_carrier_sizes", "fc_server_run", "fc_server_destroy")
+            "fc_server_add_carrier", "fc_server_carrier_sizes", "fc_server_run", "fc_server_destroy",
+            "fc_plan_device_status")
 
 
 class FcGroup(ctypes.Structure):
@@ -124,6 +126,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fc_server_run.restype = ctypes.c_int
         lib.fc_server_destroy.argtypes = [vp]
         lib.fc_server_destroy.restype = None
+        lib.fc_plan_device_status.argtypes = [vp]
+        lib.fc_plan_device_status.restype = ctypes.c_int
         lib.fc_plan_destroy.argtypes = [vp]
         lib.fc_plan_destroy.restype = None
         lib.fc_status_string.argtypes = [ctypes.c_int]

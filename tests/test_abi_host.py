@@ -157,3 +157,19 @@ def test_uneven_carriers_plan_on_the_host(fc):
         assert n & (n - 1) == 0 and 128 <= n <= 4096
     assert seen_bw == {"5MHz", "10MHz", "20MHz", "50MHz", "100MHz"}
     assert seen_scs == {"15kHz", "30kHz", "60kHz"}
+
+
+def test_tensor_flag_plans_its_workspace(fc):
+    """FC_FLAG_TENSOR_DFT on the 100 MHz carrier: R rows of 4096 bins more workspace
+    and three TX / RX kernels; other geometries ignore the flag."""
+    import dataclasses
+    geom = wl.config_100mhz(2)
+    a = fc.fc_geometry_check(geom)
+    b = fc.fc_geometry_check(dataclasses.replace(geom, flags=4))
+    d = fo.Dims(geom.groups[0], geom.subbands[0])
+    n_low = sum(fo.low_rate_cp(d, fo.CONTINUOUS)) + d.B * d.L_ofdm
+    R = fo.continuous_block_count(n_low, fo.lead_pad_low(geom.groups[0], d), d)
+    assert b.workspace_per_stream - a.workspace_per_stream == R * 4096 * 8
+    assert (b.tx_kernels, b.rx_kernels) == (3, 3)
+    m = wl.config_mixed_20mhz()
+    assert fc.fc_geometry_check(dataclasses.replace(m, flags=4)).workspace_per_stream == 0

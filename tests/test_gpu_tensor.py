@@ -1,0 +1,89 @@
+"""GPU parity of the tensor-core FC path (FC_FLAG_TENSOR_DFT: four-step GEMM-DFT on
+tcgen05, BF16 hi/lo split with three products, FP32 accumulation) against the FP64
+oracle. Bar: RMS-normalised error <= 3e-5 (-90 dB), derived from the split: each
+operand keeps ~16 significant bits (x - hi - lo <= 2^-18 |x|), so one 64-point GEMM
+stage adds ~4e-6 RMS and the two transforms of a block ~1e-5; the reduced-precision
+budget of the path is -60 dB (1e-3)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import fc_oracle as fo
+
+pytestmark = pytest.mark.gpu
+TOL_TC = 3e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2008_00672_gb300 import build
+    build.build()
+    return torch
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def c64(a):
+    return np.asarray(a).astype(np.complex64)
+
+
+def run(torch, geom, S, seed):
+    from paper_2008_00672_gb300 import Plan
+    plan = Plan(geom)
+    grid = c64(wl.qam_grid(geom, S, seed))
+    g = torch.from_numpy(grid).cuda()
+    w = torch.empty((S, plan.wave_len), dtype=torch.complex64, device="cuda")
+    plan.tx_synthesize(g, w)
+    ref_tx = [fo.tx_frame(geom, grid[s].astype(np.complex128)) for s in range(S)]
+    rx_np = np.stack([c64(wl.awgn(ref_tx[s], 30.0, seed + 11 * s)).astype(np.complex128) for s in range(S)])
+    est = torch.empty_like(g)
+    plan.rx_analyze(torch.from_numpy(c64(rx_np)).cuda(), est)
+    torch.cuda.synchronize()
+    from paper_2008_00672_gb300 import fc
+    status = fc.load_library().fc_plan_device_status(plan.handle)
+    w, e = w.cpu().numpy(), est.cpu().numpy()
+    plan.close()
+    et = max(rel(w[s], ref_tx[s]) for s in range(S))
+    er = max(rel(e[s], fo.rx_frame(geom, rx_np[s])) for s in range(S)) if geom.scheme_rx == fo.OLS else 0.0
+    return et, er, status
+
+
+def test_tensor_path_nr100mhz(torch_cuda):
+    geom = dataclasses.replace(wl.config_100mhz(2), flags=4)
+    et, er, status = run(torch_cuda, geom, 3, 97)       # 3 streams: an odd number of transforms
+    assert status == 0
+    assert et <= TOL_TC and er <= TOL_TC, (et, er)
+
+
+@pytest.mark.parametrize("stx", [fo.OLA, fo.OLS])
+def test_tensor_path_offset_carrier(torch_cuda, stx):
+    """c != 0 exercises phi_r, the shift and the bin map; OLS TX the S window."""
+    n_cp = wl.nr_normal_cp(4096, 30, 5)
+    g = wl.Group(4096, 2048, n_cp)
+    sb = wl.Subband(4096, 4096, 1200, 733, 0, wl.rc_transition_weights(4096, 1200, 8))
+    geom = wl.Geometry(fo.CONTINUOUS, stx, fo.OLS, (g,), (sb,), flags=4)
+    et, er, status = run(torch_cuda, geom, 2, 101)
+    assert status == 0
+    assert et <= TOL_TC and er <= TOL_TC, (et, er)
+
+
+def test_tensor_and_fp32_paths_agree(torch_cuda):
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import Plan
+    base = wl.config_100mhz(1)
+    grid = torch.from_numpy(c64(wl.qam_grid(base, 2, 7))).cuda()
+    outs = []
+    for flags in (0, 4):
+        plan = Plan(dataclasses.replace(base, flags=flags))
+        w = torch.empty((2, plan.wave_len), dtype=torch.complex64, device="cuda")
+        plan.tx_synthesize(grid, w)
+        torch.cuda.synchronize()
+        outs.append(w.cpu().numpy())
+        plan.close()
+    assert rel(outs[1], outs[0]) <= TOL_TC
