@@ -106,6 +106,8 @@ cudaError_t fc_set_smem_limits(size_t max_dynamic_smem);
 #define FC_TC_TX_IFFT 1
 #define FC_TC_RX_FFT 2
 #define FC_TC_RX_IFFT 3
+#define FC_TC_OFDM_MOD 4     // OFDM IDFT + CP insertion into the low-rate stream (L_OFDM = 4096)
+#define FC_TC_OFDM_DEMOD 5   // CP removal + OFDM DFT + active bins (overlap-save RX stream)
 cudaError_t fc_launch_tc(const FcPlanDev* dP, const unsigned char* dft64, int pass, int n_streams, int n_blocks,
                          const float2* in, float2* out, float2* ws, int* err, int num_sms, cudaStream_t st);
 cudaError_t fc_set_tc_smem_limits();

@@ -94,6 +94,7 @@ struct fc_plan {
   std::vector<int> tx_nchunks, rx_nchunks;
   bool warp_path = false;                   // warp-specialised symbol-sync kernels apply
   bool tc_tx = false, tc_rx = false;        // tensor-core FC passes apply (FC_FLAG_TENSOR_DFT)
+  bool tc_ofdm = false;                     // and the OFDM (I)DFT too (L_OFDM = 4096)
   const unsigned char* d_dft64 = nullptr;   // DFT-64 B operand images (hi, lo)
   int* d_err = nullptr;                     // device error word of the tensor-core kernels
   FcJob* d_wjobs = nullptr;                 // jobs regrouped per chunk for the warp kernels
@@ -584,6 +585,7 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   pl->warp_path = warp_ok;
   pl->tc_tx = tc_tx;
   pl->tc_rx = tc_rx;
+  pl->tc_ofdm = tc_tx && sh[0].Lo == 4096;
   if (tc_tx) {
     pl->d_dft64 = base + off_dft;
     pl->d_err = reinterpret_cast<int*>(base + off_err);
@@ -656,10 +658,13 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const float2* grid, fl
   if (plan->h.mode == FC_SYMBOL_SYNC)
     return fc_launch_tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, grid,
                              wave, plan->smem_tx, st);
-  cudaError_t e = fc_launch_ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid, workspace,
-                                     plan->smem_ofdm, st);
   if (plan->tc_tx && !c.second) {
     const int R = plan->h.g[0].R;
+    cudaError_t e = plan->tc_ofdm ? fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_OFDM_MOD, n_streams,
+                                                 plan->h.g[0].B, grid, nullptr, workspace, plan->d_err,
+                                                 plan->num_sms, st)
+                                  : fc_launch_ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid,
+                                                       workspace, plan->smem_ofdm, st);
     if (e == cudaSuccess)
       e = cudaMemsetAsync(wave, 0, (size_t)n_streams * plan->h.frame_len * sizeof(float2), st);
     if (e == cudaSuccess)
@@ -670,6 +675,8 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const float2* grid, fl
                        plan->d_err, plan->num_sms, st);
     return e;
   }
+  cudaError_t e = fc_launch_ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid, workspace,
+                                     plan->smem_ofdm, st);
   if (e == cudaSuccess)
     e = fc_launch_tx_cont(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, workspace,
                           wave, plan->smem_tx, st);
@@ -693,7 +700,10 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const float2* wave, fl
       e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_RX_IFFT, n_streams, R, nullptr, nullptr, workspace,
                        plan->d_err, plan->num_sms, st);
     if (e == cudaSuccess)
-      e = fc_launch_ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, grid, plan->smem_ofdm, st);
+      e = plan->tc_ofdm ? fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_OFDM_DEMOD, n_streams, plan->h.g[0].B,
+                                       nullptr, grid, workspace, plan->d_err, plan->num_sms, st)
+                        : fc_launch_ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, grid,
+                                               plan->smem_ofdm, st);
     return e;
   }
   cudaError_t e = fc_launch_rx_cont(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams,

@@ -79,67 +79,116 @@ struct TcArgs {
   int* err;                     // set to 1 when a bounded wait gives up
 };
 
-// ---- prologue: element i of transform g (the block r of stream s), already conjugated
-// for the inverse passes --------------------------------------------------------------
-__device__ __forceinline__ float2 tc_in(const TcArgs& a, const FcGroupDev& G, const FcSubDev& S, int g, int i) {
-  const int s = g / G.R, r = g - s * G.R;
-  const FcPlanDev& P = *a.P;
-  switch (a.pass) {
-    case FC_TC_TX_FFT: {                      // padded low-rate stream, A window for OLA
-      if (P.scheme_tx == FC_OLA && (i < S.L_L || i >= S.L_L + S.L_S)) return czero();
-      const long long idx = (long long)r * S.L_S + i - S.S_L;
-      if (idx < 0 || idx >= S.n_low) return czero();
-      return __ldg(a.ws + (long long)s * P.ws_len + S.ws_off + idx);
-    }
-    case FC_TC_TX_IFFT:
-    case FC_TC_RX_IFFT: {                     // spectrum row, conjugated: IDFT = conj DFT conj
-      const float2 v = __ldg(a.ws + (long long)s * P.ws_len + P.tc_off + (long long)r * kN + i);
-      return make_float2(v.x, -v.y);
-    }
-    default: {                                // RX_FFT: block r of the received frame
-      return __ldg(a.in + (long long)s * P.frame_len + G.offset + (long long)r * G.N_S + i);
-    }
+// FC parameters of the one subband, read once per CTA into registers (reading them
+// through the plan pointer would reload them after every store the compiler cannot
+// prove disjoint).
+struct TcK {
+  long long ws_len, ws_off, tc_off, frame_len, offset, grid_len, grid_off;
+  int N_S, N_L, R, L_L, L_S, S_L, n_low, c, Lact, B;
+  bool ola_tx;
+  const float* __restrict__ dtx;
+  const float* __restrict__ drx;
+  const int* __restrict__ lcp;
+  const int* __restrict__ soff;
+};
+
+__device__ __forceinline__ TcK tc_consts(const FcPlanDev& P) {
+  const FcGroupDev& G = P.g[0];
+  const FcSubDev& S = P.s[0];
+  TcK k;
+  k.ws_len = P.ws_len; k.ws_off = S.ws_off; k.tc_off = P.tc_off; k.frame_len = P.frame_len; k.offset = G.offset;
+  k.grid_len = P.grid_len; k.grid_off = S.grid_off;
+  k.N_S = G.N_S; k.N_L = G.N_L; k.R = G.R; k.L_L = S.L_L; k.L_S = S.L_S; k.S_L = S.S_L; k.n_low = S.n_low;
+  k.c = S.c; k.Lact = S.Lact; k.B = G.B;
+  k.ola_tx = P.scheme_tx == FC_OLA; k.dtx = S.dtx; k.drx = S.drx; k.lcp = S.lcp; k.soff = S.soff;
+  return k;
+}
+
+// transform g = (stream s, block or symbol r); the symbol passes also need the
+// symbol's low-rate CP and start in the low-rate stream
+struct TcCtx {
+  int s, r, lcp;
+  long long soff;
+};
+
+template <int PASS>
+__device__ __forceinline__ TcCtx tc_ctx(const TcK& K, int g) {
+  constexpr bool sym = PASS == FC_TC_OFDM_MOD || PASS == FC_TC_OFDM_DEMOD;
+  const int nT = sym ? K.B : K.R;
+  TcCtx c;
+  c.s = g / nT;
+  c.r = g - c.s * nT;
+  c.lcp = 0;
+  c.soff = 0;
+  if constexpr (sym) {
+    c.lcp = __ldg(K.lcp + c.r);
+    c.soff = __ldg(K.soff + c.r);
+  }
+  return c;
+}
+
+// signed subcarrier f of bin k and its index in the grid row (or -1): the active
+// subcarriers occupy f in [-floor(L_act/2), ceil(L_act/2))
+__device__ __forceinline__ int tc_active(int k, int Lact) {
+  const int f = k < kN / 2 ? k : k - kN;
+  const int lo = Lact / 2;
+  return (f >= -lo && f < Lact - lo) ? f + lo : -1;
+}
+
+// ---- prologue: element i of transform c, already conjugated for the inverse passes -------
+template <int PASS>
+__device__ __forceinline__ float2 tc_in(const float2* __restrict__ in, const float2* __restrict__ ws, const TcK& K,
+                                        const TcCtx& c, int i) {
+  if constexpr (PASS == FC_TC_TX_FFT) {       // padded low-rate stream, A window for OLA
+    if (K.ola_tx && (i < K.L_L || i >= K.L_L + K.L_S)) return czero();
+    const long long idx = (long long)c.r * K.L_S + i - K.S_L;
+    if (idx < 0 || idx >= K.n_low) return czero();
+    return __ldg(ws + (long long)c.s * K.ws_len + K.ws_off + idx);
+  } else if constexpr (PASS == FC_TC_RX_FFT) {   // block r of the received frame
+    return __ldg(in + (long long)c.s * K.frame_len + K.offset + (long long)c.r * K.N_S + i);
+  } else if constexpr (PASS == FC_TC_OFDM_MOD) { // active subcarriers of symbol r (conjugated)
+    const int a = tc_active(i, K.Lact);
+    if (a < 0) return czero();
+    const float2 v = __ldg(in + (long long)c.s * K.grid_len + K.grid_off + (long long)c.r * K.Lact + a);
+    return make_float2(v.x, -v.y);
+  } else if constexpr (PASS == FC_TC_OFDM_DEMOD) {   // symbol r after its CP in the low-rate stream
+    return __ldg(ws + (long long)c.s * K.ws_len + K.ws_off + c.soff + c.lcp + i);
+  } else {                                    // spectrum row, conjugated: IDFT = conj DFT conj
+    const float2 v = __ldg(ws + (long long)c.s * K.ws_len + K.tc_off + (long long)c.r * kN + i);
+    return make_float2(v.x, -v.y);
   }
 }
 
-// ---- epilogue: bin (or time) k of transform g --------------------------------------------
-__device__ __forceinline__ void tc_out(const TcArgs& a, const FcGroupDev& G, const FcSubDev& S, float2 ph, int g,
-                                       int k, float2 X) {
-  const int s = g / G.R, r = g - s * G.R;
-  const FcPlanDev& P = *a.P;
-  switch (a.pass) {
-    case FC_TC_TX_FFT: {                      // shift, D_m (with the scalings), phi_r, bin map (I = 1)
-      const int p = (k + kN / 2) & (kN - 1);
-      const float w = __ldg(S.dtx + p);
-      const int q = (k + S.c) & (kN - 1);
-      a.ws[(long long)s * P.ws_len + P.tc_off + (long long)r * kN + q] = cscale(cmul(ph, X), w);
-      break;
-    }
-    case FC_TC_TX_IFFT: {                     // y = conj(X); OLA add or OLS S window
-      const float2 y = make_float2(X.x, -X.y);
-      float2* o = a.out + (long long)s * P.frame_len + G.offset + (long long)r * G.N_S + k;
-      if (P.scheme_tx == FC_OLA) {
-        atomicAdd(&o->x, y.x);
-        atomicAdd(&o->y, y.y);
-      } else if (k >= G.N_L && k < G.N_L + G.N_S) {
-        *o = y;
-      }
-      break;
-    }
-    case FC_TC_RX_FFT: {                      // gather with conj(phi_r), D_m, inverse shift
-      const int kk = (k - S.c) & (kN - 1);
-      const int p = (kk + kN / 2) & (kN - 1);
-      const float w = __ldg(S.drx + p);
-      a.ws[(long long)s * P.ws_len + P.tc_off + (long long)r * kN + kk] = cscale(cmulc(X, ph), w);
-      break;
-    }
-    default: {                                // RX_IFFT: OLS keeps [L_L, L_L + L_S) of each block
-      if (k < S.L_L || k >= S.L_L + S.L_S) break;
-      const long long idx = (long long)r * S.L_S + k - S.S_L;
-      if (idx >= 0 && idx < S.n_low)
-        a.ws[(long long)s * P.ws_len + S.ws_off + idx] = make_float2(X.x, -X.y);
-      break;
-    }
+// ---- epilogue: bin (or time) k of transform c ----------------------------------------------
+template <int PASS>
+__device__ __forceinline__ void tc_out(float2* __restrict__ out, float2* __restrict__ ws, const TcK& K, float2 ph,
+                                       const TcCtx& c, int k, float2 X) {
+  if constexpr (PASS == FC_TC_TX_FFT) {       // shift, D_m (with the scalings), phi_r, bin map (I = 1)
+    const float w = __ldg(K.dtx + ((k + kN / 2) & (kN - 1)));
+    ws[(long long)c.s * K.ws_len + K.tc_off + (long long)c.r * kN + ((k + K.c) & (kN - 1))] = cscale(cmul(ph, X), w);
+  } else if constexpr (PASS == FC_TC_TX_IFFT) {   // y = conj(X); OLA add or OLS S window
+    const float2 y = make_float2(X.x, -X.y);
+    float2* o = out + (long long)c.s * K.frame_len + K.offset + (long long)c.r * K.N_S + k;
+    if (K.ola_tx)
+      atomicAdd(o, y);
+    else if (k >= K.N_L && k < K.N_L + K.N_S)
+      *o = y;
+  } else if constexpr (PASS == FC_TC_RX_FFT) {    // gather with conj(phi_r), D_m, inverse shift
+    const int kk = (k - K.c) & (kN - 1);
+    const float w = __ldg(K.drx + ((kk + kN / 2) & (kN - 1)));
+    ws[(long long)c.s * K.ws_len + K.tc_off + (long long)c.r * kN + kk] = cscale(cmulc(X, ph), w);
+  } else if constexpr (PASS == FC_TC_OFDM_MOD) {  // time sample k of the symbol, and its CP copy
+    const float2 x = make_float2(X.x, -X.y);
+    float2* d = ws + (long long)c.s * K.ws_len + K.ws_off + c.soff;
+    d[c.lcp + k] = x;
+    if (k >= kN - c.lcp) d[k - (kN - c.lcp)] = x;
+  } else if constexpr (PASS == FC_TC_OFDM_DEMOD) {   // active bins into the grid row
+    const int a = tc_active(k, K.Lact);
+    if (a >= 0) out[(long long)c.s * K.grid_len + K.grid_off + (long long)c.r * K.Lact + a] = X;
+  } else {                                    // RX_IFFT: OLS keeps [L_L, L_L + L_S) of each block
+    if (k < K.L_L || k >= K.L_L + K.L_S) return;
+    const long long idx = (long long)c.r * K.L_S + k - K.S_L;
+    if (idx >= 0 && idx < K.n_low) ws[(long long)c.s * K.ws_len + K.ws_off + idx] = make_float2(X.x, -X.y);
   }
 }
 
@@ -156,6 +205,7 @@ __device__ __forceinline__ void issue_mmas(uint32_t tcol, uint32_t a_hi, uint32_
   }
 }
 
+template <int PASS>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
@@ -168,9 +218,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
   unsigned char* a_lo = sm + 3 * kOp;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const FcPlanDev& P = *args.P;
-  const FcGroupDev& G = P.g[0];
-  const FcSubDev& S = P.s[0];
-  const float2* __restrict__ tw = P.sz[G.size_N].tw;        // W_4096^m
+  const TcK K = tc_consts(P);
+  const float2* __restrict__ tw = P.sz[P.g[0].size_N].tw;   // W_4096^m
+  const float2* __restrict__ twL = P.sz[P.s[0].size_L].tw;
+  const float2* __restrict__ g_in = args.in;
+  float2* __restrict__ g_out = args.out;
+  float2* __restrict__ g_ws = args.ws;
 
   // DFT-64 operand images into shared memory (already swizzled on the host)
   {
@@ -191,20 +244,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
   const uint32_t tbase = tmem_base;
   const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo), sb_hi = smem_u32(b_hi), sb_lo = smem_u32(b_lo);
 
-  const int total = args.n_streams * G.R;
+  constexpr bool kSym = PASS == FC_TC_OFDM_MOD || PASS == FC_TC_OFDM_DEMOD;
+  const int total = args.n_streams * (kSym ? K.B : K.R);
   const int n_tiles = (total + 1) / 2;
   const int q = warp & 3, h = warp >> 2;          // TMEM lane quadrant, column half
   const int row = 32 * q + lane;                   // this thread's accumulator row
   const int rt = row >> 6, rlo = row & 63;         // transform in the tile, row within it
   uint32_t phase = 0;
+  // twiddles W4096^(n2 k1) of this thread's row n2 = rlo and k1 = 32 h + 16 c + m: a seed
+  // per c and the step W4096^n2 (fixed for the kernel), advanced by multiplication
+  // (16 steps add at most ~2e-6 relative error)
+  const float2 tw_step = __ldg(tw + rlo);
+  const float2 tw_seed0 = __ldg(tw + ((rlo * (32 * h)) & (kN - 1)));
+  const float2 tw_seed1 = __ldg(tw + ((rlo * (32 * h + 16)) & (kN - 1)));
 
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    // ---- prologue: A1[64 t + n2][(n1, re/im)] = x_t[64 n1 + n2] -----------------------
-    for (int e = tid; e < 2 * kN; e += kThreads) {
-      const int t = e >> 12, i = e & (kN - 1);
+    // ---- prologue: A1[64 t + n2][(n1, re/im)] = x_t[64 n1 + n2], 16 loads in flight ----
+#pragma unroll 1
+    for (int t = 0; t < 2; ++t) {
       const int g = 2 * tile + t;
-      const float2 v = g < total ? tc_in(args, G, S, g, i) : czero();
-      split_store(a_hi, a_lo, op_off(64 * t + (i & 63), 2 * (i >> 6)), v);
+      const bool valid = g < total;
+      const TcCtx cx = tc_ctx<PASS>(K, valid ? g : 0);
+      float2 v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = valid ? tc_in<PASS>(g_in, g_ws, K, cx, tid + kThreads * j) : czero();
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int i = tid + kThreads * j;
+        split_store(a_hi, a_lo, op_off(64 * t + (i & 63), 2 * (i >> 6)), v[j]);
+      }
     }
     fence_async_smem();
     __syncthreads();
@@ -227,11 +295,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     for (int c = 0; c < 2; ++c) {
       float d[32];
       tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h + 32 * c), d);
+      float2 w = c ? tw_seed1 : tw_seed0;
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
         const int k1 = 32 * h + 16 * c + m;
-        const float2 w = __ldg(tw + ((rlo * k1) & (kN - 1)));
         split_store(a_hi, a_lo, op_off(64 * rt + k1, 2 * rlo), cmul(make_float2(d[2 * m], d[2 * m + 1]), w));
+        w = cmul(w, tw_step);
       }
     }
     fence_async_smem();
@@ -253,9 +322,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     // ---- epilogue: thread row (t = rt, k1 = rlo), k2 in [32 h, 32 h + 32) ----------------
     const int g = 2 * tile + rt;
     if (g < total) {
-      const int s = g / G.R, r = g - s * G.R;
-      (void)s;
-      const float2 ph = root_pos_tc(P.sz[S.size_L].tw, S.L, (long long)r * S.c * S.L_S);   // phi_r
+      const TcCtx cx = tc_ctx<PASS>(K, g);
+      const float2 ph = root_pos_tc(twL, kN, (long long)cx.r * K.c * K.L_S);   // phi_r (L = 4096)
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         float d[32];
@@ -263,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
           const int k2 = 32 * h + 16 * c + m;
-          tc_out(args, G, S, ph, g, rlo + 64 * k2, make_float2(d[2 * m], d[2 * m + 1]));
+          tc_out<PASS>(g_out, g_ws, K, ph, cx, rlo + 64 * k2, make_float2(d[2 * m], d[2 * m + 1]));
         }
       }
     }
@@ -283,12 +351,26 @@ cudaError_t fc_launch_tc(const FcPlanDev* dP, const unsigned char* dft64, int pa
   const int tiles = (n_streams * n_blocks + 1) / 2;
   const int grid = tiles < num_sms ? tiles : num_sms;
   if (grid < 1) return cudaSuccess;
-  k_tc_fc<<<grid, kThreads, kSmem, st>>>(a);
+  switch (pass) {
+    case FC_TC_TX_FFT: k_tc_fc<FC_TC_TX_FFT><<<grid, kThreads, kSmem, st>>>(a); break;
+    case FC_TC_TX_IFFT: k_tc_fc<FC_TC_TX_IFFT><<<grid, kThreads, kSmem, st>>>(a); break;
+    case FC_TC_RX_FFT: k_tc_fc<FC_TC_RX_FFT><<<grid, kThreads, kSmem, st>>>(a); break;
+    case FC_TC_OFDM_MOD: k_tc_fc<FC_TC_OFDM_MOD><<<grid, kThreads, kSmem, st>>>(a); break;
+    case FC_TC_OFDM_DEMOD: k_tc_fc<FC_TC_OFDM_DEMOD><<<grid, kThreads, kSmem, st>>>(a); break;
+    default: k_tc_fc<FC_TC_RX_IFFT><<<grid, kThreads, kSmem, st>>>(a); break;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t fc_set_tc_smem_limits() {
-  return cudaFuncSetAttribute(k_tc_fc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_tc_fc<FC_TC_TX_FFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem))) return e;
+  if ((e = cudaFuncSetAttribute(k_tc_fc<FC_TC_TX_IFFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem))) return e;
+  if ((e = cudaFuncSetAttribute(k_tc_fc<FC_TC_RX_FFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem))) return e;
+  if ((e = cudaFuncSetAttribute(k_tc_fc<FC_TC_OFDM_MOD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem))) return e;
+  if ((e = cudaFuncSetAttribute(k_tc_fc<FC_TC_OFDM_DEMOD>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem)))
+    return e;
+  return cudaFuncSetAttribute(k_tc_fc<FC_TC_RX_IFFT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
 }
 
 // Host image of the DFT-64 B operand (N 128 = (re, im) of output k, K 128 = (re, im) of
