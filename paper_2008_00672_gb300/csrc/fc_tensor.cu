@@ -16,7 +16,7 @@
 // each operand reach the product (relative error ~1e-5 per transform), far below the
 // -60 dB budget of the reduced-precision path.
 //
-// One CTA (256 threads, 8 warps) per SM works through tiles of two transforms
+// One CTA (512 threads, 16 warps) per SM works through tiles of two transforms
 // (M = 128 rows): every thread stages operands into shared memory (128-byte swizzle,
 // the layout the MMA descriptors name), one thread issues the MMAs, warps read the
 // accumulator back with tcgen05.ld. The FC steps around the transforms are fused into
@@ -38,10 +38,11 @@ using namespace fcdev;
 using namespace fctc;
 
 constexpr int kN = 4096;
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kChunk = 128 * 128;          // bytes of one 64-element K chunk of a 128-row operand
 constexpr int kOp = 2 * kChunk;            // one 128 x 128 BF16 operand (K = 128): 32 KB
-constexpr int kSmem = 4 * kOp + 1024;      // B hi, B lo, A hi, A lo, plus alignment slack
+constexpr int kStage = 2 * 4096 * 8;      // FP32 input of the next tile (two transforms): 64 KB
+constexpr int kSmem = 4 * kOp + kStage + 1024;   // B hi, B lo, A hi, A lo, staging, alignment slack
 constexpr uint32_t kIdesc =                // kind::f16, BF16 x BF16 -> FP32, K-major, M = N = 128
     (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 
@@ -135,28 +136,57 @@ __device__ __forceinline__ int tc_active(int k, int Lact) {
   return (f >= -lo && f < Lact - lo) ? f + lo : -1;
 }
 
-// ---- prologue: element i of transform c, already conjugated for the inverse passes -------
+// ---- prologue: where element i of transform c comes from (NULL: zero). The inverse
+// passes take the conjugate (IDFT = conj DFT conj), applied when the element is staged.
 template <int PASS>
-__device__ __forceinline__ float2 tc_in(const float2* __restrict__ in, const float2* __restrict__ ws, const TcK& K,
-                                        const TcCtx& c, int i) {
+__device__ __forceinline__ const float2* tc_src(const float2* __restrict__ in, const float2* __restrict__ ws,
+                                                const TcK& K, const TcCtx& c, int i) {
   if constexpr (PASS == FC_TC_TX_FFT) {       // padded low-rate stream, A window for OLA
-    if (K.ola_tx && (i < K.L_L || i >= K.L_L + K.L_S)) return czero();
+    if (K.ola_tx && (i < K.L_L || i >= K.L_L + K.L_S)) return nullptr;
     const long long idx = (long long)c.r * K.L_S + i - K.S_L;
-    if (idx < 0 || idx >= K.n_low) return czero();
-    return __ldg(ws + (long long)c.s * K.ws_len + K.ws_off + idx);
+    if (idx < 0 || idx >= K.n_low) return nullptr;
+    return ws + (long long)c.s * K.ws_len + K.ws_off + idx;
   } else if constexpr (PASS == FC_TC_RX_FFT) {   // block r of the received frame
-    return __ldg(in + (long long)c.s * K.frame_len + K.offset + (long long)c.r * K.N_S + i);
-  } else if constexpr (PASS == FC_TC_OFDM_MOD) { // active subcarriers of symbol r (conjugated)
+    return in + (long long)c.s * K.frame_len + K.offset + (long long)c.r * K.N_S + i;
+  } else if constexpr (PASS == FC_TC_OFDM_MOD) { // active subcarriers of symbol r
     const int a = tc_active(i, K.Lact);
-    if (a < 0) return czero();
-    const float2 v = __ldg(in + (long long)c.s * K.grid_len + K.grid_off + (long long)c.r * K.Lact + a);
-    return make_float2(v.x, -v.y);
+    if (a < 0) return nullptr;
+    return in + (long long)c.s * K.grid_len + K.grid_off + (long long)c.r * K.Lact + a;
   } else if constexpr (PASS == FC_TC_OFDM_DEMOD) {   // symbol r after its CP in the low-rate stream
-    return __ldg(ws + (long long)c.s * K.ws_len + K.ws_off + c.soff + c.lcp + i);
-  } else {                                    // spectrum row, conjugated: IDFT = conj DFT conj
-    const float2 v = __ldg(ws + (long long)c.s * K.ws_len + K.tc_off + (long long)c.r * kN + i);
-    return make_float2(v.x, -v.y);
+    return ws + (long long)c.s * K.ws_len + K.ws_off + c.soff + c.lcp + i;
+  } else {                                    // spectrum row
+    return ws + (long long)c.s * K.ws_len + K.tc_off + (long long)c.r * kN + i;
   }
+}
+
+template <int PASS>
+constexpr bool tc_conj_in() {
+  return PASS == FC_TC_TX_IFFT || PASS == FC_TC_RX_IFFT || PASS == FC_TC_OFDM_MOD;
+}
+
+// 8-byte asynchronous copy global -> shared; src NULL fills zeros (source size 0)
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src, const float2* valid_ptr) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src ? src : valid_ptr),
+               "r"(src ? 8 : 0)
+               : "memory");
+}
+
+// Stage the raw input of `tile` (two transforms) into stg[t][i]; completes at cp.async.wait_all.
+template <int PASS>
+__device__ __forceinline__ void tc_prefetch(float2* stg, const float2* __restrict__ in, const float2* __restrict__ ws,
+                                            const TcK& K, int tile, int total, int tid) {
+#pragma unroll 1
+  for (int t = 0; t < 2; ++t) {
+    const int g = 2 * tile + t;
+    const bool valid = g < total;
+    const TcCtx cx = tc_ctx<PASS>(K, valid ? g : 0);
+#pragma unroll 4
+    for (int j = 0; j < kN / kThreads; ++j) {
+      const int i = tid + kThreads * j;
+      cp_async8(stg + t * kN + i, valid ? tc_src<PASS>(in, ws, K, cx, i) : nullptr, ws);
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 // ---- epilogue: bin (or time) k of transform c ----------------------------------------------
@@ -216,6 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
   unsigned char* b_lo = sm + kOp;
   unsigned char* a_hi = sm + 2 * kOp;
   unsigned char* a_lo = sm + 3 * kOp;
+  float2* stg = reinterpret_cast<float2*>(sm + 4 * kOp);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const FcPlanDev& P = *args.P;
   const TcK K = tc_consts(P);
@@ -247,35 +278,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
   constexpr bool kSym = PASS == FC_TC_OFDM_MOD || PASS == FC_TC_OFDM_DEMOD;
   const int total = args.n_streams * (kSym ? K.B : K.R);
   const int n_tiles = (total + 1) / 2;
-  const int q = warp & 3, h = warp >> 2;          // TMEM lane quadrant, column half
+  const int q = warp & 3, h = warp >> 2;          // TMEM lane quadrant, column quarter
   const int row = 32 * q + lane;                   // this thread's accumulator row
   const int rt = row >> 6, rlo = row & 63;         // transform in the tile, row within it
   uint32_t phase = 0;
-  // twiddles W4096^(n2 k1) of this thread's row n2 = rlo and k1 = 32 h + 16 c + m: a seed
-  // per c and the step W4096^n2 (fixed for the kernel), advanced by multiplication
-  // (16 steps add at most ~2e-6 relative error)
+  // twiddles W4096^(n2 k1) of this thread's row n2 = rlo and k1 = 16 h + m: a seed and the
+  // step W4096^n2 (both fixed for the kernel), advanced by multiplication (15 steps add
+  // at most ~2e-6 relative error)
   const float2 tw_step = __ldg(tw + rlo);
-  const float2 tw_seed0 = __ldg(tw + ((rlo * (32 * h)) & (kN - 1)));
-  const float2 tw_seed1 = __ldg(tw + ((rlo * (32 * h + 16)) & (kN - 1)));
+  const float2 tw_seed = __ldg(tw + ((rlo * (16 * h)) & (kN - 1)));
 
+  if (blockIdx.x < n_tiles) tc_prefetch<PASS>(stg, g_in, g_ws, K, blockIdx.x, total, tid);
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    // ---- prologue: A1[64 t + n2][(n1, re/im)] = x_t[64 n1 + n2], 16 loads in flight ----
-#pragma unroll 1
-    for (int t = 0; t < 2; ++t) {
-      const int g = 2 * tile + t;
-      const bool valid = g < total;
-      const TcCtx cx = tc_ctx<PASS>(K, valid ? g : 0);
-      float2 v[16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = valid ? tc_in<PASS>(g_in, g_ws, K, cx, tid + kThreads * j) : czero();
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int i = tid + kThreads * j;
-        split_store(a_hi, a_lo, op_off(64 * t + (i & 63), 2 * (i >> 6)), v[j]);
-      }
+    // ---- prologue: A1[64 t + n2][(n1, re/im)] = x_t[64 n1 + n2] from the staged input ----
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+#pragma unroll 4
+    for (int e = tid; e < 2 * kN; e += kThreads) {
+      float2 v = stg[e];
+      if (tc_conj_in<PASS>()) v.y = -v.y;
+      const int t = e >> 12, i = e & (kN - 1);
+      split_store(a_hi, a_lo, op_off(64 * t + (i & 63), 2 * (i >> 6)), v);
     }
     fence_async_smem();
     __syncthreads();
+    // the staging buffer is free: fetch the next tile while this one is transformed
+    if (tile + (int)gridDim.x < n_tiles) tc_prefetch<PASS>(stg, g_in, g_ws, K, tile + gridDim.x, total, tid);
     if (tid == 0) {
       tc_fence_after();
       issue_mmas(tbase, sa_hi, sa_lo, sb_hi, sb_lo);
@@ -290,15 +318,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     __syncthreads();
     if (abort_flag) break;
     // ---- twiddles; A3[64 t + k1][(n2, re/im)] = A1'[64 t + n2][k1] W4096^(n2 k1) ----------
-    // thread: row (t = rt, n2 = rlo), columns of k1 in [32 h, 32 h + 32)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
+    // thread: row (t = rt, n2 = rlo), k1 in [16 h, 16 h + 16)
+    {
       float d[32];
-      tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h + 32 * c), d);
-      float2 w = c ? tw_seed1 : tw_seed0;
+      tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * h), d);
+      float2 w = tw_seed;
 #pragma unroll
       for (int m = 0; m < 16; ++m) {
-        const int k1 = 32 * h + 16 * c + m;
+        const int k1 = 16 * h + m;
         split_store(a_hi, a_lo, op_off(64 * rt + k1, 2 * rlo), cmul(make_float2(d[2 * m], d[2 * m + 1]), w));
         w = cmul(w, tw_step);
       }
@@ -319,20 +346,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     tc_fence_after();
     __syncthreads();
     if (abort_flag) break;
-    // ---- epilogue: thread row (t = rt, k1 = rlo), k2 in [32 h, 32 h + 32) ----------------
+    // ---- epilogue: thread row (t = rt, k1 = rlo), k2 in [16 h, 16 h + 16) ----------------
     const int g = 2 * tile + rt;
     if (g < total) {
       const TcCtx cx = tc_ctx<PASS>(K, g);
       const float2 ph = root_pos_tc(twL, kN, (long long)cx.r * K.c * K.L_S);   // phi_r (L = 4096)
+      float d[32];
+      tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 + 32 * h), d);
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        float d[32];
-        tmem_ld32(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 + 64 * h + 32 * c), d);
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-          const int k2 = 32 * h + 16 * c + m;
-          tc_out<PASS>(g_out, g_ws, K, ph, cx, rlo + 64 * k2, make_float2(d[2 * m], d[2 * m + 1]));
-        }
+      for (int m = 0; m < 16; ++m) {
+        const int k2 = 16 * h + m;
+        tc_out<PASS>(g_out, g_ws, K, ph, cx, rlo + 64 * k2, make_float2(d[2 * m], d[2 * m + 1]));
       }
     }
     tc_fence_before();
