@@ -63,9 +63,17 @@ def transform_flops(geom) -> float:
     return total
 
 
-def kernel_source_sha() -> str:
+KERNEL_SOURCES = {
+    "k_tx_sync_warp": ("fc_warp.cu", "fc_internal.cuh", "fc_device.cuh"),
+    "k_rx_sync_warp": ("fc_warp.cu", "fc_internal.cuh", "fc_device.cuh"),
+    "k_tc_fc": ("fc_tensor.cu", "fc_tc.cuh", "fc_internal.cuh", "fc_device.cuh"),
+}
+
+
+def kernel_source_sha(kernel: str = "") -> str:
+    """Hash of the sources a kernel is built from (traffic counters go stale when it changes)."""
     h = hashlib.sha256()
-    for f in ("fc_kernels.cu", "fc_internal.cuh"):
+    for f in KERNEL_SOURCES.get(kernel, ("fc_kernels.cu", "fc_internal.cuh", "fc_device.cuh")):
         with open(os.path.join(ROOT, "paper_2008_00672_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -79,7 +87,7 @@ def traffic_from_profile(kernel: str):
     with open(p) as f:
         d = json.load(f)
     e = d.get(kernel)
-    if not e or e.get("source_sha") != kernel_source_sha():
+    if not e or e.get("source_sha") != kernel_source_sha(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -559,7 +567,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     # ---- roofline of the dominant kernel --------------------------------------
     peaks, peak_kind = load_peaks()
     flops_frame = transform_flops(geom)
-    dom = "k_tx_sync" if tx_ms >= rx_ms else "k_rx_sync"
+    warp_dir = {d: not tuned[d][1] and plan.tx_kernels == 1 for d in ("tx", "rx")}
+    if tx_ms >= rx_ms:
+        dom = "k_tx_sync_warp" if warp_dir["tx"] else "k_tx_sync"
+    else:
+        dom = "k_rx_sync_warp" if warp_dir["rx"] else "k_rx_sync"
     dom_ms = max(tx_ms, rx_ms)
     achieved_tflops = flops_frame * S / (dom_ms * 1e-3) / 1e12
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))

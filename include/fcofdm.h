@@ -272,6 +272,14 @@ int fc_plan_device_status(const fc_plan* plan);
  */
 int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* stream);
 
+/* Records a launch shape for n_streams streams in `direction` without timing (e.g. one
+   saved from an earlier fc_plan_autotune): chunks_per_stream must be one the plan has
+   (1, 2, 4, ..., at most 64 and at most the jobs per stream); generic_kernels 1 selects
+   the generic shared-memory kernels where specialised ones exist. FC_ERR_INVALID
+   otherwise. */
+int fc_plan_set_choice(fc_plan* plan, int32_t n_streams, int32_t direction, int32_t chunks_per_stream,
+                       int32_t generic_kernels);
+
 /* The launch shape an execute call with n_streams streams will use in `direction`. */
 int fc_plan_choice(const fc_plan* plan, int32_t n_streams, int32_t direction, int32_t* chunks_per_stream,
                    int32_t* generic_kernels);

@@ -858,6 +858,18 @@ int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* strea
   return FC_OK;
 }
 
+int fc_plan_set_choice(fc_plan* plan, int32_t n_streams, int32_t direction, int32_t chunks_per_stream,
+                       int32_t generic_kernels) {
+  if (!plan || (direction != FC_TX && direction != FC_RX) || n_streams < 1 ||
+      (generic_kernels != 0 && generic_kernels != 1))
+    return fail(FC_ERR_INVALID, "bad plan, direction, n_streams or generic_kernels");
+  const auto it = std::find(plan->splits.begin(), plan->splits.end(), (int)chunks_per_stream);
+  if (it == plan->splits.end()) return fail(FC_ERR_INVALID, "chunks_per_stream is not one of the plan's splits");
+  std::lock_guard<std::mutex> lock(plan->tune_mu);
+  plan->tuned[{n_streams, direction}] = {(int)(it - plan->splits.begin()), (int)generic_kernels};
+  return FC_OK;
+}
+
 int fc_plan_choice(const fc_plan* plan, int32_t n_streams, int32_t direction, int32_t* chunks_per_stream,
                    int32_t* generic_kernels) {
   if (!plan || (direction != FC_TX && direction != FC_RX) || n_streams < 1)

@@ -31,7 +31,7 @@ EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize
             "fc_state_destroy", "fc_tx_synthesize_stream", "fc_rx_analyze_stream", "fc_plan_autotune",
             "fc_plan_choice", "fc_batch_create", "fc_batch_launch", "fc_batch_destroy", "fc_server_create",
             "fc_server_add_carrier", "fc_server_carrier_sizes", "fc_server_run", "fc_server_destroy",
-            "fc_plan_device_status")
+            "fc_plan_device_status", "fc_plan_set_choice")
 
 
 class FcGroup(ctypes.Structure):
@@ -108,6 +108,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fc_rx_analyze_stream.restype = ctypes.c_int
         lib.fc_plan_autotune.argtypes = [vp, i32, i32, vp]
         lib.fc_plan_autotune.restype = ctypes.c_int
+        lib.fc_plan_set_choice.argtypes = [vp, i32, i32, i32, i32]
+        lib.fc_plan_set_choice.restype = ctypes.c_int
         lib.fc_plan_choice.argtypes = [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         lib.fc_plan_choice.restype = ctypes.c_int
         lib.fc_batch_create.argtypes = [ctypes.POINTER(FcBatchItem), i32, i32, i32, ctypes.POINTER(vp)]
@@ -246,6 +248,11 @@ def fc_plan_autotune(plan, n_streams: int, reps: int = 5, stream: int = 0):
     _check(load_library().fc_plan_autotune(plan, int(n_streams), int(reps), stream or None), "fc_plan_autotune")
 
 
+def fc_plan_set_choice(plan, n_streams: int, direction: int, chunks_per_stream: int, generic_kernels: int = 0):
+    _check(load_library().fc_plan_set_choice(plan, int(n_streams), int(direction), int(chunks_per_stream),
+                                             int(generic_kernels)), "fc_plan_set_choice")
+
+
 def fc_plan_choice(plan, n_streams: int, direction: int):
     """(chunks per stream, generic kernels) an execute call with n_streams will use."""
     k, g = ctypes.c_int32(), ctypes.c_int32()
@@ -348,6 +355,9 @@ class Plan:
     def autotune(self, n_streams: int, reps: int = 5, stream=None):
         """Measure every launch shape for n_streams streams and keep the fastest."""
         fc_plan_autotune(self.handle, n_streams, reps, self._stream_handle(stream))
+
+    def set_choice(self, n_streams: int, direction: int, chunks_per_stream: int, generic_kernels: int = 0):
+        fc_plan_set_choice(self.handle, n_streams, direction, chunks_per_stream, generic_kernels)
 
     def choice(self, n_streams: int, direction: int):
         return fc_plan_choice(self.handle, n_streams, direction)

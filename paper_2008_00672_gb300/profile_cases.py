@@ -1,0 +1,66 @@
+"""Fixed invocations of the library's kernels for profilers.
+
+    python -m paper_2008_00672_gb300.profile_cases CASE --streams S [--warm W]
+
+builds the case's plan, sets the launch shape the benchmark uses, runs W warm-up
+TX + RX passes and then one more TX + RX pass, so that `ncu -k <kernel> -s <skip>`
+can pick launches of a known shape. Inputs are seeded QAM grids; the RX input is the
+TX output (its values do not change the kernels' work).
+
+Cases:
+  warp20     20 MHz mixed numerology, symbol-synchronized (one-warp-per-symbol kernels;
+             TX 1 chunk per stream, RX 4 chunks per stream)
+  generic20  the same geometry on the generic shared-memory kernels
+  tensor100  100 MHz / 273 PRB carrier, 10 slots, on the tensor-core passes
+  fp32_100   the same carrier on the FP32 shared-memory kernels
+"""
+import argparse
+import dataclasses
+
+import numpy as np
+
+import workloads as wl
+
+from . import FC_FLAG_GENERIC_KERNELS, FC_FLAG_TENSOR_DFT, FC_RX, FC_TX, Plan, build
+
+
+def make_case(name: str):
+    if name == "warp20":
+        return wl.config_mixed_20mhz(), {FC_TX: (1, 0), FC_RX: (4, 0)}
+    if name == "generic20":
+        return dataclasses.replace(wl.config_mixed_20mhz(), flags=FC_FLAG_GENERIC_KERNELS), {}
+    if name == "tensor100":
+        return dataclasses.replace(wl.config_100mhz(10), flags=FC_FLAG_TENSOR_DFT), {}
+    if name == "fp32_100":
+        return wl.config_100mhz(10), {}
+    raise SystemExit(f"unknown case {name}")
+
+
+def main():
+    import torch
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["warp20", "generic20", "tensor100", "fp32_100"])
+    ap.add_argument("--streams", type=int, default=256)
+    ap.add_argument("--warm", type=int, default=1)
+    args = ap.parse_args()
+    build.build()
+    geom, shape = make_case(args.case)
+    plan = Plan(geom)
+    S = args.streams
+    for d, (k, g) in shape.items():
+        plan.set_choice(S, d, k, g)
+    base = wl.qam_grid(geom, min(S, 64), wl.default_seed(2)).astype(np.complex64)
+    grid = torch.from_numpy(base).cuda().repeat(-(-S // base.shape[0]), 1)[:S].contiguous()
+    wave = torch.empty((S, plan.wave_len), dtype=torch.complex64, device="cuda")
+    est = torch.empty_like(grid)
+    for _ in range(args.warm + 1):
+        plan.tx_synthesize(grid, wave)
+        plan.rx_analyze(wave, est)
+    torch.cuda.synchronize()
+    plan.close()
+    print(f"{args.case}: {S} streams, {args.warm} warm-up passes + 1, launches per pass "
+          f"TX {plan.tx_kernels} RX {plan.rx_kernels}")
+
+
+if __name__ == "__main__":
+    main()

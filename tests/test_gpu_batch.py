@@ -122,3 +122,15 @@ def test_autotune_keeps_results_and_records_a_choice(torch_cuda):
     assert rel(after[S - 1].cpu().numpy(), ref) <= TOL
     assert rel(after.cpu().numpy(), before.cpu().numpy()) < 1e-6
     plan.close()
+
+
+def test_set_choice_round_trip_and_validation(torch_cuda):
+    from paper_2008_00672_gb300 import FC_RX, FC_TX, FcError, Plan
+    plan = Plan(wl.config_mixed_20mhz())
+    plan.set_choice(100, FC_RX, 4, 0)
+    assert plan.choice(100, FC_RX) == (4, 0)
+    plan.set_choice(100, FC_TX, 2, 1)
+    assert plan.choice(100, FC_TX) == (2, 1)
+    with pytest.raises(FcError):
+        plan.set_choice(100, FC_TX, 3, 0)          # not a split the plan has
+    plan.close()
