@@ -529,6 +529,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
 
     # ---- RX variant: the joint IDFT/DFT form of eq:reduc (FC_FLAG_REDUCED_RX), same input ----
     plan_red = Plan(dataclasses.replace(geom, flags=FC_FLAG_REDUCED_RX), device=local_rank)
+    plan_red.set_choice(S, FC_RX, *tuned["rx"])          # same launch shape as the timed RX
     for _ in range(3):
         plan_red.rx_analyze(rx_in, est)
     red = []
