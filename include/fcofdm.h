@@ -355,6 +355,34 @@ int fc_server_run(fc_server* server, const fc_serve_request* requests, int32_t n
 /* Frees every carrier and the lanes (after synchronising them). Safe on NULL. */
 void fc_server_destroy(fc_server* server);
 
+/*
+ * Host-buffer execute calls (no counterpart in the paper; how a host application feeds
+ * the path). A pipeline owns `depth` slots of device buffers for `chunk_streams` streams
+ * (input, output, workspace) and one CUDA stream per slot; fc_tx_synthesize_host /
+ * fc_rx_analyze_host split n_streams into chunks, and chunk i copies its host input to
+ * slot i mod depth, runs fc_tx_synthesize / fc_rx_analyze there and copies the result
+ * back, on that slot's CUDA stream. Copies in both directions and the kernels of
+ * different chunks therefore overlap. The calls are asynchronous with respect to the
+ * host (ordered after earlier work on `stream`, and later work on `stream` waits for
+ * them); host buffers must stay valid until then and should be page-locked (pageable
+ * memory makes the copies synchronous and removes the overlap). Results equal the
+ * device calls on the same data. A pipeline serves one call at a time: order calls on
+ * the same pipeline through one `stream`.
+ */
+typedef struct fc_pipeline fc_pipeline;
+
+/* Allocates depth x (grid + wave + workspace for chunk_streams streams) on the plan's
+   device; 1 <= depth <= 16. The plan must outlive the pipeline. */
+int fc_pipeline_create(const fc_plan* plan, int32_t chunk_streams, int32_t depth, fc_pipeline** out);
+void fc_pipeline_destroy(fc_pipeline* pipeline);
+
+/* host grid [n_streams][grid_len] -> host wave [n_streams][wave_len] */
+int fc_tx_synthesize_host(fc_pipeline* pipeline, int32_t n_streams, const void* host_grid, void* host_wave,
+                          void* stream);
+/* host wave [n_streams][wave_len] -> host grid [n_streams][grid_len] */
+int fc_rx_analyze_host(fc_pipeline* pipeline, int32_t n_streams, const void* host_wave, void* host_grid,
+                       void* stream);
+
 /* Frees the plan's device tables. Safe on NULL. Must not race with running calls. */
 void fc_plan_destroy(fc_plan* plan);
 

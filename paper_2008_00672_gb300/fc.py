@@ -31,7 +31,8 @@ EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize
             "fc_state_destroy", "fc_tx_synthesize_stream", "fc_rx_analyze_stream", "fc_plan_autotune",
             "fc_plan_choice", "fc_batch_create", "fc_batch_launch", "fc_batch_destroy", "fc_server_create",
             "fc_server_add_carrier", "fc_server_carrier_sizes", "fc_server_run", "fc_server_destroy",
-            "fc_plan_device_status", "fc_plan_set_choice")
+            "fc_plan_device_status", "fc_plan_set_choice", "fc_pipeline_create", "fc_pipeline_destroy",
+            "fc_tx_synthesize_host", "fc_rx_analyze_host")
 
 
 class FcGroup(ctypes.Structure):
@@ -130,6 +131,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fc_server_destroy.restype = None
         lib.fc_plan_device_status.argtypes = [vp]
         lib.fc_plan_device_status.restype = ctypes.c_int
+        lib.fc_pipeline_create.argtypes = [vp, i32, i32, ctypes.POINTER(vp)]
+        lib.fc_pipeline_create.restype = ctypes.c_int
+        lib.fc_pipeline_destroy.argtypes = [vp]
+        lib.fc_pipeline_destroy.restype = None
+        lib.fc_tx_synthesize_host.argtypes = [vp, i32, vp, vp, vp]
+        lib.fc_tx_synthesize_host.restype = ctypes.c_int
+        lib.fc_rx_analyze_host.argtypes = [vp, i32, vp, vp, vp]
+        lib.fc_rx_analyze_host.restype = ctypes.c_int
         lib.fc_plan_destroy.argtypes = [vp]
         lib.fc_plan_destroy.restype = None
         lib.fc_status_string.argtypes = [ctypes.c_int]
@@ -309,6 +318,28 @@ def fc_server_run(server, requests) -> list:
 def fc_server_destroy(server):
     if server:
         load_library().fc_server_destroy(server)
+
+
+def fc_pipeline_create(plan, chunk_streams: int, depth: int = 3) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load_library().fc_pipeline_create(plan, int(chunk_streams), int(depth), ctypes.byref(h)),
+           "fc_pipeline_create")
+    return h
+
+
+def fc_pipeline_destroy(pipeline):
+    if pipeline:
+        load_library().fc_pipeline_destroy(pipeline)
+
+
+def fc_tx_synthesize_host(pipeline, n_streams: int, host_grid: int, host_wave: int, stream: int = 0):
+    _check(load_library().fc_tx_synthesize_host(pipeline, int(n_streams), host_grid, host_wave, stream or None),
+           "fc_tx_synthesize_host")
+
+
+def fc_rx_analyze_host(pipeline, n_streams: int, host_wave: int, host_grid: int, stream: int = 0):
+    _check(load_library().fc_rx_analyze_host(pipeline, int(n_streams), host_wave, host_grid, stream or None),
+           "fc_rx_analyze_host")
 
 
 def fc_plan_destroy(plan):
@@ -517,6 +548,47 @@ class Server:
     def close(self):
         if self.handle:
             fc_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pipeline:
+    """Owns one fc_pipeline: host-buffer TX / RX with copies and kernels of chunks of
+    streams overlapped. tx(grid, wave) / rx(wave, grid) take contiguous complex64 CPU
+    tensors (page-locked for overlap) and are asynchronous on `stream`."""
+
+    def __init__(self, plan: Plan, chunk_streams: int, depth: int = 3):
+        self.plan = plan
+        self.handle = fc_pipeline_create(plan.handle, chunk_streams, depth)
+
+    @staticmethod
+    def _host(a, b, la, lb) -> int:
+        import torch
+        for t in (a, b):
+            if t.dtype != torch.complex64 or t.is_cuda or not t.is_contiguous():
+                raise ValueError("expected contiguous complex64 host tensors")
+        if a.numel() % la or b.numel() % lb or a.numel() // la != b.numel() // lb:
+            raise ValueError("input and output sizes do not match the plan")
+        return a.numel() // la
+
+    def tx(self, host_grid, host_wave, stream=None):
+        n = self._host(host_grid, host_wave, self.plan.grid_len, self.plan.wave_len)
+        fc_tx_synthesize_host(self.handle, n, host_grid.data_ptr(), host_wave.data_ptr(), Plan._stream_handle(stream))
+        return host_wave
+
+    def rx(self, host_wave, host_grid, stream=None):
+        n = self._host(host_wave, host_grid, self.plan.wave_len, self.plan.grid_len)
+        fc_rx_analyze_host(self.handle, n, host_wave.data_ptr(), host_grid.data_ptr(), Plan._stream_handle(stream))
+        return host_grid
+
+    def close(self):
+        if self.handle:
+            fc_pipeline_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
