@@ -87,3 +87,52 @@ def test_tensor_and_fp32_paths_agree(torch_cuda):
         outs.append(w.cpu().numpy())
         plan.close()
     assert rel(outs[1], outs[0]) <= TOL_TC
+
+
+def test_tensor_path_bench_size_sampled(torch_cuda):
+    """The launch the bench times (32 streams x 10 slots): first and last stream vs the
+    oracle, TX and RX."""
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import Plan
+    geom = dataclasses.replace(wl.config_100mhz(10), flags=4)
+    S = 32
+    plan = Plan(geom)
+    base = c64(wl.qam_grid(geom, 4, wl.default_seed(3)))
+    grid = np.tile(base, (S // 4, 1))
+    g = torch.from_numpy(grid).cuda()
+    w = torch.empty((S, plan.wave_len), dtype=torch.complex64, device="cuda")
+    plan.tx_synthesize(g, w)
+    est = torch.empty_like(g)
+    plan.rx_analyze(w, est)
+    torch.cuda.synchronize()
+    for s in (0, S - 1):
+        ref_w = fo.tx_frame(geom, grid[s].astype(np.complex128))
+        wv = w[s].cpu().numpy()
+        assert rel(wv, ref_w) <= TOL_TC
+        ref_e = fo.rx_frame(geom, wv.astype(np.complex128))
+        assert rel(est[s].cpu().numpy(), ref_e) <= TOL_TC
+    plan.close()
+
+
+def test_tensor_path_stream_calls(torch_cuda):
+    """Stream calls on the tensor-core path: two slots of the 100 MHz carrier equal one
+    oracle frame of the two-slot geometry."""
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import Plan, State
+    from tests.test_stream_semantics import k_slots, stack_grids
+    geom = dataclasses.replace(wl.config_100mhz(1), flags=4)
+    plan = Plan(geom)
+    T, D = plan.slot_len, plan.stream_delay
+    st = State(plan, 1)
+    grids = [c64(wl.qam_grid(geom, 1, 300 + k))[0] for k in range(2)]
+    outs = []
+    for k in range(3):
+        gk = grids[k] if k < 2 else np.zeros_like(grids[0])
+        o = torch.empty((1, T), dtype=torch.complex64, device="cuda")
+        st.tx(torch.from_numpy(gk).cuda().reshape(1, -1), o)
+        outs.append(o.cpu().numpy()[0])
+    got = np.concatenate(outs)[:2 * T + D]
+    ref = fo.tx_frame(k_slots(geom, 2), stack_grids(geom, [x.astype(np.complex128) for x in grids]))
+    assert rel(got, ref) <= TOL_TC
+    st.close()
+    plan.close()
