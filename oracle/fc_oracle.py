@@ -340,6 +340,15 @@ def sync_theta(d: Dims, n: int) -> complex:
 def tx_sync_subband(grid_rows: np.ndarray, group, sub, scheme: int) -> np.ndarray:
     """Symbol-synchronized FC synthesis of one subband, all B symbols, length Q."""
     d = Dims(group, sub)
+    l_cp = low_rate_cp(d, SYMBOL_SYNC)
+    symbols = [cp_insert(ofdm_modulate(grid_rows[n], d.L), l_cp[n]) for n in range(d.B)]
+    return tx_sync_subband_time(symbols, group, sub, scheme)
+
+
+def tx_sync_subband_time(symbols: list, group, sub, scheme: int) -> np.ndarray:
+    """The FC part of tx_sync_subband (eq:padding onward) on given low-rate CP-OFDM
+    symbols: symbols[n] holds L_CP,m,n + L samples (CP, then the body)."""
+    d = Dims(group, sub)
     sync_check(d)
     l_cp = low_rate_cp(d, SYMBOL_SYNC)
     sig = sync_sigma(d)
@@ -347,7 +356,9 @@ def tx_sync_subband(grid_rows: np.ndarray, group, sub, scheme: int) -> np.ndarra
     out = np.zeros(sync_waveform_len(d), dtype=np.complex128)
     for n in range(d.B):
         lc = l_cp[n]
-        x_cp = cp_insert(ofdm_modulate(grid_rows[n], L), lc)
+        x_cp = np.asarray(symbols[n], dtype=np.complex128)
+        if len(x_cp) != lc + L:
+            raise ValueError("symbol n needs L_CP,n + L samples")
         s_ln = d.L_L - lc                                        # S_L,m,n
         z = np.concatenate([np.zeros(s_ln), x_cp, np.zeros(d.L_T)])    # eq:padding, 3L/2
         Z = np.stack([z[0:L], z[L // 2: L // 2 + L]], axis=1)   # (R_L^{(r)})^T z
@@ -372,10 +383,17 @@ def rx_sync_subband(x: np.ndarray, group, sub, scheme: int) -> np.ndarray:
     """Symbol-synchronized FC analysis + OFDM demodulation of one subband.
     Returns [B, L_act] QAM estimates."""
     d = Dims(group, sub)
+    return np.stack([ofdm_demodulate(row, d.L_act) for row in rx_sync_subband_time(x, group, sub, scheme)])
+
+
+def rx_sync_subband_time(x: np.ndarray, group, sub, scheme: int) -> np.ndarray:
+    """The FC part of rx_sync_subband: [B, L] recovered OFDM symbols x_hat_OFDM
+    (eq:concat2, CP removed), before demodulation."""
+    d = Dims(group, sub)
     sync_check(d)
     sig = sync_sigma(d)
     L, N = d.L, d.N
-    out = np.zeros((d.B, d.L_act), dtype=np.complex128)
+    out = np.zeros((d.B, L), dtype=np.complex128)
     for n in range(d.B):
         wn = x[sig[n]: sig[n] + 3 * N // 2]                      # Gamma_{sigma_n}^T x (reading R8)
         Wb = np.stack([wn[0:N], wn[N // 2: N // 2 + N]], axis=1)  # (R_N^{(r)})^T
@@ -389,8 +407,7 @@ def rx_sync_subband(x: np.ndarray, group, sub, scheme: int) -> np.ndarray:
         zs = np.zeros(3 * L // 2, dtype=np.complex128)
         zs[0:L] += Zb[:, 0]                                      # R_L^{(0)}
         zs[L // 2: L // 2 + L] += Zb[:, 1]                       # R_L^{(1)}
-        x_ofdm = zs[d.L_L: d.L_L + L]                            # extension removal (reading R7)
-        out[n] = ofdm_demodulate(x_ofdm, d.L_act)
+        out[n] = zs[d.L_L: d.L_L + L]                            # extension removal (reading R7)
     return out
 
 
@@ -485,16 +502,44 @@ def continuous_stream(rows: np.ndarray, d: Dims, l_cp: list) -> np.ndarray:
     return np.concatenate([cp_insert(ofdm_modulate(rows[n], d.L_ofdm), l_cp[n]) for n in range(d.B)])
 
 
-def tx_frame(geom, grid: np.ndarray) -> np.ndarray:
-    """One stream: QAM grid -> high-rate FC-F-OFDM waveform x = sum_m w_m."""
+def time_lengths(geom) -> tuple:
+    """Per-subband lengths of the time-domain I/O: TX takes every symbol's low-rate CP
+    and body (sum_n L_CP,m,n + L_OFDM,m), RX gives every symbol's body (B L_OFDM,m)."""
+    tx, rx = [], []
+    for sub in geom.subbands:
+        g = geom.groups[sub.group]
+        d = Dims(g, sub)
+        l_cp = low_rate_cp(d, geom.mode)
+        tx.append(sum(l_cp) + d.B * d.L_ofdm)
+        rx.append(d.B * d.L_ofdm)
+    return tx, rx
+
+
+def tx_frame(geom, grid: np.ndarray, io_time: bool = False) -> np.ndarray:
+    """One stream: QAM grid -> high-rate FC-F-OFDM waveform x = sum_m w_m. With
+    io_time, `grid` is instead the low-rate CP-OFDM signal of every subband (subband
+    after subband, time_lengths), fed to the FC part directly."""
     offs, flen = frame_layout(geom)
     out = np.zeros(flen, dtype=np.complex128)
-    for m, (sub, rows) in enumerate(zip(geom.subbands, split_grid(geom, np.asarray(grid)))):
+    if io_time:
+        parts, pos = [], 0
+        for n_t in time_lengths(geom)[0]:
+            parts.append(np.asarray(grid, dtype=np.complex128)[pos:pos + n_t])
+            pos += n_t
+    else:
+        parts = split_grid(geom, np.asarray(grid))
+    for m, (sub, rows) in enumerate(zip(geom.subbands, parts)):
         g = geom.groups[sub.group]
-        if geom.mode == SYMBOL_SYNC:
+        d = Dims(g, sub)
+        if geom.mode == SYMBOL_SYNC and io_time:
+            l_cp = low_rate_cp(d, SYMBOL_SYNC)
+            starts = np.cumsum([0] + [lc + d.L for lc in l_cp])
+            w = tx_sync_subband_time([rows[starts[n]:starts[n + 1]] for n in range(d.B)], g, sub, geom.scheme_tx)
+        elif geom.mode == SYMBOL_SYNC:
             w = tx_sync_subband(rows, g, sub, geom.scheme_tx)
+        elif io_time:
+            w = tx_continuous_subband(rows, g, sub, geom.scheme_tx)
         else:
-            d = Dims(g, sub)
             w = tx_continuous_subband(continuous_stream(rows, d, low_rate_cp(d, CONTINUOUS)),
                                       g, sub, geom.scheme_tx)
         o = offs[sub.group]
@@ -502,9 +547,11 @@ def tx_frame(geom, grid: np.ndarray) -> np.ndarray:
     return out
 
 
-def rx_frame(geom, wave: np.ndarray, simplified: bool = False) -> np.ndarray:
+def rx_frame(geom, wave: np.ndarray, simplified: bool = False, io_time: bool = False) -> np.ndarray:
     """One stream: received waveform -> QAM estimates in the grid layout.
-    simplified=True uses eq:reduc for symbol-synchronized OLS RX."""
+    simplified=True uses eq:reduc for symbol-synchronized OLS RX. With io_time, the
+    recovered OFDM symbols before demodulation instead (every symbol's L_OFDM body,
+    subband after subband, time_lengths)."""
     offs, flen = frame_layout(geom)
     wave = np.asarray(wave, dtype=np.complex128)
     parts = []
@@ -512,6 +559,16 @@ def rx_frame(geom, wave: np.ndarray, simplified: bool = False) -> np.ndarray:
         g = geom.groups[sub.group]
         o = offs[sub.group]
         d = Dims(g, sub)
+        if io_time and geom.mode == SYMBOL_SYNC:
+            parts.append(rx_sync_subband_time(wave[o:], g, sub, geom.scheme_rx).reshape(-1))
+            continue
+        if io_time:
+            l_cp = low_rate_cp(d, CONTINUOUS)
+            offs_low = continuous_symbol_offsets(d, l_cp)
+            s_hat = rx_continuous_subband(wave[o:], g, sub, geom.scheme_rx, offs_low[-1])
+            parts.append(np.concatenate([s_hat[offs_low[n] + l_cp[n]: offs_low[n] + l_cp[n] + d.L_ofdm]
+                                         for n in range(d.B)]))
+            continue
         if geom.mode == SYMBOL_SYNC and simplified:
             if geom.scheme_rx != OLS:
                 raise ValueError("eq:reduc is the overlap-save RX")

@@ -467,3 +467,47 @@ def test_simplified_rx_equals_direct(N, L, c, n_cp):
     a = fo.rx_frame(gm, w)
     b = fo.rx_frame(gm, w, simplified=True)
     assert np.allclose(a, b, atol=1e-10 * np.max(np.abs(a)))
+
+
+# ---------------------------------------------------------------------------
+# time-domain I/O (the FC part alone)
+# ---------------------------------------------------------------------------
+
+def _time_input_from_grid(geom, grid):
+    """Concatenated low-rate CP-OFDM symbols of every subband, from a QAM grid."""
+    parts = []
+    for sub, rows in zip(geom.subbands, fo.split_grid(geom, grid)):
+        d = fo.Dims(geom.groups[sub.group], sub)
+        l_cp = fo.low_rate_cp(d, geom.mode)
+        parts += [fo.cp_insert(fo.ofdm_modulate(rows[n], d.L_ofdm), l_cp[n]) for n in range(d.B)]
+    return np.concatenate(parts)
+
+
+@pytest.mark.parametrize("mode,stx,srx", [(fo.SYMBOL_SYNC, fo.OLA, fo.OLS), (fo.SYMBOL_SYNC, fo.OLS, fo.OLA),
+                                          (fo.CONTINUOUS, fo.OLA, fo.OLA), (fo.CONTINUOUS, fo.OLS, fo.OLS)])
+def test_time_io_is_the_fc_part_of_the_grid_path(mode, stx, srx):
+    """Catches a time layout (CP, body, subband order) or a scale that differs from the
+    OFDM stage: TX on the modulated symbols equals TX on the grid, and RX bodies
+    demodulated equal RX on the grid."""
+    rng = np.random.default_rng(5)
+    g1 = wl.Group(64, 32, (16, 8, 8, 12) if mode == fo.SYMBOL_SYNC else (8, 8, 8, 8))
+    subs = (wl.Subband(32, 32, 18, 7, 0, wl.rc_transition_weights(32, 18, 3)),
+            wl.Subband(32, 32, 10, -12, 0, wl.rc_transition_weights(32, 10, 3)))
+    geom = wl.Geometry(mode, stx, srx, (g1,), subs)
+    grid = crand(rng, geom.grid_len())
+    t_in = _time_input_from_grid(geom, grid)
+    assert len(t_in) == sum(fo.time_lengths(geom)[0])
+    w_grid = fo.tx_frame(geom, grid)
+    w_time = fo.tx_frame(geom, t_in, io_time=True)
+    assert np.max(np.abs(w_time - w_grid)) < 1e-12 * np.max(np.abs(w_grid))
+    x = crand(rng, len(w_grid))
+    bodies = fo.rx_frame(geom, x, io_time=True)
+    assert len(bodies) == sum(fo.time_lengths(geom)[1])
+    est, pos = [], 0
+    for sub in geom.subbands:
+        d = fo.Dims(geom.groups[sub.group], sub)
+        for n in range(d.B):
+            est.append(fo.ofdm_demodulate(bodies[pos:pos + d.L_ofdm], d.L_act))
+            pos += d.L_ofdm
+    ref = fo.rx_frame(geom, x)
+    assert np.max(np.abs(np.concatenate(est) - ref)) < 1e-12 * np.max(np.abs(ref))
