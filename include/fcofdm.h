@@ -104,6 +104,16 @@ typedef struct fc_geometry {
    around them; TX with OLA or OLS, RX with OLS. The result agrees with the FP32 path to
    about 1e-5 (RMS, relative). Other geometries ignore the flag. */
 #define FC_FLAG_TENSOR_DFT 4
+/* Time-domain I/O: TX takes, instead of the QAM grid, the low-rate CP-OFDM signal of
+   every subband (per stream, subband after subband in creation order; per subband every
+   symbol's L_CP,m,n samples of CP then its L_OFDM,m samples of body, true scale,
+   fc_sizes.time_tx_len per stream), and RX returns, instead of QAM estimates, every
+   symbol's recovered body before OFDM demodulation (per subband B_g x L_OFDM,m samples,
+   fc_sizes.time_rx_len per stream). This is the FC part alone (Sec. III from eq:padding /
+   eq:BDM on, Sec. IV up to eq:concat2 / CP removal), for callers with their own OFDM or
+   non-OFDM signals. Runs on the generic kernels (and on the tensor-core block passes,
+   whose OFDM passes it replaces by copies). */
+#define FC_FLAG_IO_TIME 8
 
 #define FC_MAX_GROUPS 4
 #define FC_MAX_SUBBANDS 16
@@ -119,6 +129,11 @@ typedef struct fc_sizes {
   int64_t slot_len;        /* T: samples one stream call emits (TX) or takes (RX);
                               0 if the geometry cannot stream (see fc_state_create)    */
   int64_t stream_delay;    /* D = wave_len - slot_len: TX tail / RX look-behind length */
+  int64_t time_tx_len;     /* complex samples of the time-domain TX input per stream    */
+  int64_t time_rx_len;     /* complex samples of the time-domain RX output per stream   */
+  int64_t tx_in_len;       /* what TX reads per stream: grid_len, or time_tx_len with
+                              FC_FLAG_IO_TIME                                           */
+  int64_t rx_out_len;      /* what RX writes per stream: grid_len or time_rx_len        */
 } fc_sizes;
 
 typedef struct fc_plan fc_plan;

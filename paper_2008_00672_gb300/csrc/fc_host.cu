@@ -62,8 +62,8 @@ int run(fc_pipeline* p, int dir, int32_t n_streams, const void* host_in, void* h
   if (!host_in || !host_out) return fc_internal_fail(FC_ERR_INVALID, "host buffer is NULL");
   DevGuard dg(p->device);
   if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
-  const size_t in_len = (size_t)(dir == FC_TX ? p->sz.grid_len : p->sz.wave_len);
-  const size_t out_len = (size_t)(dir == FC_TX ? p->sz.wave_len : p->sz.grid_len);
+  const size_t in_len = (size_t)(dir == FC_TX ? p->sz.tx_in_len : p->sz.wave_len);
+  const size_t out_len = (size_t)(dir == FC_TX ? p->sz.wave_len : p->sz.rx_out_len);
   const cudaStream_t caller = (cudaStream_t)stream;
   cudaError_t e = cudaEventRecord(p->fork, caller);
   for (size_t l = 0; l < p->lanes.size() && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(p->lanes[l], p->fork, 0);
@@ -128,7 +128,8 @@ int fc_pipeline_create(const fc_plan* plan, int32_t chunk_streams, int32_t depth
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) p->done.push_back(ev);
     // one allocation per slot: grid, wave (16-byte aligned for the float4 reductions), workspace
-    const size_t g_b = ((size_t)chunk_streams * p->sz.grid_len * sizeof(float2) + 255) & ~(size_t)255;
+    const size_t g_len = (size_t)std::max(p->sz.tx_in_len, p->sz.rx_out_len);   // grid or time I/O
+    const size_t g_b = ((size_t)chunk_streams * g_len * sizeof(float2) + 255) & ~(size_t)255;
     const size_t w_b = ((size_t)chunk_streams * p->sz.wave_len * sizeof(float2) + 255) & ~(size_t)255;
     void* m = nullptr;
     if (e == cudaSuccess) e = cudaMalloc(&m, g_b + w_b + p->ws_bytes);

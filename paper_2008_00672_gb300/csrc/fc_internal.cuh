@@ -52,7 +52,8 @@ struct FcSubDev {
   const float* dtx;   // [L] D_m * sqrt(I)/(sqrt(L_OFDM) N)
   const float* drx;   // [L] D_m / (sqrt(I) L sqrt(L_OFDM))
   const int* lcp;     // [B] L_CP,m,n
-  const int* soff;    // [B] continuous: symbol start in the low-rate stream
+  const int* soff;    // [B] symbol start in the low-rate stream (CP first)
+  int time_tx_off, time_rx_off;   // FC_FLAG_IO_TIME: subband offset in a stream's time I/O
 };
 
 struct FcJob {
@@ -75,6 +76,7 @@ struct FcPlanDev {
   long long grid_len;
   long long ws_len;   // workspace complex elements per stream
   long long tc_off;   // tensor-core path: workspace offset of the R x 4096 spectrum rows
+  int time_tx_len, time_rx_len;   // FC_FLAG_IO_TIME: per-stream time I/O lengths
   int ring;           // TX ring length (power of two)
   int ybuf;           // spectrum buffer length (complex)
   int wbuf;           // low-rate buffer length (complex)

@@ -25,6 +25,7 @@ namespace {
 // complex helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -375,7 +376,8 @@ k_tx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
   float2* W = Y + P.ybuf;
   const int stream = blockIdx.x / n_chunks;
   const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
-  const float2* gsrc = grid + (size_t)stream * P.grid_len;
+  const bool io_time = (P.flags & FC_FLAG_IO_TIME) != 0;
+  const float2* gsrc = grid + (size_t)stream * (io_time ? P.time_tx_len : P.grid_len);
   float2* wdst = wave + (size_t)stream * P.frame_len;
   const int mask = P.ring - 1;
   zero_buf(ring, P.ring);
@@ -392,8 +394,10 @@ k_tx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
       const FcSubDev& S = P.s[m];
       const int L = S.L, q4 = L / 4;
       const int lcp = S.lcp[n];
-      // T1: OFDM symbol (eq:TX_OFDMmod, scaling folded into D)
-      ofdm_symbol_to_time(P, S, gsrc + S.grid_off + (long long)n * S.Lact, W);
+      // T1: OFDM symbol (eq:TX_OFDMmod, scaling folded into D); time-domain input: the
+      // caller's CP and body, brought to the same scale (sqrt(L_OFDM))
+      const float2* tin = gsrc + S.time_tx_off + S.soff[n];
+      if (!io_time) ofdm_symbol_to_time(P, S, gsrc + S.grid_off + (long long)n * S.Lact, W);
       // T2-T3: CP insertion, zero padding to 3L/2 (eq:padding), two segments with the
       // dynamic-overlap analysis windows a_{m,0}, a_{m,1} (OLA) or none (OLS)
       float2* Z = W + L;
@@ -402,9 +406,15 @@ k_tx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
         const int zi = r * (L / 2) + idx - r * L;     // index in the padded symbol z_n
         bool in = zi >= q4 - lcp && zi < q4 + L;
         if (P.scheme_tx == FC_OLA) in = in && (r == 0 ? zi < 3 * q4 : zi >= 3 * q4);
-        int bi = zi - q4;
-        if (bi < 0) bi += L;
-        Z[idx] = in ? W[bi] : make_float2(0.f, 0.f);
+        float2 v = make_float2(0.f, 0.f);
+        if (in && io_time) {
+          v = cscale(__ldg(tin + zi - (q4 - lcp)), sqrtf((float)S.Lofdm));
+        } else if (in) {
+          int bi = zi - q4;
+          if (bi < 0) bi += L;
+          v = W[bi];
+        }
+        Z[idx] = v;
       }
       __syncthreads();
       // T4: short DFTs of both blocks
@@ -457,7 +467,8 @@ k_rx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
   const int stream = blockIdx.x / n_chunks;
   const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
   const float2* src = wave + (size_t)stream * P.frame_len;
-  float2* gdst = grid + (size_t)stream * P.grid_len;
+  const bool io_time = (P.flags & FC_FLAG_IO_TIME) != 0;
+  float2* gdst = grid + (size_t)stream * (io_time ? P.time_rx_len : P.grid_len);
   const bool ola = P.scheme_rx == FC_OLA;
 
   for (int j = ch.j0; j < ch.j1; ++j) {
@@ -498,8 +509,10 @@ k_rx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
           if (u >= L / 2) v = cadd(v, W[L + u - L / 2]);
         }
         X[t] = v;
+        if (io_time) gdst[S.time_rx_off + (long long)n * L + t] = cscale(v, sqrtf((float)S.Lofdm));   // body, true scale
       }
       __syncthreads();
+      if (io_time) continue;
       // R6: OFDM demodulation, active bins out
       fft_inplace<false>(X, 1, P.sz[S.size_O]);
       float2* row = gdst + S.grid_off + (long long)n * S.Lact;
@@ -540,9 +553,14 @@ k_ofdm_mod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2* 
   int m, n;
   if (!locate_symbol(P, m, n, blockIdx.x - stream * syms_per_stream)) return;
   const FcSubDev& S = P.s[m];
-  ofdm_symbol_to_time(P, S, grid + (size_t)stream * P.grid_len + S.grid_off + (long long)n * S.Lact, buf);
   const int L = S.Lofdm, lcp = S.lcp[n];
   float2* dst = ws + (size_t)stream * P.ws_len + S.ws_off + S.soff[n];
+  if (P.flags & FC_FLAG_IO_TIME) {       // the caller's CP and body, brought to the kernels' scale
+    const float2* src = grid + (size_t)stream * P.time_tx_len + S.time_tx_off + S.soff[n];
+    for (int i = threadIdx.x; i < lcp + L; i += FC_THREADS) dst[i] = cscale(__ldg(src + i), sqrtf((float)S.Lofdm));
+    return;
+  }
+  ofdm_symbol_to_time(P, S, grid + (size_t)stream * P.grid_len + S.grid_off + (long long)n * S.Lact, buf);
   for (int i = threadIdx.x; i < lcp + L; i += FC_THREADS) {   // K_{L_CP} (eq:TX_CPins)
     int bi = i - lcp;
     if (bi < 0) bi += L;
@@ -711,7 +729,10 @@ k_ofdm_demod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2
       for (int r = r_hi; r >= 0 && Pu - r * S.L_S < S.L; --r) v = cadd(v, __ldg(s + (long long)r * S.L + Pu - r * S.L_S));
     }
     buf[t] = v;
+    if (P.flags & FC_FLAG_IO_TIME)       // the body before demodulation, true scale
+      grid[(size_t)stream * P.time_rx_len + S.time_rx_off + (long long)n * Lo + t] = cscale(v, sqrtf((float)S.Lofdm));
   }
+  if (P.flags & FC_FLAG_IO_TIME) return;
   __syncthreads();
   fft_inplace<false>(buf, 1, P.sz[S.size_O]);
   float2* row = grid + (size_t)stream * P.grid_len + S.grid_off + (long long)n * S.Lact;

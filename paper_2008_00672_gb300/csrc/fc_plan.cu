@@ -176,6 +176,12 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     if (sync) {
       if (o.L % 4) return fail(FC_ERR_INVALID, "symbol-sync needs 4 | L");
       if (o.Lo != o.L) return fail(FC_ERR_INVALID, "symbol-sync needs L_OFDM = L");
+      o.soff.resize(g.B);                 // symbol starts of the time-domain I/O
+      int acc = 0;
+      for (int n = 0; n < g.B; ++n) {
+        o.soff[n] = acc;
+        acc += o.lcp[n] + o.Lo;
+      }
     } else {
       if ((long long)o.Lo * g.N % o.L) return fail(FC_ERR_INVALID, "N_OFDM = L_OFDM N / L is not an integer");
       if ((long long)g.lead_hi * o.L % g.N) return fail(FC_ERR_INVALID, "lead pad is not an integer at low rate");
@@ -388,7 +394,8 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   }
 
   // warp-specialised path: symbol-sync, one subband per group, I = 2, L in {512, 1024}
-  bool warp_ok = sync && !(geo->flags & FC_FLAG_GENERIC_KERNELS) && (frame_len % 2 == 0);
+  const bool io_time = (geo->flags & FC_FLAG_IO_TIME) != 0;
+  bool warp_ok = sync && !(geo->flags & FC_FLAG_GENERIC_KERNELS) && !io_time && (frame_len % 2 == 0);
   for (int g = 0; g < G && warp_ok; ++g) {
     if (gh[g].subs.size() != 1) { warp_ok = false; break; }
     const SubHost& o = sh[gh[g].subs[0]];
@@ -487,6 +494,22 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     z.nominal_len = nom;
   }
   z.workspace_per_stream = ws_len * (long long)sizeof(float2);
+  // time-domain I/O layout: per subband (creation order) every symbol's CP and body (TX)
+  // or body (RX)
+  std::vector<long long> t_tx_off(M), t_rx_off(M);
+  long long t_tx = 0, t_rx = 0;
+  for (int m = 0; m < M; ++m) {
+    const GroupHost& g = gh[sh[m].g];
+    t_tx_off[m] = t_tx;
+    t_rx_off[m] = t_rx;
+    for (int n = 0; n < g.B; ++n) t_tx += sh[m].lcp[n] + sh[m].Lo;
+    t_rx += (long long)g.B * sh[m].Lo;
+  }
+  if (t_tx > 0x7fffffffLL || t_rx > 0x7fffffffLL) return fail(FC_ERR_UNSUPPORTED, "time-domain I/O too long");
+  z.time_tx_len = t_tx;
+  z.time_rx_len = t_rx;
+  z.tx_in_len = io_time ? t_tx : grid_len;
+  z.rx_out_len = io_time ? t_rx : grid_len;
   z.slot_len = streamable ? slot_len : 0;
   z.stream_delay = streamable ? stream_delay : 0;
   z.tx_kernels = sync ? 1 : (tc_tx ? 3 : 2);
@@ -525,6 +548,8 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   P.grid_len = grid_len;
   P.ws_len = ws_len;
   P.tc_off = tc_off;
+  P.time_tx_len = (int)t_tx;
+  P.time_rx_len = (int)t_rx;
   P.ring = ring;
   P.ybuf = ybuf;
   P.wbuf = wbuf;
@@ -565,6 +590,8 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     d.drx = reinterpret_cast<const float*>(base + off_drx[m]);
     d.lcp = reinterpret_cast<const int*>(base + off_lcp[m]);
     d.soff = reinterpret_cast<const int*>(base + off_soff[m]);
+    d.time_tx_off = (int)t_tx_off[m];
+    d.time_rx_off = (int)t_rx_off[m];
   }
   std::memcpy(blob.bytes.data() + off_plan, &P, sizeof(P));
   if (upload) {
@@ -585,7 +612,7 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   pl->warp_path = warp_ok;
   pl->tc_tx = tc_tx;
   pl->tc_rx = tc_rx;
-  pl->tc_ofdm = tc_tx && sh[0].Lo == 4096;
+  pl->tc_ofdm = tc_tx && sh[0].Lo == 4096 && !io_time;
   if (tc_tx) {
     pl->d_dft64 = base + off_dft;
     pl->d_err = reinterpret_cast<int*>(base + off_err);

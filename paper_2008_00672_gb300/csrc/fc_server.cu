@@ -94,8 +94,8 @@ int fc_server_add_carrier(fc_server* s, const fc_geometry* geometry, int32_t* ca
   if (sz.slot_len == 0) return fc_internal_fail(FC_ERR_UNSUPPORTED, "carrier geometry cannot stream slot by slot");
   // admission: everything this carrier will hold on the device must fit in free HBM
   // minus the reserve (plan tables are bounded by a generous 8 MiB estimate)
-  const size_t io = align256((size_t)sz.grid_len * 8) + align256((size_t)sz.slot_len * 8) +
-                    align256((size_t)sz.workspace_per_stream);
+  const size_t g_len = (size_t)(sz.tx_in_len > sz.rx_out_len ? sz.tx_in_len : sz.rx_out_len);   // grid or time I/O
+  const size_t io = align256(g_len * 8) + align256((size_t)sz.slot_len * 8) + align256((size_t)sz.workspace_per_stream);
   const size_t state = ((size_t)2 * sz.wave_len + 2 + (size_t)2 * sz.stream_delay) * 8;
   const size_t need = io + state + ((size_t)8 << 20);
   DevGuard dg(s->device);
@@ -126,9 +126,9 @@ int fc_server_add_carrier(fc_server* s, const fc_geometry* geometry, int32_t* ca
   }
   unsigned char* p = (unsigned char*)c.d_io;
   c.d_grid = (float2*)p;
-  c.d_slot = (float2*)(p + align256((size_t)sz.grid_len * 8));
+  c.d_slot = (float2*)(p + align256(g_len * 8));
   c.ws_bytes = (size_t)sz.workspace_per_stream;
-  c.ws = c.ws_bytes ? (void*)(p + align256((size_t)sz.grid_len * 8) + align256((size_t)sz.slot_len * 8)) : nullptr;
+  c.ws = c.ws_bytes ? (void*)(p + align256(g_len * 8) + align256((size_t)sz.slot_len * 8)) : nullptr;
   c.lane = (int)(s->carriers.size() % s->lanes.size());
   *carrier_id = (int32_t)s->carriers.size();
   s->carriers.push_back(c);
@@ -174,8 +174,8 @@ int fc_server_run(fc_server* s, const fc_serve_request* reqs, int32_t n, double*
       const bool tx = r.direction == FC_TX;
       float2* d_in = tx ? c.d_grid : c.d_slot;
       float2* d_out = tx ? c.d_slot : c.d_grid;
-      const size_t in_b = (size_t)(tx ? c.sz.grid_len : c.sz.slot_len) * 8;
-      const size_t out_b = (size_t)(tx ? c.sz.slot_len : c.sz.grid_len) * 8;
+      const size_t in_b = (size_t)(tx ? c.sz.tx_in_len : c.sz.slot_len) * 8;
+      const size_t out_b = (size_t)(tx ? c.sz.slot_len : c.sz.rx_out_len) * 8;
       e = cudaMemcpyAsync(d_in, r.host_in, in_b, cudaMemcpyHostToDevice, st);
       if (e != cudaSuccess) break;
       rc = tx ? fc_tx_synthesize_stream(c.plan, c.state, d_in, d_out, c.ws, c.ws_bytes, (void*)st)

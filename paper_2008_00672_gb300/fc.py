@@ -23,6 +23,7 @@ FC_CONTINUOUS, FC_SYMBOL_SYNC = 0, 1
 FC_FLAG_GENERIC_KERNELS = 1
 FC_FLAG_REDUCED_RX = 2
 FC_FLAG_TENSOR_DFT = 4
+FC_FLAG_IO_TIME = 8
 FC_OLA, FC_OLS = 0, 1
 FC_TX, FC_RX = 0, 1
 
@@ -56,7 +57,9 @@ class FcGeometry(ctypes.Structure):
 class FcSizes(ctypes.Structure):
     _fields_ = [("grid_len", ctypes.c_int64), ("wave_len", ctypes.c_int64), ("nominal_len", ctypes.c_int64),
                 ("workspace_per_stream", ctypes.c_int64), ("tx_kernels", ctypes.c_int32),
-                ("rx_kernels", ctypes.c_int32), ("slot_len", ctypes.c_int64), ("stream_delay", ctypes.c_int64)]
+                ("rx_kernels", ctypes.c_int32), ("slot_len", ctypes.c_int64), ("stream_delay", ctypes.c_int64),
+                ("time_tx_len", ctypes.c_int64), ("time_rx_len", ctypes.c_int64), ("tx_in_len", ctypes.c_int64),
+                ("rx_out_len", ctypes.c_int64)]
 
 
 class FcBatchItem(ctypes.Structure):
@@ -370,6 +373,8 @@ class Plan:
         self.rx_kernels = int(s.rx_kernels)
         self.slot_len = int(s.slot_len)
         self.stream_delay = int(s.stream_delay)
+        self.tx_in_len = int(s.tx_in_len)       # grid_len, or the time-domain TX input length
+        self.rx_out_len = int(s.rx_out_len)     # grid_len, or the time-domain RX output length
         self._ws = None
 
     def close(self):
@@ -411,7 +416,7 @@ class Plan:
         return int(stream.cuda_stream)
 
     def tx_synthesize(self, grid, wave_out, workspace=None, stream=None):
-        n = self._streams(grid, self.grid_len, wave_out, self.wave_len)
+        n = self._streams(grid, self.tx_in_len, wave_out, self.wave_len)
         ws = workspace if workspace is not None else self.workspace(n)
         fc_tx_synthesize(self.handle, n, grid.data_ptr(), wave_out.data_ptr(),
                          ws.data_ptr() if ws is not None else 0,
@@ -419,7 +424,7 @@ class Plan:
         return wave_out
 
     def rx_analyze(self, wave, grid_out, workspace=None, stream=None):
-        n = self._streams(wave, self.wave_len, grid_out, self.grid_len)
+        n = self._streams(wave, self.wave_len, grid_out, self.rx_out_len)
         ws = workspace if workspace is not None else self.workspace(n)
         fc_rx_analyze(self.handle, n, wave.data_ptr(), grid_out.data_ptr(),
                       ws.data_ptr() if ws is not None else 0,
@@ -463,7 +468,7 @@ class State:
 
     def tx(self, grid, slot_out, workspace=None, stream=None):
         p = self.plan
-        n = Plan._streams(grid, p.grid_len, slot_out, p.slot_len)
+        n = Plan._streams(grid, p.tx_in_len, slot_out, p.slot_len)
         if n != self.n_streams:
             raise ValueError("the state was created for another number of streams")
         ws = workspace if workspace is not None else p.workspace(n)
@@ -474,7 +479,7 @@ class State:
 
     def rx(self, slot_in, grid_out, workspace=None, stream=None):
         p = self.plan
-        n = Plan._streams(slot_in, p.slot_len, grid_out, p.grid_len)
+        n = Plan._streams(slot_in, p.slot_len, grid_out, p.rx_out_len)
         if n != self.n_streams:
             raise ValueError("the state was created for another number of streams")
         ws = workspace if workspace is not None else p.workspace(n)
@@ -495,9 +500,9 @@ class Batch:
             plan, direction, src, dst = it[:4]
             state = it[4] if len(it) > 4 else None
             if state is not None:
-                ls, ld = (plan.grid_len, plan.slot_len) if direction == FC_TX else (plan.slot_len, plan.grid_len)
+                ls, ld = (plan.tx_in_len, plan.slot_len) if direction == FC_TX else (plan.slot_len, plan.rx_out_len)
             else:
-                ls, ld = (plan.grid_len, plan.wave_len) if direction == FC_TX else (plan.wave_len, plan.grid_len)
+                ls, ld = (plan.tx_in_len, plan.wave_len) if direction == FC_TX else (plan.wave_len, plan.rx_out_len)
             n = Plan._streams(src, ls, dst, ld)
             self._keep.append((plan, src, dst, state))
             c_items.append(FcBatchItem(plan.handle.value, state.handle.value if state is not None else None,
@@ -538,7 +543,7 @@ class Server:
         reqs = []
         for t, cid, direction, h_in, h_out in requests:
             z = self.sizes[cid]
-            n_in, n_out = (z.grid_len, z.slot_len) if direction == FC_TX else (z.slot_len, z.grid_len)
+            n_in, n_out = (z.tx_in_len, z.slot_len) if direction == FC_TX else (z.slot_len, z.rx_out_len)
             for x, n in ((h_in, n_in), (h_out, n_out)):
                 if x.dtype != torch.complex64 or x.is_cuda or not x.is_contiguous() or x.numel() != n:
                     raise ValueError("expected contiguous complex64 host tensors of the carrier's sizes")
@@ -577,12 +582,12 @@ class Pipeline:
         return a.numel() // la
 
     def tx(self, host_grid, host_wave, stream=None):
-        n = self._host(host_grid, host_wave, self.plan.grid_len, self.plan.wave_len)
+        n = self._host(host_grid, host_wave, self.plan.tx_in_len, self.plan.wave_len)
         fc_tx_synthesize_host(self.handle, n, host_grid.data_ptr(), host_wave.data_ptr(), Plan._stream_handle(stream))
         return host_wave
 
     def rx(self, host_wave, host_grid, stream=None):
-        n = self._host(host_wave, host_grid, self.plan.wave_len, self.plan.grid_len)
+        n = self._host(host_wave, host_grid, self.plan.wave_len, self.plan.rx_out_len)
         fc_rx_analyze_host(self.handle, n, host_wave.data_ptr(), host_grid.data_ptr(), Plan._stream_handle(stream))
         return host_grid
 

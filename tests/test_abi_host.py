@@ -173,3 +173,17 @@ def test_tensor_flag_plans_its_workspace(fc):
     assert (b.tx_kernels, b.rx_kernels) == (3, 3)
     m = wl.config_mixed_20mhz()
     assert fc.fc_geometry_check(dataclasses.replace(m, flags=4)).workspace_per_stream == 0
+
+
+def test_time_io_sizes(fc):
+    """Time-domain I/O lengths follow the oracle's layout; the active I/O lengths switch
+    from the grid to them only with FC_FLAG_IO_TIME."""
+    import dataclasses
+    for name in ("single5", "mixed20"):
+        geom = wl.NAMED[name]()
+        s = fc.fc_geometry_check(geom)
+        tx, rx = fo.time_lengths(geom)
+        assert (s.time_tx_len, s.time_rx_len) == (sum(tx), sum(rx))
+        assert (s.tx_in_len, s.rx_out_len) == (s.grid_len, s.grid_len)
+        t = fc.fc_geometry_check(dataclasses.replace(geom, flags=8))
+        assert (t.tx_in_len, t.rx_out_len) == (sum(tx), sum(rx))
