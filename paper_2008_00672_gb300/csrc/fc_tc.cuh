@@ -1,7 +1,7 @@
 // Blackwell (sm_103a) tensor-core building blocks in inline PTX: mbarriers with
 // bounded waits, 2-D TMA tile loads, tcgen05 TMEM allocation, MMA (kind::f16,
 // FP16 operands, FP32 accumulation, both operands K-major with 128-byte swizzle)
-// and TMEM loads. Used by the GEMM form of FC synthesis (fc_tensor.cu).
+// and TMEM loads. Used by the tensor-core GEMM-DFT passes (fc_tensor.cu).
 #pragma once
 
 #include <cstdint>
@@ -48,7 +48,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
 }
 
 // ---------------------------------------------------------------------------
-// TMA
+// TMA (2-D tiled load into shared memory, completion counted on an mbarrier)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
   asm volatile(
@@ -132,21 +132,5 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&r)[32]) {
 #pragma unroll
   for (int i = 0; i < 32; ++i) r[i] = __uint_as_float(u[i]);
 }
-
-// ---------------------------------------------------------------------------
-// GEMM tile core: D(128 x BN, TMEM, FP32) = A(128 x K) * B(BN x K)^T, both FP16 K-major,
-// K in steps of 64 through an S-stage TMA pipeline. Thread `producer` issues the TMA
-// loads, thread `issuer` the MMAs; everyone else returns immediately. Returns false if
-// a bounded wait gave up (the caller reports FC_ERR_TIMEOUT).
-// smem layout per stage: A tile (128 rows x 128 B) then B tile (BN rows x 128 B),
-// each 1024-byte aligned.
-// ---------------------------------------------------------------------------
-template <int BN, int S>
-struct GemmSmem {
-  static constexpr int kA = 128 * 128;
-  static constexpr int kB = BN * 128;
-  static constexpr int kStage = kA + kB;
-  static constexpr int kBytes = S * kStage;
-};
 
 }  // namespace fctc

@@ -171,6 +171,38 @@ __device__ __forceinline__ void cp_async8(float2* dst, const float2* src, const 
                : "memory");
 }
 
+// The inverse block passes read whole spectrum rows (4096 contiguous samples, 16-byte
+// aligned: workspace rows start at even complex offsets): one bulk copy per row,
+// completing on an mbarrier. The other passes gather or window: per-element copies.
+template <int PASS>
+constexpr bool tc_bulk() {
+  return PASS == FC_TC_TX_IFFT || PASS == FC_TC_RX_IFFT;
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Bulk form (one thread): both rows of `tile` into stg[t][.] on `bar` (rows past the
+// end are not fetched; the staging step zeroes them).
+template <int PASS>
+__device__ __forceinline__ void tc_prefetch_bulk(float2* stg, const float2* __restrict__ ws, const TcK& K, int tile,
+                                                 int total, uint64_t* bar) {
+  uint32_t bytes = 0;
+  for (int t = 0; t < 2; ++t) bytes += (2 * tile + t < total) ? kN * 8u : 0u;
+  fence_async_smem();                    // earlier generic reads of stg before the async writes
+  mbar_arrive_expect_tx(bar, bytes);
+  for (int t = 0; t < 2; ++t) {
+    const int g = 2 * tile + t;
+    if (g >= total) continue;
+    const TcCtx cx = tc_ctx<PASS>(K, g);
+    bulk_copy(stg + t * kN, ws + (long long)cx.s * K.ws_len + K.tc_off + (long long)cx.r * kN, kN * 8u, bar);
+  }
+}
+
 // Stage the raw input of `tile` (two transforms) into stg[t][i]; completes at cp.async.wait_all.
 template <int PASS>
 __device__ __forceinline__ void tc_prefetch(float2* stg, const float2* __restrict__ in, const float2* __restrict__ ws,
@@ -239,6 +271,7 @@ template <int PASS>
 __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t stg_bar;    // bulk staging copies (inverse block passes)
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -265,6 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
   if (warp == 0) tmem_alloc(&tmem_base, 256);
   if (tid == 0) {
     mbar_init(&bar, 1);
+    mbar_init(&stg_bar, 1);
     fence_mbar_init();
     abort_flag = 0;
   }
@@ -288,22 +322,42 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
   const float2 tw_step = __ldg(tw + rlo);
   const float2 tw_seed = __ldg(tw + ((rlo * (16 * h)) & (kN - 1)));
 
-  if (blockIdx.x < n_tiles) tc_prefetch<PASS>(stg, g_in, g_ws, K, blockIdx.x, total, tid);
+  uint32_t stg_phase = 0;
+  if (blockIdx.x < n_tiles) {
+    if (!tc_bulk<PASS>())
+      tc_prefetch<PASS>(stg, g_in, g_ws, K, blockIdx.x, total, tid);
+    else if (tid == 0)
+      tc_prefetch_bulk<PASS>(stg, g_ws, K, blockIdx.x, total, &stg_bar);
+  }
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
     // ---- prologue: A1[64 t + n2][(n1, re/im)] = x_t[64 n1 + n2] from the staged input ----
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (!tc_bulk<PASS>()) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+    } else {
+      if (!mbar_wait(&stg_bar, stg_phase)) {
+        atomicExch(args.err, 1);
+        abort_flag = 1;
+      }
+      stg_phase ^= 1;
+    }
     __syncthreads();
+    if (abort_flag) break;
 #pragma unroll 4
     for (int e = tid; e < 2 * kN; e += kThreads) {
-      float2 v = stg[e];
-      if (tc_conj_in<PASS>()) v.y = -v.y;
       const int t = e >> 12, i = e & (kN - 1);
+      float2 v = (!tc_bulk<PASS>() || 2 * tile + t < total) ? stg[e] : czero();
+      if (tc_conj_in<PASS>()) v.y = -v.y;
       split_store(a_hi, a_lo, op_off(64 * t + (i & 63), 2 * (i >> 6)), v);
     }
     fence_async_smem();
     __syncthreads();
     // the staging buffer is free: fetch the next tile while this one is transformed
-    if (tile + (int)gridDim.x < n_tiles) tc_prefetch<PASS>(stg, g_in, g_ws, K, tile + gridDim.x, total, tid);
+    if (tile + (int)gridDim.x < n_tiles) {
+      if (!tc_bulk<PASS>())
+        tc_prefetch<PASS>(stg, g_in, g_ws, K, tile + gridDim.x, total, tid);
+      else if (tid == 0)
+        tc_prefetch_bulk<PASS>(stg, g_ws, K, tile + gridDim.x, total, &stg_bar);
+    }
     if (tid == 0) {
       tc_fence_after();
       issue_mmas(tbase, sa_hi, sa_lo, sb_hi, sb_lo);
