@@ -53,6 +53,15 @@ __host__ __device__ __forceinline__ uint32_t op_off(int row, int k) {
   return (uint32_t)(j * kChunk + row * 128 + ((((byte >> 4) ^ (row & 7))) << 4) + (byte & 15));
 }
 
+// v = hi + lo in BF16 pairs, returned as the 32-bit words the operand stores
+__device__ __forceinline__ void split_pack(float2 v, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(v.x - hf.x, v.y - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
 __device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, uint32_t off, float2 v) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
   const float2 hf = __bfloat1622float2(h);
@@ -342,12 +351,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     }
     __syncthreads();
     if (abort_flag) break;
-#pragma unroll 4
-    for (int e = tid; e < 2 * kN; e += kThreads) {
-      const int t = e >> 12, i = e & (kN - 1);
-      float2 v = (!tc_bulk<PASS>() || 2 * tile + t < total) ? stg[e] : czero();
-      if (tc_conj_in<PASS>()) v.y = -v.y;
-      split_store(a_hi, a_lo, op_off(64 * t + (i & 63), 2 * (i >> 6)), v);
+    // each thread converts x_t[64 n1 + n2] for four consecutive n1 = 4 a .. 4 a + 3 of one
+    // n2: reads coalesced across the warp (consecutive n2), one 16-byte store per hi/lo
+#pragma unroll
+    for (int it = 0; it < 2 * kN / 4 / kThreads; ++it) {
+      const int e4 = tid + kThreads * it;
+      const int t = e4 >> 10, n2 = e4 & 63, a = (e4 >> 6) & 15;
+      const bool live = !tc_bulk<PASS>() || 2 * tile + t < total;
+      uint32_t hi[4], lo[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float2 v = live ? stg[t * kN + 64 * (4 * a + j) + n2] : czero();
+        if (tc_conj_in<PASS>()) v.y = -v.y;
+        split_pack(v, hi[j], lo[j]);
+      }
+      const uint32_t off = op_off(64 * t + n2, 8 * a);           // 16-byte aligned unit
+      *reinterpret_cast<uint4*>(a_hi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+      *reinterpret_cast<uint4*>(a_lo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
     fence_async_smem();
     __syncthreads();
