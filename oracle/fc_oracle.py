@@ -585,5 +585,27 @@ def rx_frame(geom, wave: np.ndarray, simplified: bool = False, io_time: bool = F
     return np.concatenate(parts)
 
 
+# ---------------------------------------------------------------------------
+# The paper's complexity model (Sec. V-A, eq:highrate, eq:lowrate): real
+# multiplications, split-radix transforms with three real multiplications per
+# complex multiplication. Analytic; it counts, it does not compute signals.
+# ---------------------------------------------------------------------------
+
+def mu(n: int) -> int:
+    """Real multiplications of an n-point split-radix FFT: n log2 n - 3 n + 4."""
+    return int(round(n * math.log2(n))) - 3 * n + 4
+
+
+def complexity_per_symbol(n_long: int, subbands: list, alpha: int = 2, beta: float = 1.0) -> float:
+    """C_high-rate + sum_m C_low-rate,m per OFDM symbol (eq:highrate, eq:lowrate):
+    alpha mu(N) + sum_m [alpha beta mu(L_m) + 6 alpha N_tb,m + mu(L_OFDM,m)], with
+    subbands given as (L_m, L_OFDM,m, N_tb,m); alpha = 2 FC blocks per symbol, beta = 1
+    for the direct RX and 1/2 for the simplified RX of eq:reduc."""
+    total = alpha * mu(n_long)
+    for L, L_ofdm, n_tb in subbands:
+        total += alpha * beta * mu(L) + 6 * alpha * n_tb + mu(L_ofdm)
+    return total
+
+
 def frame_len(geom) -> int:
     return frame_layout(geom)[1]

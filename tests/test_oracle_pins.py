@@ -511,3 +511,103 @@ def test_time_io_is_the_fc_part_of_the_grid_path(mode, stx, srx):
             pos += d.L_ofdm
     ref = fo.rx_frame(geom, x)
     assert np.max(np.abs(np.concatenate(est) - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------------------
+# the paper's complexity model (printed values)
+# ---------------------------------------------------------------------------
+
+def test_complexity_printed_values():
+    """Sec. V-A prints mu(128) = 516 and mu(16) = 20, and the simplified RX replaces
+    three low-rate transforms (two short IDFTs, one OFDM DFT) by two (beta = 1/2)."""
+    assert fo.mu(128) == 516 and fo.mu(16) == 20
+    L = 128
+    direct = 2 * 1.0 * fo.mu(L) + fo.mu(L)           # transform part of C_low-rate, beta = 1
+    reduced = 2 * 0.5 * fo.mu(L) + fo.mu(L)          # beta = 1/2
+    assert abs((direct - reduced) / direct - 1 / 3) < 1e-12
+    # the per-symbol total adds the weights (6 alpha N_tb) and the shared long transform
+    c = fo.complexity_per_symbol(256, [(128, 128, 8)])
+    assert c == 2 * fo.mu(256) + 2 * fo.mu(128) + 6 * 2 * 8 + fo.mu(128)
+
+
+# ---------------------------------------------------------------------------
+# the symbol-synchronized frame as explicit matrices from the printed equations
+# ---------------------------------------------------------------------------
+
+def _frame_matrix(geom):
+    """TX of one subband as sum_n Gamma_{sigma_n} sum_r R_N^{(r)} [S_r] F_r(theta_n)
+    [A_r] R_L^{(r)} Pad_n K_{CP,n} X_OFDM, each factor a dense matrix written from its
+    equation (eq:TX_OFDMmod, eq:TX_CPins, eq:padding, eq:ola_proc windows, eq:ola_synthesis
+    blocks, R placement, eq:multi-symb), for brute force over every basis input."""
+    g, sub = geom.groups[0], geom.subbands[0]
+    N, L, B, La, c = g.n_long, sub.l_short, len(g.n_cp), sub.n_active, sub.centre_bin
+    I = N / L
+    L_L, L_T, N_L, N_T = L // 4, L // 4, N // 4, N // 4
+    L_S, N_S = L // 2, N // 2
+    l_cp = [n_cp * L // N for n_cp in g.n_cp]
+    W = lambda n: np.exp(-2j * np.pi * np.outer(np.arange(n), np.arange(n)) / n)
+    Winv = lambda n: np.conj(W(n)) / n
+    act = np.zeros((L, La))
+    for a in range(La):
+        act[(a - La // 2) % L, a] = 1.0                              # signed frequencies
+    Xofdm = np.sqrt(L) * Winv(L) @ act
+    Pshift = np.zeros((L, L))
+    for p in range(L):
+        Pshift[p, (p - L // 2) % L] = 1.0                            # P^(L/2)
+    Dm = np.diag(np.asarray(sub.weights, float))
+    Q = N_L + N_T + B * N + sum(g.n_cp[1:])
+    T = np.zeros((Q, B * La), dtype=complex)
+    cps = 0
+    sigma = 0
+    for n in range(B):
+        if n > 0:
+            cps += g.n_cp[n]
+            sigma = n * N + cps
+        theta = np.exp(2j * np.pi * c * cps / N)
+        lc = l_cp[n]
+        K = np.vstack([np.eye(L)[L - lc:], np.eye(L)]) if lc else np.eye(L)
+        pad = np.zeros((3 * L // 2, lc + L))
+        pad[L_L - lc: L_L + L, :] = np.eye(lc + L)
+        for r in range(2):
+            RL = np.zeros((L, 3 * L // 2))
+            RL[:, r * L // 2: r * L // 2 + L] = np.eye(L)
+            if geom.scheme_tx == fo.OLA:
+                win = np.zeros(L)
+                if r == 0:
+                    win[L_L - lc: L_L + L_S] = 1.0
+                else:
+                    win[L_L: L_L + L_S] = 1.0
+                A = np.diag(win)
+            else:
+                A = np.eye(L)
+            phi = np.exp(2j * np.pi * r * c * L_S / L)
+            Xi = np.zeros((N, L), dtype=complex)
+            for p in range(L):
+                Xi[(c + p - L // 2) % N, p] = phi * theta
+            F = np.sqrt(I) * Winv(N) @ Xi @ Dm @ Pshift @ W(L)
+            if geom.scheme_tx == fo.OLS:
+                s_win = np.zeros(N)
+                if r == 0:
+                    s_win[N_L - g.n_cp[n]: N_L + N_S] = 1.0
+                else:
+                    s_win[N_L: N_L + N_S] = 1.0
+                F = np.diag(s_win) @ F
+            RN = np.zeros((3 * N // 2, N))
+            RN[r * N // 2: r * N // 2 + N, :] = np.eye(N)
+            Gam = np.zeros((Q, 3 * N // 2))
+            Gam[sigma: sigma + 3 * N // 2, :] = np.eye(3 * N // 2)
+            T[:, n * La:(n + 1) * La] += Gam @ RN @ F @ A @ RL @ pad @ K @ Xofdm
+    return T
+
+
+@pytest.mark.parametrize("stx", [fo.OLA, fo.OLS])
+def test_sync_frame_matches_matrix_transcription(stx):
+    """Catches an index, window, phase or placement slip anywhere in the symbol-sync
+    assembly: every basis input through the oracle equals the column of the matrix."""
+    D = wl.rc_transition_weights(16, 8, 2)
+    geom = geom1(fo.SYMBOL_SYNC, stx, fo.OLS, 32, 16, 16, 16, 8, 5, (8, 4, 0), D)
+    T = _frame_matrix(geom)
+    for j in range(T.shape[1]):
+        e = np.zeros(T.shape[1], dtype=complex)
+        e[j] = 1.0
+        assert np.max(np.abs(fo.tx_frame(geom, e) - T[:, j])) < 1e-12
