@@ -10,13 +10,21 @@
  *     overlap, CP-phase compensation theta_n, CP extrapolation and symbol-wise
  *     OLA (Sec. III-C..E, eq:padding, eq:multi-symb, eq:waveformLen);
  *   - the RX counterparts (Sec. IV, eq:ola_analysis, eq:ols_analysis, eq:concat2),
- *   - CP-OFDM modulation/demodulation of every subband (eq:TX_OFDMmod, eq:TX_CPins).
+ *   - CP-OFDM modulation/demodulation of every subband (eq:TX_OFDMmod, eq:TX_CPins);
+ *   - the simplified overlap-save RX of eq:reduc (FC_FLAG_REDUCED_RX).
+ *
+ * Around the frame calls (fc_tx_synthesize / fc_rx_analyze) the ABI offers, none of
+ * it from the paper: slot-by-slot streams (fc_state), host-buffer pipelines
+ * (fc_pipeline), batches of carriers of different shapes replayed as one CUDA graph
+ * (fc_batch), a serving loop (fc_server), launch-shape autotuning and an
+ * allocation-free TX; and as fc_geometry.flags: tensor-core transforms for 4096-point
+ * carriers (FC_FLAG_TENSOR_DFT) and time-domain I/O of the FC part (FC_FLAG_IO_TIME).
  *
  * Every compute step runs in CUDA kernels for sm_103a. Nothing here falls back
  * to the CPU. All functions return an FC_* status; none throws.
  *
- * Data layout (all device buffers, caller-owned, complex64 = interleaved
- * {float re, float im}, 8-byte aligned; 16-byte alignment recommended):
+ * Data layout (device buffers of the frame calls, caller-owned, complex64 =
+ * interleaved {float re, float im}, 8-byte aligned; 16-byte alignment recommended):
  *   grid  [n_streams][grid_len]: per stream, subband after subband (in the
  *         order given at plan creation), [B_g][L_act,m] QAM symbols with the
  *         active subcarriers in ascending signed frequency
