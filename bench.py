@@ -33,7 +33,8 @@ if ROOT not in sys.path:
 METRIC = "FC TX+RX Msamples/s on 1 GB300 at stated EVM vs FP64 oracle; % HBM peak; p99 slot ms"
 WORKLOAD = "nr20mhz_mixed_15k51prb_30k24prb_symsync_1ms"
 E2E_CHUNK = 128      # streams per chunk of the host-buffer pipelines
-E2E_DEPTH = 4        # device buffer slots / CUDA streams of the pipeline
+E2E_DEPTH = 4        # device buffer slots / CUDA streams of each pipeline
+E2E_PIPES = 2        # pipelines per direction
 SNR_DB = 30.0
 
 
@@ -489,18 +490,24 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     chunk = min(S, E2E_CHUNK)
     if not args.no_autotune:
         plan.autotune(chunk, reps=5)
-    # TX and RX each get a pipeline and a CUDA stream, so TX's device-to-host copies
-    # (waveforms) overlap RX's host-to-device copies (waveforms) and vice versa
-    pipe_tx, pipe_rx = Pipeline(plan, chunk, E2E_DEPTH), Pipeline(plan, chunk, E2E_DEPTH)
-    s_tx, s_rx = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    # TX and RX each get E2E_PIPES pipelines on their own CUDA streams (each on a share
+    # of the streams), so TX's device-to-host copies (waveforms) overlap RX's
+    # host-to-device copies (waveforms) and vice versa
+    pipes = [(Pipeline(plan, chunk, E2E_DEPTH), Pipeline(plan, chunk, E2E_DEPTH)) for _ in range(E2E_PIPES)]
+    lanes = [(torch.cuda.Stream(dev), torch.cuda.Stream(dev)) for _ in range(E2E_PIPES)]
+    share = -(-S // E2E_PIPES)
 
     def e2e_step():
-        s_tx.wait_stream(st)
-        s_rx.wait_stream(st)
-        pipe_tx.tx(h_grid, h_wave, stream=s_tx)
-        pipe_rx.rx(h_rx, h_est, stream=s_rx)
-        st.wait_stream(s_tx)
-        st.wait_stream(s_rx)
+        for i, (p_tx, p_rx) in enumerate(pipes):
+            sl = slice(i * share, min(S, (i + 1) * share))
+            s_tx, s_rx = lanes[i]
+            s_tx.wait_stream(st)
+            s_rx.wait_stream(st)
+            p_tx.tx(h_grid[sl], h_wave[sl], stream=s_tx)
+            p_rx.rx(h_rx[sl], h_est[sl], stream=s_rx)
+        for s_tx, s_rx in lanes:
+            st.wait_stream(s_tx)
+            st.wait_stream(s_rx)
 
     for _ in range(max(1, args.warmup)):
         e2e_step()
@@ -513,15 +520,16 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         e2e_step()
     e1.record(st)
     torch.cuda.synchronize(dev)
-    pipe_tx.close()
-    pipe_rx.close()
+    for p_tx, p_rx in pipes:
+        p_tx.close()
+        p_rx.close()
     e2e_ms = e0.elapsed_time(e1)
     e2e_ms = max_over_ranks(e2e_ms, dev)
     e2e_value = whole_job_msps(2 * nominal * S, world, e2e_steps, e2e_ms)
     h2d = (grid.numel() + rx_in.numel()) * 8
     d2h = (wave.numel() + est.numel()) * 8
-    e2e_how = (f"fc_tx_synthesize_host + fc_rx_analyze_host side by side, {chunk} streams per chunk, "
-               f"{E2E_DEPTH} slots each")
+    e2e_how = (f"fc_tx_synthesize_host + fc_rx_analyze_host side by side, {E2E_PIPES} pipelines per direction, "
+               f"{chunk} streams per chunk, {E2E_DEPTH} slots each")
 
     if rank != 0:
         return
