@@ -313,7 +313,7 @@ def serving_bench(torch, dev, n_requests: int) -> dict:
     fixed 100 MHz / 273 PRB carrier alone."""
     import numpy as np
     import workloads as wl
-    from paper_2008_00672_gb300 import Server
+    from paper_2008_00672_gb300 import FC_FLAG_TENSOR_DFT, Server
 
     def one(carriers, n_req, seed):
         srv = Server(device=dev.index or 0, n_lanes=8, hbm_reserve_bytes=4 << 30)
@@ -342,6 +342,8 @@ def serving_bench(torch, dev, n_requests: int) -> dict:
     return {"budget_ms": 0.5,
             "uneven_16_carriers": one(mix, n_requests, wl.default_seed(5)),
             "nr100mhz_carrier": one([wl.config_100mhz(1)], max(1000, n_requests // 4), wl.default_seed(5) + 1),
+            "nr100mhz_carrier_tensor_path": one([dataclasses.replace(wl.config_100mhz(1), flags=FC_FLAG_TENSOR_DFT)],
+                                                max(1000, n_requests // 4), wl.default_seed(5) + 1),
             "latency": "arrival to completion of H2D copy + stream call + D2H copy, host clock"}
 
 
@@ -401,6 +403,33 @@ def nr100_paths_bench(torch, dev, st, peaks: dict, n_streams: int = 32) -> dict:
     out["tx_rel_diff_tensor_vs_fp32"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
     out["workload"] = f"nr100mhz_30khz_273prb_N4096 x 10 slots, {n_streams} streams, continuous OLA TX / OLS RX"
     return out
+
+
+def tensor_path_accuracy(torch, dev, fo) -> dict:
+    """EVM contribution of the tensor-core path (FC_FLAG_TENSOR_DFT) against the FP64
+    oracle on one stream of two slots of the 100 MHz carrier (TX waveform and RX
+    estimates on the TX output), in dB: 20 log10 of the RMS-normalised error."""
+    import dataclasses
+    import numpy as np
+    import workloads as wl
+    from paper_2008_00672_gb300 import FC_FLAG_TENSOR_DFT, Plan
+    geom = dataclasses.replace(wl.config_100mhz(2), flags=FC_FLAG_TENSOR_DFT)
+    grid = wl.qam_grid(geom, 1, wl.default_seed(3))
+    plan = Plan(geom, device=dev.index or 0)
+    g = torch.from_numpy(grid.astype(np.complex64)).to(dev)
+    w = torch.empty((1, plan.wave_len), dtype=torch.complex64, device=dev)
+    e = torch.empty_like(g)
+    plan.tx_synthesize(g, w)
+    plan.rx_analyze(w, e)
+    torch.cuda.synchronize(dev)
+    wv, ev = w.cpu().numpy()[0], e.cpu().numpy()[0]
+    plan.close()
+    w_ref = fo.tx_frame(geom, grid[0])
+    e_ref = fo.rx_frame(geom, wv.astype(np.complex128))
+    tx = float(np.linalg.norm(wv - w_ref) / np.linalg.norm(w_ref))
+    rx = float(np.linalg.norm(ev - e_ref) / np.linalg.norm(e_ref))
+    return {"tx_rel_rms": tx, "rx_rel_rms": rx, "tx_evm_contribution_db": round(20 * np.log10(tx), 1),
+            "rx_evm_contribution_db": round(20 * np.log10(rx), 1), "budget_db": -60.0}
 
 
 def run_gpu(args, rank: int, world: int, local_rank: int):
@@ -571,21 +600,17 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     nr100 = nr100_paths_bench(torch, dev, st, load_peaks()[0])
     serving = serving_bench(torch, dev, args.serve_requests) if args.serve_requests > 0 else None
 
-    # ---- accuracy of the timed path against the FP64 oracle (one sampled stream) ----
-    from oracle import fc_oracle as fo
+    # ---- one sampled stream of the timed path, kept for the oracle check of the CPU leg ----
     s_chk = S - 1
     gref = grid[s_chk].cpu().numpy().astype(np.complex128)
-    w_ref = fo.tx_frame(geom, gref)
     plan.tx_synthesize(grid, wave)
     plan.rx_analyze(rx_in, est)
     torch.cuda.synchronize(dev)
     w_gpu = wave[s_chk].cpu().numpy()
     r_in = rx_in[s_chk].cpu().numpy().astype(np.complex128)
-    e_ref = fo.rx_frame(geom, r_in)
     e_gpu = est[s_chk].cpu().numpy()
-    tx_err = float(np.linalg.norm(w_gpu - w_ref) / np.linalg.norm(w_ref))
-    rx_err = float(np.linalg.norm(e_gpu - e_ref) / np.linalg.norm(e_ref))
     evm_db = float(10 * np.log10(np.sum(np.abs(e_gpu - gref) ** 2) / np.sum(np.abs(gref) ** 2)))
+    accuracy = {"evm_db_awgn30": evm_db}
 
     # ---- roofline of the dominant kernel --------------------------------------
     peaks, peak_kind = load_peaks()
@@ -612,9 +637,16 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                                 "algorithmic_bytes_per_launch": bytes_frame * S, "peak_kind": peak_kind},
                 "tx_ms": round(tx_ms, 4), "rx_ms": round(rx_ms, 4)}
 
-    # ---- CPU baseline (oracle on the host cores, bounded sample) ---------------
+    # ---- CPU leg: the oracle on the host cores (bounded sample), which also checks the
+    # sampled stream of the timed path and the tensor-core path of the 100 MHz carrier ----
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
+        from oracle import fc_oracle as fo
+        w_ref = fo.tx_frame(geom, gref)
+        e_ref = fo.rx_frame(geom, r_in)
+        accuracy["tx_rel_rms_vs_oracle"] = float(np.linalg.norm(w_gpu - w_ref) / np.linalg.norm(w_ref))
+        accuracy["rx_rel_rms_vs_oracle"] = float(np.linalg.norm(e_gpu - e_ref) / np.linalg.norm(e_ref))
+        accuracy["nr100mhz_tensor_path"] = tensor_path_accuracy(torch, dev, fo)
         cores = os.cpu_count() or 1
         pool = oracle_pool(cores)
         try:
@@ -639,7 +671,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                    "d2h_bytes_per_step": d2h, "path": e2e_how},
            "latency_1stream_ms": {"p50": round(lat[len(lat) // 2], 4), "p99": round(lat[int(0.99 * len(lat))], 4),
                                   "slot_budget_ms": 1.0},
-           "accuracy": {"tx_rel_rms_vs_oracle": tx_err, "rx_rel_rms_vs_oracle": rx_err, "evm_db_awgn30": evm_db},
+           "accuracy": accuracy,
            "rx_variants": rx_variants, "uneven_carriers": uneven, "serving": serving, "nr100mhz_paths": nr100,
            "clocks": clk, "gpu_launches": args.steps * (plan.tx_kernels + plan.rx_kernels)}
     print(json.dumps(out), flush=True)
