@@ -18,6 +18,9 @@ in 5G New Radio"):
   CP extrapolation of Sec. III-E.
 * Continuous and symbol-synchronized FC analysis, OLA or OLS (Sec. IV,
   eq:ola_analysis, eq:ols_analysis, eq:1, eq:concat2) and OFDM demodulation.
+* The simplified symbol-synchronized OLS RX (Sec. V-B, eq:FCcomb, eq:reduc).
+* The FC part alone on time-domain signals (tx_frame / rx_frame with io_time).
+* The complexity model of Sec. V-A (eq:highrate, eq:lowrate), analytic counts only.
 
 Every DFT is the plain O(n^2) definition W_n[k,t] = exp(-j 2 pi k t / n) with the
 exponent reduced exactly (k*t mod n) before the FP64 exp; the independent FC
@@ -49,7 +52,9 @@ DFT closed forms, delayed identity, brute-force linear convolution, exact
 adjoint between TX-OLA and RX-OLS (and TX-OLS / RX-OLA), symbol locality,
 zero-CP equivalence of symbol-synchronized and continuous processing, exact
 continuous-vs-synchronized agreement at I=1 (pins theta_n), tone and
-round-trip checks. The transition weights D_m are an input (the paper does not
+round-trip checks, eq:reduc against the direct RX, the symbol-synchronized frame
+against its equations written as explicit matrices (every basis input), the time-
+domain entry points against the grid path, and the printed complexity values. The transition weights D_m are an input (the paper does not
 print them): parity unpinned for their values, which never enter the oracle's
 arithmetic beyond a diagonal multiply.
 """
