@@ -288,6 +288,9 @@ def uneven_carriers_bench(torch, dev, st, steps: int) -> dict:
     batch = Batch(items, n_lanes=8, use_graph=True)
     ms_graph = timed(batch.launch, reps)
     batch.close()
+    batch = Batch(items, n_lanes=8, use_graph=True, persistent=True)
+    ms_persistent = timed(batch.launch, reps)
+    batch.close()
     for c in cs:
         c[0].autotune(1, reps=3)
     batch = Batch(items, n_lanes=8, use_graph=True)
@@ -300,9 +303,10 @@ def uneven_carriers_bench(torch, dev, st, steps: int) -> dict:
                         "symbol-sync OLA TX + OLS RX",
             "samples_per_pass": samples, "kernels_per_pass": launches,
             "one_by_one_ms": round(ms_seq, 4), "batch_graph_ms": round(ms_graph, 4),
-            "batch_graph_autotuned_ms": round(ms_tuned, 4),
+            "batch_graph_persistent_ms": round(ms_persistent, 4), "batch_graph_autotuned_ms": round(ms_tuned, 4),
             "msamples_per_s": {"one_by_one": round(samples / ms_seq / 1e3, 1),
                                "batch_graph": round(samples / ms_graph / 1e3, 1),
+                               "batch_graph_persistent": round(samples / ms_persistent / 1e3, 1),
                                "batch_graph_autotuned": round(samples / ms_tuned / 1e3, 1)}}
 
 

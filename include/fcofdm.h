@@ -312,10 +312,11 @@ int fc_plan_choice(const fc_plan* plan, int32_t n_streams, int32_t direction, in
  * plans of different geometries (carriers with their own bandwidth, numerology and
  * subbands) as one unit: the calls are spread over `n_lanes` internal CUDA streams
  * that fork from and join back into the caller's stream, so small carriers run side
- * by side instead of one after another. With use_graph != 0 the first fc_batch_launch
+ * by side instead of one after another. With FC_BATCH_GRAPH the first fc_batch_launch
  * captures the whole fork/join into a CUDA graph and later launches replay it (one
  * host call for every kernel of every item); the items' pointers are then fixed, so
- * refill the same buffers between launches. Items with a state are stream calls
+ * refill the same buffers between launches. With FC_BATCH_PERSISTENT the items that
+ * run on the generic symbol-sync kernels share one persistent launch per direction. Items with a state are stream calls
  * (fc_tx_synthesize_stream / fc_rx_analyze_stream), others frame calls. Items must
  * not share output buffers, workspaces or states. Every item's result equals that of
  * its own call.
@@ -333,9 +334,15 @@ typedef struct fc_batch_item {
 
 typedef struct fc_batch fc_batch;
 
-/* Copies the item list; allocates the lanes, events and missing workspaces. */
-int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes, int32_t use_graph,
-                    fc_batch** out);
+/* mode bits of fc_batch_create */
+#define FC_BATCH_GRAPH 1       /* capture the first launch into a CUDA graph, replay it after */
+#define FC_BATCH_PERSISTENT 2  /* frame calls that run on the generic symbol-sync kernels go into one
+                                  work queue per direction (one item = one chunk of one stream),
+                                  run by one persistent launch that takes items largest plan first */
+
+/* Copies the item list; allocates the lanes, events, missing workspaces and (with
+   FC_BATCH_PERSISTENT) the work queues. `mode` is an OR of the FC_BATCH_* bits. */
+int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes, int32_t mode, fc_batch** out);
 int fc_batch_launch(fc_batch* batch, void* stream);
 void fc_batch_destroy(fc_batch* batch);
 

@@ -6,6 +6,7 @@
 // different grid sizes; one after another, the small ones leave most of the 152 SMs
 // idle and every call pays its launch latency. Side by side on lanes they fill the
 // GPU together, and a graph replay issues all of them with one host call.
+#include <algorithm>
 #include <cstdio>
 #include <vector>
 
@@ -20,7 +21,20 @@ struct fc_batch {
   cudaEvent_t ev_fork = nullptr, ev_enter = nullptr, ev_exit = nullptr;
   bool use_graph = false;
   cudaGraphExec_t exec = nullptr;
-  std::vector<void*> owned;                       // workspaces the batch allocated
+  std::vector<void*> owned;                       // workspaces and work lists the batch allocated
+  // persistent mode: the generic symbol-sync frame calls of every item as queues of
+  // (plan, stream, chunk) work items, one per direction and occupancy class (CTAs per
+  // SM their shared memory allows), each run by one persistent launch
+  struct Queue {
+    int dir = 0;
+    FcWork* d_work = nullptr;
+    int n = 0;
+    size_t smem = 0;
+  };
+  std::vector<char> in_queue;                     // item runs through a queue
+  std::vector<Queue> queues;
+  int* d_next = nullptr;                          // one counter per queue
+  int num_sms = 0;
 };
 
 namespace {
@@ -61,7 +75,14 @@ int issue(fc_batch* b) {
   cudaError_t e = cudaEventRecord(b->ev_fork, b->origin);
   for (size_t l = 0; l < b->lanes.size() && e == cudaSuccess; ++l) e = cudaStreamWaitEvent(b->lanes[l], b->ev_fork, 0);
   if (e != cudaSuccess) return cuda_err(e, "batch fork");
+  for (size_t q = 0; q < b->queues.size() && e == cudaSuccess; ++q) {   // the queues, on the first lanes
+    const fc_batch::Queue& Q = b->queues[q];
+    e = fc_launch_sync_multi(Q.dir == FC_TX, Q.d_work, Q.n, b->d_next + q, b->num_sms, Q.smem,
+                             b->lanes[q % b->lanes.size()]);
+  }
+  if (e != cudaSuccess) return cuda_err(e, "persistent queue launch");
   for (size_t i = 0; i < b->items.size(); ++i) {
+    if (!b->in_queue.empty() && b->in_queue[i]) continue;
     const int rc = run_item(b->items[i], b->lanes[i % b->lanes.size()]);
     if (rc != FC_OK) return rc;
   }
@@ -86,8 +107,7 @@ void release(fc_batch* b) {
 
 extern "C" {
 
-int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes, int32_t use_graph,
-                    fc_batch** out) {
+int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes, int32_t mode, fc_batch** out) {
   if (!out) return fc_internal_fail(FC_ERR_INVALID, "out is NULL");
   *out = nullptr;
   if (!items || n_items < 1) return fc_internal_fail(FC_ERR_INVALID, "need at least one item");
@@ -105,7 +125,7 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
   fc_batch* b = new fc_batch();
   b->device = dev;
   b->items.assign(items, items + n_items);
-  b->use_graph = use_graph != 0;
+  b->use_graph = (mode & FC_BATCH_GRAPH) != 0;
   cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
   for (int l = 0; l < n_lanes && e == cudaSuccess; ++l) {
     cudaStream_t s = nullptr;
@@ -136,6 +156,57 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
       b->owned.push_back(p);
       it.workspace = p;
       it.workspace_bytes = need;
+    }
+  }
+  // persistent mode: generic symbol-sync frame calls go to queues by direction and by
+  // occupancy class (1, 2, 3 or 4 CTAs of 512 threads per SM for their shared memory),
+  // items of the largest plans first (each CTA of a launch takes the next item)
+  if (e == cudaSuccess && (mode & FC_BATCH_PERSISTENT)) {
+    b->in_queue.assign(b->items.size(), 0);
+    b->num_sms = fc_internal_num_sms(b->items[0].plan);
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    std::vector<size_t> order(b->items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::vector<long long> size(b->items.size());
+    for (size_t i = 0; i < size.size(); ++i) {
+      fc_sizes sz;
+      fc_query(b->items[i].plan, &sz);
+      size[i] = sz.wave_len;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return size[x] > size[y]; });
+    std::vector<FcWork> work[2][4];
+    size_t smem_of[2][4] = {};
+    for (size_t i : order) {
+      const fc_batch_item& it = b->items[i];
+      if (it.state || it.n_streams == 0) continue;
+      std::vector<FcWork> mine;
+      size_t smem = 0;
+      if (!fc_internal_sync_work(it.plan, it.direction, it.n_streams, it.in, it.out, mine, &smem)) continue;
+      const size_t per_cta = smem + 4096;                         // + static plan copy and slack
+      int cls = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)dev_smem / per_cta)) - 1;
+      b->in_queue[i] = 1;
+      work[it.direction][cls].insert(work[it.direction][cls].end(), mine.begin(), mine.end());
+      smem_of[it.direction][cls] = std::max(smem_of[it.direction][cls], smem);
+    }
+    for (int dir = 0; dir < 2; ++dir)
+      for (int cls = 0; cls < 4; ++cls) {
+        if (work[dir][cls].empty() || e != cudaSuccess) continue;
+        fc_batch::Queue Q;
+        Q.dir = dir;
+        Q.n = (int)work[dir][cls].size();
+        Q.smem = smem_of[dir][cls];
+        e = cudaMalloc(&Q.d_work, work[dir][cls].size() * sizeof(FcWork));
+        if (e == cudaSuccess) {
+          b->owned.push_back(Q.d_work);
+          e = cudaMemcpy(Q.d_work, work[dir][cls].data(), work[dir][cls].size() * sizeof(FcWork),
+                         cudaMemcpyHostToDevice);
+        }
+        b->queues.push_back(Q);
+      }
+    if (e == cudaSuccess && !b->queues.empty()) {
+      e = cudaMalloc(&b->d_next, b->queues.size() * sizeof(int));
+      if (e == cudaSuccess) b->owned.push_back(b->d_next);
     }
   }
   if (e != cudaSuccess) {

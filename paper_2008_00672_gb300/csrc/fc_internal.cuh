@@ -3,6 +3,8 @@
 // value; per-symbol and per-bin tables live in one device allocation.
 #pragma once
 
+#include <vector>
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -87,6 +89,18 @@ struct FcPlanDev {
 };
 
 // kernel launchers (defined in fc_kernels.cu); dP is the plan's device copy
+// one work item of the persistent multi-plan symbol-sync launch: one chunk of one stream
+struct FcWork {
+  const FcPlanDev* plan;
+  const FcJob* jobs;
+  const FcChunk* chunk;
+  const float2* in;
+  float2* out;
+  int stream;
+  int pad;
+};
+cudaError_t fc_launch_sync_multi(bool tx, const FcWork* work, int n_work, int* next, int num_sms, size_t smem,
+                                 cudaStream_t st);
 cudaError_t fc_launch_tx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
                               int n_streams, const float2* grid, float2* wave, size_t smem, cudaStream_t st);
 cudaError_t fc_launch_rx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
@@ -124,3 +138,10 @@ cudaError_t fc_set_warp_smem_limits();
 // helpers for entry points defined outside fc_plan.cu
 int fc_internal_fail(int code, const char* msg);     // records fc_last_error() and returns code
 int fc_internal_plan_device(const fc_plan* plan);    // the device a plan was created on
+// Appends the work items of one frame call (direction FC_TX / FC_RX) on the generic
+// symbol-sync kernels and returns true, or returns false when the plan's call does not
+// run there (continuous mode, or the specialised kernels apply); *smem gets the call's
+// dynamic shared memory.
+bool fc_internal_sync_work(const fc_plan* plan, int dir, int n_streams, const void* in, void* out,
+                           std::vector<FcWork>& work, size_t* smem);
+int fc_internal_num_sms(const fc_plan* plan);

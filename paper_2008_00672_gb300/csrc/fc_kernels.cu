@@ -365,17 +365,14 @@ __device__ __forceinline__ void rx_gather(const FcSubDev& S, int N, const float2
 // ---------------------------------------------------------------------------
 // Symbol-synchronized TX (Sec. III-C..E)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(FC_THREADS, 1)
-k_tx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
-          int n_chunks, const float2* __restrict__ grid, float2* __restrict__ wave) {
-  __shared__ FcPlanDev P;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  load_plan(P, gP);
+// One chunk of one stream: the CTA runs the chunk's symbol jobs in order and owns
+// the output samples [ch.t0, ch.t1) of the stream (written once, from the ring).
+__device__ __forceinline__ void tx_sync_chunk(const FcPlanDev& P, const FcJob* __restrict__ jobs, const FcChunk ch,
+                                              int stream, const float2* __restrict__ grid, float2* __restrict__ wave,
+                                              unsigned char* smem_raw) {
   float2* ring = reinterpret_cast<float2*>(smem_raw);
   float2* Y = ring + P.ring;
   float2* W = Y + P.ybuf;
-  const int stream = blockIdx.x / n_chunks;
-  const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
   const bool io_time = (P.flags & FC_FLAG_IO_TIME) != 0;
   const float2* gsrc = grid + (size_t)stream * (io_time ? P.time_tx_len : P.grid_len);
   float2* wdst = wave + (size_t)stream * P.frame_len;
@@ -453,19 +450,24 @@ k_tx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
   if (ch.t1 > flushed) ring_flush(ring, mask, wdst, flushed, ch.t1);
 }
 
-// ---------------------------------------------------------------------------
-// Symbol-synchronized RX (Sec. IV)
-// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(FC_THREADS, 1)
-k_rx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
-          int n_chunks, const float2* __restrict__ wave, float2* __restrict__ grid) {
+k_tx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
+          int n_chunks, const float2* __restrict__ grid, float2* __restrict__ wave) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   load_plan(P, gP);
+  const int stream = blockIdx.x / n_chunks;
+  tx_sync_chunk(P, jobs, chunks[blockIdx.x - stream * n_chunks], stream, grid, wave, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Symbol-synchronized RX (Sec. IV)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void rx_sync_chunk(const FcPlanDev& P, const FcJob* __restrict__ jobs, const FcChunk ch,
+                                              int stream, const float2* __restrict__ wave, float2* __restrict__ grid,
+                                              unsigned char* smem_raw) {
   float2* Y = reinterpret_cast<float2*>(smem_raw);
   float2* W = Y + P.ybuf;
-  const int stream = blockIdx.x / n_chunks;
-  const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
   const float2* src = wave + (size_t)stream * P.frame_len;
   const bool io_time = (P.flags & FC_FLAG_IO_TIME) != 0;
   float2* gdst = grid + (size_t)stream * (io_time ? P.time_rx_len : P.grid_len);
@@ -523,6 +525,47 @@ k_rx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
       }
       __syncthreads();
     }
+  }
+}
+
+__global__ void __launch_bounds__(FC_THREADS, 1)
+k_rx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
+          int n_chunks, const float2* __restrict__ wave, float2* __restrict__ grid) {
+  __shared__ FcPlanDev P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  load_plan(P, gP);
+  const int stream = blockIdx.x / n_chunks;
+  rx_sync_chunk(P, jobs, chunks[blockIdx.x - stream * n_chunks], stream, wave, grid, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// Symbol-synchronized TX or RX of many plans in one persistent launch: each CTA takes
+// the next work item (plan, stream, chunk) from a device counter, reloads its shared
+// plan copy only when the plan changes, and runs the chunk.
+// ---------------------------------------------------------------------------
+template <bool TX>
+__global__ void __launch_bounds__(FC_THREADS, 1)
+k_sync_multi(const FcWork* __restrict__ work, int n_work, int* __restrict__ next) {
+  __shared__ FcPlanDev P;
+  __shared__ int item;
+  __shared__ const FcPlanDev* loaded;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (threadIdx.x == 0) loaded = nullptr;
+  while (true) {
+    if (threadIdx.x == 0) item = atomicAdd(next, 1);
+    __syncthreads();
+    const int i = item;
+    if (i >= n_work) break;
+    const FcWork w = work[i];
+    if (w.plan != loaded) {
+      load_plan(P, w.plan);                     // ends with a barrier
+      if (threadIdx.x == 0) loaded = w.plan;
+    }
+    if (TX)
+        tx_sync_chunk(P, w.jobs, *w.chunk, w.stream, w.in, w.out, smem_raw);
+    else
+      rx_sync_chunk(P, w.jobs, *w.chunk, w.stream, w.in, w.out, smem_raw);
+    __syncthreads();                            // item and the plan copy are reused
   }
 }
 
@@ -748,6 +791,23 @@ k_ofdm_demod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+cudaError_t fc_launch_sync_multi(bool tx, const FcWork* work, int n_work, int* next, int num_sms, size_t smem,
+                                 cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(int), st);
+  if (e != cudaSuccess || n_work == 0) return e;
+  int per_sm = 0;
+  e = tx ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sync_multi<true>, FC_THREADS, smem)
+         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sync_multi<false>, FC_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  int n_ctas = num_sms * (per_sm > 0 ? per_sm : 1);
+  if (n_ctas > n_work) n_ctas = n_work;
+  if (tx)
+    k_sync_multi<true><<<n_ctas, FC_THREADS, smem, st>>>(work, n_work, next);
+  else
+    k_sync_multi<false><<<n_ctas, FC_THREADS, smem, st>>>(work, n_work, next);
+  return cudaGetLastError();
+}
+
 cudaError_t fc_launch_tx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
                               int n_streams, const float2* grid, float2* wave, size_t smem, cudaStream_t st) {
   k_tx_sync<<<dim3((unsigned)(n_streams * n_chunks)), FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, grid, wave);
@@ -788,6 +848,10 @@ cudaError_t fc_set_smem_limits(size_t max_smem) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_tx_sync, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
   if ((e = cudaFuncSetAttribute(k_rx_sync, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_sync_multi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_sync_multi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
+    return e;
   if ((e = cudaFuncSetAttribute(k_tx_cont, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
   if ((e = cudaFuncSetAttribute(k_rx_cont, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
   if ((e = cudaFuncSetAttribute(k_ofdm_mod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;

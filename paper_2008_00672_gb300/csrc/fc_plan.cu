@@ -746,6 +746,23 @@ int fc_internal_fail(int code, const char* msg) { return fail(code, msg); }
 
 int fc_internal_plan_device(const fc_plan* plan) { return plan ? plan->device : -1; }
 
+int fc_internal_num_sms(const fc_plan* plan) { return plan ? plan->num_sms : 0; }
+
+bool fc_internal_sync_work(const fc_plan* plan, int dir, int n_streams, const void* in, void* out,
+                           std::vector<FcWork>& work, size_t* smem) {
+  if (!plan || plan->h.mode != FC_SYMBOL_SYNC || n_streams < 1) return false;
+  const std::pair<int, int> c = choose(plan, n_streams, dir);
+  if (plan->warp_path && !c.second) return false;       // the specialised kernels run this call
+  const size_t k = (size_t)c.first;
+  const FcChunk* chunks = dir == FC_TX ? plan->tx_chunks[k] : plan->rx_chunks[k];
+  const int n_chunks = dir == FC_TX ? plan->tx_nchunks[k] : plan->rx_nchunks[k];
+  for (int s = 0; s < n_streams; ++s)
+    for (int ch = 0; ch < n_chunks; ++ch)
+      work.push_back(FcWork{plan->d_plan, plan->d_jobs, chunks + ch, (const float2*)in, (float2*)out, s, 0});
+  *smem = dir == FC_TX ? plan->smem_tx : plan->smem_rx;
+  return true;
+}
+
 extern "C" {
 
 int fc_plan_create(fc_plan** out, const fc_geometry* geometry, int32_t device) {

@@ -273,11 +273,14 @@ def fc_plan_choice(plan, n_streams: int, direction: int):
     return int(k.value), int(g.value)
 
 
-def fc_batch_create(items, n_lanes: int = 8, use_graph: bool = True) -> ctypes.c_void_p:
+FC_BATCH_GRAPH, FC_BATCH_PERSISTENT = 1, 2
+
+
+def fc_batch_create(items, n_lanes: int = 8, use_graph: bool = True, persistent: bool = False) -> ctypes.c_void_p:
     arr = (FcBatchItem * len(items))(*items)
     h = ctypes.c_void_p()
-    _check(load_library().fc_batch_create(arr, len(items), int(n_lanes), int(bool(use_graph)), ctypes.byref(h)),
-           "fc_batch_create")
+    mode = (FC_BATCH_GRAPH if use_graph else 0) | (FC_BATCH_PERSISTENT if persistent else 0)
+    _check(load_library().fc_batch_create(arr, len(items), int(n_lanes), mode, ctypes.byref(h)), "fc_batch_create")
     return h
 
 
@@ -493,7 +496,7 @@ class Batch:
     """Owns one fc_batch over (plan, direction, input tensor, output tensor[, state])
     items; launch() runs them all (forked over lanes, replayed as a CUDA graph)."""
 
-    def __init__(self, items, n_lanes: int = 8, use_graph: bool = True):
+    def __init__(self, items, n_lanes: int = 8, use_graph: bool = True, persistent: bool = False):
         self._keep = []
         c_items = []
         for it in items:
@@ -507,7 +510,7 @@ class Batch:
             self._keep.append((plan, src, dst, state))
             c_items.append(FcBatchItem(plan.handle.value, state.handle.value if state is not None else None,
                                        int(direction), n, src.data_ptr(), dst.data_ptr(), None, 0))
-        self.handle = fc_batch_create(c_items, n_lanes, use_graph)
+        self.handle = fc_batch_create(c_items, n_lanes, use_graph, persistent)
 
     def launch(self, stream=None):
         fc_batch_launch(self.handle, Plan._stream_handle(stream))

@@ -42,8 +42,8 @@ def setup(torch, carriers, n_streams, seed):
     return out
 
 
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_batch_uneven_carriers_match_oracle(torch_cuda, use_graph):
+@pytest.mark.parametrize("use_graph,persistent", [(True, False), (False, False), (True, True), (False, True)])
+def test_batch_uneven_carriers_match_oracle(torch_cuda, use_graph, persistent):
     torch = torch_cuda
     from paper_2008_00672_gb300 import FC_RX, FC_TX, Batch
     carriers = wl.config_uneven_carriers(seed=1400, n_carriers=8, n_slots=1)
@@ -58,7 +58,7 @@ def test_batch_uneven_carriers_match_oracle(torch_cuda, use_graph):
         c["rx_in"] = torch.from_numpy(c64(x)).cuda()
     items = [(c["plan"], FC_TX, c["grid"], c["wave"]) for c in cs] + \
             [(c["plan"], FC_RX, c["rx_in"], c["est"]) for c in cs]
-    b = Batch(items, n_lanes=4, use_graph=use_graph)
+    b = Batch(items, n_lanes=4, use_graph=use_graph, persistent=persistent)
     for _ in range(2):                       # second launch replays the graph
         for c in cs:
             c["wave"].zero_()
