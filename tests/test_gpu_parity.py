@@ -35,9 +35,11 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def gpu_tx_rx(torch, geom, grid, wave_rx):
+def gpu_tx_rx(torch, geom, grid, wave_rx, shape=None):
     from paper_2008_00672_gb300 import Plan
     plan = Plan(geom)
+    for direction, (chunks, generic) in (shape or {}).items():   # a launch shape the autotuner can pick
+        plan.set_choice(grid.shape[0], direction, chunks, generic)
     g = torch.from_numpy(c64(grid)).cuda()
     w = torch.empty((grid.shape[0], plan.wave_len), dtype=torch.complex64, device="cuda")
     plan.tx_synthesize(g, w)
@@ -50,7 +52,7 @@ def gpu_tx_rx(torch, geom, grid, wave_rx):
     return out
 
 
-def check_geometry(torch, geom, n_streams, seed, snr_db=30.0, streams_to_check=None):
+def check_geometry(torch, geom, n_streams, seed, snr_db=30.0, streams_to_check=None, shape=None):
     grid = c64(wl.qam_grid(geom, n_streams, seed)).astype(np.complex128)
     idx = list(range(n_streams)) if streams_to_check is None else streams_to_check
     ref_tx = {s: fo.tx_frame(geom, grid[s]) for s in idx}
@@ -60,7 +62,7 @@ def check_geometry(torch, geom, n_streams, seed, snr_db=30.0, streams_to_check=N
     for s in idx:
         wave_rx[s] = wl.awgn(ref_tx[s], snr_db, seed + 7919 * (s + 1))
     wave_rx = c64(wave_rx).astype(np.complex128)
-    w, e = gpu_tx_rx(torch, geom, grid, wave_rx)
+    w, e = gpu_tx_rx(torch, geom, grid, wave_rx, shape)
     # FC_FLAG_REDUCED_RX: compare with the oracle's own eq:reduc form
     reduced = bool(geom.flags & 2) and geom.mode == wl.SYMBOL_SYNC and geom.scheme_rx == fo.OLS
     worst = (0.0, 0.0)
@@ -263,11 +265,14 @@ def test_batch_invariance(torch_cuda, name, flags):
 # full benchmark size: sampled streams against the oracle
 # ---------------------------------------------------------------------------
 
-def test_bench_size_sampled_streams(torch_cuda):
-    """The benchmark's batch of 1 ms subframes (2048 streams): three sampled
-    streams, including the last, against the oracle."""
+@pytest.mark.parametrize("shape", [None, {0: (1, 0), 1: (4, 0)}, {0: (2, 0), 1: (2, 0)}],
+                         ids=["built-in", "tx1-rx4", "tx2-rx2"])
+def test_bench_size_sampled_streams(torch_cuda, shape):
+    """The benchmark's batch of 1 ms subframes (2048 streams) in the launch shapes its
+    set-up autotuning picks (chunks per stream for TX / RX; measured: TX 1, RX 4):
+    three sampled streams, including the last, against the oracle."""
     geom = wl.config_mixed_20mhz()
-    check_geometry(torch_cuda, geom, 2048, wl.default_seed(2), streams_to_check=[0, 1025, 2047])
+    check_geometry(torch_cuda, geom, 2048, wl.default_seed(2), streams_to_check=[0, 1025, 2047], shape=shape)
 
 
 # ---------------------------------------------------------------------------
