@@ -247,10 +247,13 @@ def run_reference(args, rank: int, world: int):
 def uneven_carriers_bench(torch, dev, st, steps: int) -> dict:
     """TX + RX of 64 carriers of uneven shape (one stream each, 4 slots): the batch
     executor with a CUDA graph over 8 lanes, against the same calls issued one by one
-    on one stream, and with autotuned launch shapes."""
+    on one stream, and with autotuned launch shapes; then the same batch with complex-
+    BF16 I/O buffers (FC_FLAG_IO_BF16)."""
+    import dataclasses
+
     import numpy as np
     import workloads as wl
-    from paper_2008_00672_gb300 import FC_RX, FC_TX, Batch, Plan
+    from paper_2008_00672_gb300 import FC_FLAG_IO_BF16, FC_RX, FC_TX, Batch, Plan
 
     carriers = wl.config_uneven_carriers(seed=wl.default_seed(4), n_carriers=64, n_slots=4)
     cs = []
@@ -297,7 +300,34 @@ def uneven_carriers_bench(torch, dev, st, steps: int) -> dict:
     ms_tuned = timed(batch.launch, reps)
     batch.close()
     launches = sum(c[0].tx_kernels + c[0].rx_kernels for c in cs)
-    for c in cs:
+    # complex-BF16 I/O: the same carriers, inputs rounded to BF16, 4 bytes a sample
+    bf = []
+    for i, geom in enumerate(carriers):
+        plan = Plan(dataclasses.replace(geom, flags=geom.flags | FC_FLAG_IO_BF16), device=dev.index or 0)
+        grid = torch.view_as_real(cs[i][1]).to(torch.bfloat16).contiguous()
+        wave = torch.empty((1, plan.wave_len, 2), dtype=torch.bfloat16, device=dev)
+        est = torch.empty((1, plan.grid_len, 2), dtype=torch.bfloat16, device=dev)
+        plan.tx_synthesize(grid, wave)
+        bf.append((plan, grid, wave, wave.clone(), est))
+    items_bf = [(c[0], FC_TX, c[1], c[2]) for c in bf] + [(c[0], FC_RX, c[3], c[4]) for c in bf]
+    batch = Batch(items_bf, n_lanes=8, use_graph=True)
+    ms_bf_graph = timed(batch.launch, reps)
+    batch.close()
+    batch = Batch(items_bf, n_lanes=8, use_graph=True, persistent=True)
+    ms_bf_persistent = timed(batch.launch, reps)
+    batch.close()
+    # BF16 result against the complex64 result of the same calls (input and output rounding)
+    num = den = 0.0
+    for c, b in zip(cs, bf):
+        c[0].tx_synthesize(c[1], c[2])
+        b[0].tx_synthesize(b[1], b[2])
+        torch.cuda.synchronize(dev)
+        ref = torch.view_as_real(c[2]).double()
+        num += float(((b[2].double() - ref) ** 2).sum())
+        den += float((ref ** 2).sum())
+    bf16_db = 10 * np.log10(num / den)
+    io_bytes = sum(2 * (c[0].grid_len + c[0].wave_len) for c in cs)     # TX + RX, one stream each
+    for c in cs + bf:
         c[0].close()
     return {"workload": "64 carriers (5-100 MHz, 15/30/60 kHz, 1-8 subbands each), 1 stream x 4 slots each, "
                         "symbol-sync OLA TX + OLS RX",
@@ -307,7 +337,14 @@ def uneven_carriers_bench(torch, dev, st, steps: int) -> dict:
             "msamples_per_s": {"one_by_one": round(samples / ms_seq / 1e3, 1),
                                "batch_graph": round(samples / ms_graph / 1e3, 1),
                                "batch_graph_persistent": round(samples / ms_persistent / 1e3, 1),
-                               "batch_graph_autotuned": round(samples / ms_tuned / 1e3, 1)}}
+                               "batch_graph_autotuned": round(samples / ms_tuned / 1e3, 1)},
+            "bf16_io": {"batch_graph_ms": round(ms_bf_graph, 4), "batch_graph_persistent_ms": round(ms_bf_persistent, 4),
+                        "msamples_per_s": {"batch_graph": round(samples / ms_bf_graph / 1e3, 1),
+                                           "batch_graph_persistent": round(samples / ms_bf_persistent / 1e3, 1)},
+                        "io_bytes_per_pass": {"complex64": 8 * io_bytes, "bf16": 4 * io_bytes},
+                        "tx_vs_complex64_db": round(bf16_db, 1),
+                        "note": "same carriers and calls with complex-BF16 buffers; the difference to the "
+                                "complex64 result is the BF16 rounding of input and output"}}
 
 
 def serving_bench(torch, dev, n_requests: int) -> dict:

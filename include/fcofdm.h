@@ -18,13 +18,15 @@
  * (fc_pipeline), batches of carriers of different shapes replayed as one CUDA graph
  * (fc_batch), a serving loop (fc_server), launch-shape autotuning and an
  * allocation-free TX; and as fc_geometry.flags: tensor-core transforms for 4096-point
- * carriers (FC_FLAG_TENSOR_DFT) and time-domain I/O of the FC part (FC_FLAG_IO_TIME).
+ * carriers (FC_FLAG_TENSOR_DFT), time-domain I/O of the FC part (FC_FLAG_IO_TIME) and
+ * complex-BF16 I/O buffers (FC_FLAG_IO_BF16).
  *
  * Every compute step runs in CUDA kernels for sm_103a. Nothing here falls back
  * to the CPU. All functions return an FC_* status; none throws.
  *
  * Data layout (device buffers of the frame calls, caller-owned, complex64 =
- * interleaved {float re, float im}, 8-byte aligned; 16-byte alignment recommended):
+ * interleaved {float re, float im}, 8-byte aligned; 16-byte alignment recommended;
+ * with FC_FLAG_IO_BF16 complex BF16 = {bfloat16 re, bfloat16 im}, 4-byte aligned):
  *   grid  [n_streams][grid_len]: per stream, subband after subband (in the
  *         order given at plan creation), [B_g][L_act,m] QAM symbols with the
  *         active subcarriers in ascending signed frequency
@@ -122,6 +124,17 @@ typedef struct fc_geometry {
    non-OFDM signals. Runs on the generic kernels (and on the tensor-core block passes,
    whose OFDM passes it replaces by copies). */
 #define FC_FLAG_IO_TIME 8
+/* Complex-BF16 I/O: every caller buffer of the plan's calls (grid or time-domain input,
+   waveform, slots; device and host) holds complex samples as interleaved
+   {bfloat16 re, bfloat16 im}, 4 bytes a sample (fc_sizes.sample_bytes), 4-byte aligned.
+   The lengths in fc_sizes are unchanged. The kernels read BF16, compute in FP32 exactly
+   as without the flag, and round each output sample once to the nearest BF16 (ties to
+   even): the result is the complex64 result rounded to BF16, up to the FP32 path's own
+   error at rounding boundaries. Stream calls keep their TX tail and RX look-behind in
+   FP32, so a streamed slot is rounded once too. Runs on the generic kernels; the
+   specialised and tensor-core kernels (FC_FLAG_TENSOR_DFT) do not apply. Combines with
+   FC_FLAG_IO_TIME. */
+#define FC_FLAG_IO_BF16 16
 
 #define FC_MAX_GROUPS 4
 #define FC_MAX_SUBBANDS 16
@@ -142,6 +155,7 @@ typedef struct fc_sizes {
   int64_t tx_in_len;       /* what TX reads per stream: grid_len, or time_tx_len with
                               FC_FLAG_IO_TIME                                           */
   int64_t rx_out_len;      /* what RX writes per stream: grid_len or time_rx_len        */
+  int64_t sample_bytes;    /* bytes of one complex I/O sample: 8, or 4 with FC_FLAG_IO_BF16 */
 } fc_sizes;
 
 typedef struct fc_plan fc_plan;
@@ -363,7 +377,8 @@ typedef struct fc_serve_request {
   double arrival_s;        /* seconds after the start of fc_server_run; non-decreasing  */
   int32_t carrier;         /* id from fc_server_add_carrier                             */
   int32_t direction;       /* FC_TX: grid in, slot_len samples out; FC_RX: the reverse  */
-  const void* host_in;     /* host complex64 (page-locked memory for asynchronous copies) */
+  const void* host_in;     /* host samples, complex64 or (FC_FLAG_IO_BF16) complex BF16;
+                              page-locked memory for asynchronous copies                */
   void* host_out;
 } fc_serve_request;
 

@@ -21,6 +21,9 @@ in 5G New Radio"):
 * The simplified symbol-synchronized OLS RX (Sec. V-B, eq:FCcomb, eq:reduc).
 * The FC part alone on time-domain signals (tx_frame / rx_frame with io_time).
 * The complexity model of Sec. V-A (eq:highrate, eq:lowrate), analytic counts only.
+* BF16 rounding of complex samples (bf16_round), for the expected values of complex-BF16
+  I/O: the paper computes in full precision; a BF16 output is the exact result rounded
+  once to the nearest BF16 value (8 significand bits, ties to even), per real component.
 
 Every DFT is the plain O(n^2) definition W_n[k,t] = exp(-j 2 pi k t / n) with the
 exponent reduced exactly (k*t mod n) before the FP64 exp; the independent FC
@@ -54,7 +57,8 @@ zero-CP equivalence of symbol-synchronized and continuous processing, exact
 continuous-vs-synchronized agreement at I=1 (pins theta_n), tone and
 round-trip checks, eq:reduc against the direct RX, the symbol-synchronized frame
 against its equations written as explicit matrices (every basis input), the time-
-domain entry points against the grid path, and the printed complexity values. The transition weights D_m are an input (the paper does not
+domain entry points against the grid path, the printed complexity values, and BF16
+rounding against torch's CPU conversion, hand-worked ties and the half-ulp bound. The transition weights D_m are an input (the paper does not
 print them): parity unpinned for their values, which never enter the oracle's
 arithmetic beyond a diagonal multiply.
 """
@@ -614,3 +618,32 @@ def complexity_per_symbol(n_long: int, subbands: list, alpha: int = 2, beta: flo
 
 def frame_len(geom) -> int:
     return frame_layout(geom)[1]
+
+
+# ---------------------------------------------------------------------------
+# BF16 rounding (complex-BF16 I/O). bfloat16 keeps the float32 exponent range and 8
+# significand bits (7 stored). A nonzero real v with 2^e <= |v| < 2^(e+1) has spacing
+# 2^(e-7) (e clamped at -126 below the normal range); its BF16 value is the nearest
+# multiple of that spacing, ties to the even multiple. Magnitudes beyond the BF16 range
+# (about 3.4e38) do not occur in these signals and are not handled.
+# ---------------------------------------------------------------------------
+
+def _bf16_round_real(v: np.ndarray) -> np.ndarray:
+    v = np.asarray(v, dtype=np.float64)
+    out = np.zeros_like(v)
+    nz = v != 0
+    a = np.abs(v[nz])
+    _, ex = np.frexp(a)                     # a = f 2^ex, 1/2 <= f < 1, so e = ex - 1
+    e = np.maximum(ex - 1, -126)
+    spacing = np.ldexp(1.0, e - 7)
+    q = np.round(a / spacing)               # exact quotient; numpy rounds halves to even
+    out[nz] = np.sign(v[nz]) * q * spacing
+    return out
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """x rounded to complex BF16 (real and imaginary parts separately), as complex128."""
+    x = np.asarray(x)
+    if np.iscomplexobj(x):
+        return _bf16_round_real(x.real) + 1j * _bf16_round_real(x.imag)
+    return _bf16_round_real(x)

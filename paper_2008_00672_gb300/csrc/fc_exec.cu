@@ -27,6 +27,7 @@ struct fc_batch {
   // SM their shared memory allows), each run by one persistent launch
   struct Queue {
     int dir = 0;
+    int io = 0;                                   // FC_IO_* bits shared by its items
     FcWork* d_work = nullptr;
     int n = 0;
     size_t smem = 0;
@@ -77,7 +78,7 @@ int issue(fc_batch* b) {
   if (e != cudaSuccess) return cuda_err(e, "batch fork");
   for (size_t q = 0; q < b->queues.size() && e == cudaSuccess; ++q) {   // the queues, on the first lanes
     const fc_batch::Queue& Q = b->queues[q];
-    e = fc_launch_sync_multi(Q.dir == FC_TX, Q.d_work, Q.n, b->d_next + q, b->num_sms, Q.smem,
+    e = fc_launch_sync_multi(Q.dir == FC_TX, Q.d_work, Q.n, Q.io, b->d_next + q, b->num_sms, Q.smem,
                              b->lanes[q % b->lanes.size()]);
   }
   if (e != cudaSuccess) return cuda_err(e, "persistent queue launch");
@@ -158,9 +159,10 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
       it.workspace_bytes = need;
     }
   }
-  // persistent mode: generic symbol-sync frame calls go to queues by direction and by
-  // occupancy class (1, 2, 3 or 4 CTAs of 512 threads per SM for their shared memory),
-  // items of the largest plans first (each CTA of a launch takes the next item)
+  // persistent mode: generic symbol-sync frame calls go to queues by direction, by I/O
+  // type (complex64 or complex BF16) and by occupancy class (1, 2, 3 or 4 CTAs of 512
+  // threads per SM for their shared memory), items of the largest plans first (each CTA
+  // of a launch takes the next item)
   if (e == cudaSuccess && (mode & FC_BATCH_PERSISTENT)) {
     b->in_queue.assign(b->items.size(), 0);
     b->num_sms = fc_internal_num_sms(b->items[0].plan);
@@ -175,8 +177,8 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
       size[i] = sz.wave_len;
     }
     std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return size[x] > size[y]; });
-    std::vector<FcWork> work[2][4];
-    size_t smem_of[2][4] = {};
+    std::vector<FcWork> work[2][2][4];   // [direction][BF16 I/O][occupancy class]
+    size_t smem_of[2][2][4] = {};
     for (size_t i : order) {
       const fc_batch_item& it = b->items[i];
       if (it.state || it.n_streams == 0) continue;
@@ -185,25 +187,29 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
       if (!fc_internal_sync_work(it.plan, it.direction, it.n_streams, it.in, it.out, mine, &smem)) continue;
       const size_t per_cta = smem + 4096;                         // + static plan copy and slack
       int cls = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)dev_smem / per_cta)) - 1;
+      const int bf = fc_internal_io(it.plan) != 0;
       b->in_queue[i] = 1;
-      work[it.direction][cls].insert(work[it.direction][cls].end(), mine.begin(), mine.end());
-      smem_of[it.direction][cls] = std::max(smem_of[it.direction][cls], smem);
+      std::vector<FcWork>& w = work[it.direction][bf][cls];
+      w.insert(w.end(), mine.begin(), mine.end());
+      smem_of[it.direction][bf][cls] = std::max(smem_of[it.direction][bf][cls], smem);
     }
     for (int dir = 0; dir < 2; ++dir)
-      for (int cls = 0; cls < 4; ++cls) {
-        if (work[dir][cls].empty() || e != cudaSuccess) continue;
-        fc_batch::Queue Q;
-        Q.dir = dir;
-        Q.n = (int)work[dir][cls].size();
-        Q.smem = smem_of[dir][cls];
-        e = cudaMalloc(&Q.d_work, work[dir][cls].size() * sizeof(FcWork));
-        if (e == cudaSuccess) {
-          b->owned.push_back(Q.d_work);
-          e = cudaMemcpy(Q.d_work, work[dir][cls].data(), work[dir][cls].size() * sizeof(FcWork),
-                         cudaMemcpyHostToDevice);
+      for (int bf = 0; bf < 2; ++bf)
+        for (int cls = 0; cls < 4; ++cls) {
+          const std::vector<FcWork>& w = work[dir][bf][cls];
+          if (w.empty() || e != cudaSuccess) continue;
+          fc_batch::Queue Q;
+          Q.dir = dir;
+          Q.io = bf ? (FC_IO_IN_BF16 | FC_IO_OUT_BF16) : 0;
+          Q.n = (int)w.size();
+          Q.smem = smem_of[dir][bf][cls];
+          e = cudaMalloc(&Q.d_work, w.size() * sizeof(FcWork));
+          if (e == cudaSuccess) {
+            b->owned.push_back(Q.d_work);
+            e = cudaMemcpy(Q.d_work, w.data(), w.size() * sizeof(FcWork), cudaMemcpyHostToDevice);
+          }
+          b->queues.push_back(Q);
         }
-        b->queues.push_back(Q);
-      }
     if (e == cudaSuccess && !b->queues.empty()) {
       e = cudaMalloc(&b->d_next, b->queues.size() * sizeof(int));
       if (e == cudaSuccess) b->owned.push_back(b->d_next);

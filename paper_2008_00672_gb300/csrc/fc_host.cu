@@ -20,7 +20,7 @@ struct fc_pipeline {
   std::vector<cudaStream_t> lanes;
   std::vector<cudaEvent_t> done;
   cudaEvent_t fork = nullptr;
-  std::vector<float2*> grid, wave;
+  std::vector<unsigned char*> grid, wave;
   std::vector<void*> ws;
   size_t ws_bytes = 0;
   std::vector<void*> owned;
@@ -75,15 +75,16 @@ int run(fc_pipeline* p, int dir, int32_t n_streams, const void* host_in, void* h
     used = std::max(used, slot + 1);
     const cudaStream_t st = p->lanes[slot];
     const int s0 = c * p->chunk, ns = std::min(p->chunk, n_streams - s0);
-    float2* d_in = dir == FC_TX ? p->grid[slot] : p->wave[slot];
-    float2* d_out = dir == FC_TX ? p->wave[slot] : p->grid[slot];
-    e = cudaMemcpyAsync(d_in, (const float2*)host_in + (size_t)s0 * in_len, (size_t)ns * in_len * sizeof(float2),
+    const size_t sb = (size_t)p->sz.sample_bytes;   // complex64 or complex BF16
+    unsigned char* d_in = dir == FC_TX ? p->grid[slot] : p->wave[slot];
+    unsigned char* d_out = dir == FC_TX ? p->wave[slot] : p->grid[slot];
+    e = cudaMemcpyAsync(d_in, (const unsigned char*)host_in + (size_t)s0 * in_len * sb, (size_t)ns * in_len * sb,
                         cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_err(e, "pipeline host-to-device copy");
     const int rc = dir == FC_TX ? fc_tx_synthesize(p->plan, ns, d_in, d_out, p->ws[slot], p->ws_bytes, (void*)st)
                                 : fc_rx_analyze(p->plan, ns, d_in, d_out, p->ws[slot], p->ws_bytes, (void*)st);
     if (rc != FC_OK) return rc;
-    e = cudaMemcpyAsync((float2*)host_out + (size_t)s0 * out_len, d_out, (size_t)ns * out_len * sizeof(float2),
+    e = cudaMemcpyAsync((unsigned char*)host_out + (size_t)s0 * out_len * sb, d_out, (size_t)ns * out_len * sb,
                         cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_err(e, "pipeline device-to-host copy");
   }
@@ -129,14 +130,15 @@ int fc_pipeline_create(const fc_plan* plan, int32_t chunk_streams, int32_t depth
     if (e == cudaSuccess) p->done.push_back(ev);
     // one allocation per slot: grid, wave (16-byte aligned for the float4 reductions), workspace
     const size_t g_len = (size_t)std::max(p->sz.tx_in_len, p->sz.rx_out_len);   // grid or time I/O
-    const size_t g_b = ((size_t)chunk_streams * g_len * sizeof(float2) + 255) & ~(size_t)255;
-    const size_t w_b = ((size_t)chunk_streams * p->sz.wave_len * sizeof(float2) + 255) & ~(size_t)255;
+    const size_t sb = (size_t)p->sz.sample_bytes;
+    const size_t g_b = ((size_t)chunk_streams * g_len * sb + 255) & ~(size_t)255;
+    const size_t w_b = ((size_t)chunk_streams * p->sz.wave_len * sb + 255) & ~(size_t)255;
     void* m = nullptr;
     if (e == cudaSuccess) e = cudaMalloc(&m, g_b + w_b + p->ws_bytes);
     if (e == cudaSuccess) {
       p->owned.push_back(m);
-      p->grid.push_back((float2*)m);
-      p->wave.push_back((float2*)((unsigned char*)m + g_b));
+      p->grid.push_back((unsigned char*)m);
+      p->wave.push_back((unsigned char*)m + g_b);
       p->ws.push_back(p->ws_bytes ? (void*)((unsigned char*)m + g_b + w_b) : nullptr);
     }
   }

@@ -88,31 +88,38 @@ struct FcPlanDev {
   FcSize sz[FC_MAX_SIZES];
 };
 
+// I/O sample type of a generic-kernel launch: complex64 unless the bit is set, then
+// complex BF16 ({bf16 re, bf16 im}). A frame call of an FC_FLAG_IO_BF16 plan sets both;
+// stream calls keep their internal frame in FP32 (TX: BF16 in, FP32 out; RX: the reverse).
+#define FC_IO_IN_BF16 1
+#define FC_IO_OUT_BF16 2
+
 // kernel launchers (defined in fc_kernels.cu); dP is the plan's device copy
 // one work item of the persistent multi-plan symbol-sync launch: one chunk of one stream
 struct FcWork {
   const FcPlanDev* plan;
   const FcJob* jobs;
   const FcChunk* chunk;
-  const float2* in;
-  float2* out;
+  const void* in;
+  void* out;
   int stream;
-  int pad;
+  int io;             // FC_IO_* bits: 0 or FC_IO_IN_BF16 | FC_IO_OUT_BF16
 };
-cudaError_t fc_launch_sync_multi(bool tx, const FcWork* work, int n_work, int* next, int num_sms, size_t smem,
+// every item of one launch has the same io (0 or FC_IO_IN_BF16 | FC_IO_OUT_BF16)
+cudaError_t fc_launch_sync_multi(bool tx, const FcWork* work, int n_work, int io, int* next, int num_sms, size_t smem,
                                  cudaStream_t st);
 cudaError_t fc_launch_tx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                              int n_streams, const float2* grid, float2* wave, size_t smem, cudaStream_t st);
+                              int n_streams, const void* grid, void* wave, int io, size_t smem, cudaStream_t st);
 cudaError_t fc_launch_rx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                              int n_streams, const float2* wave, float2* grid, size_t smem, cudaStream_t st);
-cudaError_t fc_launch_ofdm_mod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const float2* grid,
-                               float2* ws, size_t smem, cudaStream_t st);
+                              int n_streams, const void* wave, void* grid, int io, size_t smem, cudaStream_t st);
+cudaError_t fc_launch_ofdm_mod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const void* grid,
+                               float2* ws, int io, size_t smem, cudaStream_t st);
 cudaError_t fc_launch_tx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                              int n_streams, const float2* ws, float2* wave, size_t smem, cudaStream_t st);
+                              int n_streams, const float2* ws, void* wave, int io, size_t smem, cudaStream_t st);
 cudaError_t fc_launch_rx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                              int n_streams, const float2* wave, float2* ws, size_t smem, cudaStream_t st);
+                              int n_streams, const void* wave, float2* ws, int io, size_t smem, cudaStream_t st);
 cudaError_t fc_launch_ofdm_demod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const float2* ws,
-                                 float2* grid, size_t smem, cudaStream_t st);
+                                 void* grid, int io, size_t smem, cudaStream_t st);
 // raise the dynamic shared-memory limit of every kernel on the current device
 cudaError_t fc_set_smem_limits(size_t max_dynamic_smem);
 
@@ -144,4 +151,11 @@ int fc_internal_plan_device(const fc_plan* plan);    // the device a plan was cr
 // dynamic shared memory.
 bool fc_internal_sync_work(const fc_plan* plan, int dir, int n_streams, const void* in, void* out,
                            std::vector<FcWork>& work, size_t* smem);
+// A frame call (direction FC_TX / FC_RX) with the I/O types io (FC_IO_* bits) instead of
+// the plan's own; the stream calls use it to keep their frames in FP32. Same checks and
+// status as fc_tx_synthesize / fc_rx_analyze.
+int fc_internal_frame(const fc_plan* plan, int dir, int n_streams, const void* in, void* out, void* workspace,
+                      size_t workspace_bytes, void* stream, int io);
+// The FC_IO_* bits of the plan's frame calls.
+int fc_internal_io(const fc_plan* plan);
 int fc_internal_num_sms(const fc_plan* plan);

@@ -17,6 +17,8 @@
 // Symbol-synchronized jobs are (group, symbol) pairs and process the two FC
 // blocks of a symbol as a batch of two (Sec. III-C); continuous jobs are pairs
 // of consecutive FC blocks (Sec. III-B).
+#include <cuda_bf16.h>
+
 #include "fc_internal.cuh"
 
 namespace {
@@ -30,6 +32,14 @@ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
+// I/O samples: complex64 (float2) or complex BF16 (bf2 = {re, im}); the arithmetic is
+// FP32 either way, and a BF16 output is rounded once, to nearest, ties to even.
+using bf2 = __nv_bfloat162;
+__device__ __forceinline__ float2 io_ld(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 io_ld(const bf2* p) { return __bfloat1622float2(__ldg(p)); }
+__device__ __forceinline__ void io_st(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void io_st(bf2* p, float2 v) { *p = __float22bfloat162_rn(v); }
+
 // multiply by -i (forward transform) or +i (inverse transform)
 template <bool INV>
 __device__ __forceinline__ float2 mul_mi(float2 a) {
@@ -293,12 +303,13 @@ __device__ __forceinline__ int active_index(int i, int n, int n_act) {
 }
 
 // Copy ring[from, to) to dst and clear it, in segments no longer than the ring.
-__device__ __forceinline__ void ring_flush(float2* ring, int mask, float2* __restrict__ dst, int from, int to) {
+template <typename TO>
+__device__ __forceinline__ void ring_flush(float2* ring, int mask, TO* __restrict__ dst, int from, int to) {
   while (from < to) {
     const int seg = min(to - from, mask + 1);
     for (int i = threadIdx.x; i < seg; i += FC_THREADS) {
       const int T = from + i;
-      dst[T] = ring[T & mask];
+      io_st(dst + T, ring[T & mask]);
       ring[T & mask] = make_float2(0.f, 0.f);
     }
     __syncthreads();
@@ -307,12 +318,13 @@ __device__ __forceinline__ void ring_flush(float2* ring, int mask, float2* __res
 }
 
 // OFDM modulation of one symbol into buf[0, Lofdm): active bins, inverse DFT (unscaled).
-__device__ __forceinline__ void ofdm_symbol_to_time(const FcPlanDev& P, const FcSubDev& S, const float2* __restrict__ row,
+template <typename TI>
+__device__ __forceinline__ void ofdm_symbol_to_time(const FcPlanDev& P, const FcSubDev& S, const TI* __restrict__ row,
                                                     float2* buf) {
   const int L = S.Lofdm;
   for (int i = threadIdx.x; i < L; i += FC_THREADS) {
     const int a = active_index(i, L, S.Lact);
-    buf[i] = a >= 0 ? __ldg(row + a) : make_float2(0.f, 0.f);
+    buf[i] = a >= 0 ? io_ld(row + a) : make_float2(0.f, 0.f);
   }
   __syncthreads();
   fft_inplace<true>(buf, 1, P.sz[S.size_O]);
@@ -367,15 +379,16 @@ __device__ __forceinline__ void rx_gather(const FcSubDev& S, int N, const float2
 // ---------------------------------------------------------------------------
 // One chunk of one stream: the CTA runs the chunk's symbol jobs in order and owns
 // the output samples [ch.t0, ch.t1) of the stream (written once, from the ring).
+template <typename TI, typename TO>
 __device__ __forceinline__ void tx_sync_chunk(const FcPlanDev& P, const FcJob* __restrict__ jobs, const FcChunk ch,
-                                              int stream, const float2* __restrict__ grid, float2* __restrict__ wave,
+                                              int stream, const TI* __restrict__ grid, TO* __restrict__ wave,
                                               unsigned char* smem_raw) {
   float2* ring = reinterpret_cast<float2*>(smem_raw);
   float2* Y = ring + P.ring;
   float2* W = Y + P.ybuf;
   const bool io_time = (P.flags & FC_FLAG_IO_TIME) != 0;
-  const float2* gsrc = grid + (size_t)stream * (io_time ? P.time_tx_len : P.grid_len);
-  float2* wdst = wave + (size_t)stream * P.frame_len;
+  const TI* gsrc = grid + (size_t)stream * (io_time ? P.time_tx_len : P.grid_len);
+  TO* wdst = wave + (size_t)stream * P.frame_len;
   const int mask = P.ring - 1;
   zero_buf(ring, P.ring);
   int flushed = ch.t0;
@@ -393,7 +406,7 @@ __device__ __forceinline__ void tx_sync_chunk(const FcPlanDev& P, const FcJob* _
       const int lcp = S.lcp[n];
       // T1: OFDM symbol (eq:TX_OFDMmod, scaling folded into D); time-domain input: the
       // caller's CP and body, brought to the same scale (sqrt(L_OFDM))
-      const float2* tin = gsrc + S.time_tx_off + S.soff[n];
+      const TI* tin = gsrc + S.time_tx_off + S.soff[n];
       if (!io_time) ofdm_symbol_to_time(P, S, gsrc + S.grid_off + (long long)n * S.Lact, W);
       // T2-T3: CP insertion, zero padding to 3L/2 (eq:padding), two segments with the
       // dynamic-overlap analysis windows a_{m,0}, a_{m,1} (OLA) or none (OLS)
@@ -405,7 +418,7 @@ __device__ __forceinline__ void tx_sync_chunk(const FcPlanDev& P, const FcJob* _
         if (P.scheme_tx == FC_OLA) in = in && (r == 0 ? zi < 3 * q4 : zi >= 3 * q4);
         float2 v = make_float2(0.f, 0.f);
         if (in && io_time) {
-          v = cscale(__ldg(tin + zi - (q4 - lcp)), sqrtf((float)S.Lofdm));
+          v = cscale(io_ld(tin + zi - (q4 - lcp)), sqrtf((float)S.Lofdm));
         } else if (in) {
           int bi = zi - q4;
           if (bi < 0) bi += L;
@@ -450,9 +463,10 @@ __device__ __forceinline__ void tx_sync_chunk(const FcPlanDev& P, const FcJob* _
   if (ch.t1 > flushed) ring_flush(ring, mask, wdst, flushed, ch.t1);
 }
 
+template <typename TI, typename TO>
 __global__ void __launch_bounds__(FC_THREADS, 1)
 k_tx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
-          int n_chunks, const float2* __restrict__ grid, float2* __restrict__ wave) {
+          int n_chunks, const TI* __restrict__ grid, TO* __restrict__ wave) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   load_plan(P, gP);
@@ -463,14 +477,15 @@ k_tx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
 // ---------------------------------------------------------------------------
 // Symbol-synchronized RX (Sec. IV)
 // ---------------------------------------------------------------------------
+template <typename TI, typename TO>
 __device__ __forceinline__ void rx_sync_chunk(const FcPlanDev& P, const FcJob* __restrict__ jobs, const FcChunk ch,
-                                              int stream, const float2* __restrict__ wave, float2* __restrict__ grid,
+                                              int stream, const TI* __restrict__ wave, TO* __restrict__ grid,
                                               unsigned char* smem_raw) {
   float2* Y = reinterpret_cast<float2*>(smem_raw);
   float2* W = Y + P.ybuf;
-  const float2* src = wave + (size_t)stream * P.frame_len;
+  const TI* src = wave + (size_t)stream * P.frame_len;
   const bool io_time = (P.flags & FC_FLAG_IO_TIME) != 0;
-  float2* gdst = grid + (size_t)stream * (io_time ? P.time_rx_len : P.grid_len);
+  TO* gdst = grid + (size_t)stream * (io_time ? P.time_rx_len : P.grid_len);
   const bool ola = P.scheme_rx == FC_OLA;
 
   for (int j = ch.j0; j < ch.j1; ++j) {
@@ -481,7 +496,7 @@ __device__ __forceinline__ void rx_sync_chunk(const FcPlanDev& P, const FcJob* _
     for (int idx = threadIdx.x; idx < 2 * N; idx += FC_THREADS) {
       const int r = idx >= N;
       const int t = idx - r * N;
-      float2 v = __ldg(src + jb.start + r * h + t);
+      float2 v = io_ld(src + jb.start + r * h + t);
       if (ola && !(t >= G.N_L && t < G.N_L + G.N_S)) v = make_float2(0.f, 0.f);
       Y[idx] = v;
     }
@@ -511,26 +526,27 @@ __device__ __forceinline__ void rx_sync_chunk(const FcPlanDev& P, const FcJob* _
           if (u >= L / 2) v = cadd(v, W[L + u - L / 2]);
         }
         X[t] = v;
-        if (io_time) gdst[S.time_rx_off + (long long)n * L + t] = cscale(v, sqrtf((float)S.Lofdm));   // body, true scale
+        if (io_time) io_st(gdst + S.time_rx_off + (long long)n * L + t, cscale(v, sqrtf((float)S.Lofdm)));   // body, true scale
       }
       __syncthreads();
       if (io_time) continue;
       // R6: OFDM demodulation, active bins out
       fft_inplace<false>(X, 1, P.sz[S.size_O]);
-      float2* row = gdst + S.grid_off + (long long)n * S.Lact;
+      TO* row = gdst + S.grid_off + (long long)n * S.Lact;
       for (int a = threadIdx.x; a < S.Lact; a += FC_THREADS) {
         int bin = a - S.Lact / 2;
         if (bin < 0) bin += L;
-        row[a] = X[bin];
+        io_st(row + a, X[bin]);
       }
       __syncthreads();
     }
   }
 }
 
+template <typename TI, typename TO>
 __global__ void __launch_bounds__(FC_THREADS, 1)
 k_rx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
-          int n_chunks, const float2* __restrict__ wave, float2* __restrict__ grid) {
+          int n_chunks, const TI* __restrict__ wave, TO* __restrict__ grid) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   load_plan(P, gP);
@@ -541,9 +557,10 @@ k_rx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
 // ---------------------------------------------------------------------------
 // Symbol-synchronized TX or RX of many plans in one persistent launch: each CTA takes
 // the next work item (plan, stream, chunk) from a device counter, reloads its shared
-// plan copy only when the plan changes, and runs the chunk.
+// plan copy only when the plan changes, and runs the chunk. One launch serves items of
+// one I/O type T (a queue holds complex64 or complex-BF16 items, never both).
 // ---------------------------------------------------------------------------
-template <bool TX>
+template <bool TX, typename T>
 __global__ void __launch_bounds__(FC_THREADS, 1)
 k_sync_multi(const FcWork* __restrict__ work, int n_work, int* __restrict__ next) {
   __shared__ FcPlanDev P;
@@ -561,10 +578,10 @@ k_sync_multi(const FcWork* __restrict__ work, int n_work, int* __restrict__ next
       load_plan(P, w.plan);                     // ends with a barrier
       if (threadIdx.x == 0) loaded = w.plan;
     }
-    if (TX)
-        tx_sync_chunk(P, w.jobs, *w.chunk, w.stream, w.in, w.out, smem_raw);
+    if (TX)                                     // frame calls: input and output of one type T
+      tx_sync_chunk(P, w.jobs, *w.chunk, w.stream, (const T*)w.in, (T*)w.out, smem_raw);
     else
-      rx_sync_chunk(P, w.jobs, *w.chunk, w.stream, w.in, w.out, smem_raw);
+      rx_sync_chunk(P, w.jobs, *w.chunk, w.stream, (const T*)w.in, (T*)w.out, smem_raw);
     __syncthreads();                            // item and the plan copy are reused
   }
 }
@@ -585,8 +602,9 @@ __device__ __forceinline__ bool locate_symbol(const FcPlanDev& P, int& m, int& n
   return false;
 }
 
+template <typename TI>
 __global__ void __launch_bounds__(FC_THREADS, 1)
-k_ofdm_mod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2* __restrict__ grid,
+k_ofdm_mod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const TI* __restrict__ grid,
            float2* __restrict__ ws) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -599,8 +617,8 @@ k_ofdm_mod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2* 
   const int L = S.Lofdm, lcp = S.lcp[n];
   float2* dst = ws + (size_t)stream * P.ws_len + S.ws_off + S.soff[n];
   if (P.flags & FC_FLAG_IO_TIME) {       // the caller's CP and body, brought to the kernels' scale
-    const float2* src = grid + (size_t)stream * P.time_tx_len + S.time_tx_off + S.soff[n];
-    for (int i = threadIdx.x; i < lcp + L; i += FC_THREADS) dst[i] = cscale(__ldg(src + i), sqrtf((float)S.Lofdm));
+    const TI* src = grid + (size_t)stream * P.time_tx_len + S.time_tx_off + S.soff[n];
+    for (int i = threadIdx.x; i < lcp + L; i += FC_THREADS) dst[i] = cscale(io_ld(src + i), sqrtf((float)S.Lofdm));
     return;
   }
   ofdm_symbol_to_time(P, S, grid + (size_t)stream * P.grid_len + S.grid_off + (long long)n * S.Lact, buf);
@@ -614,9 +632,10 @@ k_ofdm_mod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2* 
 // ---------------------------------------------------------------------------
 // Continuous mode, stage 2 (TX): FC blocks over [0_{S_L}; s; 0_{S_L}] (eq:BDM)
 // ---------------------------------------------------------------------------
+template <typename TO>
 __global__ void __launch_bounds__(FC_THREADS, 1)
 k_tx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
-          int n_chunks, const float2* __restrict__ ws, float2* __restrict__ wave) {
+          int n_chunks, const float2* __restrict__ ws, TO* __restrict__ wave) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   load_plan(P, gP);
@@ -626,7 +645,7 @@ k_tx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
   const int stream = blockIdx.x / n_chunks;
   const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
   const float2* wsrc = ws + (size_t)stream * P.ws_len;
-  float2* wdst = wave + (size_t)stream * P.frame_len;
+  TO* wdst = wave + (size_t)stream * P.frame_len;
   const int mask = P.ring - 1;
   const bool ols = P.scheme_tx == FC_OLS;
   zero_buf(ring, P.ring);
@@ -689,9 +708,10 @@ k_tx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
 // Continuous mode, stage 1 (RX): FC analysis blocks -> low-rate stream (OLS,
 // disjoint kept parts) or per-block outputs (OLA, summed by the demodulator)
 // ---------------------------------------------------------------------------
+template <typename TI>
 __global__ void __launch_bounds__(FC_THREADS, 1)
 k_rx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
-          int n_chunks, const float2* __restrict__ wave, float2* __restrict__ ws) {
+          int n_chunks, const TI* __restrict__ wave, float2* __restrict__ ws) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   load_plan(P, gP);
@@ -699,7 +719,7 @@ k_rx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
   float2* V = Y + P.ybuf;
   const int stream = blockIdx.x / n_chunks;
   const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
-  const float2* src = wave + (size_t)stream * P.frame_len;
+  const TI* src = wave + (size_t)stream * P.frame_len;
   float2* wdst = ws + (size_t)stream * P.ws_len;
   const bool ola = P.scheme_rx == FC_OLA;
 
@@ -711,7 +731,7 @@ k_rx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
       const int b = idx >= N;
       const int t = idx - b * N;
       float2 v = make_float2(0.f, 0.f);
-      if (b < nb && (!ola || (t >= G.N_L && t < G.N_L + G.N_S))) v = __ldg(src + jb.start + b * G.N_S + t);
+      if (b < nb && (!ola || (t >= G.N_L && t < G.N_L + G.N_S))) v = io_ld(src + jb.start + b * G.N_S + t);
       Y[idx] = v;
     }
     __syncthreads();
@@ -746,9 +766,10 @@ k_rx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
 // ---------------------------------------------------------------------------
 // Continuous mode, stage 2 (RX): CP removal and OFDM demodulation
 // ---------------------------------------------------------------------------
+template <typename TO>
 __global__ void __launch_bounds__(FC_THREADS, 1)
 k_ofdm_demod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2* __restrict__ ws,
-             float2* __restrict__ grid) {
+             TO* __restrict__ grid) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   load_plan(P, gP);
@@ -773,16 +794,16 @@ k_ofdm_demod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2
     }
     buf[t] = v;
     if (P.flags & FC_FLAG_IO_TIME)       // the body before demodulation, true scale
-      grid[(size_t)stream * P.time_rx_len + S.time_rx_off + (long long)n * Lo + t] = cscale(v, sqrtf((float)S.Lofdm));
+      io_st(grid + (size_t)stream * P.time_rx_len + S.time_rx_off + (long long)n * Lo + t, cscale(v, sqrtf((float)S.Lofdm)));
   }
   if (P.flags & FC_FLAG_IO_TIME) return;
   __syncthreads();
   fft_inplace<false>(buf, 1, P.sz[S.size_O]);
-  float2* row = grid + (size_t)stream * P.grid_len + S.grid_off + (long long)n * S.Lact;
+  TO* row = grid + (size_t)stream * P.grid_len + S.grid_off + (long long)n * S.Lact;
   for (int a = threadIdx.x; a < S.Lact; a += FC_THREADS) {
     int bin = a - S.Lact / 2;
     if (bin < 0) bin += Lo;
-    row[a] = buf[bin];
+    io_st(row + a, buf[bin]);
   }
 }
 
@@ -791,70 +812,118 @@ k_ofdm_demod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t fc_launch_sync_multi(bool tx, const FcWork* work, int n_work, int* next, int num_sms, size_t smem,
-                                 cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(int), st);
-  if (e != cudaSuccess || n_work == 0) return e;
+namespace {
+template <bool TX, typename T>
+cudaError_t launch_multi(const FcWork* work, int n_work, int* next, int num_sms, size_t smem, cudaStream_t st) {
   int per_sm = 0;
-  e = tx ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sync_multi<true>, FC_THREADS, smem)
-         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sync_multi<false>, FC_THREADS, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sync_multi<TX, T>, FC_THREADS, smem);
   if (e != cudaSuccess) return e;
   int n_ctas = num_sms * (per_sm > 0 ? per_sm : 1);
   if (n_ctas > n_work) n_ctas = n_work;
-  if (tx)
-    k_sync_multi<true><<<n_ctas, FC_THREADS, smem, st>>>(work, n_work, next);
-  else
-    k_sync_multi<false><<<n_ctas, FC_THREADS, smem, st>>>(work, n_work, next);
+  k_sync_multi<TX, T><<<n_ctas, FC_THREADS, smem, st>>>(work, n_work, next);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t fc_launch_sync_multi(bool tx, const FcWork* work, int n_work, int io, int* next, int num_sms, size_t smem,
+                                 cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(next, 0, sizeof(int), st);
+  if (e != cudaSuccess || n_work == 0) return e;
+  if (io != 0 && io != (FC_IO_IN_BF16 | FC_IO_OUT_BF16)) return cudaErrorInvalidValue;
+  if (tx)
+    return io ? launch_multi<true, bf2>(work, n_work, next, num_sms, smem, st)
+              : launch_multi<true, float2>(work, n_work, next, num_sms, smem, st);
+  return io ? launch_multi<false, bf2>(work, n_work, next, num_sms, smem, st)
+            : launch_multi<false, float2>(work, n_work, next, num_sms, smem, st);
 }
 
 cudaError_t fc_launch_tx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                              int n_streams, const float2* grid, float2* wave, size_t smem, cudaStream_t st) {
-  k_tx_sync<<<dim3((unsigned)(n_streams * n_chunks)), FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, grid, wave);
+                              int n_streams, const void* grid, void* wave, int io, size_t smem, cudaStream_t st) {
+  const dim3 g((unsigned)(n_streams * n_chunks));
+  if (io == 0)
+    k_tx_sync<<<g, FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, (const float2*)grid, (float2*)wave);
+  else if (io == (FC_IO_IN_BF16 | FC_IO_OUT_BF16))
+    k_tx_sync<<<g, FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, (const bf2*)grid, (bf2*)wave);
+  else if (io == FC_IO_IN_BF16)
+    k_tx_sync<<<g, FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, (const bf2*)grid, (float2*)wave);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 cudaError_t fc_launch_rx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                              int n_streams, const float2* wave, float2* grid, size_t smem, cudaStream_t st) {
-  k_rx_sync<<<dim3((unsigned)(n_streams * n_chunks)), FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, wave, grid);
+                              int n_streams, const void* wave, void* grid, int io, size_t smem, cudaStream_t st) {
+  const dim3 g((unsigned)(n_streams * n_chunks));
+  if (io == 0)
+    k_rx_sync<<<g, FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, (const float2*)wave, (float2*)grid);
+  else if (io == (FC_IO_IN_BF16 | FC_IO_OUT_BF16))
+    k_rx_sync<<<g, FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, (const bf2*)wave, (bf2*)grid);
+  else if (io == FC_IO_OUT_BF16)
+    k_rx_sync<<<g, FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, (const float2*)wave, (bf2*)grid);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
-cudaError_t fc_launch_ofdm_mod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const float2* grid,
-                               float2* ws, size_t smem, cudaStream_t st) {
-  k_ofdm_mod<<<dim3((unsigned)(n_streams * syms_per_stream)), FC_THREADS, smem, st>>>(dP, syms_per_stream, grid, ws);
+cudaError_t fc_launch_ofdm_mod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const void* grid,
+                               float2* ws, int io, size_t smem, cudaStream_t st) {
+  const dim3 g((unsigned)(n_streams * syms_per_stream));
+  if (io & FC_IO_IN_BF16)
+    k_ofdm_mod<<<g, FC_THREADS, smem, st>>>(dP, syms_per_stream, (const bf2*)grid, ws);
+  else
+    k_ofdm_mod<<<g, FC_THREADS, smem, st>>>(dP, syms_per_stream, (const float2*)grid, ws);
   return cudaGetLastError();
 }
 
 cudaError_t fc_launch_tx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                              int n_streams, const float2* ws, float2* wave, size_t smem, cudaStream_t st) {
-  k_tx_cont<<<dim3((unsigned)(n_streams * n_chunks)), FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, ws, wave);
+                              int n_streams, const float2* ws, void* wave, int io, size_t smem, cudaStream_t st) {
+  const dim3 g((unsigned)(n_streams * n_chunks));
+  if (io & FC_IO_OUT_BF16)
+    k_tx_cont<<<g, FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, ws, (bf2*)wave);
+  else
+    k_tx_cont<<<g, FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, ws, (float2*)wave);
   return cudaGetLastError();
 }
 
 cudaError_t fc_launch_rx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                              int n_streams, const float2* wave, float2* ws, size_t smem, cudaStream_t st) {
-  k_rx_cont<<<dim3((unsigned)(n_streams * n_chunks)), FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, wave, ws);
+                              int n_streams, const void* wave, float2* ws, int io, size_t smem, cudaStream_t st) {
+  const dim3 g((unsigned)(n_streams * n_chunks));
+  if (io & FC_IO_IN_BF16)
+    k_rx_cont<<<g, FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, (const bf2*)wave, ws);
+  else
+    k_rx_cont<<<g, FC_THREADS, smem, st>>>(dP, jobs, chunks, n_chunks, (const float2*)wave, ws);
   return cudaGetLastError();
 }
 
 cudaError_t fc_launch_ofdm_demod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const float2* ws,
-                                 float2* grid, size_t smem, cudaStream_t st) {
-  k_ofdm_demod<<<dim3((unsigned)(n_streams * syms_per_stream)), FC_THREADS, smem, st>>>(dP, syms_per_stream, ws, grid);
+                                 void* grid, int io, size_t smem, cudaStream_t st) {
+  const dim3 g((unsigned)(n_streams * syms_per_stream));
+  if (io & FC_IO_OUT_BF16)
+    k_ofdm_demod<<<g, FC_THREADS, smem, st>>>(dP, syms_per_stream, ws, (bf2*)grid);
+  else
+    k_ofdm_demod<<<g, FC_THREADS, smem, st>>>(dP, syms_per_stream, ws, (float2*)grid);
   return cudaGetLastError();
 }
 
+namespace {
+template <typename K>
+cudaError_t raise_smem(K kernel, size_t max_smem) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+}
+}  // namespace
+
 cudaError_t fc_set_smem_limits(size_t max_smem) {
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_tx_sync, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
-  if ((e = cudaFuncSetAttribute(k_rx_sync, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
-  if ((e = cudaFuncSetAttribute(k_sync_multi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_sync_multi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem)))
-    return e;
-  if ((e = cudaFuncSetAttribute(k_tx_cont, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
-  if ((e = cudaFuncSetAttribute(k_rx_cont, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
-  if ((e = cudaFuncSetAttribute(k_ofdm_mod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
-  if ((e = cudaFuncSetAttribute(k_ofdm_demod, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem))) return e;
+  const cudaError_t e[] = {
+      raise_smem(k_tx_sync<float2, float2>, max_smem), raise_smem(k_tx_sync<bf2, bf2>, max_smem),
+      raise_smem(k_tx_sync<bf2, float2>, max_smem),    raise_smem(k_rx_sync<float2, float2>, max_smem),
+      raise_smem(k_rx_sync<bf2, bf2>, max_smem),       raise_smem(k_rx_sync<float2, bf2>, max_smem),
+      raise_smem(k_sync_multi<true, float2>, max_smem), raise_smem(k_sync_multi<false, float2>, max_smem),
+      raise_smem(k_sync_multi<true, bf2>, max_smem),    raise_smem(k_sync_multi<false, bf2>, max_smem),
+      raise_smem(k_tx_cont<float2>, max_smem),         raise_smem(k_tx_cont<bf2>, max_smem),
+      raise_smem(k_rx_cont<float2>, max_smem),         raise_smem(k_rx_cont<bf2>, max_smem),
+      raise_smem(k_ofdm_mod<float2>, max_smem),        raise_smem(k_ofdm_mod<bf2>, max_smem),
+      raise_smem(k_ofdm_demod<float2>, max_smem),      raise_smem(k_ofdm_demod<bf2>, max_smem)};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
   return cudaSuccess;
 }

@@ -92,6 +92,7 @@ struct fc_plan {
   std::vector<int> splits;                  // chunk counts per stream available
   std::vector<const FcChunk*> tx_chunks, rx_chunks;
   std::vector<int> tx_nchunks, rx_nchunks;
+  int io = 0;                               // FC_IO_* bits of the frame calls (FC_FLAG_IO_BF16)
   bool warp_path = false;                   // warp-specialised symbol-sync kernels apply
   bool tc_tx = false, tc_rx = false;        // tensor-core FC passes apply (FC_FLAG_TENSOR_DFT)
   bool tc_ofdm = false;                     // and the OFDM (I)DFT too (L_OFDM = 4096)
@@ -394,8 +395,11 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   }
 
   // warp-specialised path: symbol-sync, one subband per group, I = 2, L in {512, 1024}
+  // (complex-BF16 I/O runs on the generic kernels: their outputs are written once, from
+  // FP32 values, where the specialised kernels accumulate into the output buffer)
   const bool io_time = (geo->flags & FC_FLAG_IO_TIME) != 0;
-  bool warp_ok = sync && !(geo->flags & FC_FLAG_GENERIC_KERNELS) && !io_time && (frame_len % 2 == 0);
+  const bool io_bf16 = (geo->flags & FC_FLAG_IO_BF16) != 0;
+  bool warp_ok = sync && !(geo->flags & FC_FLAG_GENERIC_KERNELS) && !io_time && !io_bf16 && (frame_len % 2 == 0);
   for (int g = 0; g < G && warp_ok; ++g) {
     if (gh[g].subs.size() != 1) { warp_ok = false; break; }
     const SubHost& o = sh[gh[g].subs[0]];
@@ -448,7 +452,7 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
 
   // tensor-core FC passes: continuous, one group, one subband, L = N = 4096; RX only
   // for overlap-save (the OLA analysis keeps the FP32 kernels)
-  const bool tc_tx = (geo->flags & FC_FLAG_TENSOR_DFT) && !sync && G == 1 && M == 1 && sh[0].L == 4096 &&
+  const bool tc_tx = (geo->flags & FC_FLAG_TENSOR_DFT) && !io_bf16 && !sync && G == 1 && M == 1 && sh[0].L == 4096 &&
                      gh[0].N == 4096;
   const bool tc_rx = tc_tx && geo->scheme_rx == FC_OLS;
 
@@ -510,6 +514,8 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   z.time_rx_len = t_rx;
   z.tx_in_len = io_time ? t_tx : grid_len;
   z.rx_out_len = io_time ? t_rx : grid_len;
+  z.sample_bytes = io_bf16 ? 4 : 8;
+  pl->io = io_bf16 ? (FC_IO_IN_BF16 | FC_IO_OUT_BF16) : 0;
   z.slot_len = streamable ? slot_len : 0;
   z.stream_delay = streamable ? stream_delay : 0;
   z.tx_kernels = sync ? 1 : (tc_tx ? 3 : 2);
@@ -655,7 +661,8 @@ int check_io(const fc_plan* plan, int32_t n_streams, const void* in, const void*
   if (n_streams < 0) return fail(FC_ERR_INVALID, "n_streams < 0");
   if (n_streams == 0) return FC_OK;
   if (!in || !out) return fail(FC_ERR_INVALID, "input or output pointer is NULL");
-  if (((uintptr_t)in | (uintptr_t)out) & 7) return fail(FC_ERR_INVALID, "buffers must be 8-byte aligned");
+  if (((uintptr_t)in | (uintptr_t)out) & (uintptr_t)(plan->sizes.sample_bytes - 1))
+    return fail(FC_ERR_INVALID, "buffers must be aligned to the sample size (8 bytes, 4 with FC_FLAG_IO_BF16)");
   const long long need = (long long)n_streams * plan->sizes.workspace_per_stream;
   if (need > 0) {
     if (!ws || ws_bytes < (size_t)need) return fail(FC_ERR_INVALID, "workspace missing or too small");
@@ -675,23 +682,27 @@ std::pair<int, int> choose(const fc_plan* pl, int n_streams, int dir) {
   return {(int)pick_split(pl, n_streams), 0};
 }
 
-cudaError_t launch_tx(const fc_plan* plan, int n_streams, const float2* grid, float2* wave, float2* workspace,
-                      cudaStream_t st, std::pair<int, int> c) {
+// io: FC_IO_* bits of this call's input and output; the specialised and tensor-core
+// kernels take complex64 only (a plan with FC_FLAG_IO_BF16 never selects them)
+cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* out, float2* workspace,
+                      cudaStream_t st, std::pair<int, int> c, int io) {
   const size_t k = (size_t)c.first;
+  const float2* grid = (const float2*)in;
+  float2* wave = (float2*)out;
   // float4 reductions of the warp kernel need a 16-byte aligned waveform
-  if (plan->warp_path && !c.second && ((uintptr_t)wave & 15) == 0)
+  if (plan->warp_path && !c.second && io == 0 && ((uintptr_t)wave & 15) == 0)
     return fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams,
                                   plan->h.frame_len, grid, wave, st);
   if (plan->h.mode == FC_SYMBOL_SYNC)
-    return fc_launch_tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, grid,
-                             wave, plan->smem_tx, st);
-  if (plan->tc_tx && !c.second) {
+    return fc_launch_tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, in,
+                             out, io, plan->smem_tx, st);
+  if (plan->tc_tx && !c.second && io == 0) {
     const int R = plan->h.g[0].R;
     cudaError_t e = plan->tc_ofdm ? fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_OFDM_MOD, n_streams,
                                                  plan->h.g[0].B, grid, nullptr, workspace, plan->d_err,
                                                  plan->num_sms, st)
                                   : fc_launch_ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid,
-                                                       workspace, plan->smem_ofdm, st);
+                                                       workspace, 0, plan->smem_ofdm, st);
     if (e == cudaSuccess)
       e = cudaMemsetAsync(wave, 0, (size_t)n_streams * plan->h.frame_len * sizeof(float2), st);
     if (e == cudaSuccess)
@@ -702,24 +713,26 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const float2* grid, fl
                        plan->d_err, plan->num_sms, st);
     return e;
   }
-  cudaError_t e = fc_launch_ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid, workspace,
+  cudaError_t e = fc_launch_ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, in, workspace, io,
                                      plan->smem_ofdm, st);
   if (e == cudaSuccess)
     e = fc_launch_tx_cont(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, workspace,
-                          wave, plan->smem_tx, st);
+                          out, io, plan->smem_tx, st);
   return e;
 }
 
-cudaError_t launch_rx(const fc_plan* plan, int n_streams, const float2* wave, float2* grid, float2* workspace,
-                      cudaStream_t st, std::pair<int, int> c) {
+cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* out, float2* workspace,
+                      cudaStream_t st, std::pair<int, int> c, int io) {
   const size_t k = (size_t)c.first;
-  if (plan->warp_path && !c.second)
+  const float2* wave = (const float2*)in;
+  float2* grid = (float2*)out;
+  if (plan->warp_path && !c.second && io == 0)
     return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams,
                                   wave, grid, st);
   if (plan->h.mode == FC_SYMBOL_SYNC)
-    return fc_launch_rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, wave,
-                             grid, plan->smem_rx, st);
-  if (plan->tc_rx && !c.second) {
+    return fc_launch_rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, in,
+                             out, io, plan->smem_rx, st);
+  if (plan->tc_rx && !c.second && io == 0) {
     const int R = plan->h.g[0].R;
     cudaError_t e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_RX_FFT, n_streams, R, wave, nullptr, workspace,
                                  plan->d_err, plan->num_sms, st);
@@ -730,13 +743,14 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const float2* wave, fl
       e = plan->tc_ofdm ? fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_OFDM_DEMOD, n_streams, plan->h.g[0].B,
                                        nullptr, grid, workspace, plan->d_err, plan->num_sms, st)
                         : fc_launch_ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, grid,
-                                               plan->smem_ofdm, st);
+                                               0, plan->smem_ofdm, st);
     return e;
   }
   cudaError_t e = fc_launch_rx_cont(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams,
-                                    wave, workspace, plan->smem_rx, st);
+                                    in, workspace, io, plan->smem_rx, st);
   if (e == cudaSuccess)
-    e = fc_launch_ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, grid, plan->smem_ofdm, st);
+    e = fc_launch_ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, out, io, plan->smem_ofdm,
+                             st);
   return e;
 }
 
@@ -748,6 +762,20 @@ int fc_internal_plan_device(const fc_plan* plan) { return plan ? plan->device : 
 
 int fc_internal_num_sms(const fc_plan* plan) { return plan ? plan->num_sms : 0; }
 
+int fc_internal_io(const fc_plan* plan) { return plan ? plan->io : 0; }
+
+int fc_internal_frame(const fc_plan* plan, int dir, int n_streams, const void* in, void* out, void* workspace,
+                      size_t workspace_bytes, void* stream, int io) {
+  int rc = check_io(plan, n_streams, in, out, workspace, workspace_bytes);
+  if (rc != FC_OK || n_streams == 0) return rc;
+  DeviceGuard dg(plan->device);
+  if (!dg.ok) return fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  const std::pair<int, int> c = choose(plan, n_streams, dir);
+  const cudaError_t e = dir == FC_TX ? launch_tx(plan, n_streams, in, out, (float2*)workspace, (cudaStream_t)stream, c, io)
+                                     : launch_rx(plan, n_streams, in, out, (float2*)workspace, (cudaStream_t)stream, c, io);
+  return e == cudaSuccess ? FC_OK : cuda_fail(e, dir == FC_TX ? "TX kernel launch" : "RX kernel launch");
+}
+
 bool fc_internal_sync_work(const fc_plan* plan, int dir, int n_streams, const void* in, void* out,
                            std::vector<FcWork>& work, size_t* smem) {
   if (!plan || plan->h.mode != FC_SYMBOL_SYNC || n_streams < 1) return false;
@@ -758,7 +786,7 @@ bool fc_internal_sync_work(const fc_plan* plan, int dir, int n_streams, const vo
   const int n_chunks = dir == FC_TX ? plan->tx_nchunks[k] : plan->rx_nchunks[k];
   for (int s = 0; s < n_streams; ++s)
     for (int ch = 0; ch < n_chunks; ++ch)
-      work.push_back(FcWork{plan->d_plan, plan->d_jobs, chunks + ch, (const float2*)in, (float2*)out, s, 0});
+      work.push_back(FcWork{plan->d_plan, plan->d_jobs, chunks + ch, in, out, s, plan->io});
   *smem = dir == FC_TX ? plan->smem_tx : plan->smem_rx;
   return true;
 }
@@ -824,24 +852,14 @@ int fc_query(const fc_plan* plan, fc_sizes* out) {
 
 int fc_tx_synthesize(const fc_plan* plan, int32_t n_streams, const void* grid_in, void* wave_out, void* workspace,
                      size_t workspace_bytes, void* stream) {
-  int rc = check_io(plan, n_streams, grid_in, wave_out, workspace, workspace_bytes);
-  if (rc != FC_OK || n_streams == 0) return rc;
-  DeviceGuard dg(plan->device);
-  if (!dg.ok) return fail(FC_ERR_CUDA, "cudaSetDevice failed");
-  const cudaError_t e = launch_tx(plan, n_streams, (const float2*)grid_in, (float2*)wave_out, (float2*)workspace,
-                                  (cudaStream_t)stream, choose(plan, n_streams, FC_TX));
-  return e == cudaSuccess ? FC_OK : cuda_fail(e, "TX kernel launch");
+  return fc_internal_frame(plan, FC_TX, n_streams, grid_in, wave_out, workspace, workspace_bytes, stream,
+                           plan ? plan->io : 0);
 }
 
 int fc_rx_analyze(const fc_plan* plan, int32_t n_streams, const void* wave_in, void* grid_out, void* workspace,
                   size_t workspace_bytes, void* stream) {
-  int rc = check_io(plan, n_streams, wave_in, grid_out, workspace, workspace_bytes);
-  if (rc != FC_OK || n_streams == 0) return rc;
-  DeviceGuard dg(plan->device);
-  if (!dg.ok) return fail(FC_ERR_CUDA, "cudaSetDevice failed");
-  const cudaError_t e = launch_rx(plan, n_streams, (const float2*)wave_in, (float2*)grid_out, (float2*)workspace,
-                                  (cudaStream_t)stream, choose(plan, n_streams, FC_RX));
-  return e == cudaSuccess ? FC_OK : cuda_fail(e, "RX kernel launch");
+  return fc_internal_frame(plan, FC_RX, n_streams, wave_in, grid_out, workspace, workspace_bytes, stream,
+                           plan ? plan->io : 0);
 }
 
 int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* stream) {
@@ -851,7 +869,9 @@ int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* strea
   if (!dg.ok) return fail(FC_ERR_CUDA, "cudaSetDevice failed");
   cudaStream_t st = (cudaStream_t)stream;
   const fc_sizes& z = plan->sizes;
-  const size_t n_grid = (size_t)n_streams * z.grid_len, n_wave = (size_t)n_streams * z.wave_len;
+  // complex64-sized buffers also hold a BF16 call's samples; grid or time-domain I/O
+  const size_t n_grid = (size_t)n_streams * (size_t)std::max(z.tx_in_len, z.rx_out_len);
+  const size_t n_wave = (size_t)n_streams * z.wave_len;
   const size_t ws_bytes = (size_t)n_streams * z.workspace_per_stream;
   // tuning buffers (zeros: the kernels' time does not depend on the values)
   unsigned char* mem = nullptr;
@@ -874,8 +894,8 @@ int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* strea
       for (int k = 0; k < (int)plan->splits.size() && e == cudaSuccess; ++k) {
         const std::pair<int, int> c{k, generic};
         auto run = [&]() {
-          return dir == FC_TX ? launch_tx(plan, n_streams, grid, wave, ws, st, c)
-                              : launch_rx(plan, n_streams, wave, grid, ws, st, c);
+          return dir == FC_TX ? launch_tx(plan, n_streams, grid, wave, ws, st, c, plan->io)
+                              : launch_rx(plan, n_streams, wave, grid, ws, st, c, plan->io);
         };
         for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = run();
         if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);

@@ -23,8 +23,8 @@ struct Carrier {
   fc_state* state = nullptr;
   fc_sizes sz{};
   void* d_io = nullptr;            // one allocation: grid, slot, workspace
-  float2* d_grid = nullptr;
-  float2* d_slot = nullptr;
+  unsigned char* d_grid = nullptr; // fc_sizes.sample_bytes per sample
+  unsigned char* d_slot = nullptr;
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int lane = 0;
@@ -95,7 +95,8 @@ int fc_server_add_carrier(fc_server* s, const fc_geometry* geometry, int32_t* ca
   // admission: everything this carrier will hold on the device must fit in free HBM
   // minus the reserve (plan tables are bounded by a generous 8 MiB estimate)
   const size_t g_len = (size_t)(sz.tx_in_len > sz.rx_out_len ? sz.tx_in_len : sz.rx_out_len);   // grid or time I/O
-  const size_t io = align256(g_len * 8) + align256((size_t)sz.slot_len * 8) + align256((size_t)sz.workspace_per_stream);
+  const size_t sb = (size_t)sz.sample_bytes;   // caller-facing buffers: complex64 or complex BF16
+  const size_t io = align256(g_len * sb) + align256((size_t)sz.slot_len * sb) + align256((size_t)sz.workspace_per_stream);
   const size_t state = ((size_t)2 * sz.wave_len + 2 + (size_t)2 * sz.stream_delay) * 8;
   const size_t need = io + state + ((size_t)8 << 20);
   DevGuard dg(s->device);
@@ -125,10 +126,10 @@ int fc_server_add_carrier(fc_server* s, const fc_geometry* geometry, int32_t* ca
     return cuda_err(e, "cudaMalloc of carrier buffers");
   }
   unsigned char* p = (unsigned char*)c.d_io;
-  c.d_grid = (float2*)p;
-  c.d_slot = (float2*)(p + align256(g_len * 8));
+  c.d_grid = p;
+  c.d_slot = p + align256(g_len * sb);
   c.ws_bytes = (size_t)sz.workspace_per_stream;
-  c.ws = c.ws_bytes ? (void*)(p + align256(g_len * 8) + align256((size_t)sz.slot_len * 8)) : nullptr;
+  c.ws = c.ws_bytes ? (void*)(p + align256(g_len * sb) + align256((size_t)sz.slot_len * sb)) : nullptr;
   c.lane = (int)(s->carriers.size() % s->lanes.size());
   *carrier_id = (int32_t)s->carriers.size();
   s->carriers.push_back(c);
@@ -172,10 +173,11 @@ int fc_server_run(fc_server* s, const fc_serve_request* reqs, int32_t n, double*
       Carrier& c = s->carriers[r.carrier];
       cudaStream_t st = s->lanes[c.lane];
       const bool tx = r.direction == FC_TX;
-      float2* d_in = tx ? c.d_grid : c.d_slot;
-      float2* d_out = tx ? c.d_slot : c.d_grid;
-      const size_t in_b = (size_t)(tx ? c.sz.tx_in_len : c.sz.slot_len) * 8;
-      const size_t out_b = (size_t)(tx ? c.sz.slot_len : c.sz.rx_out_len) * 8;
+      unsigned char* d_in = tx ? c.d_grid : c.d_slot;
+      unsigned char* d_out = tx ? c.d_slot : c.d_grid;
+      const size_t sb = (size_t)c.sz.sample_bytes;
+      const size_t in_b = (size_t)(tx ? c.sz.tx_in_len : c.sz.slot_len) * sb;
+      const size_t out_b = (size_t)(tx ? c.sz.slot_len : c.sz.rx_out_len) * sb;
       e = cudaMemcpyAsync(d_in, r.host_in, in_b, cudaMemcpyHostToDevice, st);
       if (e != cudaSuccess) break;
       rc = tx ? fc_tx_synthesize_stream(c.plan, c.state, d_in, d_out, c.ws, c.ws_bytes, (void*)st)

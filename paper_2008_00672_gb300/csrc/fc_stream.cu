@@ -8,7 +8,13 @@
 // frames at offsets k T (TX), and slot k of the K-slot analysis only reads samples
 // [k T, k T + Q) (RX). So a TX call runs the one-slot frame and carries D samples; an RX
 // call prepends the D samples it kept from the previous input.
+//
+// The frame, the tail and the look-behind stay complex64 whatever the plan's I/O type:
+// with FC_FLAG_IO_BF16 a TX slot (frame + tail) and an RX estimate are rounded to BF16
+// once, when written to the caller's buffer, and BF16 inputs widen to FP32 exactly.
 #include <cstdio>
+
+#include <cuda_bf16.h>
 
 #include "fc_internal.cuh"
 
@@ -44,9 +50,15 @@ int cuda_err(cudaError_t e, const char* where) {
   return fc_internal_fail(e == cudaErrorMemoryAllocation ? FC_ERR_NOMEM : FC_ERR_CUDA, msg);
 }
 
+__device__ __forceinline__ void put(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void put(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
+__device__ __forceinline__ float2 get(const float2* p) { return *p; }
+__device__ __forceinline__ float2 get(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
+
 // out[s][t] = frame[s][t] + tail[s][t] (t < D);  tail[s][t] = frame[s][T + t] (t < D).
 // Each (s, t < D) is read and rewritten by the same thread.
-__global__ void k_stream_tx(const float2* __restrict__ frame, float2* __restrict__ tail, float2* __restrict__ out,
+template <typename TO>
+__global__ void k_stream_tx(const float2* __restrict__ frame, float2* __restrict__ tail, TO* __restrict__ out,
                             long long total, long long Q, long long T, long long D) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
@@ -60,23 +72,24 @@ __global__ void k_stream_tx(const float2* __restrict__ frame, float2* __restrict
       v.y += c.y;
       *tl = f[T + t];
     }
-    out[i] = v;
+    put(out + i, v);
   }
 }
 
 // frame[s][t] = look[s][t] (t < D) or in[s][t - D];  look[s][t] = in[s][T - D + t] (t < D).
-__global__ void k_stream_rx(const float2* __restrict__ in, float2* __restrict__ look, float2* __restrict__ frame,
+template <typename TI>
+__global__ void k_stream_rx(const TI* __restrict__ in, float2* __restrict__ look, float2* __restrict__ frame,
                             long long total, long long Q, long long T, long long D) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long s = i / Q, t = i - s * Q;
-    const float2* x = in + s * T;
+    const TI* x = in + s * T;
     if (t < D) {
       float2* lk = look + s * D + t;
       frame[i] = *lk;
-      *lk = x[T - D + t];
+      *lk = get(x + T - D + t);
     } else {
-      frame[i] = x[t - D];
+      frame[i] = get(x + t - D);
     }
   }
 }
@@ -98,7 +111,8 @@ int check_state(const fc_plan* plan, const fc_state* st, const void* in, const v
     return fc_internal_fail(FC_ERR_INVALID, "state and plan are on different devices");
   if (st->n_streams == 0) return FC_OK;
   if (!in || !out) return fc_internal_fail(FC_ERR_INVALID, "input or output pointer is NULL");
-  if (((uintptr_t)in | (uintptr_t)out) & 7) return fc_internal_fail(FC_ERR_INVALID, "buffers must be 8-byte aligned");
+  if (((uintptr_t)in | (uintptr_t)out) & (uintptr_t)(sz->sample_bytes - 1))
+    return fc_internal_fail(FC_ERR_INVALID, "buffers must be aligned to the sample size (8 bytes, 4 with FC_FLAG_IO_BF16)");
   return FC_OK;
 }
 
@@ -177,14 +191,21 @@ int fc_tx_synthesize_stream(const fc_plan* plan, fc_state* state, const void* gr
   fc_sizes sz;
   int rc = check_state(plan, state, grid_in, slot_out, &sz);
   if (rc != FC_OK || state->n_streams == 0) return rc;
-  rc = fc_tx_synthesize(plan, state->n_streams, grid_in, state->tx_frame, workspace, workspace_bytes, stream);
+  const int io = fc_internal_io(plan);
+  rc = fc_internal_frame(plan, FC_TX, state->n_streams, grid_in, state->tx_frame, workspace, workspace_bytes, stream,
+                         io & FC_IO_IN_BF16);
   if (rc != FC_OK) return rc;
   DevGuard dg(state->device);
   if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
   const long long total = (long long)state->n_streams * state->slot_len;
   const long long Q = sz.wave_len;
-  k_stream_tx<<<grid_for(total), 256, 0, (cudaStream_t)stream>>>(state->tx_frame, state->tail, (float2*)slot_out,
-                                                                  total, Q, state->slot_len, state->delay);
+  const cudaStream_t cs = (cudaStream_t)stream;
+  if (io & FC_IO_OUT_BF16)
+    k_stream_tx<<<grid_for(total), 256, 0, cs>>>(state->tx_frame, state->tail, (__nv_bfloat162*)slot_out, total, Q,
+                                                 state->slot_len, state->delay);
+  else
+    k_stream_tx<<<grid_for(total), 256, 0, cs>>>(state->tx_frame, state->tail, (float2*)slot_out, total, Q,
+                                                 state->slot_len, state->delay);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? FC_OK : cuda_err(e, "stream TX epilogue launch");
 }
@@ -199,13 +220,18 @@ int fc_rx_analyze_stream(const fc_plan* plan, fc_state* state, const void* slot_
     if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
     const long long Q = sz.wave_len;
     const long long total = (long long)state->n_streams * Q;
-    k_stream_rx<<<grid_for(total), 256, 0, (cudaStream_t)stream>>>((const float2*)slot_in, state->look,
-                                                                    state->rx_frame, total, Q, state->slot_len,
-                                                                    state->delay);
+    const cudaStream_t cs = (cudaStream_t)stream;
+    if (fc_internal_io(plan) & FC_IO_IN_BF16)
+      k_stream_rx<<<grid_for(total), 256, 0, cs>>>((const __nv_bfloat162*)slot_in, state->look, state->rx_frame, total,
+                                                   Q, state->slot_len, state->delay);
+    else
+      k_stream_rx<<<grid_for(total), 256, 0, cs>>>((const float2*)slot_in, state->look, state->rx_frame, total, Q,
+                                                   state->slot_len, state->delay);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(e, "stream RX prologue launch");
   }
-  return fc_rx_analyze(plan, state->n_streams, state->rx_frame, grid_out, workspace, workspace_bytes, stream);
+  return fc_internal_frame(plan, FC_RX, state->n_streams, state->rx_frame, grid_out, workspace, workspace_bytes, stream,
+                           fc_internal_io(plan) & FC_IO_OUT_BF16);
 }
 
 }  // extern "C"

@@ -7,7 +7,9 @@ not been built the first call raises ``RuntimeError``.
 The functions keep the C names (``fc_plan_create``, ``fc_query``,
 ``fc_tx_synthesize``, ``fc_rx_analyze``, ``fc_plan_destroy``,
 ``fc_status_string``). ``Plan`` is a small owner object around them that takes
-torch device tensors (complex64) and the current torch CUDA stream.
+torch device tensors (complex64, or with ``FC_FLAG_IO_BF16`` bfloat16 tensors holding
+interleaved (re, im) pairs, e.g. of shape [streams, length, 2]) and the current torch
+CUDA stream.
 """
 from __future__ import annotations
 
@@ -24,6 +26,7 @@ FC_FLAG_GENERIC_KERNELS = 1
 FC_FLAG_REDUCED_RX = 2
 FC_FLAG_TENSOR_DFT = 4
 FC_FLAG_IO_TIME = 8
+FC_FLAG_IO_BF16 = 16
 FC_OLA, FC_OLS = 0, 1
 FC_TX, FC_RX = 0, 1
 
@@ -59,7 +62,7 @@ class FcSizes(ctypes.Structure):
                 ("workspace_per_stream", ctypes.c_int64), ("tx_kernels", ctypes.c_int32),
                 ("rx_kernels", ctypes.c_int32), ("slot_len", ctypes.c_int64), ("stream_delay", ctypes.c_int64),
                 ("time_tx_len", ctypes.c_int64), ("time_rx_len", ctypes.c_int64), ("tx_in_len", ctypes.c_int64),
-                ("rx_out_len", ctypes.c_int64)]
+                ("rx_out_len", ctypes.c_int64), ("sample_bytes", ctypes.c_int64)]
 
 
 class FcBatchItem(ctypes.Structure):
@@ -362,7 +365,8 @@ def fc_status_string(status: int) -> str:
 # --------------------------------------------------------------------------
 
 class Plan:
-    """Owns one fc_plan; execute calls take complex64 CUDA tensors."""
+    """Owns one fc_plan; execute calls take complex64 CUDA tensors, or bfloat16 CUDA
+    tensors of (re, im) pairs when the plan was made with FC_FLAG_IO_BF16."""
 
     def __init__(self, geom, device: int = 0):
         self.device = int(device)
@@ -378,6 +382,8 @@ class Plan:
         self.stream_delay = int(s.stream_delay)
         self.tx_in_len = int(s.tx_in_len)       # grid_len, or the time-domain TX input length
         self.rx_out_len = int(s.rx_out_len)     # grid_len, or the time-domain RX output length
+        self.sample_bytes = int(s.sample_bytes)
+        self.io_bf16 = self.sample_bytes == 4   # complex-BF16 I/O buffers
         self._ws = None
 
     def close(self):
@@ -419,7 +425,7 @@ class Plan:
         return int(stream.cuda_stream)
 
     def tx_synthesize(self, grid, wave_out, workspace=None, stream=None):
-        n = self._streams(grid, self.tx_in_len, wave_out, self.wave_len)
+        n = self._streams(grid, self.tx_in_len, wave_out, self.wave_len, self.io_bf16)
         ws = workspace if workspace is not None else self.workspace(n)
         fc_tx_synthesize(self.handle, n, grid.data_ptr(), wave_out.data_ptr(),
                          ws.data_ptr() if ws is not None else 0,
@@ -427,7 +433,7 @@ class Plan:
         return wave_out
 
     def rx_analyze(self, wave, grid_out, workspace=None, stream=None):
-        n = self._streams(wave, self.wave_len, grid_out, self.rx_out_len)
+        n = self._streams(wave, self.wave_len, grid_out, self.rx_out_len, self.io_bf16)
         ws = workspace if workspace is not None else self.workspace(n)
         fc_rx_analyze(self.handle, n, wave.data_ptr(), grid_out.data_ptr(),
                       ws.data_ptr() if ws is not None else 0,
@@ -435,14 +441,24 @@ class Plan:
         return grid_out
 
     @staticmethod
-    def _streams(a, la, b, lb) -> int:
+    def _samples(t, bf16: bool, cuda: bool) -> int:
+        """Complex samples in t (complex64, or bfloat16 (re, im) pairs)."""
         import torch
-        for t in (a, b):
-            if t.dtype != torch.complex64 or not t.is_cuda or not t.is_contiguous():
-                raise ValueError("expected contiguous complex64 CUDA tensors")
-        if a.numel() % la or b.numel() % lb or a.numel() // la != b.numel() // lb:
+        want = torch.bfloat16 if bf16 else torch.complex64
+        if t.dtype != want or t.is_cuda != cuda or not t.is_contiguous():
+            raise ValueError(f"expected contiguous {'bfloat16 (re, im)' if bf16 else 'complex64'} "
+                             f"{'CUDA' if cuda else 'host'} tensors")
+        n = t.numel()
+        if bf16 and n % 2:
+            raise ValueError("a bfloat16 tensor of complex samples has an even number of elements")
+        return n // 2 if bf16 else n
+
+    @staticmethod
+    def _streams(a, la, b, lb, bf16: bool = False, cuda: bool = True) -> int:
+        na, nb = Plan._samples(a, bf16, cuda), Plan._samples(b, bf16, cuda)
+        if na % la or nb % lb or na // la != nb // lb:
             raise ValueError("input and output sizes do not match the plan")
-        return a.numel() // la
+        return na // la
 
 
 class State:
@@ -471,7 +487,7 @@ class State:
 
     def tx(self, grid, slot_out, workspace=None, stream=None):
         p = self.plan
-        n = Plan._streams(grid, p.tx_in_len, slot_out, p.slot_len)
+        n = Plan._streams(grid, p.tx_in_len, slot_out, p.slot_len, p.io_bf16)
         if n != self.n_streams:
             raise ValueError("the state was created for another number of streams")
         ws = workspace if workspace is not None else p.workspace(n)
@@ -482,7 +498,7 @@ class State:
 
     def rx(self, slot_in, grid_out, workspace=None, stream=None):
         p = self.plan
-        n = Plan._streams(slot_in, p.slot_len, grid_out, p.rx_out_len)
+        n = Plan._streams(slot_in, p.slot_len, grid_out, p.rx_out_len, p.io_bf16)
         if n != self.n_streams:
             raise ValueError("the state was created for another number of streams")
         ws = workspace if workspace is not None else p.workspace(n)
@@ -506,7 +522,7 @@ class Batch:
                 ls, ld = (plan.tx_in_len, plan.slot_len) if direction == FC_TX else (plan.slot_len, plan.rx_out_len)
             else:
                 ls, ld = (plan.tx_in_len, plan.wave_len) if direction == FC_TX else (plan.wave_len, plan.rx_out_len)
-            n = Plan._streams(src, ls, dst, ld)
+            n = Plan._streams(src, ls, dst, ld, plan.io_bf16)
             self._keep.append((plan, src, dst, state))
             c_items.append(FcBatchItem(plan.handle.value, state.handle.value if state is not None else None,
                                        int(direction), n, src.data_ptr(), dst.data_ptr(), None, 0))
@@ -548,8 +564,8 @@ class Server:
             z = self.sizes[cid]
             n_in, n_out = (z.tx_in_len, z.slot_len) if direction == FC_TX else (z.slot_len, z.rx_out_len)
             for x, n in ((h_in, n_in), (h_out, n_out)):
-                if x.dtype != torch.complex64 or x.is_cuda or not x.is_contiguous() or x.numel() != n:
-                    raise ValueError("expected contiguous complex64 host tensors of the carrier's sizes")
+                if Plan._samples(x, z.sample_bytes == 4, cuda=False) != n:
+                    raise ValueError("expected host tensors of the carrier's sizes")
             reqs.append(FcServeRequest(float(t), int(cid), int(direction), h_in.data_ptr(), h_out.data_ptr()))
         return fc_server_run(self.handle, reqs)
 
@@ -567,22 +583,16 @@ class Server:
 
 class Pipeline:
     """Owns one fc_pipeline: host-buffer TX / RX with copies and kernels of chunks of
-    streams overlapped. tx(grid, wave) / rx(wave, grid) take contiguous complex64 CPU
-    tensors (page-locked for overlap) and are asynchronous on `stream`."""
+    streams overlapped. tx(grid, wave) / rx(wave, grid) take contiguous CPU tensors of
+    the plan's sample type (complex64, or bfloat16 (re, im) pairs; page-locked for
+    overlap) and are asynchronous on `stream`."""
 
     def __init__(self, plan: Plan, chunk_streams: int, depth: int = 3):
         self.plan = plan
         self.handle = fc_pipeline_create(plan.handle, chunk_streams, depth)
 
-    @staticmethod
-    def _host(a, b, la, lb) -> int:
-        import torch
-        for t in (a, b):
-            if t.dtype != torch.complex64 or t.is_cuda or not t.is_contiguous():
-                raise ValueError("expected contiguous complex64 host tensors")
-        if a.numel() % la or b.numel() % lb or a.numel() // la != b.numel() // lb:
-            raise ValueError("input and output sizes do not match the plan")
-        return a.numel() // la
+    def _host(self, a, b, la, lb) -> int:
+        return Plan._streams(a, la, b, lb, self.plan.io_bf16, cuda=False)
 
     def tx(self, host_grid, host_wave, stream=None):
         n = self._host(host_grid, host_wave, self.plan.tx_in_len, self.plan.wave_len)

@@ -187,3 +187,23 @@ def test_time_io_sizes(fc):
         assert (s.tx_in_len, s.rx_out_len) == (s.grid_len, s.grid_len)
         t = fc.fc_geometry_check(dataclasses.replace(geom, flags=8))
         assert (t.tx_in_len, t.rx_out_len) == (sum(tx), sum(rx))
+
+
+def test_bf16_io_sizes(fc):
+    """FC_FLAG_IO_BF16 halves the bytes of a sample and nothing else: the lengths stay,
+    the workspace stays FP32, and the tensor-core passes (which accumulate into the
+    output) give way to the generic kernels."""
+    import dataclasses
+    for geom in (wl.config_single_5mhz(), wl.config_mixed_20mhz(), wl.config_100mhz(2)):
+        a = fc.fc_geometry_check(geom)
+        b = fc.fc_geometry_check(dataclasses.replace(geom, flags=16))
+        assert (a.sample_bytes, b.sample_bytes) == (8, 4)
+        for f in ("grid_len", "wave_len", "slot_len", "stream_delay", "tx_in_len", "rx_out_len"):
+            assert getattr(a, f) == getattr(b, f), f
+        assert b.workspace_per_stream == a.workspace_per_stream
+    g = wl.config_100mhz(2)
+    t = fc.fc_geometry_check(dataclasses.replace(g, flags=4 | 16))
+    assert (t.tx_kernels, t.rx_kernels) == (2, 2)
+    assert t.workspace_per_stream == fc.fc_geometry_check(g).workspace_per_stream
+    it = fc.fc_geometry_check(dataclasses.replace(wl.config_single_5mhz(), flags=8 | 16))
+    assert it.sample_bytes == 4 and it.tx_in_len == it.time_tx_len

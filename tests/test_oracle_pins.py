@@ -611,3 +611,32 @@ def test_sync_frame_matches_matrix_transcription(stx):
         e = np.zeros(T.shape[1], dtype=complex)
         e[j] = 1.0
         assert np.max(np.abs(fo.tx_frame(geom, e) - T[:, j])) < 1e-12
+
+
+def test_bf16_round_ties_bound_and_library():
+    """BF16 rounding of the complex-BF16 I/O expected values: hand-worked ties to even
+    (catches ties away from zero and a significand of 7 instead of 8 bits), the half-ulp
+    bound and idempotence (catches a binade off by one), and torch's CPU float32 ->
+    bfloat16 conversion on float32 inputs, where one rounding is the whole conversion."""
+    torch = pytest.importorskip("torch")
+    # spacing 2^-7 on [1, 2), 1 on [128, 256), 2^-133 among the subnormals
+    worked = [(1 + 2.0**-8, 1.0), (1 + 3 * 2.0**-8, 1 + 2.0**-6), (-(1 + 2.0**-8), -1.0),
+              (1 + 2.0**-7, 1 + 2.0**-7), (1 + 2.0**-8 + 2.0**-30, 1 + 2.0**-7), (254.5, 254.0), (255.5, 256.0),
+              (1.5 * 2.0**-133, 2.0**-132), (0.0, 0.0), (3.0, 3.0)]
+    for v, want in worked:
+        assert fo.bf16_round(np.array([v]))[0] == want, (v, want)
+    z = fo.bf16_round(np.array([1 + 2.0**-8 + 1j * (255.5)]))[0]
+    assert z == 1.0 + 256.0j
+    rng = np.random.default_rng(7)
+    v = (rng.standard_normal(20000) * 10.0 ** rng.uniform(-30, 30, 20000)).astype(np.float32)
+    k = rng.integers(128, 256, 4000)
+    e = rng.integers(-120, 120, 4000)
+    ties = (np.ldexp(k + 0.5, e - 7) * rng.choice([-1.0, 1.0], 4000)).astype(np.float32)   # exact in float32
+    v = np.concatenate([v, ties])
+    lib = torch.from_numpy(v).to(torch.bfloat16).to(torch.float64).numpy()
+    mine = fo.bf16_round(v.astype(np.float64))
+    assert np.array_equal(mine, lib)
+    w = rng.standard_normal(20000) * 10.0 ** rng.uniform(-20, 20, 20000)
+    r = fo.bf16_round(w)
+    assert np.all(np.abs(r - w) <= 2.0**-8 * np.abs(w))
+    assert np.array_equal(fo.bf16_round(r), r)
