@@ -317,8 +317,13 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
 
 // ---------------------------------------------------------------------------
 // RX jobs: one function per numerology, each with its transforms specialised for
-// their direction (the RX kernel holds few enough job shapes for its instruction
-// working set, and the specialised transforms execute fewer instructions).
+// their direction (they execute fewer instructions than conj(FFT(conj(x)))). The loops
+// over blocks and bin parities stay rolled, so that each job holds one copy of each
+// transform it uses (three for L = 1024 and three for L = 512): the instruction working
+// set, more than the arithmetic, limits this kernel (rolling the L = 1024 job from seven
+// inlined transforms to three took its time from 1.99 to 1.47 ms at 2048 streams, a few
+// hundred bytes of spills included). The L = 1024 block loop carries only block 0's part
+// of the symbol body into the block-1 iteration, which assembles and demodulates it.
 // ---------------------------------------------------------------------------
 template <int K, bool INV>
 __device__ __forceinline__ void step_twiddles_k(float2* v, const float2* __restrict__ tw, int lane) {
@@ -479,38 +484,56 @@ __device__ __noinline__ void rx_job_1024_reduced(const FcPlanDev& P, const FcGro
   }
 }
 
+// OLA: the scheme (a template parameter, so that the overlap-save form carries only the
+// 16 values per lane it needs across the block loop)
+template <bool OLA>
 __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                             const float2* __restrict__ src, float2* __restrict__ gdst, float2* scr,
                                             float2* map, int lane) {
   constexpr int L = 1024;
+  constexpr bool ola = OLA;
+  constexpr int kCarry = OLA ? 24 : 16;
   const float2* __restrict__ twL = P.sz[S.size_L].tw;
   const float2* __restrict__ twN = P.sz[G.size_N].tw;
   const int n = jb.index;
-  const bool ola = P.scheme_rx == FC_OLA;
-  float2 h[32];
-#pragma unroll
+  // the part of the symbol body that block 0 contributes, x_ofdm[lane + 32 k] for k < 16
+  // (OLS) or k < 24 (OLA), carried into the block-1 iteration, which assembles the body
+  // and demodulates it
+  float2 h0[kCarry];
+#pragma unroll 1
   for (int r = 0; r < 2; ++r) {
-    // R1-R2: block r, radix-2 split of the 2048-point DFT into even and odd bins
+    // R1-R2: block r, radix-2 split of the 2048-point DFT into even (s = 0) and odd bins
     const float2* __restrict__ x = src + jb.start + r * (2048 / 2);
-    float2 u[32], w[32];
+    float2 u[32];
     // R3: gather the subband's 1024 bins with conj(phi_r theta_n), D_m, inverse shift; the even
     // bins right after their transform, so only one half-spectrum is live in registers
     const float2 ph = root_pos(twN, 2048, (long long)S.c * (G.cps[n] + r * G.N_S));
-#pragma unroll
+#pragma unroll 1
     for (int s = 0; s < 2; ++s) {
-      float2 (&X)[32] = s ? w : u;
-      // even bins: DFT of x0 + x1; odd bins: DFT of (x0 - x1) exp(-j 2 pi tp / 2048)
+      if (s == 0) {
 #pragma unroll
-      for (int a = 0; a < 32; ++a) {
-        const int tp = 32 * a + lane;
-        float2 x0 = __ldg(x + tp), x1 = __ldg(x + tp + 1024);
-        if (ola) {                                 // A window [N_L, N_L + N_S) = [512, 1536)
-          if (tp < 512) x0 = czero();
-          if (tp >= 512) x1 = czero();
+        for (int a = 0; a < 32; ++a) {
+          const int tp = 32 * a + lane;
+          float2 x0 = __ldg(x + tp), x1 = __ldg(x + tp + 1024);
+          if (ola) {                               // A window [N_L, N_L + N_S) = [512, 1536)
+            if (tp < 512) x0 = czero();
+            if (tp >= 512) x1 = czero();
+          }
+          u[a] = cadd(x0, x1);
         }
-        X[a] = s ? cmul(csub(x0, x1), __ldg(twN + tp)) : cadd(x0, x1);
+      } else {
+#pragma unroll
+        for (int a = 0; a < 32; ++a) {
+          const int tp = 32 * a + lane;
+          float2 x0 = __ldg(x + tp), x1 = __ldg(x + tp + 1024);
+          if (ola) {
+            if (tp < 512) x0 = czero();
+            if (tp >= 512) x1 = czero();
+          }
+          u[a] = cmul(csub(x0, x1), __ldg(twN + tp));   // (x0 - x1) exp(-j 2 pi tp / 2048)
+        }
       }
-      warp_fft1024_d<false>(X, scr, twL, lane);     // bin 2 (k1 + 32 k2) + s
+      warp_fft1024_d<false>(u, scr, twL, lane);     // bin 2 (k1 + 32 k2) + s
 #pragma unroll
       for (int k2 = 0; k2 < 32; ++k2) {
         const int q = 2 * (lane + 32 * k2) + s;
@@ -518,7 +541,7 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
         if (kt >= 1024) kt -= 2048;
         if (kt >= -L / 2 && kt < L / 2) {
           const float wt = weight(S, S.drx, kt + L / 2);
-          map[kt & (L - 1)] = cscale(cmulc(X[k2], ph), wt);
+          map[kt & (L - 1)] = cscale(cmulc(u[k2], ph), wt);
         }
       }
     }
@@ -528,27 +551,28 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
     __syncwarp();
     // R4: short IDFT
     warp_fft1024_d<true>(u, scr, twL, lane);        // z_r[k1 + 32 k2] in u[k2]
-    // R5: S window + concatenation (eq:concat2), or OLA of both blocks; x_ofdm[t], t = lane + 32 k2
-    if (!ola) {
+    // R5: S window + concatenation (eq:concat2), or OLA of both blocks; x_ofdm[t], t = lane + 32 k
+    if (r == 0) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) h[16 * r + j] = u[j + 8];
-    } else {
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        if (r == 0) h[k] = (k < 24) ? u[k + 8] : czero();
-        else if (k >= 8) h[k] = cadd(h[k], u[k - 8]);
-      }
+      for (int k = 0; k < kCarry; ++k) h0[k] = u[k + 8];
+      continue;
     }
-  }
-  // R6: OFDM demodulation and active-bin output
-  warp_fft1024_d<false>(h, scr, twL, lane);
-  const int hl = S.Lact / 2, hu = S.Lact - hl;
-  float2* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
+    float2 h[32];
 #pragma unroll
-  for (int k2 = 0; k2 < 32; ++k2) {
-    const int bin = lane + 32 * k2;
-    const int f = bin < L / 2 ? bin : bin - L;
-    if (f >= -hl && f < hu) row[f + hl] = h[k2];
+    for (int k = 0; k < 32; ++k) {
+      if (!OLA) h[k] = k < 16 ? h0[k] : u[k - 8];
+      else h[k] = k < 8 ? h0[k] : (k < kCarry ? cadd(h0[k], u[k - 8]) : u[k - 8]);
+    }
+    // R6: OFDM demodulation and active-bin output
+    warp_fft1024_d<false>(h, scr, twL, lane);
+    const int hl = S.Lact / 2, hu = S.Lact - hl;
+    float2* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) {
+      const int bin = lane + 32 * k2;
+      const int f = bin < L / 2 ? bin : bin - L;
+      if (f >= -hl && f < hu) row[f + hl] = h[k2];
+    }
   }
 }
 
@@ -563,11 +587,10 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
   const float2* __restrict__ twN = P.sz[G.size_N].tw;
   const int n = jb.index;
   const bool ola = P.scheme_rx == FC_OLA;
-  float2 X0[32], X1[32];
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
+#pragma unroll 1
+  for (int r = 0; r < 2; ++r) {                      // one copy of the block DFT in the code
     const float2* __restrict__ x = src + jb.start + r * (1024 / 2);
-    float2 (&u)[32] = r ? X1 : X0;
+    float2 u[32];
 #pragma unroll
     for (int a = 0; a < 32; ++a) {
       const int t = 32 * a + lane;
@@ -576,11 +599,7 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
       u[a] = xv;
     }
     warp_fft1024_d<false>(u, scr, twN, lane);       // bin k1 + 32 k2
-  }
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
     const float2 ph = root_pos(twN, 1024, (long long)S.c * (G.cps[n] + r * G.N_S));
-    const float2 (&u)[32] = r ? X1 : X0;
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) {
       const int q = lane + 32 * k2;
@@ -696,7 +715,8 @@ k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     const FcSubDev& S = P.s[G.first_sub];
     if (S.L == 1024 && (P.flags & FC_FLAG_REDUCED_RX) && P.scheme_rx == FC_OLS)
       rx_job_1024_reduced(P, G, S, jb, src, gdst, scr, map, lane);
-    else if (S.L == 1024) rx_job_1024(P, G, S, jb, src, gdst, scr, map, lane);
+    else if (S.L == 1024 && P.scheme_rx == FC_OLA) rx_job_1024<true>(P, G, S, jb, src, gdst, scr, map, lane);
+    else if (S.L == 1024) rx_job_1024<false>(P, G, S, jb, src, gdst, scr, map, lane);
     else rx_job_512(P, G, S, jb, src, gdst, scr, map, lane);
   }
 }

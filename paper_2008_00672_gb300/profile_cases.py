@@ -1,15 +1,17 @@
 """Fixed invocations of the library's kernels for profilers.
 
     python -m paper_2008_00672_gb300.profile_cases CASE --streams S [--warm W]
+        [--tx-chunks K --rx-chunks K]
 
-builds the case's plan, sets the launch shape the benchmark uses, runs W warm-up
+builds the case's plan, sets a fixed launch shape (the case's default, or the chunks
+per stream given, e.g. the ones the benchmark's autotuner reports), runs W warm-up
 TX + RX passes and then one more TX + RX pass, so that `ncu -k <kernel> -s <skip>`
 can pick launches of a known shape. Inputs are seeded QAM grids; the RX input is the
 TX output (its values do not change the kernels' work).
 
 Cases:
   warp20     20 MHz mixed numerology, symbol-synchronized (one-warp-per-symbol kernels;
-             TX 1 chunk per stream, RX 4 chunks per stream)
+             default TX 1 chunk per stream, RX 2 chunks per stream)
   generic20  the same geometry on the generic shared-memory kernels
   tensor100  100 MHz / 273 PRB carrier, 10 slots, on the tensor-core passes
   fp32_100   the same carrier on the FP32 shared-memory kernels
@@ -26,7 +28,7 @@ from . import FC_FLAG_GENERIC_KERNELS, FC_FLAG_TENSOR_DFT, FC_RX, FC_TX, Plan, b
 
 def make_case(name: str):
     if name == "warp20":
-        return wl.config_mixed_20mhz(), {FC_TX: (1, 0), FC_RX: (4, 0)}
+        return wl.config_mixed_20mhz(), {FC_TX: (1, 0), FC_RX: (2, 0)}
     if name == "generic20":
         return dataclasses.replace(wl.config_mixed_20mhz(), flags=FC_FLAG_GENERIC_KERNELS), {}
     if name == "tensor100":
@@ -42,9 +44,14 @@ def main():
     ap.add_argument("case", choices=["warp20", "generic20", "tensor100", "fp32_100"])
     ap.add_argument("--streams", type=int, default=256)
     ap.add_argument("--warm", type=int, default=1)
+    ap.add_argument("--tx-chunks", type=int, default=0, help="chunks per stream of the TX launch (0: the case's)")
+    ap.add_argument("--rx-chunks", type=int, default=0, help="chunks per stream of the RX launch (0: the case's)")
     args = ap.parse_args()
     build.build()
     geom, shape = make_case(args.case)
+    for d, k in ((FC_TX, args.tx_chunks), (FC_RX, args.rx_chunks)):
+        if k:
+            shape[d] = (k, 0)
     plan = Plan(geom)
     S = args.streams
     for d, (k, g) in shape.items():
