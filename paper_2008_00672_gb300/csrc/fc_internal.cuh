@@ -22,6 +22,10 @@
 #define FC_MAX_PASSES 8
 #define FC_MAX_ELEMS_PER_THREAD 16   // in-place FFT: batch*n <= FC_THREADS*16
 
+// Elements a transform buffer of logical length n takes in shared memory: the generic
+// kernels store logical element l at l + l/16 (one float2 of padding after every 16).
+__host__ __device__ constexpr int fc_padded_len(int n) { return n + (n + 15) / 16; }
+
 struct FcSize {
   int n;
   int npass;
@@ -79,9 +83,9 @@ struct FcPlanDev {
   long long ws_len;   // workspace complex elements per stream
   long long tc_off;   // tensor-core path: workspace offset of the R x 4096 spectrum rows
   int time_tx_len, time_rx_len;   // FC_FLAG_IO_TIME: per-stream time I/O lengths
-  int ring;           // TX ring length (power of two)
-  int ybuf;           // spectrum buffer length (complex)
-  int wbuf;           // low-rate buffer length (complex)
+  int ring;           // TX ring length (>= the longest job span and FC_THREADS)
+  int ybuf;           // spectrum buffer length (complex, padded)
+  int wbuf;           // low-rate buffer length (complex, padded)
   int max_span;       // longest job output span
   FcGroupDev g[FC_MAX_GROUPS];
   FcSubDev s[FC_MAX_SUBBANDS];

@@ -12,7 +12,9 @@
 //     Gamma_sigma placement of eq:multi-symb, and the sum over subbands and
 //     numerology groups) happens in a shared-memory ring that each CTA owns for
 //     a contiguous range of output time; a range is written to HBM exactly once,
-//     when no later job can touch it.
+//     when no later job can touch it;
+//   * every transform buffer in shared memory holds logical element l at index
+//     l + l/16 (one float2 of padding after every 16, see sp()).
 //
 // Symbol-synchronized jobs are (group, symbol) pairs and process the two FC
 // blocks of a symbol as a batch of two (Sec. III-C); continuous jobs are pairs
@@ -39,6 +41,13 @@ __device__ __forceinline__ float2 io_ld(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ float2 io_ld(const bf2* p) { return __bfloat1622float2(__ldg(p)); }
 __device__ __forceinline__ void io_st(float2* p, float2 v) { *p = v; }
 __device__ __forceinline__ void io_st(bf2* p, float2 v) { *p = __float22bfloat162_rn(v); }
+
+// Physical index of logical element l of a transform buffer in shared memory. One float2
+// of padding after every 16 spreads the first Stockham pass's stores (R consecutive
+// outputs per thread, a stride of R float2 across the warp) over distinct banks, and
+// keeps the unit-stride accesses of the other passes conflict-free. A buffer of logical
+// length n takes fc_padded_len(n) elements.
+__device__ __forceinline__ int sp(int l) { return l + (l >> 4); }
 
 // multiply by -i (forward transform) or +i (inverse transform)
 template <bool INV>
@@ -202,10 +211,10 @@ __device__ __forceinline__ void pass_load(float2 (&v)[FC_MAX_ELEMS_PER_THREAD], 
       const int b = idx / nb;
       const int i = idx - b * nb;
       const int k = i % p;
-      const float2* s = a + b * n + i;
+      const int s = b * n + i;
       float2 w[R];
 #pragma unroll
-      for (int j = 0; j < R; ++j) w[j] = s[j * nb];
+      for (int j = 0; j < R; ++j) w[j] = a[sp(s + j * nb)];
       if (p > 1) {
 #pragma unroll
         for (int j = 1; j < R; ++j) {
@@ -234,15 +243,16 @@ __device__ __forceinline__ void pass_store(const float2 (&v)[FC_MAX_ELEMS_PER_TH
       const int b = idx / nb;
       const int i = idx - b * nb;
       const int k = i % p;
-      float2* d = a + b * n + (i - k) * R + k;
+      const int d = b * n + (i - k) * R + k;
 #pragma unroll
-      for (int j = 0; j < R; ++j) d[j * p] = v[u * R + j];
+      for (int j = 0; j < R; ++j) a[sp(d + j * p)] = v[u * R + j];
     }
   }
 }
 
-// In-place Stockham FFT over `batch` contiguous transforms of size n in shared
-// memory. Pass s with radix R and p = product of the previous radices:
+// In-place Stockham FFT over `batch` contiguous transforms of size n in a padded
+// shared-memory buffer (logical index l at sp(l)). Pass s with radix R and p = product
+// of the previous radices:
 //   butterfly i (0 <= i < n/R), k = i mod p, inputs a[i + j n/R] * W_{pR}^{j k},
 //   DFT_R, outputs to a[(i - k) R + k + j p]. All threads read their butterflies
 //   into registers, synchronise, then write back, so one buffer suffices.
@@ -302,15 +312,23 @@ __device__ __forceinline__ int active_index(int i, int n, int n_act) {
   return (f >= -lo && f < n_act - lo) ? f + lo : -1;
 }
 
+// The TX ring holds output time T at ring[T mod RS]; RS (the longest job span rounded
+// up, at least FC_THREADS) need not be a power of two, so a thread steps its index by
+// FC_THREADS and wraps it.
+__device__ __forceinline__ int ring_step(int r, int RS) {
+  r += FC_THREADS;
+  return r >= RS ? r - RS : r;
+}
+
 // Copy ring[from, to) to dst and clear it, in segments no longer than the ring.
 template <typename TO>
-__device__ __forceinline__ void ring_flush(float2* ring, int mask, TO* __restrict__ dst, int from, int to) {
+__device__ __forceinline__ void ring_flush(float2* ring, int RS, TO* __restrict__ dst, int from, int to) {
   while (from < to) {
-    const int seg = min(to - from, mask + 1);
-    for (int i = threadIdx.x; i < seg; i += FC_THREADS) {
-      const int T = from + i;
-      io_st(dst + T, ring[T & mask]);
-      ring[T & mask] = make_float2(0.f, 0.f);
+    const int seg = min(to - from, RS);
+    int r = ((from + (int)threadIdx.x) % RS + RS) % RS;
+    for (int i = threadIdx.x; i < seg; i += FC_THREADS, r = ring_step(r, RS)) {
+      io_st(dst + from + i, ring[r]);
+      ring[r] = make_float2(0.f, 0.f);
     }
     __syncthreads();
     from += seg;
@@ -324,7 +342,7 @@ __device__ __forceinline__ void ofdm_symbol_to_time(const FcPlanDev& P, const Fc
   const int L = S.Lofdm;
   for (int i = threadIdx.x; i < L; i += FC_THREADS) {
     const int a = active_index(i, L, S.Lact);
-    buf[i] = a >= 0 ? io_ld(row + a) : make_float2(0.f, 0.f);
+    buf[sp(i)] = a >= 0 ? io_ld(row + a) : make_float2(0.f, 0.f);
   }
   __syncthreads();
   fft_inplace<true>(buf, 1, P.sz[S.size_O]);
@@ -342,8 +360,8 @@ __device__ __forceinline__ void tx_map(const FcSubDev& S, int N, const float2* Z
     int q = (S.c + p - h) % N;
     if (q < 0) q += N;
     const float w = __ldg(S.dtx + p);
-    const float2 v = cmul(Z[r * L + k], r ? ph1 : ph0);
-    float2& y = Y[r * N + q];
+    const float2 v = cmul(Z[sp(r * L + k)], r ? ph1 : ph0);
+    float2& y = Y[sp(r * N + q)];
     y.x = fmaf(v.x, w, y.x);
     y.y = fmaf(v.y, w, y.y);
   }
@@ -364,12 +382,12 @@ __device__ __forceinline__ void rx_gather(const FcSubDev& S, int N, const float2
       int q = (S.c + p - h) % N;
       if (q < 0) q += N;
       const float2 ph = r ? ph1 : ph0;
-      const float2 y = Y[r * N + q];
+      const float2 y = Y[sp(r * N + q)];
       const float w = __ldg(S.drx + p);
       // y * conj(ph) * w
       v = make_float2((y.x * ph.x + y.y * ph.y) * w, (y.y * ph.x - y.x * ph.y) * w);
     }
-    V[idx] = v;
+    V[sp(idx)] = v;
   }
   __syncthreads();
 }
@@ -386,11 +404,11 @@ __device__ __forceinline__ void tx_sync_chunk(const FcPlanDev& P, const FcJob* _
   float2* ring = reinterpret_cast<float2*>(smem_raw);
   float2* Y = ring + P.ring;
   float2* W = Y + P.ybuf;
+  const int RS = P.ring;
   const bool io_time = (P.flags & FC_FLAG_IO_TIME) != 0;
   const TI* gsrc = grid + (size_t)stream * (io_time ? P.time_tx_len : P.grid_len);
   TO* wdst = wave + (size_t)stream * P.frame_len;
-  const int mask = P.ring - 1;
-  zero_buf(ring, P.ring);
+  zero_buf(ring, RS);
   int flushed = ch.t0;
   __syncthreads();
 
@@ -398,7 +416,7 @@ __device__ __forceinline__ void tx_sync_chunk(const FcPlanDev& P, const FcJob* _
     const FcJob jb = jobs[j];
     const FcGroupDev& G = P.g[jb.group];
     const int N = G.N, n = jb.index;
-    zero_buf(Y, 2 * N);
+    zero_buf(Y, fc_padded_len(2 * N));
     __syncthreads();
     for (int m = G.first_sub; m < G.first_sub + G.n_sub; ++m) {
       const FcSubDev& S = P.s[m];
@@ -410,7 +428,7 @@ __device__ __forceinline__ void tx_sync_chunk(const FcPlanDev& P, const FcJob* _
       if (!io_time) ofdm_symbol_to_time(P, S, gsrc + S.grid_off + (long long)n * S.Lact, W);
       // T2-T3: CP insertion, zero padding to 3L/2 (eq:padding), two segments with the
       // dynamic-overlap analysis windows a_{m,0}, a_{m,1} (OLA) or none (OLS)
-      float2* Z = W + L;
+      float2* Z = W + fc_padded_len(L);
       for (int idx = threadIdx.x; idx < 2 * L; idx += FC_THREADS) {
         const int r = idx >= L;
         const int zi = r * (L / 2) + idx - r * L;     // index in the padded symbol z_n
@@ -422,9 +440,9 @@ __device__ __forceinline__ void tx_sync_chunk(const FcPlanDev& P, const FcJob* _
         } else if (in) {
           int bi = zi - q4;
           if (bi < 0) bi += L;
-          v = W[bi];
+          v = W[sp(bi)];
         }
-        Z[idx] = v;
+        Z[sp(idx)] = v;
       }
       __syncthreads();
       // T4: short DFTs of both blocks
@@ -440,27 +458,25 @@ __device__ __forceinline__ void tx_sync_chunk(const FcPlanDev& P, const FcJob* _
     // T7: R_N^{(r)} combination (OLS windows s_{m,0}, s_{m,1}), Gamma_sigma placement into the ring
     const int h = N / 2, ncp = G.ncp[n];
     const bool ols = P.scheme_tx == FC_OLS;
-    for (int tau = threadIdx.x; tau < 3 * h; tau += FC_THREADS) {
+    int r = ((jb.start + (int)threadIdx.x) % RS + RS) % RS;
+    for (int tau = threadIdx.x; tau < 3 * h; tau += FC_THREADS, r = ring_step(r, RS)) {
       float2 v = make_float2(0.f, 0.f);
-      if (tau < N && (!ols || (tau >= G.N_L - ncp && tau < G.N_L + G.N_S))) v = cadd(v, Y[tau]);
+      if (tau < N && (!ols || (tau >= G.N_L - ncp && tau < G.N_L + G.N_S))) v = cadd(v, Y[sp(tau)]);
       if (tau >= h) {
         const int t = tau - h;
-        if (!ols || (t >= G.N_L && t < G.N_L + G.N_S)) v = cadd(v, Y[N + t]);
+        if (!ols || (t >= G.N_L && t < G.N_L + G.N_S)) v = cadd(v, Y[sp(N + t)]);
       }
       const int T = jb.start + tau;
-      if (T >= flushed && T < ch.t1) {
-        float2& rr = ring[T & mask];
-        rr = cadd(rr, v);
-      }
+      if (T >= flushed && T < ch.t1) ring[r] = cadd(ring[r], v);
     }
     __syncthreads();
     const int upto = (j + 1 < ch.j1) ? min(jobs[j + 1].start, ch.t1) : ch.t1;
     if (upto > flushed) {
-      ring_flush(ring, mask, wdst, flushed, upto);
+      ring_flush(ring, RS, wdst, flushed, upto);
       flushed = upto;
     }
   }
-  if (ch.t1 > flushed) ring_flush(ring, mask, wdst, flushed, ch.t1);
+  if (ch.t1 > flushed) ring_flush(ring, RS, wdst, flushed, ch.t1);
 }
 
 template <typename TI, typename TO>
@@ -498,7 +514,7 @@ __device__ __forceinline__ void rx_sync_chunk(const FcPlanDev& P, const FcJob* _
       const int t = idx - r * N;
       float2 v = io_ld(src + jb.start + r * h + t);
       if (ola && !(t >= G.N_L && t < G.N_L + G.N_S)) v = make_float2(0.f, 0.f);
-      Y[idx] = v;
+      Y[sp(idx)] = v;
     }
     __syncthreads();
     // R2: long DFTs
@@ -514,18 +530,18 @@ __device__ __forceinline__ void rx_sync_chunk(const FcPlanDev& P, const FcJob* _
       // R4: short IDFTs (1/(sqrt(I) L) folded into D)
       fft_inplace<true>(W, 2, P.sz[S.size_L]);
       // R5: S window and concatenation (eq:concat2), or OLA of the two blocks
-      float2* X = W + 2 * L;
+      float2* X = W + fc_padded_len(2 * L);
       for (int t = threadIdx.x; t < L; t += FC_THREADS) {
         float2 v;
         if (!ola) {
-          v = t < L / 2 ? W[q4 + t] : W[L + t - q4];
+          v = t < L / 2 ? W[sp(q4 + t)] : W[sp(L + t - q4)];
         } else {
           const int u = q4 + t;
           v = make_float2(0.f, 0.f);
-          if (u < L) v = cadd(v, W[u]);
-          if (u >= L / 2) v = cadd(v, W[L + u - L / 2]);
+          if (u < L) v = cadd(v, W[sp(u)]);
+          if (u >= L / 2) v = cadd(v, W[sp(L + u - L / 2)]);
         }
-        X[t] = v;
+        X[sp(t)] = v;
         if (io_time) io_st(gdst + S.time_rx_off + (long long)n * L + t, cscale(v, sqrtf((float)S.Lofdm)));   // body, true scale
       }
       __syncthreads();
@@ -536,7 +552,7 @@ __device__ __forceinline__ void rx_sync_chunk(const FcPlanDev& P, const FcJob* _
       for (int a = threadIdx.x; a < S.Lact; a += FC_THREADS) {
         int bin = a - S.Lact / 2;
         if (bin < 0) bin += L;
-        io_st(row + a, X[bin]);
+        io_st(row + a, X[sp(bin)]);
       }
       __syncthreads();
     }
@@ -625,7 +641,7 @@ k_ofdm_mod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const TI* __re
   for (int i = threadIdx.x; i < lcp + L; i += FC_THREADS) {   // K_{L_CP} (eq:TX_CPins)
     int bi = i - lcp;
     if (bi < 0) bi += L;
-    dst[i] = buf[bi];
+    dst[i] = buf[sp(bi)];
   }
 }
 
@@ -646,9 +662,9 @@ k_tx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
   const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
   const float2* wsrc = ws + (size_t)stream * P.ws_len;
   TO* wdst = wave + (size_t)stream * P.frame_len;
-  const int mask = P.ring - 1;
+  const int RS = P.ring;
   const bool ols = P.scheme_tx == FC_OLS;
-  zero_buf(ring, P.ring);
+  zero_buf(ring, RS);
   int flushed = ch.t0;
   __syncthreads();
 
@@ -656,7 +672,7 @@ k_tx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
     const FcJob jb = jobs[j];
     const FcGroupDev& G = P.g[jb.group];
     const int N = G.N, r0 = jb.index, nb = jb.nblk;
-    zero_buf(Y, 2 * N);
+    zero_buf(Y, fc_padded_len(2 * N));
     __syncthreads();
     for (int m = G.first_sub; m < G.first_sub + G.n_sub; ++m) {
       const FcSubDev& S = P.s[m];
@@ -669,7 +685,7 @@ k_tx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
         const int pos = (r0 + b) * S.L_S + t - S.S_L;
         float2 v = make_float2(0.f, 0.f);
         if (b < nb && pos >= 0 && pos < S.n_low && (ols || (t >= S.L_L && t < S.L_L + S.L_S))) v = __ldg(s + pos);
-        Z[idx] = v;
+        Z[sp(idx)] = v;
       }
       __syncthreads();
       fft_inplace<false>(Z, 2, P.sz[S.size_L]);
@@ -681,27 +697,25 @@ k_tx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
     fft_inplace<true>(Y, 2, P.sz[G.size_N]);
     // OLA accumulate / OLS discard (S_{m,r}) into the ring
     const int span = G.N_S + N;
-    for (int tau = threadIdx.x; tau < span; tau += FC_THREADS) {
+    int r = ((jb.start + (int)threadIdx.x) % RS + RS) % RS;
+    for (int tau = threadIdx.x; tau < span; tau += FC_THREADS, r = ring_step(r, RS)) {
       float2 v = make_float2(0.f, 0.f);
-      if (tau < N && (!ols || (tau >= G.N_L && tau < G.N_L + G.N_S))) v = cadd(v, Y[tau]);
+      if (tau < N && (!ols || (tau >= G.N_L && tau < G.N_L + G.N_S))) v = cadd(v, Y[sp(tau)]);
       if (nb > 1 && tau >= G.N_S) {
         const int t = tau - G.N_S;
-        if (!ols || (t >= G.N_L && t < G.N_L + G.N_S)) v = cadd(v, Y[N + t]);
+        if (!ols || (t >= G.N_L && t < G.N_L + G.N_S)) v = cadd(v, Y[sp(N + t)]);
       }
       const int T = jb.start + tau;
-      if (T >= flushed && T < ch.t1) {
-        float2& rr = ring[T & mask];
-        rr = cadd(rr, v);
-      }
+      if (T >= flushed && T < ch.t1) ring[r] = cadd(ring[r], v);
     }
     __syncthreads();
     const int upto = (j + 1 < ch.j1) ? min(jobs[j + 1].start, ch.t1) : ch.t1;
     if (upto > flushed) {
-      ring_flush(ring, mask, wdst, flushed, upto);
+      ring_flush(ring, RS, wdst, flushed, upto);
       flushed = upto;
     }
   }
-  if (ch.t1 > flushed) ring_flush(ring, mask, wdst, flushed, ch.t1);
+  if (ch.t1 > flushed) ring_flush(ring, RS, wdst, flushed, ch.t1);
 }
 
 // ---------------------------------------------------------------------------
@@ -732,7 +746,7 @@ k_rx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
       const int t = idx - b * N;
       float2 v = make_float2(0.f, 0.f);
       if (b < nb && (!ola || (t >= G.N_L && t < G.N_L + G.N_S))) v = io_ld(src + jb.start + b * G.N_S + t);
-      Y[idx] = v;
+      Y[sp(idx)] = v;
     }
     __syncthreads();
     fft_inplace<false>(Y, 2, P.sz[G.size_N]);
@@ -750,12 +764,12 @@ k_rx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
           const int b = idx >= S.L_S;
           const int t = S.L_L + idx - b * S.L_S;
           const int pos = (r0 + b) * S.L_S + t - S.S_L;
-          if (pos >= 0 && pos < S.n_low) d[pos] = V[b * L + t];
+          if (pos >= 0 && pos < S.n_low) d[pos] = V[sp(b * L + t)];
         }
       } else {      // keep whole blocks; overlapping parts are added by the demodulator
         for (int idx = threadIdx.x; idx < nb * L; idx += FC_THREADS) {
           const int b = idx >= L;
-          d[(long long)(r0 + b) * L + idx - b * L] = V[idx];
+          d[(long long)(r0 + b) * L + idx - b * L] = V[sp(idx)];
         }
       }
       __syncthreads();
@@ -792,7 +806,7 @@ k_ofdm_demod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2
       if (r_hi > G.R - 1) r_hi = G.R - 1;
       for (int r = r_hi; r >= 0 && Pu - r * S.L_S < S.L; --r) v = cadd(v, __ldg(s + (long long)r * S.L + Pu - r * S.L_S));
     }
-    buf[t] = v;
+    buf[sp(t)] = v;
     if (P.flags & FC_FLAG_IO_TIME)       // the body before demodulation, true scale
       io_st(grid + (size_t)stream * P.time_rx_len + S.time_rx_off + (long long)n * Lo + t, cscale(v, sqrtf((float)S.Lofdm)));
   }
@@ -803,7 +817,7 @@ k_ofdm_demod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2
   for (int a = threadIdx.x; a < S.Lact; a += FC_THREADS) {
     int bin = a - S.Lact / 2;
     if (bin < 0) bin += Lo;
-    io_st(row + a, buf[bin]);
+    io_st(row + a, buf[sp(bin)]);
   }
 }
 

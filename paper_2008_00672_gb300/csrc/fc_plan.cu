@@ -439,13 +439,16 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     const int cap = (n % 3 == 0) ? FC_THREADS * (FC_MAX_ELEMS_PER_THREAD / 3) * 3 : FC_THREADS * FC_MAX_ELEMS_PER_THREAD;
     if (2 * n > cap) return fail(FC_ERR_UNSUPPORTED, "transform too large for the in-place FFT");
   }
-  int ring = 1;
-  while (ring < max_span) ring <<= 1;
-  const int ybuf = 2 * n_max;
-  const int wbuf = sync ? 3 * l_max : 2 * l_max;
+  // TX ring: the longest job span (at least one sample per thread), a multiple of 16;
+  // transform buffers padded (fc_padded_len): symbol-sync W holds L then 2L (TX: OFDM
+  // symbol and the two segments; RX: the two short blocks and the concatenated body),
+  // continuous W the 2L of a block pair
+  const int ring = (std::max(max_span, FC_THREADS) + 15) / 16 * 16;
+  const int ybuf = fc_padded_len(2 * n_max);
+  const int wbuf = sync ? fc_padded_len(l_max) + fc_padded_len(2 * l_max) : fc_padded_len(2 * l_max);
   pl->smem_tx = (size_t)(ring + ybuf + wbuf) * sizeof(float2);
   pl->smem_rx = (size_t)(ybuf + wbuf) * sizeof(float2);
-  pl->smem_ofdm = (size_t)lo_max * sizeof(float2);
+  pl->smem_ofdm = (size_t)fc_padded_len(lo_max) * sizeof(float2);
   const size_t smem_cap = pl->smem_cap;
   if (pl->smem_tx > smem_cap || pl->smem_rx > smem_cap)
     return fail(FC_ERR_UNSUPPORTED, "geometry needs more shared memory than one SM has");
