@@ -29,7 +29,7 @@ __host__ __device__ constexpr int fc_padded_len(int n) { return n + (n + 15) / 1
 struct FcSize {
   int n;
   int npass;
-  int radix[FC_MAX_PASSES];
+  unsigned char radix[FC_MAX_PASSES];   // radices in pass order
   const float2* tw;   // tw[m] = exp(-j 2 pi m / n), m in [0, n), FP64-rounded
 };
 

@@ -197,6 +197,19 @@ struct Dft<16, INV> {
 // One register file v[] serves every radix: butterfly u of a thread occupies
 // v[u R .. u R + R). The radix-specific phases contain no barrier, so the
 // register allocator sees a single live array across the pass.
+// Butterfly idx of a pass -> (transform b, butterfly i within it, k = i mod p), without
+// a division where it can: batch is 1 or 2, and p is a power of two until the radix-3
+// passes (pm = p - 1 then, else -1).
+__device__ __forceinline__ void butterfly_of(int idx, int nb, int p, int pm, int& b, int& i, int& k) {
+  b = 0;
+  i = idx;
+  while (i >= nb) {
+    i -= nb;
+    ++b;
+  }
+  k = pm >= 0 ? (i & pm) : i % p;
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void pass_load(float2 (&v)[FC_MAX_ELEMS_PER_THREAD], const float2* a, int n, int batch,
                                           int p, const float2* __restrict__ tw) {
@@ -204,13 +217,13 @@ __device__ __forceinline__ void pass_load(float2 (&v)[FC_MAX_ELEMS_PER_THREAD], 
   const int nb = n / R;
   const int total = nb * batch;
   const int twstep = n / (p * R);
+  const int pm = (p & (p - 1)) == 0 ? p - 1 : -1;
 #pragma unroll
   for (int u = 0; u < MAXB; ++u) {
     const int idx = threadIdx.x + u * FC_THREADS;
     if (idx < total) {
-      const int b = idx / nb;
-      const int i = idx - b * nb;
-      const int k = i % p;
+      int b, i, k;
+      butterfly_of(idx, nb, p, pm, b, i, k);
       const int s = b * n + i;
       float2 w[R];
 #pragma unroll
@@ -236,13 +249,13 @@ __device__ __forceinline__ void pass_store(const float2 (&v)[FC_MAX_ELEMS_PER_TH
   constexpr int MAXB = FC_MAX_ELEMS_PER_THREAD / R;
   const int nb = n / R;
   const int total = nb * batch;
+  const int pm = (p & (p - 1)) == 0 ? p - 1 : -1;
 #pragma unroll
   for (int u = 0; u < MAXB; ++u) {
     const int idx = threadIdx.x + u * FC_THREADS;
     if (idx < total) {
-      const int b = idx / nb;
-      const int i = idx - b * nb;
-      const int k = i % p;
+      int b, i, k;
+      butterfly_of(idx, nb, p, pm, b, i, k);
       const int d = b * n + (i - k) * R + k;
 #pragma unroll
       for (int j = 0; j < R; ++j) a[sp(d + j * p)] = v[u * R + j];
@@ -250,9 +263,9 @@ __device__ __forceinline__ void pass_store(const float2 (&v)[FC_MAX_ELEMS_PER_TH
   }
 }
 
-// In-place Stockham FFT over `batch` contiguous transforms of size n in a padded
-// shared-memory buffer (logical index l at sp(l)). Pass s with radix R and p = product
-// of the previous radices:
+// In-place Stockham FFT over `batch` (1 or 2) contiguous transforms of size n in a
+// padded shared-memory buffer (logical index l at sp(l)). Pass s with radix R and p =
+// product of the previous radices:
 //   butterfly i (0 <= i < n/R), k = i mod p, inputs a[i + j n/R] * W_{pR}^{j k},
 //   DFT_R, outputs to a[(i - k) R + k + j p]. All threads read their butterflies
 //   into registers, synchronise, then write back, so one buffer suffices.

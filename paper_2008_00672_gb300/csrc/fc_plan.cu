@@ -49,17 +49,20 @@ bool is_2a3b(int n) {
   return n == 1;
 }
 
-// Radix schedule: all factors 3 as radix-3 passes; the power of two split into
-// ceil(a/4) passes of 2^(<=4), balanced, avoiding radix 2 where possible.
-void radix_plan(int n, int* radix, int* npass) {
+// Radix schedule: all factors 3 as radix-3 passes (last); the power of two 2^a in
+// ceil(a/4) balanced passes of at most radix 16. Fewer, larger passes beat smaller radices
+// that would keep more of the CTA's threads busy, because each pass costs two CTA
+// barriers: schedules with at least 256 butterflies per pass (radix 4 for one 1024-point
+// transform) made the 20 MHz symbol-sync TX kernel 33 % slower.
+void radix_plan(int n, unsigned char* radix, int* npass) {
   int a = 0, b = 0, m = n;
   while (m % 2 == 0) { m /= 2; ++a; }
   while (m % 3 == 0) { m /= 3; ++b; }
   int k = 0;
   if (a > 0) {
-    int passes = (a + 3) / 4;
-    int base = a / passes, extra = a % passes;
-    for (int i = 0; i < passes; ++i) radix[k++] = 1 << (base + (i < extra ? 1 : 0));
+    const int passes = (a + 3) / 4;
+    const int base = a / passes, extra = a % passes;
+    for (int i = 0; i < passes; ++i) radix[k++] = (unsigned char)(1 << (base + (i < extra ? 1 : 0)));
   }
   for (int i = 0; i < b; ++i) radix[k++] = 3;
   *npass = k;
