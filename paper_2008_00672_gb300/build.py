@@ -16,7 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfcofdm.so")
-SOURCES = ["fc_kernels.cu", "fc_warp.cu", "fc_plan.cu", "fc_static.cu", "fc_stream.cu", "fc_exec.cu", "fc_server.cu", "fc_tensor.cu", "fc_host.cu"]
+SOURCES = ["fc_kernels.cu", "fc_kernels_256.cu", "fc_warp.cu", "fc_plan.cu", "fc_static.cu", "fc_stream.cu", "fc_exec.cu",
+           "fc_server.cu", "fc_tensor.cu", "fc_host.cu"]
+# sources that include another source (fc_kernels_256.cu compiles fc_kernels.cu for 256-thread CTAs)
+INCLUDES = {"fc_kernels_256.cu": ["fc_kernels.cu"]}
 HEADERS = ["fc_internal.cuh", "fc_device.cuh", "fc_tc.cuh", os.path.join("..", "..", "include", "fcofdm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
@@ -42,7 +45,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     hdrs = [os.path.join(CSRC, h) for h in HEADERS]
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     objs = [os.path.join(OUT_DIR, os.path.splitext(s)[0] + ".o") for s in SOURCES]
-    jobs = [(s, o) for s, o in zip(srcs, objs) if force or _stale(o, [s] + hdrs)]
+    jobs = [(s, o) for s, o in zip(srcs, objs)
+            if force or _stale(o, [s] + hdrs + [os.path.join(CSRC, d) for d in INCLUDES.get(os.path.basename(s), [])])]
 
     def compile_one(so):
         src, obj = so

@@ -28,6 +28,7 @@ struct fc_batch {
   struct Queue {
     int dir = 0;
     int io = 0;                                   // FC_IO_* bits shared by its items
+    const FcGenKernels* gen = nullptr;            // kernel set (CTA size) of its items
     FcWork* d_work = nullptr;
     int n = 0;
     size_t smem = 0;
@@ -78,8 +79,8 @@ int issue(fc_batch* b) {
   if (e != cudaSuccess) return cuda_err(e, "batch fork");
   for (size_t q = 0; q < b->queues.size() && e == cudaSuccess; ++q) {   // the queues, on the first lanes
     const fc_batch::Queue& Q = b->queues[q];
-    e = fc_launch_sync_multi(Q.dir == FC_TX, Q.d_work, Q.n, Q.io, b->d_next + q, b->num_sms, Q.smem,
-                             b->lanes[q % b->lanes.size()]);
+    e = Q.gen->sync_multi(Q.dir == FC_TX, Q.d_work, Q.n, Q.io, b->d_next + q, b->num_sms, Q.smem,
+                          b->lanes[q % b->lanes.size()]);
   }
   if (e != cudaSuccess) return cuda_err(e, "persistent queue launch");
   for (size_t i = 0; i < b->items.size(); ++i) {
@@ -160,9 +161,9 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
     }
   }
   // persistent mode: generic symbol-sync frame calls go to queues by direction, by I/O
-  // type (complex64 or complex BF16) and by occupancy class (1, 2, 3 or 4 CTAs of 512
-  // threads per SM for their shared memory), items of the largest plans first (each CTA
-  // of a launch takes the next item)
+  // type (complex64 or complex BF16), by kernel set (512- or 256-thread CTAs) and by
+  // occupancy class (1, 2, 3 or 4 CTAs per SM for their shared memory), items of the
+  // largest plans first (each CTA of a launch takes the next item)
   if (e == cudaSuccess && (mode & FC_BATCH_PERSISTENT)) {
     b->in_queue.assign(b->items.size(), 0);
     b->num_sms = fc_internal_num_sms(b->items[0].plan);
@@ -177,8 +178,8 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
       size[i] = sz.wave_len;
     }
     std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return size[x] > size[y]; });
-    std::vector<FcWork> work[2][2][4];   // [direction][BF16 I/O][occupancy class]
-    size_t smem_of[2][2][4] = {};
+    std::vector<FcWork> work[2][2][2][4];   // [direction][BF16 I/O][256-thread set][occupancy class]
+    size_t smem_of[2][2][2][4] = {};
     for (size_t i : order) {
       const fc_batch_item& it = b->items[i];
       if (it.state || it.n_streams == 0) continue;
@@ -188,28 +189,31 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
       const size_t per_cta = smem + 4096;                         // + static plan copy and slack
       int cls = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)dev_smem / per_cta)) - 1;
       const int bf = fc_internal_io(it.plan) != 0;
+      const int t256 = fc_internal_gen(it.plan).threads == 256;
       b->in_queue[i] = 1;
-      std::vector<FcWork>& w = work[it.direction][bf][cls];
+      std::vector<FcWork>& w = work[it.direction][bf][t256][cls];
       w.insert(w.end(), mine.begin(), mine.end());
-      smem_of[it.direction][bf][cls] = std::max(smem_of[it.direction][bf][cls], smem);
+      smem_of[it.direction][bf][t256][cls] = std::max(smem_of[it.direction][bf][t256][cls], smem);
     }
     for (int dir = 0; dir < 2; ++dir)
       for (int bf = 0; bf < 2; ++bf)
-        for (int cls = 0; cls < 4; ++cls) {
-          const std::vector<FcWork>& w = work[dir][bf][cls];
-          if (w.empty() || e != cudaSuccess) continue;
-          fc_batch::Queue Q;
-          Q.dir = dir;
-          Q.io = bf ? (FC_IO_IN_BF16 | FC_IO_OUT_BF16) : 0;
-          Q.n = (int)w.size();
-          Q.smem = smem_of[dir][bf][cls];
-          e = cudaMalloc(&Q.d_work, w.size() * sizeof(FcWork));
-          if (e == cudaSuccess) {
-            b->owned.push_back(Q.d_work);
-            e = cudaMemcpy(Q.d_work, w.data(), w.size() * sizeof(FcWork), cudaMemcpyHostToDevice);
+        for (int t256 = 0; t256 < 2; ++t256)
+          for (int cls = 0; cls < 4; ++cls) {
+            const std::vector<FcWork>& w = work[dir][bf][t256][cls];
+            if (w.empty() || e != cudaSuccess) continue;
+            fc_batch::Queue Q;
+            Q.dir = dir;
+            Q.io = bf ? (FC_IO_IN_BF16 | FC_IO_OUT_BF16) : 0;
+            Q.gen = t256 ? &fc_gen_kernels_256() : &fc_gen_kernels_512();
+            Q.n = (int)w.size();
+            Q.smem = smem_of[dir][bf][t256][cls];
+            e = cudaMalloc(&Q.d_work, w.size() * sizeof(FcWork));
+            if (e == cudaSuccess) {
+              b->owned.push_back(Q.d_work);
+              e = cudaMemcpy(Q.d_work, w.data(), w.size() * sizeof(FcWork), cudaMemcpyHostToDevice);
+            }
+            b->queues.push_back(Q);
           }
-          b->queues.push_back(Q);
-        }
     if (e == cudaSuccess && !b->queues.empty()) {
       e = cudaMalloc(&b->d_next, b->queues.size() * sizeof(int));
       if (e == cudaSuccess) b->owned.push_back(b->d_next);

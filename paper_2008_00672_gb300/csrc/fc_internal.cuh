@@ -10,7 +10,15 @@
 
 #include "../../include/fcofdm.h"
 
+// The generic kernels (fc_kernels.cu) are compiled twice: for 512-thread CTAs, one per
+// SM (transforms up to 4096 points), and for 256-thread CTAs, two per SM (up to 2048
+// points; fc_kernels_256.cu). FC_THREADS is the CTA size of the compilation at hand.
+#ifndef FC_THREADS
 #define FC_THREADS 512
+#endif
+#ifndef FC_GEN_MIN_BLOCKS
+#define FC_GEN_MIN_BLOCKS 1      // resident CTAs per SM that compilation is built for
+#endif
 #define FC_WARP_THREADS 128      // warp-specialised kernels: 4 warps, one symbol job per warp
 #ifndef FC_WARP_TX_MIN_BLOCKS
 #define FC_WARP_TX_MIN_BLOCKS 2  // resident CTAs per SM the warp TX kernel is compiled for
@@ -20,7 +28,7 @@
 #endif
 #define FC_MAX_SIZES 12       // distinct transform sizes in one plan
 #define FC_MAX_PASSES 8
-#define FC_MAX_ELEMS_PER_THREAD 16   // in-place FFT: batch*n <= FC_THREADS*16
+#define FC_MAX_ELEMS_PER_THREAD 16   // in-place FFT: batch*n <= threads*16
 
 // Elements a transform buffer of logical length n takes in shared memory: the generic
 // kernels store logical element l at l + l/16 (one float2 of padding after every 16).
@@ -83,7 +91,7 @@ struct FcPlanDev {
   long long ws_len;   // workspace complex elements per stream
   long long tc_off;   // tensor-core path: workspace offset of the R x 4096 spectrum rows
   int time_tx_len, time_rx_len;   // FC_FLAG_IO_TIME: per-stream time I/O lengths
-  int ring;           // TX ring length (>= the longest job span and FC_THREADS)
+  int ring;           // TX ring length (>= the longest job span and the CTA's threads)
   int ybuf;           // spectrum buffer length (complex, padded)
   int wbuf;           // low-rate buffer length (complex, padded)
   int max_span;       // longest job output span
@@ -98,7 +106,6 @@ struct FcPlanDev {
 #define FC_IO_IN_BF16 1
 #define FC_IO_OUT_BF16 2
 
-// kernel launchers (defined in fc_kernels.cu); dP is the plan's device copy
 // one work item of the persistent multi-plan symbol-sync launch: one chunk of one stream
 struct FcWork {
   const FcPlanDev* plan;
@@ -109,23 +116,31 @@ struct FcWork {
   int stream;
   int io;             // FC_IO_* bits: 0 or FC_IO_IN_BF16 | FC_IO_OUT_BF16
 };
-// every item of one launch has the same io (0 or FC_IO_IN_BF16 | FC_IO_OUT_BF16)
-cudaError_t fc_launch_sync_multi(bool tx, const FcWork* work, int n_work, int io, int* next, int num_sms, size_t smem,
-                                 cudaStream_t st);
-cudaError_t fc_launch_tx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                              int n_streams, const void* grid, void* wave, int io, size_t smem, cudaStream_t st);
-cudaError_t fc_launch_rx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                              int n_streams, const void* wave, void* grid, int io, size_t smem, cudaStream_t st);
-cudaError_t fc_launch_ofdm_mod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const void* grid,
-                               float2* ws, int io, size_t smem, cudaStream_t st);
-cudaError_t fc_launch_tx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                              int n_streams, const float2* ws, void* wave, int io, size_t smem, cudaStream_t st);
-cudaError_t fc_launch_rx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                              int n_streams, const void* wave, float2* ws, int io, size_t smem, cudaStream_t st);
-cudaError_t fc_launch_ofdm_demod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const float2* ws,
-                                 void* grid, int io, size_t smem, cudaStream_t st);
-// raise the dynamic shared-memory limit of every kernel on the current device
-cudaError_t fc_set_smem_limits(size_t max_dynamic_smem);
+// The launchers of one compilation of the generic kernels (CTAs of `threads` threads);
+// dP is the plan's device copy.
+// In sync_multi every item of one launch has the same io (0 or FC_IO_IN_BF16 |
+// FC_IO_OUT_BF16); set_smem_limits raises the dynamic shared-memory limit of every
+// kernel of the set on the current device.
+struct FcGenKernels {
+  int threads;
+  cudaError_t (*sync_multi)(bool tx, const FcWork* work, int n_work, int io, int* next, int num_sms, size_t smem,
+                            cudaStream_t st);
+  cudaError_t (*tx_sync)(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks, int n_streams,
+                         const void* grid, void* wave, int io, size_t smem, cudaStream_t st);
+  cudaError_t (*rx_sync)(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks, int n_streams,
+                         const void* wave, void* grid, int io, size_t smem, cudaStream_t st);
+  cudaError_t (*ofdm_mod)(const FcPlanDev* dP, int syms_per_stream, int n_streams, const void* grid, float2* ws,
+                          int io, size_t smem, cudaStream_t st);
+  cudaError_t (*tx_cont)(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks, int n_streams,
+                         const float2* ws, void* wave, int io, size_t smem, cudaStream_t st);
+  cudaError_t (*rx_cont)(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks, int n_streams,
+                         const void* wave, float2* ws, int io, size_t smem, cudaStream_t st);
+  cudaError_t (*ofdm_demod)(const FcPlanDev* dP, int syms_per_stream, int n_streams, const float2* ws, void* grid,
+                            int io, size_t smem, cudaStream_t st);
+  cudaError_t (*set_smem_limits)(size_t max_dynamic_smem);
+};
+const FcGenKernels& fc_gen_kernels_512();
+const FcGenKernels& fc_gen_kernels_256();
 
 // warp-specialised symbol-synchronized kernels (fc_warp.cu); jobs are grouped per chunk
 // tensor-core FC passes (continuous, one subband, L = N = 4096)
@@ -155,6 +170,8 @@ int fc_internal_plan_device(const fc_plan* plan);    // the device a plan was cr
 // dynamic shared memory.
 bool fc_internal_sync_work(const fc_plan* plan, int dir, int n_streams, const void* in, void* out,
                            std::vector<FcWork>& work, size_t* smem);
+// The generic-kernel set a plan runs on.
+const FcGenKernels& fc_internal_gen(const fc_plan* plan);
 // A frame call (direction FC_TX / FC_RX) with the I/O types io (FC_IO_* bits) instead of
 // the plan's own; the stream calls use it to keep their frames in FP32. Same checks and
 // status as fc_tx_synthesize / fc_rx_analyze.

@@ -493,7 +493,7 @@ __device__ __forceinline__ void tx_sync_chunk(const FcPlanDev& P, const FcJob* _
 }
 
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(FC_THREADS, 1)
+__global__ void __launch_bounds__(FC_THREADS, FC_GEN_MIN_BLOCKS)
 k_tx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
           int n_chunks, const TI* __restrict__ grid, TO* __restrict__ wave) {
   __shared__ FcPlanDev P;
@@ -573,7 +573,7 @@ __device__ __forceinline__ void rx_sync_chunk(const FcPlanDev& P, const FcJob* _
 }
 
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(FC_THREADS, 1)
+__global__ void __launch_bounds__(FC_THREADS, FC_GEN_MIN_BLOCKS)
 k_rx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
           int n_chunks, const TI* __restrict__ wave, TO* __restrict__ grid) {
   __shared__ FcPlanDev P;
@@ -590,7 +590,7 @@ k_rx_sync(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
 // one I/O type T (a queue holds complex64 or complex-BF16 items, never both).
 // ---------------------------------------------------------------------------
 template <bool TX, typename T>
-__global__ void __launch_bounds__(FC_THREADS, 1)
+__global__ void __launch_bounds__(FC_THREADS, FC_GEN_MIN_BLOCKS)
 k_sync_multi(const FcWork* __restrict__ work, int n_work, int* __restrict__ next) {
   __shared__ FcPlanDev P;
   __shared__ int item;
@@ -632,7 +632,7 @@ __device__ __forceinline__ bool locate_symbol(const FcPlanDev& P, int& m, int& n
 }
 
 template <typename TI>
-__global__ void __launch_bounds__(FC_THREADS, 1)
+__global__ void __launch_bounds__(FC_THREADS, FC_GEN_MIN_BLOCKS)
 k_ofdm_mod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const TI* __restrict__ grid,
            float2* __restrict__ ws) {
   __shared__ FcPlanDev P;
@@ -662,7 +662,7 @@ k_ofdm_mod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const TI* __re
 // Continuous mode, stage 2 (TX): FC blocks over [0_{S_L}; s; 0_{S_L}] (eq:BDM)
 // ---------------------------------------------------------------------------
 template <typename TO>
-__global__ void __launch_bounds__(FC_THREADS, 1)
+__global__ void __launch_bounds__(FC_THREADS, FC_GEN_MIN_BLOCKS)
 k_tx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
           int n_chunks, const float2* __restrict__ ws, TO* __restrict__ wave) {
   __shared__ FcPlanDev P;
@@ -736,7 +736,7 @@ k_tx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
 // disjoint kept parts) or per-block outputs (OLA, summed by the demodulator)
 // ---------------------------------------------------------------------------
 template <typename TI>
-__global__ void __launch_bounds__(FC_THREADS, 1)
+__global__ void __launch_bounds__(FC_THREADS, FC_GEN_MIN_BLOCKS)
 k_rx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
           int n_chunks, const TI* __restrict__ wave, float2* __restrict__ ws) {
   __shared__ FcPlanDev P;
@@ -794,7 +794,7 @@ k_rx_cont(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, cons
 // Continuous mode, stage 2 (RX): CP removal and OFDM demodulation
 // ---------------------------------------------------------------------------
 template <typename TO>
-__global__ void __launch_bounds__(FC_THREADS, 1)
+__global__ void __launch_bounds__(FC_THREADS, FC_GEN_MIN_BLOCKS)
 k_ofdm_demod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2* __restrict__ ws,
              TO* __restrict__ grid) {
   __shared__ FcPlanDev P;
@@ -837,7 +837,7 @@ k_ofdm_demod(const FcPlanDev* __restrict__ gP, int syms_per_stream, const float2
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// launchers
+// launchers (file-local; exported as this compilation's FcGenKernels table)
 // ---------------------------------------------------------------------------
 namespace {
 template <bool TX, typename T>
@@ -850,9 +850,8 @@ cudaError_t launch_multi(const FcWork* work, int n_work, int* next, int num_sms,
   k_sync_multi<TX, T><<<n_ctas, FC_THREADS, smem, st>>>(work, n_work, next);
   return cudaGetLastError();
 }
-}  // namespace
 
-cudaError_t fc_launch_sync_multi(bool tx, const FcWork* work, int n_work, int io, int* next, int num_sms, size_t smem,
+cudaError_t launch_sync_multi(bool tx, const FcWork* work, int n_work, int io, int* next, int num_sms, size_t smem,
                                  cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(next, 0, sizeof(int), st);
   if (e != cudaSuccess || n_work == 0) return e;
@@ -864,7 +863,7 @@ cudaError_t fc_launch_sync_multi(bool tx, const FcWork* work, int n_work, int io
             : launch_multi<false, float2>(work, n_work, next, num_sms, smem, st);
 }
 
-cudaError_t fc_launch_tx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+cudaError_t launch_tx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
                               int n_streams, const void* grid, void* wave, int io, size_t smem, cudaStream_t st) {
   const dim3 g((unsigned)(n_streams * n_chunks));
   if (io == 0)
@@ -878,7 +877,7 @@ cudaError_t fc_launch_tx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcCh
   return cudaGetLastError();
 }
 
-cudaError_t fc_launch_rx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+cudaError_t launch_rx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
                               int n_streams, const void* wave, void* grid, int io, size_t smem, cudaStream_t st) {
   const dim3 g((unsigned)(n_streams * n_chunks));
   if (io == 0)
@@ -892,7 +891,7 @@ cudaError_t fc_launch_rx_sync(const FcPlanDev* dP, const FcJob* jobs, const FcCh
   return cudaGetLastError();
 }
 
-cudaError_t fc_launch_ofdm_mod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const void* grid,
+cudaError_t launch_ofdm_mod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const void* grid,
                                float2* ws, int io, size_t smem, cudaStream_t st) {
   const dim3 g((unsigned)(n_streams * syms_per_stream));
   if (io & FC_IO_IN_BF16)
@@ -902,7 +901,7 @@ cudaError_t fc_launch_ofdm_mod(const FcPlanDev* dP, int syms_per_stream, int n_s
   return cudaGetLastError();
 }
 
-cudaError_t fc_launch_tx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+cudaError_t launch_tx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
                               int n_streams, const float2* ws, void* wave, int io, size_t smem, cudaStream_t st) {
   const dim3 g((unsigned)(n_streams * n_chunks));
   if (io & FC_IO_OUT_BF16)
@@ -912,7 +911,7 @@ cudaError_t fc_launch_tx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcCh
   return cudaGetLastError();
 }
 
-cudaError_t fc_launch_rx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
+cudaError_t launch_rx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
                               int n_streams, const void* wave, float2* ws, int io, size_t smem, cudaStream_t st) {
   const dim3 g((unsigned)(n_streams * n_chunks));
   if (io & FC_IO_IN_BF16)
@@ -922,7 +921,7 @@ cudaError_t fc_launch_rx_cont(const FcPlanDev* dP, const FcJob* jobs, const FcCh
   return cudaGetLastError();
 }
 
-cudaError_t fc_launch_ofdm_demod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const float2* ws,
+cudaError_t launch_ofdm_demod(const FcPlanDev* dP, int syms_per_stream, int n_streams, const float2* ws,
                                  void* grid, int io, size_t smem, cudaStream_t st) {
   const dim3 g((unsigned)(n_streams * syms_per_stream));
   if (io & FC_IO_OUT_BF16)
@@ -932,14 +931,12 @@ cudaError_t fc_launch_ofdm_demod(const FcPlanDev* dP, int syms_per_stream, int n
   return cudaGetLastError();
 }
 
-namespace {
 template <typename K>
 cudaError_t raise_smem(K kernel, size_t max_smem) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
 }
-}  // namespace
 
-cudaError_t fc_set_smem_limits(size_t max_smem) {
+cudaError_t set_smem_limits(size_t max_smem) {
   const cudaError_t e[] = {
       raise_smem(k_tx_sync<float2, float2>, max_smem), raise_smem(k_tx_sync<bf2, bf2>, max_smem),
       raise_smem(k_tx_sync<bf2, float2>, max_smem),    raise_smem(k_rx_sync<float2, float2>, max_smem),
@@ -953,4 +950,13 @@ cudaError_t fc_set_smem_limits(size_t max_smem) {
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
   return cudaSuccess;
+}
+}  // namespace
+
+#define FC_GEN_CAT2(a, b) a##b
+#define FC_GEN_CAT(a, b) FC_GEN_CAT2(a, b)
+const FcGenKernels& FC_GEN_CAT(fc_gen_kernels_, FC_THREADS)() {
+  static const FcGenKernels k{FC_THREADS,  launch_sync_multi, launch_tx_sync,   launch_rx_sync, launch_ofdm_mod,
+                              launch_tx_cont, launch_rx_cont,  launch_ofdm_demod, set_smem_limits};
+  return k;
 }

@@ -26,6 +26,8 @@ int cuda_fail(cudaError_t e, const char* where) {
 }
 
 constexpr size_t kSmemPerBlockMax = 232448;   // 227 KB opt-in dynamic + static limit on sm_10x
+constexpr size_t kSmemPerSm = 233472;         // 228 KB shared memory per SM on sm_10x
+constexpr size_t kSmemPerCtaReserve = 1024;   // shared memory the system keeps per resident CTA
 
 // ---------------------------------------------------------------------------
 // host staging of all device tables in one allocation
@@ -87,6 +89,8 @@ struct fc_plan {
   int device = 0;
   int num_sms = 0;
   size_t smem_cap = kSmemPerBlockMax - sizeof(FcPlanDev) - 256;   // dynamic shared memory per CTA
+  size_t smem_sm = kSmemPerSm;              // shared memory per SM
+  const FcGenKernels* gen = nullptr;        // generic-kernel set (512- or 256-thread CTAs)
   FcPlanDev h{};
   FcPlanDev* d_plan = nullptr;
   unsigned char* d_mem = nullptr;
@@ -436,19 +440,33 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     l_max = std::max(l_max, o.L);
     lo_max = std::max(lo_max, o.Lo);
   }
-  // in-place FFT capacity: batch 2 of N and L
-  for (size_t i = 0; i < sizes.size(); ++i) {
-    const int n = sizes[i];
-    const int cap = (n % 3 == 0) ? FC_THREADS * (FC_MAX_ELEMS_PER_THREAD / 3) * 3 : FC_THREADS * FC_MAX_ELEMS_PER_THREAD;
-    if (2 * n > cap) return fail(FC_ERR_UNSUPPORTED, "transform too large for the in-place FFT");
-  }
+  // in-place FFT capacity of a CTA of `threads` threads: batch 2 of N and L
+  auto fits_fft = [&](int threads) {
+    for (int n : sizes) {
+      const int cap = (n % 3 == 0) ? threads * (FC_MAX_ELEMS_PER_THREAD / 3) * 3 : threads * FC_MAX_ELEMS_PER_THREAD;
+      if (2 * n > cap) return false;
+    }
+    return true;
+  };
+  if (!fits_fft(512)) return fail(FC_ERR_UNSUPPORTED, "transform too large for the in-place FFT");
   // TX ring: the longest job span (at least one sample per thread), a multiple of 16;
   // transform buffers padded (fc_padded_len): symbol-sync W holds L then 2L (TX: OFDM
   // symbol and the two segments; RX: the two short blocks and the concatenated body),
   // continuous W the 2L of a block pair
-  const int ring = (std::max(max_span, FC_THREADS) + 15) / 16 * 16;
+  auto ring_for = [&](int threads) { return (std::max(max_span, threads) + 15) / 16 * 16; };
   const int ybuf = fc_padded_len(2 * n_max);
   const int wbuf = sync ? fc_padded_len(l_max) + fc_padded_len(2 * l_max) : fc_padded_len(2 * l_max);
+  // generic kernels: 256-thread CTAs, two per SM, where every transform fits them and two
+  // CTAs' shared memory fits one SM (one CTA's barrier waits then overlap the other's
+  // work); else 512-thread CTAs, one per SM
+  const size_t static_smem = sizeof(FcPlanDev) + 256;
+  const size_t two_per_sm = pl->smem_sm / 2 > static_smem + kSmemPerCtaReserve
+                                ? pl->smem_sm / 2 - static_smem - kSmemPerCtaReserve : 0;
+  const size_t tx256 = (size_t)(ring_for(256) + ybuf + wbuf) * sizeof(float2);
+  const bool use256 = fits_fft(256) && tx256 <= two_per_sm;
+  const int threads = use256 ? 256 : 512;
+  pl->gen = use256 ? &fc_gen_kernels_256() : &fc_gen_kernels_512();
+  const int ring = ring_for(threads);
   pl->smem_tx = (size_t)(ring + ybuf + wbuf) * sizeof(float2);
   pl->smem_rx = (size_t)(ybuf + wbuf) * sizeof(float2);
   pl->smem_ofdm = (size_t)fc_padded_len(lo_max) * sizeof(float2);
@@ -700,15 +718,15 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* 
     return fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams,
                                   plan->h.frame_len, grid, wave, st);
   if (plan->h.mode == FC_SYMBOL_SYNC)
-    return fc_launch_tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, in,
-                             out, io, plan->smem_tx, st);
+    return plan->gen->tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, in,
+                              out, io, plan->smem_tx, st);
   if (plan->tc_tx && !c.second && io == 0) {
     const int R = plan->h.g[0].R;
     cudaError_t e = plan->tc_ofdm ? fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_OFDM_MOD, n_streams,
                                                  plan->h.g[0].B, grid, nullptr, workspace, plan->d_err,
                                                  plan->num_sms, st)
-                                  : fc_launch_ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid,
-                                                       workspace, 0, plan->smem_ofdm, st);
+                                  : plan->gen->ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid,
+                                                        workspace, 0, plan->smem_ofdm, st);
     if (e == cudaSuccess)
       e = cudaMemsetAsync(wave, 0, (size_t)n_streams * plan->h.frame_len * sizeof(float2), st);
     if (e == cudaSuccess)
@@ -719,11 +737,11 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* 
                        plan->d_err, plan->num_sms, st);
     return e;
   }
-  cudaError_t e = fc_launch_ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, in, workspace, io,
-                                     plan->smem_ofdm, st);
+  cudaError_t e = plan->gen->ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, in, workspace, io,
+                                      plan->smem_ofdm, st);
   if (e == cudaSuccess)
-    e = fc_launch_tx_cont(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, workspace,
-                          out, io, plan->smem_tx, st);
+    e = plan->gen->tx_cont(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, workspace,
+                           out, io, plan->smem_tx, st);
   return e;
 }
 
@@ -736,8 +754,8 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* 
     return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams,
                                   wave, grid, st);
   if (plan->h.mode == FC_SYMBOL_SYNC)
-    return fc_launch_rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, in,
-                             out, io, plan->smem_rx, st);
+    return plan->gen->rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, in,
+                              out, io, plan->smem_rx, st);
   if (plan->tc_rx && !c.second && io == 0) {
     const int R = plan->h.g[0].R;
     cudaError_t e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_RX_FFT, n_streams, R, wave, nullptr, workspace,
@@ -748,15 +766,15 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* 
     if (e == cudaSuccess)
       e = plan->tc_ofdm ? fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_OFDM_DEMOD, n_streams, plan->h.g[0].B,
                                        nullptr, grid, workspace, plan->d_err, plan->num_sms, st)
-                        : fc_launch_ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, grid,
-                                               0, plan->smem_ofdm, st);
+                        : plan->gen->ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, grid,
+                                                0, plan->smem_ofdm, st);
     return e;
   }
-  cudaError_t e = fc_launch_rx_cont(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams,
-                                    in, workspace, io, plan->smem_rx, st);
+  cudaError_t e = plan->gen->rx_cont(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams,
+                                     in, workspace, io, plan->smem_rx, st);
   if (e == cudaSuccess)
-    e = fc_launch_ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, out, io, plan->smem_ofdm,
-                             st);
+    e = plan->gen->ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, out, io, plan->smem_ofdm,
+                              st);
   return e;
 }
 
@@ -769,6 +787,8 @@ int fc_internal_plan_device(const fc_plan* plan) { return plan ? plan->device : 
 int fc_internal_num_sms(const fc_plan* plan) { return plan ? plan->num_sms : 0; }
 
 int fc_internal_io(const fc_plan* plan) { return plan ? plan->io : 0; }
+
+const FcGenKernels& fc_internal_gen(const fc_plan* plan) { return *plan->gen; }
 
 int fc_internal_frame(const fc_plan* plan, int dir, int n_streams, const void* in, void* out, void* workspace,
                       size_t workspace_bytes, void* stream, int io) {
@@ -823,9 +843,17 @@ int fc_plan_create(fc_plan** out, const fc_geometry* geometry, int32_t device) {
   }
   const size_t reserve = sizeof(FcPlanDev) + 256;   // static shared memory of the kernels
   pl->smem_cap = (size_t)optin > reserve ? (size_t)optin - reserve : 0;
+  int per_sm = 0;
+  e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+  if (e != cudaSuccess) {
+    delete pl;
+    return cuda_fail(e, "cudaDeviceGetAttribute");
+  }
+  pl->smem_sm = (size_t)per_sm;
   cudaError_t se = cudaSuccess;
   std::call_once(g_smem_once[device], [&] {
-    se = fc_set_smem_limits(pl->smem_cap);
+    se = fc_gen_kernels_512().set_smem_limits(pl->smem_cap);
+    if (se == cudaSuccess) se = fc_gen_kernels_256().set_smem_limits(pl->smem_cap);
     if (se == cudaSuccess) se = fc_set_warp_smem_limits();
     if (se == cudaSuccess) se = fc_set_tc_smem_limits();
   });
