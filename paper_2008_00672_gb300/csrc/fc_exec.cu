@@ -161,7 +161,7 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
     }
   }
   // persistent mode: generic symbol-sync frame calls go to queues by direction, by I/O
-  // type (complex64 or complex BF16), by kernel set (512- or 256-thread CTAs) and by
+  // type (complex64 or complex BF16), by kernel set (512-, 256- or 128-thread CTAs) and by
   // occupancy class (1, 2, 3 or 4 CTAs per SM for their shared memory), items of the
   // largest plans first (each CTA of a launch takes the next item)
   if (e == cudaSuccess && (mode & FC_BATCH_PERSISTENT)) {
@@ -178,8 +178,9 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
       size[i] = sz.wave_len;
     }
     std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return size[x] > size[y]; });
-    std::vector<FcWork> work[2][2][2][4];   // [direction][BF16 I/O][256-thread set][occupancy class]
-    size_t smem_of[2][2][2][4] = {};
+    std::vector<FcWork> work[2][2][3][4];   // [direction][BF16 I/O][kernel set][occupancy class]
+    size_t smem_of[2][2][3][4] = {};
+    const FcGenKernels* sets[3] = {&fc_gen_kernels_512(), &fc_gen_kernels_256(), &fc_gen_kernels_128()};
     for (size_t i : order) {
       const fc_batch_item& it = b->items[i];
       if (it.state || it.n_streams == 0) continue;
@@ -189,24 +190,24 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
       const size_t per_cta = smem + 4096;                         // + static plan copy and slack
       int cls = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)dev_smem / per_cta)) - 1;
       const int bf = fc_internal_io(it.plan) != 0;
-      const int t256 = fc_internal_gen(it.plan).threads == 256;
+      const int set = fc_internal_gen(it.plan).threads == 256 ? 1 : (fc_internal_gen(it.plan).threads == 128 ? 2 : 0);
       b->in_queue[i] = 1;
-      std::vector<FcWork>& w = work[it.direction][bf][t256][cls];
+      std::vector<FcWork>& w = work[it.direction][bf][set][cls];
       w.insert(w.end(), mine.begin(), mine.end());
-      smem_of[it.direction][bf][t256][cls] = std::max(smem_of[it.direction][bf][t256][cls], smem);
+      smem_of[it.direction][bf][set][cls] = std::max(smem_of[it.direction][bf][set][cls], smem);
     }
     for (int dir = 0; dir < 2; ++dir)
       for (int bf = 0; bf < 2; ++bf)
-        for (int t256 = 0; t256 < 2; ++t256)
+        for (int set = 0; set < 3; ++set)
           for (int cls = 0; cls < 4; ++cls) {
-            const std::vector<FcWork>& w = work[dir][bf][t256][cls];
+            const std::vector<FcWork>& w = work[dir][bf][set][cls];
             if (w.empty() || e != cudaSuccess) continue;
             fc_batch::Queue Q;
             Q.dir = dir;
             Q.io = bf ? (FC_IO_IN_BF16 | FC_IO_OUT_BF16) : 0;
-            Q.gen = t256 ? &fc_gen_kernels_256() : &fc_gen_kernels_512();
+            Q.gen = sets[set];
             Q.n = (int)w.size();
-            Q.smem = smem_of[dir][bf][t256][cls];
+            Q.smem = smem_of[dir][bf][set][cls];
             e = cudaMalloc(&Q.d_work, w.size() * sizeof(FcWork));
             if (e == cudaSuccess) {
               b->owned.push_back(Q.d_work);

@@ -10,9 +10,10 @@
 
 #include "../../include/fcofdm.h"
 
-// The generic kernels (fc_kernels.cu) are compiled twice: for 512-thread CTAs, one per
-// SM (transforms up to 4096 points), and for 256-thread CTAs, two per SM (up to 2048
-// points; fc_kernels_256.cu). FC_THREADS is the CTA size of the compilation at hand.
+// The generic kernels (fc_kernels.cu) are compiled three times: for 512-thread CTAs, one
+// per SM (transforms up to 4096 points), 256-thread CTAs, two per SM (up to 2048 points;
+// fc_kernels_256.cu), and 128-thread CTAs, four per SM (up to 1024 points;
+// fc_kernels_128.cu). FC_THREADS is the CTA size of the compilation at hand.
 #ifndef FC_THREADS
 #define FC_THREADS 512
 #endif
@@ -141,6 +142,7 @@ struct FcGenKernels {
 };
 const FcGenKernels& fc_gen_kernels_512();
 const FcGenKernels& fc_gen_kernels_256();
+const FcGenKernels& fc_gen_kernels_128();
 
 // warp-specialised symbol-synchronized kernels (fc_warp.cu); jobs are grouped per chunk
 // tensor-core FC passes (continuous, one subband, L = N = 4096)

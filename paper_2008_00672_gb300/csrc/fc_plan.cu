@@ -85,12 +85,24 @@ struct GroupHost {
 
 }  // namespace
 
+// Launch shape of one call: split index (chunks per stream), the generic kernels instead
+// of the specialised or tensor-core ones, and the generic-kernel set (-1: by the call's CTA
+// count, see gen_for)
+struct Choice {
+  int split = 0;
+  int generic = 0;
+  int set = -1;
+};
+
 struct fc_plan {
   int device = 0;
   int num_sms = 0;
   size_t smem_cap = kSmemPerBlockMax - sizeof(FcPlanDev) - 256;   // dynamic shared memory per CTA
   size_t smem_sm = kSmemPerSm;              // shared memory per SM
-  const FcGenKernels* gen = nullptr;        // generic-kernel set (512- or 256-thread CTAs)
+  // generic-kernel sets (0: 512-thread CTAs, one per SM; 1: 256, two per SM; 2: 128, four
+  // per SM) and which of them the plan's transforms and shared memory fit (0 always)
+  const FcGenKernels* gen[3] = {nullptr, nullptr, nullptr};
+  bool gen_fits[3] = {true, false, false};
   FcPlanDev h{};
   FcPlanDev* d_plan = nullptr;
   unsigned char* d_mem = nullptr;
@@ -114,7 +126,7 @@ struct fc_plan {
   // launch choices measured by fc_plan_autotune, per (n_streams, direction); execute
   // calls without an entry use the occupancy heuristic pick_split
   mutable std::mutex tune_mu;
-  std::map<std::pair<int, int>, std::pair<int, int>> tuned;   // -> (split index, generic kernels)
+  std::map<std::pair<int, int>, Choice> tuned;
 };
 
 namespace {
@@ -456,17 +468,22 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   auto ring_for = [&](int threads) { return (std::max(max_span, threads) + 15) / 16 * 16; };
   const int ybuf = fc_padded_len(2 * n_max);
   const int wbuf = sync ? fc_padded_len(l_max) + fc_padded_len(2 * l_max) : fc_padded_len(2 * l_max);
-  // generic kernels: 256-thread CTAs, two per SM, where every transform fits them and two
-  // CTAs' shared memory fits one SM (one CTA's barrier waits then overlap the other's
-  // work); else 512-thread CTAs, one per SM
+  // generic kernels: which CTA sizes (128 threads four per SM, 256 two per SM, 512 one per
+  // SM) hold every transform in their in-place FFT and fit their shared memory as many
+  // times per SM; several CTAs per SM overlap one CTA's barrier waits with the others'
+  // work, larger CTAs finish one chunk sooner (the choice per call is gen_for's)
   const size_t static_smem = sizeof(FcPlanDev) + 256;
-  const size_t two_per_sm = pl->smem_sm / 2 > static_smem + kSmemPerCtaReserve
-                                ? pl->smem_sm / 2 - static_smem - kSmemPerCtaReserve : 0;
-  const size_t tx256 = (size_t)(ring_for(256) + ybuf + wbuf) * sizeof(float2);
-  const bool use256 = fits_fft(256) && tx256 <= two_per_sm;
-  const int threads = use256 ? 256 : 512;
-  pl->gen = use256 ? &fc_gen_kernels_256() : &fc_gen_kernels_512();
-  const int ring = ring_for(threads);
+  const int ring = ring_for(512);            // serves every set (ring >= the CTA's threads)
+  auto fits_sm = [&](int threads, int per_sm) {
+    const size_t budget = pl->smem_sm / per_sm;
+    const size_t need = (size_t)(ring + ybuf + wbuf) * sizeof(float2) + static_smem + kSmemPerCtaReserve;
+    return fits_fft(threads) && need <= budget;
+  };
+  pl->gen[0] = &fc_gen_kernels_512();
+  pl->gen[1] = &fc_gen_kernels_256();
+  pl->gen[2] = &fc_gen_kernels_128();
+  pl->gen_fits[1] = fits_sm(256, 2);
+  pl->gen_fits[2] = fits_sm(128, 4);
   pl->smem_tx = (size_t)(ring + ybuf + wbuf) * sizeof(float2);
   pl->smem_rx = (size_t)(ybuf + wbuf) * sizeof(float2);
   pl->smem_ofdm = (size_t)fc_padded_len(lo_max) * sizeof(float2);
@@ -696,36 +713,51 @@ int check_io(const fc_plan* plan, int32_t n_streams, const void* in, const void*
   return FC_OK;
 }
 
-// (split index, generic) for this call: the autotuned choice if there is one
-std::pair<int, int> choose(const fc_plan* pl, int n_streams, int dir) {
+// Launch shape for this call: the autotuned or set choice if there is one
+Choice choose(const fc_plan* pl, int n_streams, int dir) {
   {
     std::lock_guard<std::mutex> lock(pl->tune_mu);
     auto it = pl->tuned.find({n_streams, dir});
     if (it != pl->tuned.end()) return it->second;
   }
-  return {(int)pick_split(pl, n_streams), 0};
+  Choice c;
+  c.split = (int)pick_split(pl, n_streams);
+  return c;
+}
+
+// Generic-kernel set of a call launching n_ctas CTAs per kernel: the chosen one, else
+// 128-thread CTAs where the call fills four per SM, else 256-thread CTAs where they fit,
+// else 512. (Measured: 128-thread CTAs lose on calls too small to fill the GPU, such as a
+// batch's one-stream calls on concurrent lanes; 256-thread CTAs win even there, and for
+// one-stream serving calls.)
+const FcGenKernels& gen_for(const fc_plan* pl, long long n_ctas, int set) {
+  if (set >= 0 && set < 3 && pl->gen_fits[set]) return *pl->gen[set];
+  if (pl->gen_fits[2] && n_ctas >= 4LL * pl->num_sms) return *pl->gen[2];
+  if (pl->gen_fits[1]) return *pl->gen[1];
+  return *pl->gen[0];
 }
 
 // io: FC_IO_* bits of this call's input and output; the specialised and tensor-core
 // kernels take complex64 only (a plan with FC_FLAG_IO_BF16 never selects them)
 cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* out, float2* workspace,
-                      cudaStream_t st, std::pair<int, int> c, int io) {
-  const size_t k = (size_t)c.first;
+                      cudaStream_t st, Choice c, int io) {
+  const size_t k = (size_t)c.split;
+  const FcGenKernels& gen = gen_for(plan, (long long)n_streams * plan->tx_nchunks[k], c.set);
   const float2* grid = (const float2*)in;
   float2* wave = (float2*)out;
   // float4 reductions of the warp kernel need a 16-byte aligned waveform
-  if (plan->warp_path && !c.second && io == 0 && ((uintptr_t)wave & 15) == 0)
+  if (plan->warp_path && !c.generic && io == 0 && ((uintptr_t)wave & 15) == 0)
     return fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams,
                                   plan->h.frame_len, grid, wave, st);
   if (plan->h.mode == FC_SYMBOL_SYNC)
-    return plan->gen->tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, in,
+    return gen.tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, in,
                               out, io, plan->smem_tx, st);
-  if (plan->tc_tx && !c.second && io == 0) {
+  if (plan->tc_tx && !c.generic && io == 0) {
     const int R = plan->h.g[0].R;
     cudaError_t e = plan->tc_ofdm ? fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_OFDM_MOD, n_streams,
                                                  plan->h.g[0].B, grid, nullptr, workspace, plan->d_err,
                                                  plan->num_sms, st)
-                                  : plan->gen->ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid,
+                                  : gen.ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid,
                                                         workspace, 0, plan->smem_ofdm, st);
     if (e == cudaSuccess)
       e = cudaMemsetAsync(wave, 0, (size_t)n_streams * plan->h.frame_len * sizeof(float2), st);
@@ -737,26 +769,27 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* 
                        plan->d_err, plan->num_sms, st);
     return e;
   }
-  cudaError_t e = plan->gen->ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, in, workspace, io,
+  cudaError_t e = gen.ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, in, workspace, io,
                                       plan->smem_ofdm, st);
   if (e == cudaSuccess)
-    e = plan->gen->tx_cont(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, workspace,
+    e = gen.tx_cont(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, workspace,
                            out, io, plan->smem_tx, st);
   return e;
 }
 
 cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* out, float2* workspace,
-                      cudaStream_t st, std::pair<int, int> c, int io) {
-  const size_t k = (size_t)c.first;
+                      cudaStream_t st, Choice c, int io) {
+  const size_t k = (size_t)c.split;
+  const FcGenKernels& gen = gen_for(plan, (long long)n_streams * plan->rx_nchunks[k], c.set);
   const float2* wave = (const float2*)in;
   float2* grid = (float2*)out;
-  if (plan->warp_path && !c.second && io == 0)
+  if (plan->warp_path && !c.generic && io == 0)
     return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams,
                                   wave, grid, st);
   if (plan->h.mode == FC_SYMBOL_SYNC)
-    return plan->gen->rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, in,
+    return gen.rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, in,
                               out, io, plan->smem_rx, st);
-  if (plan->tc_rx && !c.second && io == 0) {
+  if (plan->tc_rx && !c.generic && io == 0) {
     const int R = plan->h.g[0].R;
     cudaError_t e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_RX_FFT, n_streams, R, wave, nullptr, workspace,
                                  plan->d_err, plan->num_sms, st);
@@ -766,14 +799,14 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* 
     if (e == cudaSuccess)
       e = plan->tc_ofdm ? fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_OFDM_DEMOD, n_streams, plan->h.g[0].B,
                                        nullptr, grid, workspace, plan->d_err, plan->num_sms, st)
-                        : plan->gen->ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, grid,
+                        : gen.ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, grid,
                                                 0, plan->smem_ofdm, st);
     return e;
   }
-  cudaError_t e = plan->gen->rx_cont(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams,
+  cudaError_t e = gen.rx_cont(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams,
                                      in, workspace, io, plan->smem_rx, st);
   if (e == cudaSuccess)
-    e = plan->gen->ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, out, io, plan->smem_ofdm,
+    e = gen.ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, out, io, plan->smem_ofdm,
                               st);
   return e;
 }
@@ -788,7 +821,10 @@ int fc_internal_num_sms(const fc_plan* plan) { return plan ? plan->num_sms : 0; 
 
 int fc_internal_io(const fc_plan* plan) { return plan ? plan->io : 0; }
 
-const FcGenKernels& fc_internal_gen(const fc_plan* plan) { return *plan->gen; }
+// persistent launches fill every SM: the smallest CTAs that fit
+const FcGenKernels& fc_internal_gen(const fc_plan* plan) {
+  return *plan->gen[plan->gen_fits[2] ? 2 : (plan->gen_fits[1] ? 1 : 0)];
+}
 
 int fc_internal_frame(const fc_plan* plan, int dir, int n_streams, const void* in, void* out, void* workspace,
                       size_t workspace_bytes, void* stream, int io) {
@@ -796,7 +832,7 @@ int fc_internal_frame(const fc_plan* plan, int dir, int n_streams, const void* i
   if (rc != FC_OK || n_streams == 0) return rc;
   DeviceGuard dg(plan->device);
   if (!dg.ok) return fail(FC_ERR_CUDA, "cudaSetDevice failed");
-  const std::pair<int, int> c = choose(plan, n_streams, dir);
+  const Choice c = choose(plan, n_streams, dir);
   const cudaError_t e = dir == FC_TX ? launch_tx(plan, n_streams, in, out, (float2*)workspace, (cudaStream_t)stream, c, io)
                                      : launch_rx(plan, n_streams, in, out, (float2*)workspace, (cudaStream_t)stream, c, io);
   return e == cudaSuccess ? FC_OK : cuda_fail(e, dir == FC_TX ? "TX kernel launch" : "RX kernel launch");
@@ -805,9 +841,9 @@ int fc_internal_frame(const fc_plan* plan, int dir, int n_streams, const void* i
 bool fc_internal_sync_work(const fc_plan* plan, int dir, int n_streams, const void* in, void* out,
                            std::vector<FcWork>& work, size_t* smem) {
   if (!plan || plan->h.mode != FC_SYMBOL_SYNC || n_streams < 1) return false;
-  const std::pair<int, int> c = choose(plan, n_streams, dir);
-  if (plan->warp_path && !c.second) return false;       // the specialised kernels run this call
-  const size_t k = (size_t)c.first;
+  const Choice c = choose(plan, n_streams, dir);
+  if (plan->warp_path && !c.generic) return false;       // the specialised kernels run this call
+  const size_t k = (size_t)c.split;
   const FcChunk* chunks = dir == FC_TX ? plan->tx_chunks[k] : plan->rx_chunks[k];
   const int n_chunks = dir == FC_TX ? plan->tx_nchunks[k] : plan->rx_nchunks[k];
   for (int s = 0; s < n_streams; ++s)
@@ -854,6 +890,7 @@ int fc_plan_create(fc_plan** out, const fc_geometry* geometry, int32_t device) {
   std::call_once(g_smem_once[device], [&] {
     se = fc_gen_kernels_512().set_smem_limits(pl->smem_cap);
     if (se == cudaSuccess) se = fc_gen_kernels_256().set_smem_limits(pl->smem_cap);
+    if (se == cudaSuccess) se = fc_gen_kernels_128().set_smem_limits(pl->smem_cap);
     if (se == cudaSuccess) se = fc_set_warp_smem_limits();
     if (se == cudaSuccess) se = fc_set_tc_smem_limits();
   });
@@ -920,28 +957,34 @@ int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* strea
   cudaEvent_t ev[2] = {nullptr, nullptr};
   if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
   if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
-  std::pair<int, int> best[2] = {{0, 0}, {0, 0}};
+  Choice best[2];
   for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir) {
     float best_ms = 1e30f;
     const bool special = dir == FC_TX ? (plan->warp_path || plan->tc_tx) : (plan->warp_path || plan->tc_rx);
-    for (int generic = 0; generic <= (special ? 1 : 0) && e == cudaSuccess; ++generic) {
-      for (int k = 0; k < (int)plan->splits.size() && e == cudaSuccess; ++k) {
-        const std::pair<int, int> c{k, generic};
-        auto run = [&]() {
-          return dir == FC_TX ? launch_tx(plan, n_streams, grid, wave, ws, st, c, plan->io)
-                              : launch_rx(plan, n_streams, wave, grid, ws, st, c, plan->io);
-        };
-        for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = run();
-        if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = run();
-        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        if (e == cudaSuccess && ms < best_ms) {
-          best_ms = ms;
-          best[dir] = c;
-        }
+    // candidates: every split with the specialised kernels (where they apply), and every
+    // split on every generic-kernel set that fits
+    std::vector<Choice> cand;
+    for (int k = 0; k < (int)plan->splits.size(); ++k) {
+      if (special) cand.push_back(Choice{k, 0, -1});
+      for (int set = 0; set < 3; ++set)
+        if (plan->gen_fits[set]) cand.push_back(Choice{k, special ? 1 : 0, set});
+    }
+    for (const Choice& c : cand) {
+      if (e != cudaSuccess) break;
+      auto run = [&]() {
+        return dir == FC_TX ? launch_tx(plan, n_streams, grid, wave, ws, st, c, plan->io)
+                            : launch_rx(plan, n_streams, wave, grid, ws, st, c, plan->io);
+      };
+      for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = run();
+      if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = run();
+      if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best[dir] = c;
       }
     }
   }
@@ -964,7 +1007,7 @@ int fc_plan_set_choice(fc_plan* plan, int32_t n_streams, int32_t direction, int3
   const auto it = std::find(plan->splits.begin(), plan->splits.end(), (int)chunks_per_stream);
   if (it == plan->splits.end()) return fail(FC_ERR_INVALID, "chunks_per_stream is not one of the plan's splits");
   std::lock_guard<std::mutex> lock(plan->tune_mu);
-  plan->tuned[{n_streams, direction}] = {(int)(it - plan->splits.begin()), (int)generic_kernels};
+  plan->tuned[{n_streams, direction}] = Choice{(int)(it - plan->splits.begin()), (int)generic_kernels, -1};
   return FC_OK;
 }
 
@@ -972,10 +1015,10 @@ int fc_plan_choice(const fc_plan* plan, int32_t n_streams, int32_t direction, in
                    int32_t* generic_kernels) {
   if (!plan || (direction != FC_TX && direction != FC_RX) || n_streams < 1)
     return fail(FC_ERR_INVALID, "bad plan, direction or n_streams");
-  const std::pair<int, int> c = choose(plan, n_streams, direction);
-  if (chunks_per_stream) *chunks_per_stream = plan->splits[c.first];
+  const Choice c = choose(plan, n_streams, direction);
+  if (chunks_per_stream) *chunks_per_stream = plan->splits[c.split];
   const bool special = direction == FC_TX ? (plan->warp_path || plan->tc_tx) : (plan->warp_path || plan->tc_rx);
-  if (generic_kernels) *generic_kernels = (special && !c.second) ? 0 : 1;
+  if (generic_kernels) *generic_kernels = (special && !c.generic) ? 0 : 1;
   return FC_OK;
 }
 
