@@ -110,6 +110,8 @@ CONT_SMALL = [
     (64, 32, 64, 64, 40, 0, (16, 8, 8), -1),              # I = 1
     (128, 64, 64, 32, 20, -20, (8, 4, 4, 4, 8), -1),      # L_OFDM < L
     (64, 32, 32, 32, 20, 5, (4, 2, 2, 2), 32),            # longer lead pad
+    (64, 24, 32, 32, 20, -6, (8, 4, 4, 8), -1),           # lambda = 0.375
+    (64, 48, 32, 32, 20, 3, (8, 4, 4, 8), -1),            # lambda = 0.75
 ]
 
 
@@ -160,6 +162,13 @@ def test_single_symbol_and_full_band(torch_cuda):
 # ---------------------------------------------------------------------------
 # the named 5G NR workloads
 # ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("mode", [fo.CONTINUOUS, fo.SYMBOL_SYNC])
+def test_nr10mhz_52prb(torch_cuda, mode):
+    """The wide-band scenario of the paper's EVM figures (10 MHz, N = 1024, 52 PRB,
+    L = 768), continuous and symbol-synchronized, on the generic kernels."""
+    check_geometry(torch_cuda, wl.config_nr10mhz_52prb(mode), 3, 17)
+
 
 def test_nr5mhz_single_subband_ols(torch_cuda):
     check_geometry(torch_cuda, wl.config_single_5mhz(), 3, wl.default_seed(1))

@@ -166,6 +166,20 @@ def config_100mhz(n_slots: int = 10) -> Geometry:
                     qam_order=64)
 
 
+def config_nr10mhz_52prb(mode: int = CONTINUOUS) -> Geometry:
+    """10 MHz NR at 15.36 Msps, N=1024, 15 kHz SCS, one subband of 52 PRB (624 SC) with
+    8 raised-cosine transition bins per side, one slot of 14 symbols, 16-QAM: the
+    wide-band scenario of the paper's EVM figures (continuous or symbol-synchronized
+    processing on both sides). The paper does not state its short transform; L=768
+    (I = 4/3, the smallest 3 x 2^k above 624 + 16 bins) is this workload's choice.
+    OLA TX, OLS RX."""
+    g = Group(n_long=1024, n_overlap=512, n_cp=nr_normal_cp(1024, 15, 14))
+    sb = Subband(l_short=768, l_ofdm=768, n_active=624, centre_bin=0, group=0,
+                 weights=rc_transition_weights(768, 624, 8))
+    tag = "cont" if mode == CONTINUOUS else "symsync"
+    return Geometry(mode, OLA, OLS, (g,), (sb,), name=f"nr10mhz_15khz_52prb_L768_N1024_{tag}", qam_order=16)
+
+
 # NR sampling rates with power-of-two FFT sizes per channel bandwidth (MHz -> Msps)
 NR_RATE_MSPS = {5: 7.68, 10: 15.36, 20: 30.72, 50: 61.44, 100: 122.88}
 # (bandwidth MHz, SCS kHz) pairs NR defines: no 100 MHz at 15 kHz, no 5 MHz at 60 kHz
@@ -251,6 +265,7 @@ NAMED = {
     "single5": config_single_5mhz,
     "mixed20": config_mixed_20mhz,
     "nr100": config_100mhz,
+    "nr10_52prb": config_nr10mhz_52prb,
 }
 
 
