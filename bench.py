@@ -634,6 +634,34 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     d2h = (wave.numel() + est.numel()) * 8
     e2e_how = (f"fc_tx_synthesize_host + fc_rx_analyze_host side by side, {E2E_PIPES} pipelines per direction, "
                f"{chunk} streams per chunk, {E2E_DEPTH} slots each")
+    # the host link's bound for these bytes: plain copies of the same sizes, both
+    # directions at once (each direction on its own CUDA stream), no kernels
+    d_in = torch.empty(h2d // 4, dtype=torch.float32, device=dev)
+    d_out = torch.empty(d2h // 4, dtype=torch.float32, device=dev)
+    h_in = torch.empty(h2d // 4, dtype=torch.float32).pin_memory()
+    h_out = torch.empty(d2h // 4, dtype=torch.float32).pin_memory()
+    c_up, c_down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def copies():
+        c_up.wait_stream(st)
+        c_down.wait_stream(st)
+        with torch.cuda.stream(c_up):
+            d_in.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(c_down):
+            h_out.copy_(d_out, non_blocking=True)
+        st.wait_stream(c_up)
+        st.wait_stream(c_down)
+
+    copies()
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    for _ in range(3):
+        copies()
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    link_ms = e0.elapsed_time(e1) / 3
+    link_bound = 2 * nominal * S / link_ms / 1e3
+    del d_in, d_out, h_in, h_out
 
     if rank != 0:
         return
@@ -743,7 +771,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
                             % (grid.numel() * 8 / 1e6, wave.numel() * 8 / 1e6)},
            "roofline": roofline, "cpu_baseline": cpu,
            "e2e": {"value": round(e2e_value, 2), "unit": "Msamples/s", "h2d_bytes_per_step": h2d,
-                   "d2h_bytes_per_step": d2h, "path": e2e_how},
+                   "d2h_bytes_per_step": d2h, "path": e2e_how,
+                   "host_link_bound": {"value": round(link_bound, 2), "unit": "Msamples/s",
+                                       "ms_per_step": round(link_ms, 4), "frac": round(e2e_value / link_bound, 3),
+                                       "how": "the step's H2D and D2H bytes as plain pinned copies, both "
+                                              "directions at once, no kernels"}},
            "latency_1stream_ms": {"p50": round(lat[len(lat) // 2], 4), "p99": round(lat[int(0.99 * len(lat))], 4),
                                   "slot_budget_ms": 1.0},
            "accuracy": accuracy,
