@@ -144,7 +144,6 @@ const FcGenKernels& fc_gen_kernels_512();
 const FcGenKernels& fc_gen_kernels_256();
 const FcGenKernels& fc_gen_kernels_128();
 
-// warp-specialised symbol-synchronized kernels (fc_warp.cu); jobs are grouped per chunk
 // tensor-core FC passes (continuous, one subband, L = N = 4096)
 #define FC_TC_TX_FFT 0
 #define FC_TC_TX_IFFT 1
@@ -157,10 +156,13 @@ cudaError_t fc_launch_tc(const FcPlanDev* dP, const unsigned char* dft64, int pa
 cudaError_t fc_set_tc_smem_limits();
 void fc_tc_dft64_image(unsigned char* out);
 size_t fc_tc_dft64_image_bytes();
-cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                                   int n_streams, int frame_len, const float2* grid, float2* wave, cudaStream_t st);
-cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                                   int n_streams, const float2* wave, float2* grid, cudaStream_t st);
+// one-warp-per-symbol symbol-synchronized kernels (fc_warp.cu): the job-major item list
+// of all streams (jobs: one stream's jobs in cost order) dealt to the resident CTAs; TX
+// zeroes the waveform first
+cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, int frame_len,
+                                   const float2* grid, float2* wave, int num_sms, cudaStream_t st);
+cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams,
+                                   const float2* wave, float2* grid, int num_sms, cudaStream_t st);
 cudaError_t fc_set_warp_smem_limits();
 
 // helpers for entry points defined outside fc_plan.cu

@@ -117,9 +117,7 @@ struct fc_plan {
   bool tc_ofdm = false;                     // and the OFDM (I)DFT too (L_OFDM = 4096)
   const unsigned char* d_dft64 = nullptr;   // DFT-64 B operand images (hi, lo)
   int* d_err = nullptr;                     // device error word of the tensor-core kernels
-  FcJob* d_wjobs = nullptr;                 // jobs regrouped per chunk for the warp kernels
-  std::vector<const FcChunk*> w_chunks;
-  std::vector<int> w_nchunks;
+  FcJob* d_wjobs = nullptr;                 // one stream's jobs in cost order (warp kernels)
   size_t smem_tx = 0, smem_rx = 0, smem_ofdm = 0;
   int syms_per_stream = 0;
   fc_sizes sizes{};
@@ -425,24 +423,14 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     const bool shape = (o.L == 1024 && gh[g].N == 2048) || (o.L == 512 && gh[g].N == 1024);
     if (!shape) warp_ok = false;
   }
-  std::vector<size_t> off_wjobs_k, off_wch;
   size_t off_wjobs = 0;
   if (warp_ok) {
-    // most expensive jobs first (N = 2048 before N = 1024), dealt round-robin to the chunks
+    // one stream's jobs, most expensive first (N = 2048 before N = 1024): the warp
+    // kernels deal the job-major list of all streams to their CTAs in this order
     std::vector<FcJob> by_cost = jobs;
     std::stable_sort(by_cost.begin(), by_cost.end(),
                      [&](const FcJob& a, const FcJob& b) { return gh[a.group].N > gh[b.group].N; });
-    std::vector<FcJob> wj;
-    for (int K : splits) {
-      std::vector<FcChunk> ch;
-      for (int c = 0; c < K; ++c) {
-        const int j0 = (int)wj.size();
-        for (int j = c; j < n_jobs; j += K) wj.push_back(by_cost[j]);
-        ch.push_back(FcChunk{j0, (int)wj.size(), 0, 0});
-      }
-      off_wch.push_back(blob.add_vec(ch));
-    }
-    off_wjobs = blob.add_vec(wj);
+    off_wjobs = blob.add_vec(by_cost);
   }
 
   // ---- buffers and shared memory -------------------------------------------
@@ -664,13 +652,7 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     pl->d_dft64 = base + off_dft;
     pl->d_err = reinterpret_cast<int*>(base + off_err);
   }
-  if (warp_ok) {
-    pl->d_wjobs = reinterpret_cast<FcJob*>(base + off_wjobs);
-    for (size_t i = 0; i < splits.size(); ++i) {
-      pl->w_chunks.push_back(reinterpret_cast<const FcChunk*>(base + off_wch[i]));
-      pl->w_nchunks.push_back(splits[i]);
-    }
-  }
+  if (warp_ok) pl->d_wjobs = reinterpret_cast<FcJob*>(base + off_wjobs);
   return FC_OK;
 }
 
@@ -747,8 +729,8 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* 
   float2* wave = (float2*)out;
   // float4 reductions of the warp kernel need a 16-byte aligned waveform
   if (plan->warp_path && !c.generic && io == 0 && ((uintptr_t)wave & 15) == 0)
-    return fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams,
-                                  plan->h.frame_len, grid, wave, st);
+    return fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, plan->h.frame_len, grid, wave,
+                                  plan->num_sms, st);
   if (plan->h.mode == FC_SYMBOL_SYNC)
     return gen.tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, in,
                               out, io, plan->smem_tx, st);
@@ -784,8 +766,8 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* 
   const float2* wave = (const float2*)in;
   float2* grid = (float2*)out;
   if (plan->warp_path && !c.generic && io == 0)
-    return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->w_chunks[k], plan->w_nchunks[k], n_streams,
-                                  wave, grid, st);
+    return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, wave, grid, plan->num_sms,
+                                  st);
   if (plan->h.mode == FC_SYMBOL_SYNC)
     return gen.rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, in,
                               out, io, plan->smem_rx, st);
@@ -965,7 +947,9 @@ int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* strea
     // split on every generic-kernel set that fits
     std::vector<Choice> cand;
     for (int k = 0; k < (int)plan->splits.size(); ++k) {
-      if (special) cand.push_back(Choice{k, 0, -1});
+      // the one-warp-per-symbol kernels deal all streams' jobs to the GPU whatever the
+      // split; the tensor-core passes take no split either
+      if (special && k == 0) cand.push_back(Choice{k, 0, -1});
       for (int set = 0; set < 3; ++set)
         if (plan->gen_fits[set]) cand.push_back(Choice{k, special ? 1 : 0, set});
     }

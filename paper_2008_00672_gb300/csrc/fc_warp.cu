@@ -15,9 +15,11 @@
 //   * TX overlap-add (blocks of a symbol, neighbouring symbols, numerology
 //     groups; eq:multi-symb) is done with vector reductions into the zeroed
 //     output waveform, so warps never wait for each other.
-// Every job is a short program of stages "prepare -> forward FFT -> consume";
-// inverse transforms are conj(FFT(conj(x))). The whole kernel therefore holds a
-// single copy of the unrolled FFT, which keeps the hot code in the instruction cache.
+// A TX job is a short program of stages "prepare -> forward FFT -> consume" (inverse
+// transforms as conj(FFT(conj(x)))), so the TX kernel holds a single copy of the
+// unrolled FFT; RX jobs keep direction-specialised transforms in rolled loops (one copy
+// of each per job shape). Both kernels take the job-major list of all streams' jobs,
+// dealt to as many CTAs as the GPU holds at once.
 #include "fc_device.cuh"
 #include "fc_internal.cuh"
 
@@ -656,105 +658,120 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
 
 
 // ---------------------------------------------------------------------------
-// kernels: one CTA per (stream, chunk), warps take jobs from a shared counter
+// kernels: the job-major item list of all streams (job j of every stream, one stream's
+// jobs in cost order) dealt to the resident CTAs statically (CTA c takes items c, c + G,
+// c + 2G, ...); a CTA's warps take its items through a shared counter. Every CTA gets the
+// same mix of job shapes and the launch has no partial last wave.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_TX_MIN_BLOCKS)
-k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
-               int n_chunks, int zero_output, const float2* __restrict__ grid, float2* __restrict__ wave) {
-  __shared__ FcPlanDev P;
-  __shared__ int next_job;
-  extern __shared__ __align__(16) float2 wscr[];
-  load_plan_w(P, gP);
-  const int stream = blockIdx.x / n_chunks;
-  const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
-  if (threadIdx.x == 0) next_job = ch.j0;
-  __syncthreads();                                  // the plan copy is complete before any use
-  const float2* gsrc = grid + (size_t)stream * P.grid_len;
-  float2* wdst = wave + (size_t)stream * P.frame_len;
-  if (zero_output) {   // the CTA owns the whole stream: clear it before the reductions
-    for (int i = threadIdx.x; i < P.frame_len; i += blockDim.x) wdst[i] = czero();
-    __syncthreads();
-  }
-  const int lane = threadIdx.x & 31;
-  float2* scr = wscr + (threadIdx.x >> 5) * kScratch;
-  float2* map = scr + kTrans;
-  while (true) {
-    int j = 0;
-    if (lane == 0) j = atomicAdd(&next_job, 1);
-    j = __shfl_sync(0xffffffffu, j, 0);
-    if (j >= ch.j1) break;
-    const FcJob jb = jobs[j];
-    const FcGroupDev& G = P.g[jb.group];
-    tx_job(P, G, P.s[G.first_sub], jb, gsrc, wdst, scr, map, lane);
-  }
+// RX jobs of different streams share nothing, so no item waits for another.
+__device__ __forceinline__ void rx_dispatch(const FcPlanDev& P, const FcJob& jb, const float2* __restrict__ src,
+                                            float2* __restrict__ gdst, float2* scr, float2* map, int lane) {
+  const FcGroupDev& G = P.g[jb.group];
+  const FcSubDev& S = P.s[G.first_sub];
+  if (S.L == 1024 && (P.flags & FC_FLAG_REDUCED_RX) && P.scheme_rx == FC_OLS)
+    rx_job_1024_reduced(P, G, S, jb, src, gdst, scr, map, lane);
+  else if (S.L == 1024 && P.scheme_rx == FC_OLA) rx_job_1024<true>(P, G, S, jb, src, gdst, scr, map, lane);
+  else if (S.L == 1024) rx_job_1024<false>(P, G, S, jb, src, gdst, scr, map, lane);
+  else rx_job_512(P, G, S, jb, src, gdst, scr, map, lane);
 }
 
 __global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_RX_MIN_BLOCKS)
-k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, const FcChunk* __restrict__ chunks,
-               int n_chunks, const float2* __restrict__ wave, float2* __restrict__ grid) {
+k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, int n_jobs, int n_streams,
+                     const float2* __restrict__ wave, float2* __restrict__ grid) {
   __shared__ FcPlanDev P;
-  __shared__ int next_job;
+  __shared__ int next_item;
   extern __shared__ __align__(16) float2 wscr[];
   load_plan_w(P, gP);
-  const int stream = blockIdx.x / n_chunks;
-  const FcChunk ch = chunks[blockIdx.x - stream * n_chunks];
-  if (threadIdx.x == 0) next_job = ch.j0;
+  if (threadIdx.x == 0) next_item = 0;
   __syncthreads();                                  // the plan copy is complete before any use
-  const float2* src = wave + (size_t)stream * P.frame_len;
-  float2* gdst = grid + (size_t)stream * P.grid_len;
+  const long long total = (long long)n_jobs * n_streams;
   const int lane = threadIdx.x & 31;
   float2* scr = wscr + (threadIdx.x >> 5) * kScratch;
   float2* map = scr + kTrans;
   while (true) {
-    int j = 0;
-    if (lane == 0) j = atomicAdd(&next_job, 1);
-    j = __shfl_sync(0xffffffffu, j, 0);
-    if (j >= ch.j1) break;
-    const FcJob jb = jobs[j];
-    const FcGroupDev& G = P.g[jb.group];
-    const FcSubDev& S = P.s[G.first_sub];
-    if (S.L == 1024 && (P.flags & FC_FLAG_REDUCED_RX) && P.scheme_rx == FC_OLS)
-      rx_job_1024_reduced(P, G, S, jb, src, gdst, scr, map, lane);
-    else if (S.L == 1024 && P.scheme_rx == FC_OLA) rx_job_1024<true>(P, G, S, jb, src, gdst, scr, map, lane);
-    else if (S.L == 1024) rx_job_1024<false>(P, G, S, jb, src, gdst, scr, map, lane);
-    else rx_job_512(P, G, S, jb, src, gdst, scr, map, lane);
+    int u = 0;
+    if (lane == 0) u = atomicAdd(&next_item, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    const long long item = blockIdx.x + (long long)u * gridDim.x;
+    if (item >= total) break;
+    const int j = (int)(item / n_streams);             // job-major: job j of every stream
+    const int stream = (int)(item - (long long)j * n_streams);
+    rx_dispatch(P, jobs[j], wave + (size_t)stream * P.frame_len, grid + (size_t)stream * P.grid_len, scr, map, lane);
   }
 }
 
-
-__global__ void k_zero(float4* __restrict__ p, size_t n4) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x)
-    p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+// TX: jobs of one stream run on several CTAs and reduce into the same waveform, which
+// is zeroed beforehand.
+__global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_TX_MIN_BLOCKS)
+k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, int n_jobs, int n_streams,
+                     const float2* __restrict__ grid, float2* __restrict__ wave) {
+  __shared__ FcPlanDev P;
+  __shared__ int next_item;
+  extern __shared__ __align__(16) float2 wscr[];
+  load_plan_w(P, gP);
+  if (threadIdx.x == 0) next_item = 0;
+  __syncthreads();                                  // the plan copy is complete before any use
+  const long long total = (long long)n_jobs * n_streams;
+  const int lane = threadIdx.x & 31;
+  float2* scr = wscr + (threadIdx.x >> 5) * kScratch;
+  float2* map = scr + kTrans;
+  while (true) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(&next_item, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    const long long item = blockIdx.x + (long long)u * gridDim.x;
+    if (item >= total) break;
+    const int j = (int)(item / n_streams);             // job-major: job j of every stream
+    const int stream = (int)(item - (long long)j * n_streams);
+    const FcJob jb = jobs[j];
+    const FcGroupDev& G = P.g[jb.group];
+    tx_job(P, G, P.s[G.first_sub], jb, grid + (size_t)stream * P.grid_len, wave + (size_t)stream * P.frame_len, scr,
+           map, lane);
+  }
 }
+
 
 }  // namespace
 
 size_t fc_warp_smem_bytes() { return (size_t)kWarps * kScratch * sizeof(float2); }
 
-cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                                   int n_streams, int frame_len, const float2* grid, float2* wave, cudaStream_t st) {
-  int zero_in_kernel = n_chunks == 1;
-  if (!zero_in_kernel) {
-    const size_t n = (size_t)n_streams * frame_len;     // frame_len is even for this path
-    k_zero<<<1024, 256, 0, st>>>(reinterpret_cast<float4*>(wave), n / 2);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  k_tx_sync_warp<<<dim3((unsigned)(n_streams * n_chunks)), FC_WARP_THREADS, fc_warp_smem_bytes(), st>>>(
-      dP, jobs, chunks, n_chunks, zero_in_kernel, grid, wave);
+cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, int frame_len,
+                                   const float2* grid, float2* wave, int num_sms, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(wave, 0, (size_t)n_streams * frame_len * sizeof(float2), st);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tx_sync_warp, FC_WARP_THREADS,
+                                                    fc_warp_smem_bytes());
+  if (e != cudaSuccess) return e;
+  const long long total = (long long)n_jobs * n_streams;
+  long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
+  if (ctas > total) ctas = total;
+  if (ctas < 1) return cudaSuccess;
+  k_tx_sync_warp<<<dim3((unsigned)ctas), FC_WARP_THREADS, fc_warp_smem_bytes(), st>>>(dP, jobs, n_jobs, n_streams,
+                                                                                   grid, wave);
   return cudaGetLastError();
 }
 
-cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, const FcChunk* chunks, int n_chunks,
-                                   int n_streams, const float2* wave, float2* grid, cudaStream_t st) {
-  k_rx_sync_warp<<<dim3((unsigned)(n_streams * n_chunks)), FC_WARP_THREADS, fc_warp_smem_bytes(), st>>>(
-      dP, jobs, chunks, n_chunks, wave, grid);
+cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams,
+                                   const float2* wave, float2* grid, int num_sms, cudaStream_t st) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rx_sync_warp, FC_WARP_THREADS,
+                                                                fc_warp_smem_bytes());
+  if (e != cudaSuccess) return e;
+  const long long total = (long long)n_jobs * n_streams;
+  long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
+  if (ctas > total) ctas = total;
+  if (ctas < 1) return cudaSuccess;
+  k_rx_sync_warp<<<dim3((unsigned)ctas), FC_WARP_THREADS, fc_warp_smem_bytes(), st>>>(dP, jobs, n_jobs, n_streams,
+                                                                                   wave, grid);
   return cudaGetLastError();
 }
 
 cudaError_t fc_set_warp_smem_limits() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_tx_sync_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fc_warp_smem_bytes())))
+  if ((e = cudaFuncSetAttribute(k_tx_sync_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)fc_warp_smem_bytes())))
     return e;
-  return cudaFuncSetAttribute(k_rx_sync_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fc_warp_smem_bytes());
+  return cudaFuncSetAttribute(k_rx_sync_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)fc_warp_smem_bytes());
 }

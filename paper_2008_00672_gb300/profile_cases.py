@@ -10,8 +10,8 @@ can pick launches of a known shape. Inputs are seeded QAM grids; the RX input is
 TX output (its values do not change the kernels' work).
 
 Cases:
-  warp20     20 MHz mixed numerology, symbol-synchronized (one-warp-per-symbol kernels;
-             default TX 1 chunk per stream, RX 2 chunks per stream)
+  warp20     20 MHz mixed numerology, symbol-synchronized (one-warp-per-symbol kernels,
+             which deal all streams' jobs to the resident CTAs whatever the chunk count)
   generic20  the same geometry on the generic shared-memory kernels
   tensor100  100 MHz / 273 PRB carrier, 10 slots, on the tensor-core passes
   fp32_100   the same carrier on the FP32 shared-memory kernels

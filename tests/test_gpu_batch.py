@@ -134,3 +134,40 @@ def test_set_choice_round_trip_and_validation(torch_cuda):
     with pytest.raises(FcError):
         plan.set_choice(100, FC_TX, 3, 0)          # not a split the plan has
     plan.close()
+
+
+@pytest.mark.parametrize("name", ["nr5_cont", "mixed20_generic"])
+def test_cta_sizes_give_identical_results(torch_cuda, name):
+    """The generic kernels come in 512-, 256- and 128-thread CTAs, picked per call by the
+    number of CTAs it launches (and the persistent queues take the smallest that fits).
+    Every element sees the same operations in the same order whatever the CTA size, so a
+    stream's result is bit-identical: alone (one stream, 256-thread CTAs), among 1024
+    streams (128-thread CTAs where the plan fits them) and in a persistent batch."""
+    import dataclasses
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import FC_RX, FC_TX, Batch, Plan
+    geom = wl.config_single_5mhz() if name == "nr5_cont" else \
+        dataclasses.replace(wl.config_mixed_20mhz(), flags=1)
+    plan = Plan(geom)
+    S = 1024
+    base = c64(wl.qam_grid(geom, 4, 700))
+    grid = torch.from_numpy(base).cuda().repeat(S // 4, 1).contiguous()
+    wave = torch.empty((S, plan.wave_len), dtype=torch.complex64, device="cuda")
+    est = torch.empty_like(grid)
+    plan.tx_synthesize(grid, wave)
+    plan.rx_analyze(wave, est)
+    w1 = torch.empty((1, plan.wave_len), dtype=torch.complex64, device="cuda")
+    e1 = torch.empty((1, plan.grid_len), dtype=torch.complex64, device="cuda")
+    plan.tx_synthesize(grid[:1], w1)
+    plan.rx_analyze(wave[:1], e1)
+    torch.cuda.synchronize()
+    assert torch.equal(w1[0], wave[0]) and torch.equal(e1[0], est[0])
+    if geom.mode == 1:                      # symbol-sync: the persistent queues
+        wb = torch.empty((2, plan.wave_len), dtype=torch.complex64, device="cuda")
+        eb = torch.empty((2, plan.grid_len), dtype=torch.complex64, device="cuda")
+        b = Batch([(plan, FC_TX, grid[:2], wb), (plan, FC_RX, wave[:2], eb)], n_lanes=2, persistent=True)
+        b.launch()
+        torch.cuda.synchronize()
+        assert torch.equal(wb, wave[:2]) and torch.equal(eb, est[:2])
+        b.close()
+    plan.close()
