@@ -338,8 +338,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     else if (tid == 0)
       tc_prefetch_bulk<PASS>(stg, g_ws, K, blockIdx.x, total, &stg_bar);
   }
-  for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    // ---- prologue: A1[64 t + n2][(n1, re/im)] = x_t[64 n1 + n2] from the staged input ----
+  // Stage `tile` into A from its staged input (waiting for the copy), then start
+  // fetching tile + gridDim.x into the staging buffer. False when a bounded wait gave up.
+  auto stage = [&](int tile) -> bool {
     if (!tc_bulk<PASS>()) {
       asm volatile("cp.async.wait_all;" ::: "memory");
     } else {
@@ -350,9 +351,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
       stg_phase ^= 1;
     }
     __syncthreads();
-    if (abort_flag) break;
-    // each thread converts x_t[64 n1 + n2] for four consecutive n1 = 4 a .. 4 a + 3 of one
-    // n2: reads coalesced across the warp (consecutive n2), one 16-byte store per hi/lo
+    if (abort_flag) return false;
+    // A1[64 t + n2][(n1, re/im)] = x_t[64 n1 + n2]: each thread converts x_t[64 n1 + n2]
+    // for four consecutive n1 = 4 a .. 4 a + 3 of one n2: reads coalesced across the warp
+    // (consecutive n2), one 16-byte store per hi/lo
 #pragma unroll
     for (int it = 0; it < 2 * kN / 4 / kThreads; ++it) {
       const int e4 = tid + kThreads * it;
@@ -371,18 +373,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     }
     fence_async_smem();
     __syncthreads();
-    // the staging buffer is free: fetch the next tile while this one is transformed
+    // the staging buffer is free: fetch the tile after this one
     if (tile + (int)gridDim.x < n_tiles) {
       if (!tc_bulk<PASS>())
         tc_prefetch<PASS>(stg, g_in, g_ws, K, tile + gridDim.x, total, tid);
       else if (tid == 0)
         tc_prefetch_bulk<PASS>(stg, g_ws, K, tile + gridDim.x, total, &stg_bar);
     }
+    return true;
+  };
+  // one thread issues A x B^T into TMEM columns [col, col + 128)
+  auto mma = [&](uint32_t col) {
     if (tid == 0) {
       tc_fence_after();
-      issue_mmas(tbase, sa_hi, sa_lo, sb_hi, sb_lo);
+      issue_mmas(tbase + col, sa_hi, sa_lo, sb_hi, sb_lo);
       mma_commit(&bar);
     }
+  };
+  // wait for the last issued GEMM; false when the bounded wait gave up
+  auto wait_mma = [&]() -> bool {
     if (!mbar_wait(&bar, phase)) {
       atomicExch(args.err, 1);
       abort_flag = 1;
@@ -390,7 +399,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     phase ^= 1;
     tc_fence_after();
     __syncthreads();
-    if (abort_flag) break;
+    return !abort_flag;
+  };
+
+  // Per tile: GEMM 1 into columns [0, 128), twiddles back into A, GEMM 2 into columns
+  // [128, 256), then the next tile is staged into A and its GEMM 1 issued before this
+  // tile's epilogue reads columns [128, 256): the epilogue overlaps the next GEMM 1.
+  bool ok = blockIdx.x < n_tiles && stage(blockIdx.x);
+  if (ok) mma(0);
+  for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+    if (!wait_mma()) break;
     // ---- twiddles; A3[64 t + k1][(n2, re/im)] = A1'[64 t + n2][k1] W4096^(n2 k1) ----------
     // thread: row (t = rt, n2 = rlo), k1 in [16 h, 16 h + 16)
     {
@@ -407,19 +425,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-      issue_mmas(tbase + 128, sa_hi, sa_lo, sb_hi, sb_lo);
-      mma_commit(&bar);
+    mma(128);
+    if (!wait_mma()) break;
+    const int next = tile + (int)gridDim.x;
+    if (next < n_tiles) {
+      if (!stage(next)) break;
+      mma(0);
     }
-    if (!mbar_wait(&bar, phase)) {
-      atomicExch(args.err, 1);
-      abort_flag = 1;
-    }
-    phase ^= 1;
-    tc_fence_after();
-    __syncthreads();
-    if (abort_flag) break;
     // ---- epilogue: thread row (t = rt, k1 = rlo), k2 in [16 h, 16 h + 16) ----------------
     const int g = 2 * tile + rt;
     if (g < total) {
@@ -434,7 +446,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
       }
     }
     tc_fence_before();
-    __syncthreads();                       // A and the TMEM columns are free for the next tile
+    __syncthreads();                       // TMEM columns [128, 256) are free for the next GEMM 2
   }
   tc_fence_before();
   __syncthreads();
