@@ -56,7 +56,7 @@ struct FcGroupDev {
 };
 
 struct FcSubDev {
-  int L, Lofdm, Lact, c, group;
+  int L, Lofdm, Lact, c, group;   // c: centre bin c_m reduced to [0, N)
   int L_S, L_L, L_T;
   int S_L;            // continuous lead pad (low rate)
   int n_low;          // continuous: low-rate stream length

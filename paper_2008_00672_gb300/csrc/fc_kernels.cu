@@ -370,8 +370,8 @@ __device__ __forceinline__ void tx_map(const FcSubDev& S, int N, const float2* Z
     const int p = S.p_lo + idx - r * cnt;
     int k = p - h;
     if (k < 0) k += L;
-    int q = (S.c + p - h) % N;
-    if (q < 0) q += N;
+    int q = S.c + p - h;                               // c in [0, N), |p - h| <= L/2 <= N/2
+    q += q < 0 ? N : (q >= N ? -N : 0);
     const float w = __ldg(S.dtx + p);
     const float2 v = cmul(Z[sp(r * L + k)], r ? ph1 : ph0);
     float2& y = Y[sp(r * N + q)];
@@ -392,8 +392,8 @@ __device__ __forceinline__ void rx_gather(const FcSubDev& S, int N, const float2
     if (p >= L) p -= L;
     float2 v = make_float2(0.f, 0.f);
     if (r < nblk && p >= S.p_lo && p < S.p_hi) {
-      int q = (S.c + p - h) % N;
-      if (q < 0) q += N;
+      int q = S.c + p - h;
+      q += q < 0 ? N : (q >= N ? -N : 0);
       const float2 ph = r ? ph1 : ph0;
       const float2 y = Y[sp(r * N + q)];
       const float w = __ldg(S.drx + p);

@@ -615,7 +615,10 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   for (int m = 0; m < M; ++m) {
     const SubHost& o = sh[m];
     FcSubDev& d = P.s[slot_of[m]];
-    d.L = o.L; d.Lofdm = o.Lo; d.Lact = o.Lact; d.c = o.c; d.group = o.g;
+    // the kernels use c_m modulo N only: keep it in [0, N) so that a bin index c_m + p -
+    // floor(L/2) needs one correction, not a division
+    const int Ng = gh[o.g].N;
+    d.L = o.L; d.Lofdm = o.Lo; d.Lact = o.Lact; d.c = ((o.c % Ng) + Ng) % Ng; d.group = o.g;
     d.L_S = o.L_S; d.L_L = o.L_L; d.L_T = o.L_T; d.S_L = o.S_L; d.n_low = o.n_low;
     d.p_lo = plo[m]; d.p_hi = phi[m];
     d.size_L = s_sizeL[m]; d.size_O = s_sizeO[m];
