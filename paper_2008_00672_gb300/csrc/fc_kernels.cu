@@ -229,12 +229,23 @@ __device__ __forceinline__ void pass_load(float2 (&v)[FC_MAX_ELEMS_PER_THREAD], 
 #pragma unroll
       for (int j = 0; j < R; ++j) w[j] = a[sp(s + j * nb)];
       if (p > 1) {
+        // W_{pR}^{j k} is read from the table for j a power of two and formed as the
+        // product W^{(j - h) k} W^{h k} (h the highest power of two in j) otherwise:
+        // 4 table reads instead of 15 for radix 16, at most three roundings more.
+        float2 t[R];
 #pragma unroll
         for (int j = 1; j < R; ++j) {
-          float2 t = __ldg(tw + j * k * twstep);
-          if (INV) t.y = -t.y;
-          w[j] = cmul(w[j], t);
+          if ((j & (j - 1)) == 0) {
+            t[j] = __ldg(tw + j * k * twstep);
+            if (INV) t[j].y = -t[j].y;
+          } else {
+            int h = 1;
+            while (2 * h <= j) h *= 2;
+            t[j] = cmul(t[j - h], t[h]);
+          }
         }
+#pragma unroll
+        for (int j = 1; j < R; ++j) w[j] = cmul(w[j], t[j]);
       }
       Dft<R, INV>::run(w);
 #pragma unroll
