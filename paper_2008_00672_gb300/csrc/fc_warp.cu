@@ -663,6 +663,11 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
 // c + 2G, ...); a CTA's warps take its items through a shared counter. Every CTA gets the
 // same mix of job shapes and the launch has no partial last wave.
 // ---------------------------------------------------------------------------
+// Ask L2 for [p, p + n): one 128-byte line per lane and step (p + n within the buffer).
+__device__ __forceinline__ void prefetch_l2(const float2* p, int n, int lane) {
+  for (int i = 16 * lane; i < n; i += 16 * 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + i));
+}
+
 // RX jobs of different streams share nothing, so no item waits for another.
 __device__ __forceinline__ void rx_dispatch(const FcPlanDev& P, const FcJob& jb, const float2* __restrict__ src,
                                             float2* __restrict__ gdst, float2* scr, float2* map, int lane) {
@@ -696,6 +701,15 @@ k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     if (item >= total) break;
     const int j = (int)(item / n_streams);             // job-major: job j of every stream
     const int stream = (int)(item - (long long)j * n_streams);
+    // the input of the CTA's next item (another stream, usually not in L2): both blocks
+    // of the symbol, N + N/2 samples from its start, all of which that job reads
+    const long long nx = item + gridDim.x;
+    if (nx < total) {
+      const int jn = (int)(nx / n_streams);
+      const FcJob jbn = jobs[jn];
+      const int Nn = P.g[jbn.group].N;
+      prefetch_l2(wave + (size_t)(nx - (long long)jn * n_streams) * P.frame_len + jbn.start, Nn + Nn / 2, lane);
+    }
     rx_dispatch(P, jobs[j], wave + (size_t)stream * P.frame_len, grid + (size_t)stream * P.grid_len, scr, map, lane);
   }
 }
@@ -723,6 +737,16 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     if (item >= total) break;
     const int j = (int)(item / n_streams);             // job-major: job j of every stream
     const int stream = (int)(item - (long long)j * n_streams);
+    // the grid row of the CTA's next item (another stream, usually not in L2)
+    const long long nx = item + gridDim.x;
+    if (nx < total) {
+      const int jn = (int)(nx / n_streams);
+      const FcJob jbn = jobs[jn];
+      const FcSubDev& Sn = P.s[P.g[jbn.group].first_sub];
+      prefetch_l2(grid + (size_t)(nx - (long long)jn * n_streams) * P.grid_len + Sn.grid_off +
+                      (long long)jbn.index * Sn.Lact,
+                  Sn.Lact, lane);
+    }
     const FcJob jb = jobs[j];
     const FcGroupDev& G = P.g[jb.group];
     tx_job(P, G, P.s[G.first_sub], jb, grid + (size_t)stream * P.grid_len, wave + (size_t)stream * P.frame_len, scr,
