@@ -182,10 +182,18 @@ __device__ __forceinline__ void cp_async8(float2* dst, const float2* src, const 
 
 // The inverse block passes read whole spectrum rows (4096 contiguous samples, 16-byte
 // aligned: workspace rows start at even complex offsets): one bulk copy per row,
-// completing on an mbarrier. The other passes gather or window: per-element copies.
+// completing on an mbarrier. So does the RX block DFT when the received frame keeps its
+// blocks 16-byte aligned (tc_rx_rows_aligned). The other passes gather or window:
+// per-element copies.
 template <int PASS>
 constexpr bool tc_bulk() {
   return PASS == FC_TC_TX_IFFT || PASS == FC_TC_RX_IFFT;
+}
+
+// block r of stream s starts at in + s frame_len + offset + r N_S: 16-byte aligned for
+// every (s, r) when the base is and the three strides are even
+__device__ __forceinline__ bool tc_rx_rows_aligned(const float2* in, const TcK& K) {
+  return ((uintptr_t)in & 15) == 0 && ((K.frame_len | K.offset | (long long)K.N_S) & 1) == 0;
 }
 
 __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -198,8 +206,9 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
 // Bulk form (one thread): both rows of `tile` into stg[t][.] on `bar` (rows past the
 // end are not fetched; the staging step zeroes them).
 template <int PASS>
-__device__ __forceinline__ void tc_prefetch_bulk(float2* stg, const float2* __restrict__ ws, const TcK& K, int tile,
-                                                 int total, uint64_t* bar) {
+__device__ __forceinline__ void tc_prefetch_bulk(float2* stg, const float2* __restrict__ in,
+                                                 const float2* __restrict__ ws, const TcK& K, int tile, int total,
+                                                 uint64_t* bar) {
   uint32_t bytes = 0;
   for (int t = 0; t < 2; ++t) bytes += (2 * tile + t < total) ? kN * 8u : 0u;
   fence_async_smem();                    // earlier generic reads of stg before the async writes
@@ -208,7 +217,7 @@ __device__ __forceinline__ void tc_prefetch_bulk(float2* stg, const float2* __re
     const int g = 2 * tile + t;
     if (g >= total) continue;
     const TcCtx cx = tc_ctx<PASS>(K, g);
-    bulk_copy(stg + t * kN, ws + (long long)cx.s * K.ws_len + K.tc_off + (long long)cx.r * kN, kN * 8u, bar);
+    bulk_copy(stg + t * kN, tc_src<PASS>(in, ws, K, cx, 0), kN * 8u, bar);
   }
 }
 
@@ -332,16 +341,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
   const float2 tw_seed = __ldg(tw + ((rlo * (16 * h)) & (kN - 1)));
 
   uint32_t stg_phase = 0;
+  const bool bulk = tc_bulk<PASS>() || (PASS == FC_TC_RX_FFT && tc_rx_rows_aligned(g_in, K));
   if (blockIdx.x < n_tiles) {
-    if (!tc_bulk<PASS>())
+    if (!bulk)
       tc_prefetch<PASS>(stg, g_in, g_ws, K, blockIdx.x, total, tid);
     else if (tid == 0)
-      tc_prefetch_bulk<PASS>(stg, g_ws, K, blockIdx.x, total, &stg_bar);
+      tc_prefetch_bulk<PASS>(stg, g_in, g_ws, K, blockIdx.x, total, &stg_bar);
   }
   // Stage `tile` into A from its staged input (waiting for the copy), then start
   // fetching tile + gridDim.x into the staging buffer. False when a bounded wait gave up.
   auto stage = [&](int tile) -> bool {
-    if (!tc_bulk<PASS>()) {
+    if (!bulk) {
       asm volatile("cp.async.wait_all;" ::: "memory");
     } else {
       if (!mbar_wait(&stg_bar, stg_phase)) {
@@ -359,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     for (int it = 0; it < 2 * kN / 4 / kThreads; ++it) {
       const int e4 = tid + kThreads * it;
       const int t = e4 >> 10, n2 = e4 & 63, a = (e4 >> 6) & 15;
-      const bool live = !tc_bulk<PASS>() || 2 * tile + t < total;
+      const bool live = !bulk || 2 * tile + t < total;
       uint32_t hi[4], lo[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -375,10 +385,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     __syncthreads();
     // the staging buffer is free: fetch the tile after this one
     if (tile + (int)gridDim.x < n_tiles) {
-      if (!tc_bulk<PASS>())
+      if (!bulk)
         tc_prefetch<PASS>(stg, g_in, g_ws, K, tile + gridDim.x, total, tid);
       else if (tid == 0)
-        tc_prefetch_bulk<PASS>(stg, g_ws, K, tile + gridDim.x, total, &stg_bar);
+        tc_prefetch_bulk<PASS>(stg, g_in, g_ws, K, tile + gridDim.x, total, &stg_bar);
     }
     return true;
   };

@@ -136,3 +136,33 @@ def test_tensor_path_stream_calls(torch_cuda):
     assert rel(got, ref) <= TOL_TC
     st.close()
     plan.close()
+
+
+def test_tensor_rx_input_alignment(torch_cuda):
+    """The RX block DFT stages each 4096-sample input block with one bulk copy when every
+    block starts on a 16-byte boundary, and with per-sample copies otherwise (the ABI
+    allows 8-byte aligned buffers): both give the same estimate, which matches the oracle."""
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import Plan
+    geom = dataclasses.replace(wl.config_100mhz(1), flags=4)
+    S = 2
+    plan = Plan(geom)
+    grid = c64(wl.qam_grid(geom, S, 131))
+    rx = np.stack([c64(wl.awgn(fo.tx_frame(geom, grid[s].astype(np.complex128)), 30.0, 131 + s)) for s in range(S)])
+    flat = torch.empty(S * plan.wave_len + 1, dtype=torch.complex64, device="cuda")
+    flat[1:] = torch.from_numpy(rx.reshape(-1)).cuda()
+    shifted = flat[1:].view(S, plan.wave_len)            # 8 bytes past a 16-byte boundary
+    aligned = torch.from_numpy(rx).cuda()
+    assert shifted.data_ptr() % 16 == 8 and aligned.data_ptr() % 16 == 0
+    e_al = torch.empty((S, plan.grid_len), dtype=torch.complex64, device="cuda")
+    e_sh = torch.empty_like(e_al)
+    plan.rx_analyze(aligned, e_al)
+    plan.rx_analyze(shifted, e_sh)
+    torch.cuda.synchronize()
+    from paper_2008_00672_gb300 import fc
+    assert fc.load_library().fc_plan_device_status(plan.handle) == 0
+    a, b = e_al.cpu().numpy(), e_sh.cpu().numpy()
+    plan.close()
+    assert np.array_equal(a, b)
+    for s in range(S):
+        assert rel(a[s], fo.rx_frame(geom, rx[s].astype(np.complex128))) <= TOL_TC
