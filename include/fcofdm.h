@@ -77,7 +77,7 @@ typedef struct fc_group {
   const int32_t* n_cp;     /* N_CP,n, n = 0..B-1, high-rate samples (host, copied)     */
 } fc_group;
 
-/* One FC subband (Sec. II-B, Sec. III-A). */
+/* One FC subband (Sec. II, Sec. III-A). */
 typedef struct fc_subband {
   int32_t l_short;         /* L_m: short transform size, I_m = N/L_m (eqn:Rk)          */
   int32_t l_ofdm;          /* L_OFDM,m: OFDM (I)DFT size; symbol-sync needs L_OFDM = L */
@@ -103,7 +103,7 @@ typedef struct fc_geometry {
    (both compute the same result; this exists to test one against the other). */
 #define FC_FLAG_GENERIC_KERNELS 1
 /* Overlap-save symbol-synchronised RX of a subband with L_m = 1024, N_m = 2048 in the
-   joint form of eq:reduc (Sec. III-C): x_hat = C Omega(g_0 - Omega g_1) + Omega Omega g_1
+   joint form of eq:reduc (Sec. V-A): x_hat = C Omega(g_0 - Omega g_1) + Omega Omega g_1
    with C = W S_hat W^-1, instead of the two block IDFTs, the S window, eq:concat2 and
    the OFDM DFT. Same result up to rounding. It applies to the specialised one-warp-per-
    symbol kernels only; other RX work (OLA, other sizes, FC_FLAG_GENERIC_KERNELS) ignores it. */

@@ -18,9 +18,9 @@ in 5G New Radio"):
   CP extrapolation of Sec. III-E.
 * Continuous and symbol-synchronized FC analysis, OLA or OLS (Sec. IV,
   eq:ola_analysis, eq:ols_analysis, eq:1, eq:concat2) and OFDM demodulation.
-* The simplified symbol-synchronized OLS RX (Sec. V-B, eq:FCcomb, eq:reduc).
+* The simplified symbol-synchronized OLS RX (Sec. V-A, eq:FCcomb, eq:reduc).
 * The FC part alone on time-domain signals (tx_frame / rx_frame with io_time).
-* The complexity model of Sec. V-A (eq:highrate, eq:lowrate), analytic counts only.
+* The complexity model of Sec. V (eq:highrate, eq:lowrate), analytic counts only.
 * BF16 rounding of complex samples (bf16_round), for the expected values of complex-BF16
   I/O: the paper computes in full precision; a BF16 output is the exact result rounded
   once to the nearest BF16 value (8 significand bits, ties to even), per real component.
@@ -421,7 +421,7 @@ def rx_sync_subband_time(x: np.ndarray, group, sub, scheme: int) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
-# Simplified symbol-synchronized RX (Sec. V, "Simplified Implementation"; eq:FCcomb, eq:reduc)
+# Simplified symbol-synchronized RX (Sec. V-A; eq:FCcomb, eq:reduc)
 # ---------------------------------------------------------------------------
 
 def omega(L: int, phi: int) -> np.ndarray:
@@ -595,7 +595,7 @@ def rx_frame(geom, wave: np.ndarray, simplified: bool = False, io_time: bool = F
 
 
 # ---------------------------------------------------------------------------
-# The paper's complexity model (Sec. V-A, eq:highrate, eq:lowrate): real
+# The paper's complexity model (Sec. V, eq:highrate, eq:lowrate): real
 # multiplications, split-radix transforms with three real multiplications per
 # complex multiplication. Analytic; it counts, it does not compute signals.
 # ---------------------------------------------------------------------------

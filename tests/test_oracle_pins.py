@@ -518,7 +518,7 @@ def test_time_io_is_the_fc_part_of_the_grid_path(mode, stx, srx):
 # ---------------------------------------------------------------------------
 
 def test_complexity_printed_values():
-    """Sec. V-A prints mu(128) = 516 and mu(16) = 20, and the simplified RX replaces
+    """Sec. V prints mu(128) = 516 and mu(16) = 20, and the simplified RX replaces
     three low-rate transforms (two short IDFTs, one OFDM DFT) by two (beta = 1/2)."""
     assert fo.mu(128) == 516 and fo.mu(16) == 20
     L = 128

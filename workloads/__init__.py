@@ -44,7 +44,7 @@ class Group:
 
 @dataclass(frozen=True)
 class Subband:
-    """One FC subband (Sec. II-B); ``weights`` is D_m in fftshifted order."""
+    """One FC subband (Sec. II, Sec. III-A); ``weights`` is D_m in fftshifted order."""
     l_short: int                # L_m
     l_ofdm: int                 # L_OFDM,m
     n_active: int               # L_act,m
