@@ -341,20 +341,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
   const float2 tw_seed = __ldg(tw + ((rlo * (16 * h)) & (kN - 1)));
 
   uint32_t stg_phase = 0;
+  // what is in flight, for the exit after a failed wait: a staging copy (completing the
+  // stg_bar phase of parity stg_issue) and a GEMM (completing the bar phase mma_issue)
+  bool stg_pending = false, mma_pending = false;
+  uint32_t stg_issue = 0, mma_issue = 0;
   const bool bulk = tc_bulk<PASS>() || (PASS == FC_TC_RX_FFT && tc_rx_rows_aligned(g_in, K));
   if (blockIdx.x < n_tiles) {
     if (!bulk)
       tc_prefetch<PASS>(stg, g_in, g_ws, K, blockIdx.x, total, tid);
     else if (tid == 0)
       tc_prefetch_bulk<PASS>(stg, g_in, g_ws, K, blockIdx.x, total, &stg_bar);
+    stg_pending = true;
+    stg_issue = stg_phase;
   }
   // Stage `tile` into A from its staged input (waiting for the copy), then start
   // fetching tile + gridDim.x into the staging buffer. False when a bounded wait gave up.
   auto stage = [&](int tile) -> bool {
     if (!bulk) {
       asm volatile("cp.async.wait_all;" ::: "memory");
+      stg_pending = false;
     } else {
-      if (!mbar_wait(&stg_bar, stg_phase)) {
+      if (mbar_wait(&stg_bar, stg_phase)) {
+        stg_pending = false;
+      } else {
         atomicExch(args.err, 1);
         abort_flag = 1;
       }
@@ -389,6 +398,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
         tc_prefetch<PASS>(stg, g_in, g_ws, K, tile + gridDim.x, total, tid);
       else if (tid == 0)
         tc_prefetch_bulk<PASS>(stg, g_in, g_ws, K, tile + gridDim.x, total, &stg_bar);
+      stg_pending = true;
+      stg_issue = stg_phase;
     }
     return true;
   };
@@ -399,10 +410,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
       issue_mmas(tbase + col, sa_hi, sa_lo, sb_hi, sb_lo);
       mma_commit(&bar);
     }
+    mma_pending = true;
+    mma_issue = phase;
   };
   // wait for the last issued GEMM; false when the bounded wait gave up
   auto wait_mma = [&]() -> bool {
-    if (!mbar_wait(&bar, phase)) {
+    if (mbar_wait(&bar, phase)) {
+      mma_pending = false;
+    } else {
       atomicExch(args.err, 1);
       abort_flag = 1;
     }
@@ -457,6 +472,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     }
     tc_fence_before();
     __syncthreads();                       // TMEM columns [128, 256) are free for the next GEMM 2
+  }
+  if (abort_flag) {
+    // a bounded wait gave up: let this CTA's copies and GEMM in flight finish (again with
+    // bounded waits) before its shared memory and TMEM are released
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (bulk && stg_pending) mbar_wait(&stg_bar, stg_issue);
+    if (mma_pending) mbar_wait(&bar, mma_issue);
+    tc_fence_after();
   }
   tc_fence_before();
   __syncthreads();
