@@ -105,6 +105,36 @@ def test_invalid_geometry_rejected(fc, geom, code):
     assert ei.value.status == code
 
 
+def _ns(mode=0, stx=0, srx=1, groups=((32, 16, -1, (4,)),), subs=((16, 16, 8, 0, 0),)):
+    """A geometry as plain attributes (no workload-side validation), for the ABI checks."""
+    from types import SimpleNamespace as NS
+    gs = tuple(NS(n_long=N, n_overlap=NO, lead_pad=lead, n_cp=tuple(cp)) for N, NO, lead, cp in groups)
+    ss = tuple(NS(l_short=L, l_ofdm=Lo, n_active=act, centre_bin=c, group=g, weights=np.ones(L))
+               for L, Lo, act, c, g in subs)
+    return NS(mode=mode, scheme_tx=stx, scheme_rx=srx, groups=gs, subbands=ss, flags=0)
+
+
+@pytest.mark.parametrize("geom,code,why", [
+    (_ns(mode=7), 1, "unknown mode"),
+    (_ns(stx=5), 1, "unknown OLA/OLS scheme"),
+    (_ns(groups=((32, 32, -1, (4,)),)), 1, "need 0 <= N_O < N"),
+    (_ns(groups=((32, 16, -1, ()),)), 1, "need n_symbols >= 1"),
+    (_ns(groups=((32, 16, -1, (4, -4)),)), 1, "negative N_CP"),
+    (_ns(groups=((40, 20, -1, (0,)),), subs=((20, 20, 8, 0, 0),)), 2, "N must be 2^a 3^b"),
+    (_ns(subs=((16, 16, 8, 0, 3),)), 1, "subband group out of range"),
+    (_ns(subs=((64, 64, 8, 0, 0),)), 1, "need 1 <= L <= N"),
+    (_ns(subs=((16, 16, 0, 0, 0),)), 1, "need 1 <= L_act <= L_OFDM"),
+    (_ns(groups=((32, 16, -1, (0,)),), subs=((24, 16, 8, 0, 0),)), 1, "N_OFDM = L_OFDM N / L is not an integer"),
+    (_ns(groups=((32, 16, -1, (4,)), (32, 16, -1, (4,))),), 1, "a group has no subband"),
+    (_ns(subs=((16, 16, 8, -4, 0), (16, 8, 4, 6, 0))), 1, "equal high-rate durations"),
+])
+def test_invalid_geometry_rejected_more(fc, geom, code, why):
+    """Each host-side check of fc_geometry_check, reached by a geometry that breaks only it."""
+    with pytest.raises(fc.FcError) as ei:
+        fc.fc_geometry_check(geom)
+    assert ei.value.status == code and why in str(ei.value), str(ei.value)
+
+
 def test_oracle_rejects_the_same_invalid_geometry():
     """The oracle refuses the geometries the paper leaves undefined, as the library does."""
     for geom in [_g(1, 32, 8, 16, 16, 8, 0, (2,)), _g(1, 32, 16, 16, 16, 8, 0, (9,)),
