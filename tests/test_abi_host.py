@@ -237,3 +237,15 @@ def test_bf16_io_sizes(fc):
     assert t.workspace_per_stream == fc.fc_geometry_check(g).workspace_per_stream
     it = fc.fc_geometry_check(dataclasses.replace(wl.config_single_5mhz(), flags=8 | 16))
     assert it.sample_bytes == 4 and it.tx_in_len == it.time_tx_len
+
+
+def test_no_gpu_fails_loudly(fc):
+    """There is no CPU path: without a usable GPU, creating a plan or a server returns
+    FC_ERR_CUDA (and the binding raises) instead of computing anything on the host."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    for make in (lambda: fc.fc_plan_create(wl.config_single_5mhz()), lambda: fc.fc_server_create(0, 1, 0)):
+        with pytest.raises(fc.FcError) as ei:
+            make()
+        assert ei.value.status == fc.FC_ERR_CUDA
