@@ -298,17 +298,20 @@ int fc_plan_device_status(const fc_plan* plan);
 
 /*
  * Autotuner (no counterpart in the paper; launch-shape selection on this GPU). For
- * n_streams streams, times every launch shape the plan has for TX and for RX — the
- * number of CTAs each stream's symbol jobs are spread over (1, 2, 4, ... chunks per
- * stream), where the one-warp-per-symbol kernels apply those kernels or the generic
- * shared-memory kernels, and for the generic kernels each CTA size that fits the plan
- * (512 threads one per SM, 256 two per SM, 128 four per SM) — `reps` times each on
- * `stream`, and records the fastest per direction in the plan. Later execute calls
- * with exactly n_streams streams use it; other counts keep the built-in occupancy
- * rule (chunks so that the call launches at least two CTAs per SM; 128-thread CTAs
- * where the call fills four per SM, else 256-thread CTAs where they fit). Results do not depend on the choice beyond
- * rounding. Allocates and frees temporary device buffers
- * and synchronises `stream`: call it at set-up, not inside a stream capture.
+ * n_streams streams, times every launch shape the plan has for TX and for RX: the
+ * specialised kernels where the plan has them (one shape: the one-warp-per-symbol
+ * kernels deal all streams' symbol jobs to the CTAs resident on the GPU; the tensor-
+ * core passes one tile of two transforms per CTA step), and the generic shared-memory
+ * kernels at every number of CTAs each stream's symbol jobs are spread over (1, 2,
+ * 4, ... chunks per stream) and every CTA size that fits the plan (512 threads one per
+ * SM, 256 two per SM, 128 four per SM). Each runs `reps` times on `stream`; the
+ * fastest per direction is recorded in the plan. Later execute calls with exactly
+ * n_streams streams use it; other counts keep the built-in rule (the specialised
+ * kernels where the plan has them; else chunks so that the call launches at least two
+ * CTAs per SM, 128-thread CTAs where the call fills four per SM, else 256-thread CTAs
+ * where they fit). Results do not depend on the choice beyond rounding. Allocates and
+ * frees temporary device buffers and synchronises `stream`: call it at set-up, not
+ * inside a stream capture.
  */
 int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* stream);
 
@@ -316,7 +319,8 @@ int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* strea
    saved from an earlier fc_plan_autotune): chunks_per_stream must be one the plan has
    (1, 2, 4, ..., at most 64 and at most the jobs per stream); generic_kernels 1 selects
    the generic shared-memory kernels where specialised ones exist (their CTA size then
-   follows the built-in rule). FC_ERR_INVALID otherwise. */
+   follows the built-in rule), and chunks_per_stream applies to the generic kernels only
+   (the specialised ones have a single shape). FC_ERR_INVALID otherwise. */
 int fc_plan_set_choice(fc_plan* plan, int32_t n_streams, int32_t direction, int32_t chunks_per_stream,
                        int32_t generic_kernels);
 
