@@ -1,13 +1,15 @@
 """Fixed invocations of the library's kernels for profilers.
 
     python -m paper_2008_00672_gb300.profile_cases CASE --streams S [--warm W]
-        [--tx-chunks K --rx-chunks K]
+        [--tx-chunks K --rx-chunks K] [--time R]
 
 builds the case's plan, sets a fixed launch shape (the case's default, or the chunks
 per stream given, e.g. the ones the benchmark's autotuner reports), runs W warm-up
 TX + RX passes and then one more TX + RX pass, so that `ncu -k <kernel> -s <skip>`
 can pick launches of a known shape. Inputs are seeded QAM grids; the RX input is the
-TX output (its values do not change the kernels' work).
+TX output (its values do not change the kernels' work). With --time R it then times R
+more TX calls and R more RX calls with CUDA events on the current stream and prints
+the mean milliseconds of each (for comparing two builds of a kernel; not for ncu runs).
 
 Cases:
   warp20     20 MHz mixed numerology, symbol-synchronized (one-warp-per-symbol kernels,
@@ -46,6 +48,7 @@ def main():
     ap.add_argument("--warm", type=int, default=1)
     ap.add_argument("--tx-chunks", type=int, default=0, help="chunks per stream of the TX launch (0: the case's)")
     ap.add_argument("--rx-chunks", type=int, default=0, help="chunks per stream of the RX launch (0: the case's)")
+    ap.add_argument("--time", type=int, default=0, help="then time this many TX and RX calls (CUDA events)")
     args = ap.parse_args()
     build.build()
     geom, shape = make_case(args.case)
@@ -64,9 +67,22 @@ def main():
         plan.tx_synthesize(grid, wave)
         plan.rx_analyze(wave, est)
     torch.cuda.synchronize()
+    timed = ""
+    if args.time > 0:
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        for _ in range(args.time):
+            plan.tx_synthesize(grid, wave)
+        ev[1].record()
+        for _ in range(args.time):
+            plan.rx_analyze(wave, est)
+        ev[2].record()
+        torch.cuda.synchronize()
+        timed = (f"; mean of {args.time}: TX {ev[0].elapsed_time(ev[1]) / args.time:.4f} ms, "
+                 f"RX {ev[1].elapsed_time(ev[2]) / args.time:.4f} ms")
     plan.close()
     print(f"{args.case}: {S} streams, {args.warm} warm-up passes + 1, launches per pass "
-          f"TX {plan.tx_kernels} RX {plan.rx_kernels}")
+          f"TX {plan.tx_kernels} RX {plan.rx_kernels}{timed}")
 
 
 if __name__ == "__main__":
