@@ -248,6 +248,22 @@ int fc_state_reset(fc_state* state, void* stream);
 void fc_state_destroy(fc_state* state);
 
 /*
+ * Checkpoint / resume (no counterpart in the paper). A stream's whole state is its TX
+ * tail and RX look-behind: D = fc_sizes.stream_delay complex64 samples each per stream.
+ * fc_state_bytes gives the size of a checkpoint, 2 x n_streams x D x 8 bytes (every
+ * stream's TX tail, then every stream's look-behind). fc_state_export waits for the
+ * work queued on `stream` (a cudaStream_t, NULL = default stream) and copies the state
+ * into `host` (at least that many bytes, host memory, caller-owned). fc_state_import
+ * copies a checkpoint of exactly that size into a state created for a plan of the same
+ * geometry and the same number of streams, in order on `stream`, complete when the call
+ * returns. A stream resumed from a checkpoint continues as the one that wrote it.
+ * FC_ERR_INVALID for NULL arguments or a wrong size; FC_ERR_CUDA if a copy fails.
+ */
+int fc_state_bytes(const fc_state* state, uint64_t* bytes);
+int fc_state_export(const fc_state* state, void* host, uint64_t bytes, void* stream);
+int fc_state_import(fc_state* state, const void* host, uint64_t bytes, void* stream);
+
+/*
  * One TX stream call: grid [n_streams][grid_len] -> slot_out [n_streams][slot_len].
  * Runs fc_tx_synthesize into the state's frame buffer, then adds the carried tail to
  * the first D samples and keeps samples [T, T + D) as the next tail. Workspace and

@@ -152,7 +152,10 @@ int fc_state_create(const fc_plan* plan, int32_t n_streams, fc_state** out) {
       delete st;
       return cuda_err(e, "cudaMalloc of the stream state");
     }
+    // zeroed before the call returns: the caller's first stream call, or an import, may
+    // come on a non-blocking stream that does not wait for the legacy default stream
     e = cudaMemset(st->d_mem, 0, (size_t)elems * sizeof(float2));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) {
       cudaFree(st->d_mem);
       delete st;
@@ -184,6 +187,43 @@ void fc_state_destroy(fc_state* state) {
     if (state->d_mem) cudaFree(state->d_mem);
   }
   delete state;
+}
+
+int fc_state_bytes(const fc_state* state, uint64_t* bytes) {
+  if (!state || !bytes) return fc_internal_fail(FC_ERR_INVALID, "state or bytes is NULL");
+  *bytes = (uint64_t)(2 * (long long)state->n_streams * state->delay) * sizeof(float2);
+  return FC_OK;
+}
+
+// The checkpoint is the device range [tail, tail + 2 n_streams D): every stream's TX tail,
+// then every stream's look-behind (one allocation, see fc_state_create).
+int fc_state_export(const fc_state* state, void* host, uint64_t bytes, void* stream) {
+  uint64_t need = 0;
+  const int rc = fc_state_bytes(state, &need);
+  if (rc != FC_OK) return rc;
+  if (need == 0) return FC_OK;
+  if (!host || bytes < need) return fc_internal_fail(FC_ERR_INVALID, "host buffer missing or too small");
+  DevGuard dg(state->device);
+  if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  const cudaStream_t cs = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(host, state->tail, (size_t)need, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  return e == cudaSuccess ? FC_OK : cuda_err(e, "state export");
+}
+
+int fc_state_import(fc_state* state, const void* host, uint64_t bytes, void* stream) {
+  uint64_t need = 0;
+  const int rc = fc_state_bytes(state, &need);
+  if (rc != FC_OK) return rc;
+  if (bytes != need) return fc_internal_fail(FC_ERR_INVALID, "checkpoint size does not match the state");
+  if (need == 0) return FC_OK;
+  if (!host) return fc_internal_fail(FC_ERR_INVALID, "host is NULL");
+  DevGuard dg(state->device);
+  if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  const cudaStream_t cs = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(state->tail, host, (size_t)need, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  return e == cudaSuccess ? FC_OK : cuda_err(e, "state import");
 }
 
 int fc_tx_synthesize_stream(const fc_plan* plan, fc_state* state, const void* grid_in, void* slot_out,

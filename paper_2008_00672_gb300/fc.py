@@ -109,6 +109,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fc_state_reset.restype = ctypes.c_int
         lib.fc_state_destroy.argtypes = [vp]
         lib.fc_state_destroy.restype = None
+        lib.fc_state_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        lib.fc_state_bytes.restype = ctypes.c_int
+        lib.fc_state_export.argtypes = [vp, vp, ctypes.c_uint64, vp]
+        lib.fc_state_export.restype = ctypes.c_int
+        lib.fc_state_import.argtypes = [vp, vp, ctypes.c_uint64, vp]
+        lib.fc_state_import.restype = ctypes.c_int
         lib.fc_tx_synthesize_stream.argtypes = [vp, vp, vp, vp, vp, sz, vp]
         lib.fc_tx_synthesize_stream.restype = ctypes.c_int
         lib.fc_rx_analyze_stream.argtypes = [vp, vp, vp, vp, vp, sz, vp]
@@ -245,6 +251,20 @@ def fc_state_reset(state, stream: int = 0):
 def fc_state_destroy(state):
     if state:
         load_library().fc_state_destroy(state)
+
+
+def fc_state_bytes(state) -> int:
+    n = ctypes.c_uint64()
+    _check(load_library().fc_state_bytes(state, ctypes.byref(n)), "fc_state_bytes")
+    return n.value
+
+
+def fc_state_export(state, host: int, nbytes: int, stream: int = 0):
+    _check(load_library().fc_state_export(state, host or None, int(nbytes), stream or None), "fc_state_export")
+
+
+def fc_state_import(state, host: int, nbytes: int, stream: int = 0):
+    _check(load_library().fc_state_import(state, host or None, int(nbytes), stream or None), "fc_state_import")
 
 
 def fc_tx_synthesize_stream(plan, state, grid_in: int, slot_out: int, workspace: int = 0, workspace_bytes: int = 0,
@@ -484,6 +504,21 @@ class State:
 
     def reset(self, stream=None):
         fc_state_reset(self.handle, Plan._stream_handle(stream))
+
+    def export(self, stream=None):
+        """Checkpoint: the TX tails and RX look-behinds as host bytes (numpy uint8), after
+        the work queued on `stream` has finished."""
+        import numpy as np
+        buf = np.zeros(fc_state_bytes(self.handle), dtype=np.uint8)
+        fc_state_export(self.handle, buf.ctypes.data if buf.size else 0, buf.size, Plan._stream_handle(stream))
+        return buf
+
+    def load(self, checkpoint, stream=None):
+        """Resume from a checkpoint that export() of a state of the same plan sizes and
+        stream count returned."""
+        import numpy as np
+        buf = np.ascontiguousarray(checkpoint, dtype=np.uint8)
+        fc_state_import(self.handle, buf.ctypes.data if buf.size else 0, buf.size, Plan._stream_handle(stream))
 
     def tx(self, grid, slot_out, workspace=None, stream=None):
         p = self.plan

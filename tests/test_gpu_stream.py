@@ -123,6 +123,48 @@ def test_state_reset_restarts_the_stream(torch_cuda):
     plan.close()
 
 
+def test_state_checkpoint_resumes_the_stream(torch_cuda):
+    """fc_state_export / fc_state_import: a stream interrupted after two slots and resumed
+    from its checkpoint in a new state gives what the uninterrupted stream gives, TX and
+    RX (to rounding: reductions may add in another order); a checkpoint of another size is
+    refused."""
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import FcError, Plan, State
+    geom = STREAMABLE[0][1]
+    plan = Plan(geom)
+    S, T, K = 2, plan.slot_len, 4
+    assert plan.stream_delay > 0
+    grids = [torch.from_numpy(c64(wl.qam_grid(geom, S, 90 + k))).cuda() for k in range(K)]
+    rng = np.random.default_rng(91)
+    slots = [torch.from_numpy(c64(rng.standard_normal((S, T)) + 1j * rng.standard_normal((S, T)))).cuda()
+             for _ in range(K)]
+
+    def step(st, k):
+        o = torch.empty((S, T), dtype=torch.complex64, device="cuda")
+        e = torch.empty((S, plan.grid_len), dtype=torch.complex64, device="cuda")
+        st.tx(grids[k], o)
+        st.rx(slots[k], e)
+        return o.cpu().numpy(), e.cpu().numpy()
+
+    whole = State(plan, S)
+    ref = [step(whole, k) for k in range(K)]
+    first = State(plan, S)
+    got = [step(first, k) for k in range(2)]
+    ckpt = first.export()
+    assert ckpt.size == 2 * S * plan.stream_delay * 8
+    first.close()
+    resumed = State(plan, S)
+    resumed.load(ckpt)
+    got += [step(resumed, k) for k in range(2, K)]
+    for k, ((ro, re), (go, ge)) in enumerate(zip(ref, got)):
+        assert rel(go, ro) < 1e-6 and rel(ge, re) < 1e-6, (k, rel(go, ro), rel(ge, re))
+    with pytest.raises(FcError):
+        resumed.load(ckpt[:-8])
+    whole.close()
+    resumed.close()
+    plan.close()
+
+
 def test_state_refused_for_a_geometry_that_cannot_stream(torch_cuda):
     from paper_2008_00672_gb300 import FcError, Plan, State
     from tests.test_stream_semantics import small_sync
