@@ -230,6 +230,7 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
 }
 
 int fc_batch_launch(fc_batch* b, void* stream) {
+  FcRange nvtx_range(__func__);
   if (!b) return fc_internal_fail(FC_ERR_INVALID, "batch is NULL");
   DevGuard dg(b->device);
   if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");

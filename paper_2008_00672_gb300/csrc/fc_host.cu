@@ -163,11 +163,13 @@ void fc_pipeline_destroy(fc_pipeline* p) {
 
 int fc_tx_synthesize_host(fc_pipeline* pipeline, int32_t n_streams, const void* host_grid, void* host_wave,
                           void* stream) {
+  FcRange nvtx_range(__func__);
   return run(pipeline, FC_TX, n_streams, host_grid, host_wave, stream);
 }
 
 int fc_rx_analyze_host(fc_pipeline* pipeline, int32_t n_streams, const void* host_wave, void* host_grid,
                        void* stream) {
+  FcRange nvtx_range(__func__);
   return run(pipeline, FC_RX, n_streams, host_wave, host_grid, stream);
 }
 

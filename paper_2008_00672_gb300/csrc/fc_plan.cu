@@ -841,6 +841,7 @@ bool fc_internal_sync_work(const fc_plan* plan, int dir, int n_streams, const vo
 extern "C" {
 
 int fc_plan_create(fc_plan** out, const fc_geometry* geometry, int32_t device) {
+  FcRange nvtx_range(__func__);
   if (!out) return fail(FC_ERR_INVALID, "out is NULL");
   *out = nullptr;
   int ndev = 0;
@@ -908,17 +909,20 @@ int fc_query(const fc_plan* plan, fc_sizes* out) {
 
 int fc_tx_synthesize(const fc_plan* plan, int32_t n_streams, const void* grid_in, void* wave_out, void* workspace,
                      size_t workspace_bytes, void* stream) {
+  FcRange nvtx_range(__func__);
   return fc_internal_frame(plan, FC_TX, n_streams, grid_in, wave_out, workspace, workspace_bytes, stream,
                            plan ? plan->io : 0);
 }
 
 int fc_rx_analyze(const fc_plan* plan, int32_t n_streams, const void* wave_in, void* grid_out, void* workspace,
                   size_t workspace_bytes, void* stream) {
+  FcRange nvtx_range(__func__);
   return fc_internal_frame(plan, FC_RX, n_streams, wave_in, grid_out, workspace, workspace_bytes, stream,
                            plan ? plan->io : 0);
 }
 
 int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* stream) {
+  FcRange nvtx_range(__func__);
   if (!plan) return fail(FC_ERR_INVALID, "plan is NULL");
   if (n_streams < 1 || reps < 1) return fail(FC_ERR_INVALID, "need n_streams >= 1 and reps >= 1");
   DeviceGuard dg(plan->device);

@@ -144,6 +144,7 @@ int fc_server_carrier_sizes(const fc_server* s, int32_t carrier, fc_sizes* out) 
 }
 
 int fc_server_run(fc_server* s, const fc_serve_request* reqs, int32_t n, double* latency_s) {
+  FcRange nvtx_range(__func__);
   if (!s || (n > 0 && (!reqs || !latency_s))) return fc_internal_fail(FC_ERR_INVALID, "NULL argument");
   for (int i = 0; i < n; ++i) {
     const fc_serve_request& r = reqs[i];

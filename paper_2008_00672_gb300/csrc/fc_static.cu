@@ -27,6 +27,7 @@ void* g_static_ptr[64] = {};   // device address of the array, per device, resol
 
 extern "C" int fc_tx_synthesize_static(const fc_plan* plan, int32_t n_streams, const void* grid_in, void* wave_out,
                                        void* stream) {
+  FcRange nvtx_range(__func__);
   if (!plan) return fc_internal_fail(FC_ERR_INVALID, "plan is NULL");
   if (n_streams < 0) return fc_internal_fail(FC_ERR_INVALID, "n_streams < 0");
   fc_sizes sz;

@@ -198,6 +198,7 @@ int fc_state_bytes(const fc_state* state, uint64_t* bytes) {
 // The checkpoint is the device range [tail, tail + 2 n_streams D): every stream's TX tail,
 // then every stream's look-behind (one allocation, see fc_state_create).
 int fc_state_export(const fc_state* state, void* host, uint64_t bytes, void* stream) {
+  FcRange nvtx_range(__func__);
   uint64_t need = 0;
   const int rc = fc_state_bytes(state, &need);
   if (rc != FC_OK) return rc;
@@ -212,6 +213,7 @@ int fc_state_export(const fc_state* state, void* host, uint64_t bytes, void* str
 }
 
 int fc_state_import(fc_state* state, const void* host, uint64_t bytes, void* stream) {
+  FcRange nvtx_range(__func__);
   uint64_t need = 0;
   const int rc = fc_state_bytes(state, &need);
   if (rc != FC_OK) return rc;
@@ -228,6 +230,7 @@ int fc_state_import(fc_state* state, const void* host, uint64_t bytes, void* str
 
 int fc_tx_synthesize_stream(const fc_plan* plan, fc_state* state, const void* grid_in, void* slot_out,
                             void* workspace, size_t workspace_bytes, void* stream) {
+  FcRange nvtx_range(__func__);
   fc_sizes sz;
   int rc = check_state(plan, state, grid_in, slot_out, &sz);
   if (rc != FC_OK || state->n_streams == 0) return rc;
@@ -252,6 +255,7 @@ int fc_tx_synthesize_stream(const fc_plan* plan, fc_state* state, const void* gr
 
 int fc_rx_analyze_stream(const fc_plan* plan, fc_state* state, const void* slot_in, void* grid_out,
                          void* workspace, size_t workspace_bytes, void* stream) {
+  FcRange nvtx_range(__func__);
   fc_sizes sz;
   int rc = check_state(plan, state, slot_in, grid_out, &sz);
   if (rc != FC_OK || state->n_streams == 0) return rc;
