@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "fc_internal.cuh"
+#include "fc_trace.h"
 
 struct fc_batch {
   int device = 0;

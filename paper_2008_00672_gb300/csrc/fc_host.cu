@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "fc_internal.cuh"
+#include "fc_trace.h"
 
 struct fc_pipeline {
   const fc_plan* plan = nullptr;

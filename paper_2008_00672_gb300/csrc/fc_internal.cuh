@@ -10,17 +10,6 @@
 
 #include "../../include/fcofdm.h"
 
-#include <nvtx3/nvToolsExt.h>
-
-// An NVTX range over one ABI call, named after the call: visible on profiler timelines
-// and usable as an ncu/nsys filter; without a tool attached each push/pop is a no-op.
-struct FcRange {
-  explicit FcRange(const char* name) { nvtxRangePushA(name); }
-  ~FcRange() { nvtxRangePop(); }
-  FcRange(const FcRange&) = delete;
-  FcRange& operator=(const FcRange&) = delete;
-};
-
 // The generic kernels (fc_kernels.cu) are compiled three times: for 512-thread CTAs, one
 // per SM (transforms up to 4096 points), 256-thread CTAs, two per SM (up to 2048 points;
 // fc_kernels_256.cu), and 128-thread CTAs, four per SM (up to 1024 points;

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "fc_internal.cuh"
+#include "fc_trace.h"
 
 namespace {
 

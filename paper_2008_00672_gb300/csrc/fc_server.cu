@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "fc_internal.cuh"
+#include "fc_trace.h"
 
 namespace {
 

@@ -14,6 +14,7 @@
 #include <mutex>
 
 #include "fc_internal.cuh"
+#include "fc_trace.h"
 
 // One workspace shared by every call on a device (the contents of the last call stay there).
 static __device__ __align__(256) unsigned char g_fc_static_workspace[FC_STATIC_WORKSPACE_BYTES];

@@ -17,6 +17,7 @@
 #include <cuda_bf16.h>
 
 #include "fc_internal.cuh"
+#include "fc_trace.h"
 
 struct fc_state {
   int device = 0;
