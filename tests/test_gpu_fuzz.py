@@ -2,12 +2,15 @@
 transforms of 2^a 3^b points, interpolation ratios I in {1, 4/3, 3/2, 2, 3, 4}, one to
 three numerology groups, one to three subbands per group, random CP lists, centre bins
 and transition bands, and the kernel-selection flags. Every drawn geometry that the
-planner accepts is compared with the FP64 oracle on two streams (RMS <= 1e-5)."""
+planner accepts is compared with the FP64 oracle on two streams: RMS <= 1e-5 per stream,
+per symbol window and per grid row, and 5e-5 of the signal RMS per sample
+(`tests/parity.py`)."""
 import numpy as np
 import pytest
 
 import workloads as wl
 from oracle import fc_oracle as fo
+from tests import parity
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -21,10 +24,6 @@ def torch_cuda():
     from paper_2008_00672_gb300 import build
     build.build()
     return torch
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def draw_geometry(rng):
@@ -96,7 +95,7 @@ def test_random_geometry(torch_cuda, geometries, k):
     torch.cuda.synchronize()
     w, est = w.cpu().numpy(), est.cpu().numpy()
     plan.close()
+    ww, gw = parity.wave_windows(geom), parity.grid_windows(geom)
     for s in range(S):
-        et = rel(w[s], fo.tx_frame(geom, grid[s].astype(np.complex128)))
-        er = rel(est[s], fo.rx_frame(geom, x[s].astype(np.complex128)))
-        assert et <= TOL and er <= TOL, (geom, et, er)
+        parity.check(w[s], fo.tx_frame(geom, grid[s].astype(np.complex128)), TOL, ww, (geom, "tx", s))
+        parity.check(est[s], fo.rx_frame(geom, x[s].astype(np.complex128)), TOL, gw, (geom, "rx", s))

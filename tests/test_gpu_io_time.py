@@ -1,5 +1,7 @@
 """GPU parity of the time-domain I/O (FC_FLAG_IO_TIME: the FC part alone) against the
-oracle's time-domain entry points, on arbitrary (non-OFDM) complex inputs."""
+oracle's time-domain entry points, on arbitrary (non-OFDM) complex inputs, with the
+element-wise bounds of `tests/parity.py` (every FC block or symbol window of the
+waveform and every recovered symbol body, and every sample)."""
 import dataclasses
 
 import numpy as np
@@ -7,6 +9,7 @@ import pytest
 
 import workloads as wl
 from oracle import fc_oracle as fo
+from tests import parity
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -20,10 +23,6 @@ def torch_cuda():
     from paper_2008_00672_gb300 import build
     build.build()
     return torch
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def c64(a):
@@ -44,9 +43,10 @@ def check(torch, geom, S, seed, tol=TOL):
     plan.rx_analyze(torch.from_numpy(x).cuda(), t_out)
     torch.cuda.synchronize()
     w, t_out = w.cpu().numpy(), t_out.cpu().numpy()
+    ww, bw = parity.wave_windows(geom), parity.body_windows(geom)
     for s in range(S):
-        assert rel(w[s], fo.tx_frame(geom, t_in[s].astype(np.complex128), io_time=True)) <= tol
-        assert rel(t_out[s], fo.rx_frame(geom, x[s].astype(np.complex128), io_time=True)) <= tol
+        parity.check(w[s], fo.tx_frame(geom, t_in[s].astype(np.complex128), io_time=True), tol, ww, ("tx", s))
+        parity.check(t_out[s], fo.rx_frame(geom, x[s].astype(np.complex128), io_time=True), tol, bw, ("rx", s))
     plan.close()
 
 
