@@ -250,14 +250,17 @@ void fc_state_destroy(fc_state* state);
 /*
  * Checkpoint / resume (no counterpart in the paper). A stream's whole state is its TX
  * tail and RX look-behind: D = fc_sizes.stream_delay complex64 samples each per stream.
- * fc_state_bytes gives the size of a checkpoint, 2 x n_streams x D x 8 bytes (every
- * stream's TX tail, then every stream's look-behind). fc_state_export waits for the
- * work queued on `stream` (a cudaStream_t, NULL = default stream) and copies the state
- * into `host` (at least that many bytes, host memory, caller-owned). fc_state_import
- * copies a checkpoint of exactly that size into a state created for a plan of the same
- * geometry and the same number of streams, in order on `stream`, complete when the call
- * returns. A stream resumed from a checkpoint continues as the one that wrote it.
- * FC_ERR_INVALID for NULL arguments or a wrong size; FC_ERR_CUDA if a copy fails.
+ * fc_state_bytes gives the size of a checkpoint: a 48-byte header (a magic word, the
+ * stream count, D, the slot and frame lengths of the state that wrote it), then
+ * 2 x n_streams x D x 8 bytes (every stream's TX tail, then every stream's
+ * look-behind). fc_state_export waits for the work queued on `stream` (a cudaStream_t,
+ * NULL = default stream) and copies the state into `host` (at least that many bytes,
+ * host memory, caller-owned). fc_state_import copies a checkpoint of exactly that size
+ * into a state created for a plan of the same geometry and the same number of streams,
+ * in order on `stream`, complete when the call returns. A stream resumed from a
+ * checkpoint continues as the one that wrote it. FC_ERR_INVALID for NULL arguments, a
+ * wrong size, or a header that does not match the state (another stream count, D,
+ * slot or frame length); FC_ERR_CUDA if a copy fails.
  */
 int fc_state_bytes(const fc_state* state, uint64_t* bytes);
 int fc_state_export(const fc_state* state, void* host, uint64_t bytes, void* stream);
@@ -283,17 +286,21 @@ int fc_rx_analyze_stream(const fc_plan* plan, fc_state* state, const void* slot_
 /*
  * Allocation-free TX (no counterpart in the paper; it is a deployment option).
  * Same computation and buffer rules as fc_tx_synthesize, but the workspace is a
- * device array built into the library (FC_STATIC_WORKSPACE_BYTES per GPU, held
- * from library load until process exit) instead of a caller buffer, for callers
- * that cannot allocate device memory at run time (fixed-budget real-time loops,
- * hosts whose allocator belongs to another framework). The call never calls
- * cudaMalloc/cudaFree or any allocating routine.
+ * device array built into the library (FC_STATIC_WORKSPACE_BYTES per GPU) instead
+ * of a caller buffer, for callers that cannot allocate device memory at run time
+ * (fixed-budget real-time loops, hosts whose allocator belongs to another
+ * framework). The call never calls cudaMalloc/cudaFree or any allocating routine.
+ *  - The array is reserved on a GPU when the first plan is created there
+ *    (fc_plan_create looks up its device address with that device current) and held
+ *    until the process exits. If that reservation failed, the first call of this
+ *    entry point tries again and returns FC_ERR_NOMEM when the GPU has no room.
+ *    Make that first call before capturing the stream into a CUDA graph.
  *  - Returns FC_ERR_INVALID (see fc_last_error) if n_streams * workspace_per_stream
  *    exceeds FC_STATIC_WORKSPACE_BYTES; plans with no workspace need (symbol-sync
  *    mode) are not limited.
- *  - The first call on a device looks up the array's device address once (with
- *    the plan's device made current for that lookup); make that first call
- *    before capturing the stream into a CUDA graph.
+ *  - The array's address is kept per device for the life of the process, so
+ *    cudaDeviceReset (or releasing the primary context) is not supported while the
+ *    library is in use.
  *  - All calls on one device share the one array: calls that overlap on the GPU
  *    (different CUDA streams, or several host threads) race and corrupt each
  *    other's output. Serialise them. Nothing in the array needs clearing between

@@ -168,6 +168,7 @@ cudaError_t fc_set_warp_smem_limits();
 // helpers for entry points defined outside fc_plan.cu
 int fc_internal_fail(int code, const char* msg);     // records fc_last_error() and returns code
 int fc_internal_plan_device(const fc_plan* plan);    // the device a plan was created on
+int fc_internal_static_resolve(int dev);             // look up the static TX workspace on a device (fc_static.cu)
 // Appends the work items of one frame call (direction FC_TX / FC_RX) on the generic
 // symbol-sync kernels and returns true, or returns false when the plan's call does not
 // run there (continuous mode, or the specialised kernels apply); *smem gets the call's

@@ -891,6 +891,10 @@ int fc_plan_create(fc_plan** out, const fc_geometry* geometry, int32_t device) {
     delete pl;
     return rc;
   }
+  // Reserve the allocation-free TX entry point's device array now, at set-up, rather
+  // than at its first call. A failure here does not fail the plan (most callers never
+  // use that entry point); fc_tx_synthesize_static retries and reports it.
+  fc_internal_static_resolve(device);
   *out = pl;
   return FC_OK;
 }

@@ -13,6 +13,7 @@
 // with FC_FLAG_IO_BF16 a TX slot (frame + tail) and an RX estimate are rounded to BF16
 // once, when written to the caller's buffer, and BF16 inputs widen to FP32 exactly.
 #include <cstdio>
+#include <cstring>
 
 #include <cuda_bf16.h>
 
@@ -190,25 +191,53 @@ void fc_state_destroy(fc_state* state) {
   delete state;
 }
 
+// A checkpoint is a 48-byte header that names the state it came from, then the device
+// range [tail, tail + 2 n_streams D): every stream's TX tail, then every stream's
+// look-behind (one allocation, see fc_state_create). The header lets an import refuse a
+// checkpoint of another shape whose data happens to have the same byte count (two
+// streams of D samples against one of 2D).
+namespace {
+constexpr uint32_t kCkptMagic = 0x31534346u;   // "FCS1"
+struct CkptHeader {
+  uint32_t magic;
+  int32_t n_streams;
+  int64_t delay, slot_len, wave_len;
+  int64_t reserved[2];
+};
+static_assert(sizeof(CkptHeader) == 48, "checkpoint header layout");
+
+CkptHeader header_of(const fc_state* st) {
+  CkptHeader h{};
+  h.magic = kCkptMagic;
+  h.n_streams = st->n_streams;
+  h.delay = st->delay;
+  h.slot_len = st->slot_len;
+  h.wave_len = st->wave_len;
+  return h;
+}
+}  // namespace
+
 int fc_state_bytes(const fc_state* state, uint64_t* bytes) {
   if (!state || !bytes) return fc_internal_fail(FC_ERR_INVALID, "state or bytes is NULL");
-  *bytes = (uint64_t)(2 * (long long)state->n_streams * state->delay) * sizeof(float2);
+  *bytes = sizeof(CkptHeader) + (uint64_t)(2 * (long long)state->n_streams * state->delay) * sizeof(float2);
   return FC_OK;
 }
 
-// The checkpoint is the device range [tail, tail + 2 n_streams D): every stream's TX tail,
-// then every stream's look-behind (one allocation, see fc_state_create).
 int fc_state_export(const fc_state* state, void* host, uint64_t bytes, void* stream) {
   FcRange nvtx_range(__func__);
   uint64_t need = 0;
   const int rc = fc_state_bytes(state, &need);
   if (rc != FC_OK) return rc;
-  if (need == 0) return FC_OK;
   if (!host || bytes < need) return fc_internal_fail(FC_ERR_INVALID, "host buffer missing or too small");
+  const CkptHeader h = header_of(state);
+  memcpy(host, &h, sizeof h);
+  const uint64_t data = need - sizeof(CkptHeader);
+  if (data == 0) return FC_OK;
   DevGuard dg(state->device);
   if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
   const cudaStream_t cs = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(host, state->tail, (size_t)need, cudaMemcpyDeviceToHost, cs);
+  cudaError_t e = cudaMemcpyAsync(static_cast<unsigned char*>(host) + sizeof(CkptHeader), state->tail, (size_t)data,
+                                  cudaMemcpyDeviceToHost, cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   return e == cudaSuccess ? FC_OK : cuda_err(e, "state export");
 }
@@ -218,13 +247,23 @@ int fc_state_import(fc_state* state, const void* host, uint64_t bytes, void* str
   uint64_t need = 0;
   const int rc = fc_state_bytes(state, &need);
   if (rc != FC_OK) return rc;
-  if (bytes != need) return fc_internal_fail(FC_ERR_INVALID, "checkpoint size does not match the state");
-  if (need == 0) return FC_OK;
   if (!host) return fc_internal_fail(FC_ERR_INVALID, "host is NULL");
+  if (bytes != need) return fc_internal_fail(FC_ERR_INVALID, "checkpoint size does not match the state");
+  CkptHeader h;
+  memcpy(&h, host, sizeof h);
+  const CkptHeader want = header_of(state);
+  if (h.magic != kCkptMagic) return fc_internal_fail(FC_ERR_INVALID, "not a stream-state checkpoint");
+  if (h.n_streams != want.n_streams || h.delay != want.delay || h.slot_len != want.slot_len ||
+      h.wave_len != want.wave_len)
+    return fc_internal_fail(FC_ERR_INVALID,
+                            "checkpoint of another state (stream count, delay, slot or frame length differ)");
+  const uint64_t data = need - sizeof(CkptHeader);
+  if (data == 0) return FC_OK;
   DevGuard dg(state->device);
   if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
   const cudaStream_t cs = (cudaStream_t)stream;
-  cudaError_t e = cudaMemcpyAsync(state->tail, host, (size_t)need, cudaMemcpyHostToDevice, cs);
+  cudaError_t e = cudaMemcpyAsync(state->tail, static_cast<const unsigned char*>(host) + sizeof(CkptHeader),
+                                  (size_t)data, cudaMemcpyHostToDevice, cs);
   if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
   return e == cudaSuccess ? FC_OK : cuda_err(e, "state import");
 }

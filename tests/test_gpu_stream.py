@@ -9,6 +9,7 @@ import pytest
 
 import workloads as wl
 from oracle import fc_oracle as fo
+from tests import parity
 from tests.test_stream_semantics import STREAMABLE, k_slots, slot_len, stack_grids
 
 pytestmark = pytest.mark.gpu
@@ -59,6 +60,7 @@ def run_stream_case(torch, geom, K, S, seed):
             worst_tx = max(worst_tx, rel(tx_stream[s, k * T:(k + 1) * T], ref[k * T:(k + 1) * T]))
         if D:
             worst_tx = max(worst_tx, rel(tx_stream[s, K * T:K * T + D], ref[K * T:]))
+        parity.check(tx_stream[s, :K * T + D], ref, TOL, parity.wave_windows(big_geom), ("tx", s))
     # ---- RX: the K-slot frame plus noise, one priming call, then K calls ----
     x = np.stack([c64(wl.awgn(refs[s], 30.0, seed + 7919 * (s + 1))).astype(np.complex128) for s in range(S)])
     prime = np.zeros((S, T), dtype=np.complex128)
@@ -76,9 +78,12 @@ def run_stream_case(torch, geom, K, S, seed):
         ref = fo.split_grid(big_geom, fo.rx_frame(big_geom, x[s]))
         for k in range(K):
             got = fo.split_grid(geom, est[k][s])
+            want = []
             for m in range(len(geom.subbands)):
                 B = geom.groups[geom.subbands[m].group].n_symbols
                 worst_rx = max(worst_rx, rel(got[m], ref[m][k * B:(k + 1) * B]))
+                want.append(ref[m][k * B:(k + 1) * B].reshape(-1))
+            parity.check(est[k][s], np.concatenate(want), TOL, parity.grid_windows(geom), ("rx", s, k))
     st.close()
     plan.close()
     return worst_tx, worst_rx
@@ -126,8 +131,8 @@ def test_state_reset_restarts_the_stream(torch_cuda):
 def test_state_checkpoint_resumes_the_stream(torch_cuda):
     """fc_state_export / fc_state_import: a stream interrupted after two slots and resumed
     from its checkpoint in a new state gives what the uninterrupted stream gives, TX and
-    RX (to rounding: reductions may add in another order); a checkpoint of another size is
-    refused."""
+    RX (to rounding: reductions may add in another order); a checkpoint of another size,
+    or one whose header names another state, is refused."""
     torch = torch_cuda
     from paper_2008_00672_gb300 import FcError, Plan, State
     geom = STREAMABLE[0][1]
@@ -151,7 +156,7 @@ def test_state_checkpoint_resumes_the_stream(torch_cuda):
     first = State(plan, S)
     got = [step(first, k) for k in range(2)]
     ckpt = first.export()
-    assert ckpt.size == 2 * S * plan.stream_delay * 8
+    assert ckpt.size == 48 + 2 * S * plan.stream_delay * 8
     first.close()
     resumed = State(plan, S)
     resumed.load(ckpt)
@@ -160,6 +165,10 @@ def test_state_checkpoint_resumes_the_stream(torch_cuda):
         assert rel(go, ro) < 1e-6 and rel(ge, re) < 1e-6, (k, rel(go, ro), rel(ge, re))
     with pytest.raises(FcError):
         resumed.load(ckpt[:-8])
+    forged = ckpt.copy()
+    forged[4:8] = np.frombuffer(np.int32(S + 1).tobytes(), dtype=np.uint8)   # header: another stream count
+    with pytest.raises(FcError):
+        resumed.load(forged)
     whole.close()
     resumed.close()
     plan.close()

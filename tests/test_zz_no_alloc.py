@@ -3,8 +3,11 @@
 fc_tx_synthesize_static serves callers that cannot allocate device memory at
 run time (its workspace is an array built into the library). This test calls it
 through the C ABI twice in a row, with different inputs, and checks each output
-against fc_tx_synthesize with a caller-allocated workspace on the same input.
-It lives in its own file, collected last, and needs nothing from earlier tests.
+against fc_tx_synthesize with a caller-allocated workspace on the same input, and
+its first stream against the FP64 oracle. Around the second call it also checks the
+property the entry point is named for: the device's free memory and torch's
+allocated bytes do not change. It lives in its own file, collected last, and needs
+nothing from earlier tests.
 """
 import ctypes
 
@@ -12,6 +15,8 @@ import numpy as np
 import pytest
 
 import workloads as wl
+from oracle import fc_oracle as fo
+from tests import parity
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-5
@@ -39,12 +44,18 @@ def test_static_workspace_tx_matches_allocating_tx():
         ref = torch.empty((n, plan.wave_len), dtype=torch.complex64, device="cuda")
         plan.tx_synthesize(grid, ref)
         out = torch.full((n, plan.wave_len), float("nan"), dtype=torch.complex64, device="cuda")
+        torch.cuda.synchronize()
+        free0, used0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         st = lib.fc_tx_synthesize_static(plan.handle, n, ctypes.c_void_p(grid.data_ptr()),
                                          ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(stream))
         assert st == fc.FC_OK, lib.fc_last_error().decode()
         torch.cuda.synchronize()
+        if call == 1:       # the first call may load kernel code; the second allocates nothing at all
+            assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == used0
         err = rel(out.cpu().numpy(), ref.cpu().numpy())
         assert err <= TOL, (call, err)
+        parity.check(out[0].cpu().numpy(), fo.tx_frame(geom, grid[0].cpu().numpy().astype(np.complex128)), TOL,
+                     parity.wave_windows(geom), call)
 
     # more streams than the built-in workspace holds: a clear error, nothing launched
     too_many = (1 << 25) // plan.workspace_per_stream + 1
