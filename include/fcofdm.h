@@ -392,14 +392,28 @@ void fc_batch_destroy(fc_batch* batch);
 
 /*
  * Serving loop (no counterpart in the paper; the deployment around the FC path).
- * A server holds admitted carriers, each with a device-resident plan, a one-stream
- * fc_state and one slot of device input/output, and serves slot requests of those
- * carriers as they arrive. fc_server_run replays a request list in real time: each
- * request is issued at its arrival time on its carrier's lane (host-to-device copy of
- * the input, the stream call, device-to-host copy of the output), with no batch
- * boundary, and its latency (arrival to observed completion, host clock) is returned.
- * Requests of one carrier run in order, so each carrier's results equal its own stream
- * calls whatever else the server is doing.
+ * A server holds admitted carriers, each with a device-resident plan and a one-stream
+ * fc_state (the TX tail and RX look-behind that join consecutive slots), and serves
+ * slot requests of those carriers as they arrive, with continuous batching:
+ *  - A request is admitted when its input, output and workspace fit in the server's
+ *    request arena (device memory reserved by fc_server_set_limits) and no request of
+ *    the same carrier and direction is already in the batch being formed; admitted
+ *    requests wait in arrival order otherwise. Its arena space is freed when its output
+ *    has reached the host.
+ *  - Whenever fewer than max_inflight batches are on the device, the admitted requests
+ *    form the next batch (at most max_batch): their host-to-device copies on one CUDA
+ *    stream, their compute on a second, their device-to-host copies on a third, so
+ *    a batch's copies overlap the previous batch's compute. Within a batch, the slot
+ *    calls of every symbol-synchronized complex64 carrier run together: one persistent
+ *    launch of the generic kernels per direction and kernel class over all of them, with
+ *    one batched TX epilogue and one batched RX prologue around it. Other requests
+ *    (continuous mode, tensor-core and complex-BF16 carriers) run their own stream calls
+ *    on the server's lanes inside the same batch, concurrently with it.
+ *  - Requests of one carrier and direction run in arrival order (batches execute in
+ *    order on the compute stream), so each carrier's results equal its own stream calls
+ *    whatever else the server is doing.
+ * Latency is measured on the host clock from a request's arrival to the moment its
+ * batch's completion event is seen.
  */
 typedef struct fc_server fc_server;
 
@@ -412,19 +426,43 @@ typedef struct fc_serve_request {
   void* host_out;
 } fc_serve_request;
 
-/* n_lanes CUDA streams; admission keeps hbm_reserve_bytes of device memory free. */
+/* What fc_server_serve reports per request. */
+typedef struct fc_serve_record {
+  double latency_s;        /* arrival to observed completion (host clock)                */
+  double wait_s;           /* arrival to admission into a batch (host clock)             */
+  int32_t batch;           /* index of the batch it ran in                               */
+  int32_t batched;         /* 1: in the batch's persistent launch; 0: its own stream call */
+  float device_start_ms;   /* the batch's compute interval on the device (CUDA events),  */
+  float device_end_ms;     /*   relative to the start of the first batch's compute       */
+} fc_serve_record;
+
+/* n_lanes CUDA streams; admission keeps hbm_reserve_bytes of device memory free. The
+   request arena starts at min(256 MiB, free memory above the reserve / 2); max_batch 64,
+   max_inflight 2. */
 int fc_server_create(int32_t device, int32_t n_lanes, uint64_t hbm_reserve_bytes, fc_server** out);
 
+/* Sets the request arena (device bytes for the inputs, outputs and workspaces of
+   admitted requests; reallocated here, never during serving), the largest batch and the
+   number of batches on the device at once (1..8). FC_ERR_NOMEM when the arena does not
+   fit above the reserve; FC_ERR_INVALID for out-of-range values. Not while serving. */
+int fc_server_set_limits(fc_server* server, uint64_t arena_bytes, int32_t max_batch, int32_t max_inflight);
+
 /* Admits a carrier (its geometry must stream: fc_sizes.slot_len > 0). FC_ERR_NOMEM,
-   with nothing allocated, when its plan, state and buffers would not fit in the free
-   device memory above the reserve. */
+   with nothing allocated, when its plan and state would not fit in the free device
+   memory above the reserve, or when one of its requests could never fit in the arena. */
 int fc_server_add_carrier(fc_server* server, const fc_geometry* geometry, int32_t* carrier_id);
 
 /* The sizes of an admitted carrier (grid_len, slot_len, ...). */
 int fc_server_carrier_sizes(const fc_server* server, int32_t carrier, fc_sizes* out);
 
-/* Replays `requests` (sorted by arrival) in real time; latency_s[i] gets request i's
-   latency in seconds. Returns when every request has completed. */
+/* Replays `requests` (sorted by arrival) in real time; records[i] (may be NULL) gets
+   request i's latency, wait, batch and device interval. Returns when every request has
+   completed. Host output buffers of one carrier and direction may be shared between
+   requests only if the caller does not need the earlier results. */
+int fc_server_serve(fc_server* server, const fc_serve_request* requests, int32_t n_requests,
+                    fc_serve_record* records);
+
+/* fc_server_serve reporting only the latencies (seconds) into latency_s. */
 int fc_server_run(fc_server* server, const fc_serve_request* requests, int32_t n_requests, double* latency_s);
 
 /* Frees every carrier and the lanes (after synchronising them). Safe on NULL. */

@@ -175,8 +175,51 @@ int fc_internal_static_resolve(int dev);             // look up the static TX wo
 // dynamic shared memory.
 bool fc_internal_sync_work(const fc_plan* plan, int dir, int n_streams, const void* in, void* out,
                            std::vector<FcWork>& work, size_t* smem);
+// The same for a serving batch: the generic kernels whatever the plan would pick for a
+// frame call (complex64 symbol-sync plans only), with the smallest chunk count per
+// stream of at least want_chunks (the largest the plan has if none).
+bool fc_internal_sync_work_generic(const fc_plan* plan, int dir, int n_streams, const void* in, void* out,
+                                   int want_chunks, std::vector<FcWork>& work, size_t* smem);
 // The generic-kernel set a plan runs on.
 const FcGenKernels& fc_internal_gen(const fc_plan* plan);
+
+// Stream-state internals for the serving loop's batched slot calls (fc_stream.cu).
+struct FcStateView {
+  float2* tx_frame;   // [n_streams][wave_len]
+  float2* rx_frame;   // [n_streams][wave_len]
+  float2* tail;       // [n_streams][delay]
+  float2* look;       // [n_streams][delay]
+  long long wave_len, slot_len, delay;
+  int n_streams;
+};
+int fc_internal_state_view(const fc_state* state, FcStateView* out);
+// One slot of one stream, complex64, with the carried samples given by pointer, so that
+// several consecutive slots of one stream can be finished by one launch: TX epilogue
+// out = frame[0, T) with prev_tail added to the first D samples (prev_tail = the state's
+// tail, or the previous slot's frame + T); RX prologue frame = [prev_look; in] (prev_look
+// = the state's look-behind, or the previous slot's input + T - D). FcSlotCarry then
+// moves the last slot's carry into the state (dst[0, D) = src[0, D)), in a later launch.
+struct FcSlotTx {
+  const float2* frame;
+  const float2* prev_tail;
+  float2* out;
+  long long T, D;
+};
+struct FcSlotRx {
+  const float2* in;
+  const float2* prev_look;
+  float2* frame;
+  long long T, D;
+};
+struct FcSlotCarry {
+  const float2* src;
+  float2* dst;
+  long long D;
+};
+// One launch over n items (device arrays); max_len = the longest T (TX), T + D (RX) or D.
+cudaError_t fc_launch_slot_tx_multi(const FcSlotTx* items, int n, long long max_len, cudaStream_t st);
+cudaError_t fc_launch_slot_rx_multi(const FcSlotRx* items, int n, long long max_len, cudaStream_t st);
+cudaError_t fc_launch_slot_carry_multi(const FcSlotCarry* items, int n, long long max_len, cudaStream_t st);
 // A frame call (direction FC_TX / FC_RX) with the I/O types io (FC_IO_* bits) instead of
 // the plan's own; the stream calls use it to keep their frames in FP32. Same checks and
 // status as fc_tx_synthesize / fc_rx_analyze.

@@ -839,6 +839,21 @@ bool fc_internal_sync_work(const fc_plan* plan, int dir, int n_streams, const vo
   return true;
 }
 
+bool fc_internal_sync_work_generic(const fc_plan* plan, int dir, int n_streams, const void* in, void* out,
+                                   int want_chunks, std::vector<FcWork>& work, size_t* smem) {
+  if (!plan || plan->h.mode != FC_SYMBOL_SYNC || n_streams < 1 || plan->io != 0) return false;
+  if (plan->h.flags & FC_FLAG_IO_TIME) return false;
+  size_t k = 0;
+  while (k + 1 < plan->splits.size() && plan->splits[k] < want_chunks) ++k;
+  const FcChunk* chunks = dir == FC_TX ? plan->tx_chunks[k] : plan->rx_chunks[k];
+  const int n_chunks = dir == FC_TX ? plan->tx_nchunks[k] : plan->rx_nchunks[k];
+  for (int s = 0; s < n_streams; ++s)
+    for (int ch = 0; ch < n_chunks; ++ch)
+      work.push_back(FcWork{plan->d_plan, plan->d_jobs, chunks + ch, in, out, s, 0});
+  *smem = dir == FC_TX ? plan->smem_tx : plan->smem_rx;
+  return true;
+}
+
 extern "C" {
 
 int fc_plan_create(fc_plan** out, const fc_geometry* geometry, int32_t device) {

@@ -96,6 +96,36 @@ __global__ void k_stream_rx(const TI* __restrict__ in, float2* __restrict__ look
   }
 }
 
+// Batched slot epilogue / prologue of the serving loop: item blockIdx.y, samples over
+// blockIdx.x (grid-stride); the per-sample rules of k_stream_tx / k_stream_rx with the
+// carried samples read from prev_tail / prev_look and the state updated by a later
+// k_slot_carry_multi launch (the items of one launch only read what they share).
+__global__ void k_slot_tx_multi(const FcSlotTx* __restrict__ items, int n) {
+  const FcSlotTx it = items[blockIdx.y];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < it.T; t += (long long)gridDim.x * blockDim.x) {
+    float2 v = it.frame[t];
+    if (t < it.D) {
+      const float2 c = it.prev_tail[t];
+      v.x += c.x;
+      v.y += c.y;
+    }
+    it.out[t] = v;
+  }
+}
+
+__global__ void k_slot_rx_multi(const FcSlotRx* __restrict__ items, int n) {
+  const FcSlotRx it = items[blockIdx.y];
+  const long long Q = it.T + it.D;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < Q; t += (long long)gridDim.x * blockDim.x)
+    it.frame[t] = t < it.D ? it.prev_look[t] : it.in[t - it.D];
+}
+
+__global__ void k_slot_carry_multi(const FcSlotCarry* __restrict__ items, int n) {
+  const FcSlotCarry it = items[blockIdx.y];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < it.D; t += (long long)gridDim.x * blockDim.x)
+    it.dst[t] = it.src[t];
+}
+
 int grid_for(long long total) {
   long long b = (total + 255) / 256;
   const long long cap = 152LL * 16;   // grid-stride beyond this
@@ -119,6 +149,46 @@ int check_state(const fc_plan* plan, const fc_state* st, const void* in, const v
 }
 
 }  // namespace
+
+int fc_internal_state_view(const fc_state* st, FcStateView* out) {
+  if (!st || !out) return fc_internal_fail(FC_ERR_INVALID, "state is NULL");
+  out->tx_frame = st->tx_frame;
+  out->rx_frame = st->rx_frame;
+  out->tail = st->tail;
+  out->look = st->look;
+  out->wave_len = st->wave_len;
+  out->slot_len = st->slot_len;
+  out->delay = st->delay;
+  out->n_streams = st->n_streams;
+  return FC_OK;
+}
+
+cudaError_t fc_launch_slot_tx_multi(const FcSlotTx* items, int n, long long max_len, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  long long bx = (max_len + 255) / 256;
+  if (bx > 64) bx = 64;
+  if (bx < 1) bx = 1;
+  k_slot_tx_multi<<<dim3((unsigned)bx, (unsigned)n), 256, 0, st>>>(items, n);
+  return cudaGetLastError();
+}
+
+cudaError_t fc_launch_slot_rx_multi(const FcSlotRx* items, int n, long long max_len, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  long long bx = (max_len + 255) / 256;
+  if (bx > 64) bx = 64;
+  if (bx < 1) bx = 1;
+  k_slot_rx_multi<<<dim3((unsigned)bx, (unsigned)n), 256, 0, st>>>(items, n);
+  return cudaGetLastError();
+}
+
+cudaError_t fc_launch_slot_carry_multi(const FcSlotCarry* items, int n, long long max_len, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  long long bx = (max_len + 255) / 256;
+  if (bx > 64) bx = 64;
+  if (bx < 1) bx = 1;
+  k_slot_carry_multi<<<dim3((unsigned)bx, (unsigned)n), 256, 0, st>>>(items, n);
+  return cudaGetLastError();
+}
 
 extern "C" {
 

@@ -35,6 +35,7 @@ EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize
             "fc_state_destroy", "fc_tx_synthesize_stream", "fc_rx_analyze_stream", "fc_plan_autotune",
             "fc_plan_choice", "fc_batch_create", "fc_batch_launch", "fc_batch_destroy", "fc_server_create",
             "fc_server_add_carrier", "fc_server_carrier_sizes", "fc_server_run", "fc_server_destroy",
+            "fc_server_serve", "fc_server_set_limits",
             "fc_plan_device_status", "fc_plan_set_choice", "fc_pipeline_create", "fc_pipeline_destroy",
             "fc_tx_synthesize_host", "fc_rx_analyze_host")
 
@@ -74,6 +75,11 @@ class FcBatchItem(ctypes.Structure):
 class FcServeRequest(ctypes.Structure):
     _fields_ = [("arrival_s", ctypes.c_double), ("carrier", ctypes.c_int32), ("direction", ctypes.c_int32),
                 ("host_in", ctypes.c_void_p), ("host_out", ctypes.c_void_p)]
+
+
+class FcServeRecord(ctypes.Structure):
+    _fields_ = [("latency_s", ctypes.c_double), ("wait_s", ctypes.c_double), ("batch", ctypes.c_int32),
+                ("batched", ctypes.c_int32), ("device_start_ms", ctypes.c_float), ("device_end_ms", ctypes.c_float)]
 
 
 _lib = None
@@ -139,6 +145,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fc_server_carrier_sizes.restype = ctypes.c_int
         lib.fc_server_run.argtypes = [vp, ctypes.POINTER(FcServeRequest), i32, ctypes.POINTER(ctypes.c_double)]
         lib.fc_server_run.restype = ctypes.c_int
+        lib.fc_server_serve.argtypes = [vp, ctypes.POINTER(FcServeRequest), i32, ctypes.POINTER(FcServeRecord)]
+        lib.fc_server_serve.restype = ctypes.c_int
+        lib.fc_server_set_limits.argtypes = [vp, ctypes.c_uint64, i32, i32]
+        lib.fc_server_set_limits.restype = ctypes.c_int
         lib.fc_server_destroy.argtypes = [vp]
         lib.fc_server_destroy.restype = None
         lib.fc_plan_device_status.argtypes = [vp]
@@ -342,6 +352,19 @@ def fc_server_run(server, requests) -> list:
     lat = (ctypes.c_double * len(requests))()
     _check(load_library().fc_server_run(server, arr, len(requests), lat), "fc_server_run")
     return list(lat)
+
+
+def fc_server_serve(server, requests) -> list:
+    """requests: sequence of FcServeRequest; returns one FcServeRecord per request."""
+    arr = (FcServeRequest * len(requests))(*requests)
+    rec = (FcServeRecord * len(requests))()
+    _check(load_library().fc_server_serve(server, arr, len(requests), rec), "fc_server_serve")
+    return list(rec)
+
+
+def fc_server_set_limits(server, arena_bytes: int, max_batch: int = 64, max_inflight: int = 2):
+    _check(load_library().fc_server_set_limits(server, int(arena_bytes), int(max_batch), int(max_inflight)),
+           "fc_server_set_limits")
 
 
 def fc_server_destroy(server):
@@ -579,9 +602,10 @@ class Batch:
 
 
 class Server:
-    """Owns one fc_server. add_carrier(geom) -> id; run(requests) replays
-    (arrival_s, carrier, direction, host_in, host_out) requests in real time with
-    page-locked CPU tensors and returns the latencies (seconds)."""
+    """Owns one fc_server. add_carrier(geom) -> id; run(requests) / serve(requests)
+    replay (arrival_s, carrier, direction, host_in, host_out) requests in real time with
+    page-locked CPU tensors (continuous batching) and return the latencies (seconds) /
+    the per-request records."""
 
     def __init__(self, device: int = 0, n_lanes: int = 8, hbm_reserve_bytes: int = 0):
         self.handle = fc_server_create(device, n_lanes, hbm_reserve_bytes)
@@ -592,8 +616,16 @@ class Server:
         self.sizes.append(fc_server_carrier_sizes(self.handle, cid))
         return cid
 
+    def set_limits(self, arena_bytes: int, max_batch: int = 64, max_inflight: int = 2):
+        fc_server_set_limits(self.handle, arena_bytes, max_batch, max_inflight)
+
     def run(self, requests):
-        import torch
+        """Latencies (seconds) of the requests."""
+        return [r.latency_s for r in self.serve(requests)]
+
+    def serve(self, requests):
+        """One FcServeRecord per request: latency, wait, batch, whether it ran in the
+        batch's persistent launch, the batch's device compute interval."""
         reqs = []
         for t, cid, direction, h_in, h_out in requests:
             z = self.sizes[cid]
@@ -602,7 +634,7 @@ class Server:
                 if Plan._samples(x, z.sample_bytes == 4, cuda=False) != n:
                     raise ValueError("expected host tensors of the carrier's sizes")
             reqs.append(FcServeRequest(float(t), int(cid), int(direction), h_in.data_ptr(), h_out.data_ptr()))
-        return fc_server_run(self.handle, reqs)
+        return fc_server_serve(self.handle, reqs)
 
     def close(self):
         if self.handle:
