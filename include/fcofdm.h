@@ -315,6 +315,16 @@ int fc_tx_synthesize_static(const fc_plan* plan, int32_t n_streams, const void* 
    word. */
 int fc_plan_device_status(const fc_plan* plan);
 
+/* Test hook of the bounded waits (no counterpart in the paper). Sets how many times
+   each CTA of this plan's tensor-core kernels polls its first GEMM-completion mbarrier
+   before it gives up (default 2^22, the limit every other wait keeps). With 0 the first
+   wait gives up at once: the CTA records the failure, waits (with the default limit)
+   for its copy and GEMM in flight, releases its tensor memory and returns, so the next
+   fc_plan_device_status reports FC_ERR_TIMEOUT and the call's output is wrong; the plan
+   stays usable. Not to be changed while a call of the plan is being issued.
+   FC_ERR_INVALID for a NULL plan. */
+int fc_plan_set_first_wait_limit(fc_plan* plan, uint32_t polls);
+
 /* Directions, for the autotuner and the batch executor. */
 #define FC_TX 0
 #define FC_RX 1

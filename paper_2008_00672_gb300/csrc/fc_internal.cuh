@@ -152,7 +152,8 @@ const FcGenKernels& fc_gen_kernels_128();
 #define FC_TC_OFDM_MOD 4     // OFDM IDFT + CP insertion into the low-rate stream (L_OFDM = 4096)
 #define FC_TC_OFDM_DEMOD 5   // CP removal + OFDM DFT + active bins (overlap-save RX stream)
 cudaError_t fc_launch_tc(const FcPlanDev* dP, const unsigned char* dft64, int pass, int n_streams, int n_blocks,
-                         const float2* in, float2* out, float2* ws, int* err, int num_sms, cudaStream_t st);
+                         const float2* in, float2* out, float2* ws, int* err, int num_sms, cudaStream_t st,
+                         unsigned first_wait = 1u << 22);
 cudaError_t fc_set_tc_smem_limits();
 void fc_tc_dft64_image(unsigned char* out);
 size_t fc_tc_dft64_image_bytes();

@@ -118,6 +118,7 @@ struct fc_plan {
   bool tc_ofdm = false;                     // and the OFDM (I)DFT too (L_OFDM = 4096)
   const unsigned char* d_dft64 = nullptr;   // DFT-64 B operand images (hi, lo)
   int* d_err = nullptr;                     // device error word of the tensor-core kernels
+  unsigned tc_first_wait = 1u << 22;        // poll limit of the tensor-core kernels' first GEMM wait
   FcJob* d_wjobs = nullptr;                 // one stream's jobs in cost order (warp kernels)
   size_t smem_tx = 0, smem_rx = 0, smem_ofdm = 0;
   int syms_per_stream = 0;
@@ -742,17 +743,17 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* 
     const int R = plan->h.g[0].R;
     cudaError_t e = plan->tc_ofdm ? fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_OFDM_MOD, n_streams,
                                                  plan->h.g[0].B, grid, nullptr, workspace, plan->d_err,
-                                                 plan->num_sms, st)
+                                                 plan->num_sms, st, plan->tc_first_wait)
                                   : gen.ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, grid,
                                                         workspace, 0, plan->smem_ofdm, st);
     if (e == cudaSuccess)
       e = cudaMemsetAsync(wave, 0, (size_t)n_streams * plan->h.frame_len * sizeof(float2), st);
     if (e == cudaSuccess)
       e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_TX_FFT, n_streams, R, nullptr, nullptr, workspace,
-                       plan->d_err, plan->num_sms, st);
+                       plan->d_err, plan->num_sms, st, plan->tc_first_wait);
     if (e == cudaSuccess)
       e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_TX_IFFT, n_streams, R, nullptr, wave, workspace,
-                       plan->d_err, plan->num_sms, st);
+                       plan->d_err, plan->num_sms, st, plan->tc_first_wait);
     return e;
   }
   cudaError_t e = gen.ofdm_mod(plan->d_plan, plan->syms_per_stream, n_streams, in, workspace, io,
@@ -778,13 +779,13 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* 
   if (plan->tc_rx && !c.generic && io == 0) {
     const int R = plan->h.g[0].R;
     cudaError_t e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_RX_FFT, n_streams, R, wave, nullptr, workspace,
-                                 plan->d_err, plan->num_sms, st);
+                                 plan->d_err, plan->num_sms, st, plan->tc_first_wait);
     if (e == cudaSuccess)
       e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_RX_IFFT, n_streams, R, nullptr, nullptr, workspace,
-                       plan->d_err, plan->num_sms, st);
+                       plan->d_err, plan->num_sms, st, plan->tc_first_wait);
     if (e == cudaSuccess)
       e = plan->tc_ofdm ? fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_OFDM_DEMOD, n_streams, plan->h.g[0].B,
-                                       nullptr, grid, workspace, plan->d_err, plan->num_sms, st)
+                                       nullptr, grid, workspace, plan->d_err, plan->num_sms, st, plan->tc_first_wait)
                         : gen.ofdm_demod(plan->d_plan, plan->syms_per_stream, n_streams, workspace, grid,
                                                 0, plan->smem_ofdm, st);
     return e;
@@ -1043,6 +1044,12 @@ int fc_plan_device_status(const fc_plan* plan) {
   if (e == cudaSuccess && v) e = cudaMemset(plan->d_err, 0, sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
   return v ? fail(FC_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs") : FC_OK;
+}
+
+int fc_plan_set_first_wait_limit(fc_plan* plan, uint32_t polls) {
+  if (!plan) return fail(FC_ERR_INVALID, "plan is NULL");
+  plan->tc_first_wait = polls;
+  return FC_OK;
 }
 
 void fc_plan_destroy(fc_plan* plan) {

@@ -87,6 +87,7 @@ struct TcArgs {
   float2* out;                  // wave (TX_IFFT) or workspace
   float2* ws;                   // workspace base
   int* err;                     // set to 1 when a bounded wait gives up
+  unsigned first_wait;          // poll limit of each CTA's first GEMM-completion wait
 };
 
 // FC parameters of the one subband, read once per CTA into registers (reading them
@@ -413,9 +414,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
     mma_pending = true;
     mma_issue = phase;
   };
-  // wait for the last issued GEMM; false when the bounded wait gave up
+  // wait for the last issued GEMM; false when the bounded wait gave up. The CTA's first
+  // such wait polls at most args.first_wait times (normally the same 2^22 as every other
+  // wait; a test sets it to zero to exercise the exit below)
+  bool first_wait = true;
   auto wait_mma = [&]() -> bool {
-    if (mbar_wait(&bar, phase)) {
+    const uint32_t limit = first_wait ? args.first_wait : (1u << 22);
+    first_wait = false;
+    if (mbar_wait(&bar, phase, limit)) {
       mma_pending = false;
     } else {
       atomicExch(args.err, 1);
@@ -489,8 +495,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_fc(const TcArgs args) {
 }  // namespace
 
 cudaError_t fc_launch_tc(const FcPlanDev* dP, const unsigned char* dft64, int pass, int n_streams, int n_blocks,
-                         const float2* in, float2* out, float2* ws, int* err, int num_sms, cudaStream_t st) {
-  TcArgs a{dP, dft64, pass, n_streams, in, out, ws, err};
+                         const float2* in, float2* out, float2* ws, int* err, int num_sms, cudaStream_t st,
+                         unsigned first_wait) {
+  TcArgs a{dP, dft64, pass, n_streams, in, out, ws, err, first_wait};
   const int tiles = (n_streams * n_blocks + 1) / 2;
   const int grid = tiles < num_sms ? tiles : num_sms;
   if (grid < 1) return cudaSuccess;

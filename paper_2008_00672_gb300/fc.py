@@ -35,7 +35,7 @@ EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize
             "fc_state_destroy", "fc_tx_synthesize_stream", "fc_rx_analyze_stream", "fc_plan_autotune",
             "fc_plan_choice", "fc_batch_create", "fc_batch_launch", "fc_batch_destroy", "fc_server_create",
             "fc_server_add_carrier", "fc_server_carrier_sizes", "fc_server_run", "fc_server_destroy",
-            "fc_server_serve", "fc_server_set_limits",
+            "fc_server_serve", "fc_server_set_limits", "fc_plan_set_first_wait_limit",
             "fc_plan_device_status", "fc_plan_set_choice", "fc_pipeline_create", "fc_pipeline_destroy",
             "fc_tx_synthesize_host", "fc_rx_analyze_host")
 
@@ -145,6 +145,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fc_server_carrier_sizes.restype = ctypes.c_int
         lib.fc_server_run.argtypes = [vp, ctypes.POINTER(FcServeRequest), i32, ctypes.POINTER(ctypes.c_double)]
         lib.fc_server_run.restype = ctypes.c_int
+        lib.fc_plan_set_first_wait_limit.argtypes = [vp, ctypes.c_uint32]
+        lib.fc_plan_set_first_wait_limit.restype = ctypes.c_int
         lib.fc_server_serve.argtypes = [vp, ctypes.POINTER(FcServeRequest), i32, ctypes.POINTER(FcServeRecord)]
         lib.fc_server_serve.restype = ctypes.c_int
         lib.fc_server_set_limits.argtypes = [vp, ctypes.c_uint64, i32, i32]

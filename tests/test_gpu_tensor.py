@@ -173,3 +173,40 @@ def test_tensor_rx_input_alignment(torch_cuda):
     assert np.array_equal(a, b)
     for s in range(S):
         parity.check(a[s], fo.rx_frame(geom, rx[s].astype(np.complex128)), TOL_TC, parity.grid_windows(geom), s)
+
+
+def test_bounded_wait_gives_up_and_reports_timeout(torch_cuda):
+    """FC_ERR_TIMEOUT without a fault: with the first GEMM-completion wait of every CTA
+    limited to zero polls, each CTA gives up at once, waits for its copy and GEMM in
+    flight, frees its tensor memory and returns. fc_plan_device_status then reports
+    FC_ERR_TIMEOUT once and FC_OK after; with the default limit back, the same plan
+    matches the oracle again (TX and RX)."""
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import Plan, fc
+    lib = fc.load_library()
+    geom = dataclasses.replace(wl.config_100mhz(1), flags=4)
+    S = 2
+    plan = Plan(geom)
+    grid = c64(wl.qam_grid(geom, S, 141))
+    g = torch.from_numpy(grid).cuda()
+    w = torch.empty((S, plan.wave_len), dtype=torch.complex64, device="cuda")
+    e = torch.empty_like(g)
+    assert lib.fc_plan_set_first_wait_limit(plan.handle, 0) == fc.FC_OK
+    plan.tx_synthesize(g, w)
+    plan.rx_analyze(w, e)
+    torch.cuda.synchronize()
+    assert lib.fc_plan_device_status(plan.handle) == fc.FC_ERR_TIMEOUT
+    assert lib.fc_plan_device_status(plan.handle) == fc.FC_OK          # reported once
+    assert lib.fc_plan_set_first_wait_limit(plan.handle, 1 << 22) == fc.FC_OK
+    plan.tx_synthesize(g, w)
+    torch.cuda.synchronize()
+    assert lib.fc_plan_device_status(plan.handle) == fc.FC_OK
+    wv = w.cpu().numpy()
+    for s in range(S):
+        parity.check(wv[s], fo.tx_frame(geom, grid[s].astype(np.complex128)), TOL_TC, parity.wave_windows(geom), s)
+    plan.rx_analyze(w, e)
+    torch.cuda.synchronize()
+    assert lib.fc_plan_device_status(plan.handle) == fc.FC_OK
+    ev = e.cpu().numpy()
+    parity.check(ev[0], fo.rx_frame(geom, wv[0].astype(np.complex128)), TOL_TC, parity.grid_windows(geom))
+    plan.close()
