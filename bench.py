@@ -293,6 +293,13 @@ def uneven_carriers_bench(torch, dev, st, steps: int) -> dict:
     batch.close()
     batch = Batch(items, n_lanes=8, use_graph=True, persistent=True)
     ms_persistent = timed(batch.launch, reps)
+    # the whole batch tuned as one (queued items' chunk count for the mix)
+    batch.autotune(reps=3)
+    ms_persistent_mix = timed(batch.launch, reps)
+    batch.close()
+    batch = Batch(items, n_lanes=8, use_graph=True)
+    batch.autotune(reps=3)
+    ms_graph_mix = timed(batch.launch, reps)
     batch.close()
     for c in cs:
         c[0].autotune(1, reps=3)
@@ -334,10 +341,16 @@ def uneven_carriers_bench(torch, dev, st, steps: int) -> dict:
             "samples_per_pass": samples, "kernels_per_pass": launches,
             "one_by_one_ms": round(ms_seq, 4), "batch_graph_ms": round(ms_graph, 4),
             "batch_graph_persistent_ms": round(ms_persistent, 4), "batch_graph_autotuned_ms": round(ms_tuned, 4),
+            "batch_graph_persistent_mix_tuned_ms": round(ms_persistent_mix, 4),
+            "batch_graph_mix_tuned_ms": round(ms_graph_mix, 4),
+            "tuning": "autotuned: each carrier's plan tuned alone (launch shape and radix schedules); mix_tuned: "
+                      "fc_batch_autotune timing the whole batch per candidate chunk count",
             "msamples_per_s": {"one_by_one": round(samples / ms_seq / 1e3, 1),
                                "batch_graph": round(samples / ms_graph / 1e3, 1),
                                "batch_graph_persistent": round(samples / ms_persistent / 1e3, 1),
-                               "batch_graph_autotuned": round(samples / ms_tuned / 1e3, 1)},
+                               "batch_graph_autotuned": round(samples / ms_tuned / 1e3, 1),
+                               "batch_graph_persistent_mix_tuned": round(samples / ms_persistent_mix / 1e3, 1),
+                               "batch_graph_mix_tuned": round(samples / ms_graph_mix / 1e3, 1)},
             "bf16_io": {"batch_graph_ms": round(ms_bf_graph, 4), "batch_graph_persistent_ms": round(ms_bf_persistent, 4),
                         "msamples_per_s": {"batch_graph": round(samples / ms_bf_graph / 1e3, 1),
                                            "batch_graph_persistent": round(samples / ms_bf_persistent / 1e3, 1)},

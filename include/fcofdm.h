@@ -342,11 +342,22 @@ int fc_plan_set_first_wait_limit(fc_plan* plan, uint32_t polls);
  * n_streams streams use it; other counts keep the built-in rule (the specialised
  * kernels where the plan has them; else chunks so that the call launches at least two
  * CTAs per SM, 128-thread CTAs where the call fills four per SM, else 256-thread CTAs
- * where they fit). Results do not depend on the choice beyond rounding. Allocates and
- * frees temporary device buffers and synchronises `stream`: call it at set-up, not
- * inside a stream capture.
+ * where they fit). Then, when a chosen shape runs the generic kernels, it tunes their
+ * radix schedules: for each transform size of the plan in turn, each candidate
+ * schedule (fc_plan_radices) is timed on those directions and the fastest is written
+ * into the plan's device tables, where every later generic launch of the plan reads it
+ * (whatever its stream count). Results do not depend on the choice beyond rounding.
+ * Allocates and frees temporary device buffers and synchronises `stream`: call it at
+ * set-up, not inside a stream capture or while calls of the plan are in flight.
  */
 int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* stream);
+
+/* The radix schedule of the plan's n-point transform on the generic kernels: passes in
+   order (radices 2, 3, 4, 8, 16; their product is n) into radices[0 .. *n_passes),
+   which must hold 8 entries. Built-in rule: every factor 3 as a radix-3 pass, last; the
+   power of two in ceil(a/4) balanced passes of at most radix 16, larger first; the
+   autotuner may change it. FC_ERR_INVALID when the plan has no n-point transform. */
+int fc_plan_radices(const fc_plan* plan, int32_t n, int32_t* radices, int32_t* n_passes);
 
 /* Records a launch shape for n_streams streams in `direction` without timing (e.g. one
    saved from an earlier fc_plan_autotune): chunks_per_stream must be one the plan has
@@ -398,6 +409,17 @@ typedef struct fc_batch fc_batch;
    FC_BATCH_PERSISTENT) the work queues. `mode` is an OR of the FC_BATCH_* bits. */
 int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes, int32_t mode, fc_batch** out);
 int fc_batch_launch(fc_batch* batch, void* stream);
+
+/* Autotuner of the batch as a whole (no counterpart in the paper): times reps passes of
+   the whole batch (its work, not a graph replay; on internal streams ordered after the
+   caller's `stream`) for each candidate and keeps the fastest for the mix, where tuning
+   each carrier alone does not find it. With FC_BATCH_PERSISTENT the candidates are the
+   queued items' chunks per stream (each plan's own rule, or one count 1..64 for every
+   complex64 symbol-synchronized frame call, which also puts the one-warp-per-symbol
+   carriers into the queues); otherwise one chunk count for every frame call, which each
+   item's plan keeps as its choice for that stream count and direction. A captured graph
+   is dropped and recaptured by the next fc_batch_launch. Returns when done. */
+int fc_batch_autotune(fc_batch* batch, int32_t reps, void* stream);
 void fc_batch_destroy(fc_batch* batch);
 
 /*

@@ -36,8 +36,11 @@ struct fc_batch {
   };
   std::vector<char> in_queue;                     // item runs through a queue
   std::vector<Queue> queues;
+  std::vector<void*> queue_mem;                   // work lists and counters of the queues
   int* d_next = nullptr;                          // one counter per queue
   int num_sms = 0;
+  int persistent = 0;
+  int want_chunks = 0;                            // chunks per stream of queued items (0: each plan's rule)
 };
 
 namespace {
@@ -104,6 +107,82 @@ void release(fc_batch* b) {
   for (cudaStream_t s : b->lanes) cudaStreamDestroy(s);
   if (b->origin) cudaStreamDestroy(b->origin);
   for (void* p : b->owned) cudaFree(p);
+  for (void* p : b->queue_mem) cudaFree(p);
+}
+
+// (Re)build the persistent work queues. Generic symbol-sync frame calls go to queues by
+// direction, by I/O type (complex64 or complex BF16), by kernel set (512-, 256- or
+// 128-thread CTAs) and by occupancy class (1, 2, 3 or 4 CTAs per SM for their shared
+// memory), items of the largest plans first (each CTA of a launch takes the next item).
+// want_chunks = 0 keeps each plan's own launch shape (calls that it runs on the
+// specialised kernels stay outside the queues); want_chunks > 0 queues every complex64
+// symbol-sync frame call, the one-warp-per-symbol carriers included, with that many
+// chunks per stream (the plan's nearest split).
+cudaError_t build_queues(fc_batch* b, int want_chunks) {
+  for (void* p : b->queue_mem) cudaFree(p);
+  b->queue_mem.clear();
+  b->queues.clear();
+  b->d_next = nullptr;
+  b->in_queue.assign(b->items.size(), 0);
+  b->want_chunks = want_chunks;
+  int dev_smem = 0;
+  cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, b->device);
+  std::vector<size_t> order(b->items.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+  std::vector<long long> size(b->items.size());
+  for (size_t i = 0; i < size.size(); ++i) {
+    fc_sizes sz;
+    fc_query(b->items[i].plan, &sz);
+    size[i] = sz.wave_len;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return size[x] > size[y]; });
+  std::vector<FcWork> work[2][2][3][4];   // [direction][BF16 I/O][kernel set][occupancy class]
+  size_t smem_of[2][2][3][4] = {};
+  const FcGenKernels* sets[3] = {&fc_gen_kernels_512(), &fc_gen_kernels_256(), &fc_gen_kernels_128()};
+  for (size_t i : order) {
+    const fc_batch_item& it = b->items[i];
+    if (it.state || it.n_streams == 0) continue;
+    std::vector<FcWork> mine;
+    size_t smem = 0;
+    const bool queued =
+        want_chunks > 0 && fc_internal_io(it.plan) == 0
+            ? fc_internal_sync_work_generic(it.plan, it.direction, it.n_streams, it.in, it.out, want_chunks, mine, &smem)
+            : fc_internal_sync_work(it.plan, it.direction, it.n_streams, it.in, it.out, mine, &smem);
+    if (!queued) continue;
+    const size_t per_cta = smem + 4096;                         // + static plan copy and slack
+    int cls = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)dev_smem / per_cta)) - 1;
+    const int bf = fc_internal_io(it.plan) != 0;
+    const int set = fc_internal_gen(it.plan).threads == 256 ? 1 : (fc_internal_gen(it.plan).threads == 128 ? 2 : 0);
+    b->in_queue[i] = 1;
+    std::vector<FcWork>& w = work[it.direction][bf][set][cls];
+    w.insert(w.end(), mine.begin(), mine.end());
+    smem_of[it.direction][bf][set][cls] = std::max(smem_of[it.direction][bf][set][cls], smem);
+  }
+  cudaError_t e = cudaSuccess;
+  for (int dir = 0; dir < 2; ++dir)
+    for (int bf = 0; bf < 2; ++bf)
+      for (int set = 0; set < 3; ++set)
+        for (int cls = 0; cls < 4; ++cls) {
+          const std::vector<FcWork>& w = work[dir][bf][set][cls];
+          if (w.empty() || e != cudaSuccess) continue;
+          fc_batch::Queue Q;
+          Q.dir = dir;
+          Q.io = bf ? (FC_IO_IN_BF16 | FC_IO_OUT_BF16) : 0;
+          Q.gen = sets[set];
+          Q.n = (int)w.size();
+          Q.smem = smem_of[dir][bf][set][cls];
+          e = cudaMalloc(&Q.d_work, w.size() * sizeof(FcWork));
+          if (e == cudaSuccess) {
+            b->queue_mem.push_back(Q.d_work);
+            e = cudaMemcpy(Q.d_work, w.data(), w.size() * sizeof(FcWork), cudaMemcpyHostToDevice);
+          }
+          b->queues.push_back(Q);
+        }
+  if (e == cudaSuccess && !b->queues.empty()) {
+    e = cudaMalloc(&b->d_next, b->queues.size() * sizeof(int));
+    if (e == cudaSuccess) b->queue_mem.push_back(b->d_next);
+  }
+  return e;
 }
 
 }  // namespace
@@ -161,65 +240,10 @@ int fc_batch_create(const fc_batch_item* items, int32_t n_items, int32_t n_lanes
       it.workspace_bytes = need;
     }
   }
-  // persistent mode: generic symbol-sync frame calls go to queues by direction, by I/O
-  // type (complex64 or complex BF16), by kernel set (512-, 256- or 128-thread CTAs) and by
-  // occupancy class (1, 2, 3 or 4 CTAs per SM for their shared memory), items of the
-  // largest plans first (each CTA of a launch takes the next item)
   if (e == cudaSuccess && (mode & FC_BATCH_PERSISTENT)) {
-    b->in_queue.assign(b->items.size(), 0);
+    b->persistent = 1;
     b->num_sms = fc_internal_num_sms(b->items[0].plan);
-    int dev_smem = 0;
-    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    std::vector<size_t> order(b->items.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
-    std::vector<long long> size(b->items.size());
-    for (size_t i = 0; i < size.size(); ++i) {
-      fc_sizes sz;
-      fc_query(b->items[i].plan, &sz);
-      size[i] = sz.wave_len;
-    }
-    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return size[x] > size[y]; });
-    std::vector<FcWork> work[2][2][3][4];   // [direction][BF16 I/O][kernel set][occupancy class]
-    size_t smem_of[2][2][3][4] = {};
-    const FcGenKernels* sets[3] = {&fc_gen_kernels_512(), &fc_gen_kernels_256(), &fc_gen_kernels_128()};
-    for (size_t i : order) {
-      const fc_batch_item& it = b->items[i];
-      if (it.state || it.n_streams == 0) continue;
-      std::vector<FcWork> mine;
-      size_t smem = 0;
-      if (!fc_internal_sync_work(it.plan, it.direction, it.n_streams, it.in, it.out, mine, &smem)) continue;
-      const size_t per_cta = smem + 4096;                         // + static plan copy and slack
-      int cls = (int)std::min<size_t>(4, std::max<size_t>(1, (size_t)dev_smem / per_cta)) - 1;
-      const int bf = fc_internal_io(it.plan) != 0;
-      const int set = fc_internal_gen(it.plan).threads == 256 ? 1 : (fc_internal_gen(it.plan).threads == 128 ? 2 : 0);
-      b->in_queue[i] = 1;
-      std::vector<FcWork>& w = work[it.direction][bf][set][cls];
-      w.insert(w.end(), mine.begin(), mine.end());
-      smem_of[it.direction][bf][set][cls] = std::max(smem_of[it.direction][bf][set][cls], smem);
-    }
-    for (int dir = 0; dir < 2; ++dir)
-      for (int bf = 0; bf < 2; ++bf)
-        for (int set = 0; set < 3; ++set)
-          for (int cls = 0; cls < 4; ++cls) {
-            const std::vector<FcWork>& w = work[dir][bf][set][cls];
-            if (w.empty() || e != cudaSuccess) continue;
-            fc_batch::Queue Q;
-            Q.dir = dir;
-            Q.io = bf ? (FC_IO_IN_BF16 | FC_IO_OUT_BF16) : 0;
-            Q.gen = sets[set];
-            Q.n = (int)w.size();
-            Q.smem = smem_of[dir][bf][set][cls];
-            e = cudaMalloc(&Q.d_work, w.size() * sizeof(FcWork));
-            if (e == cudaSuccess) {
-              b->owned.push_back(Q.d_work);
-              e = cudaMemcpy(Q.d_work, w.data(), w.size() * sizeof(FcWork), cudaMemcpyHostToDevice);
-            }
-            b->queues.push_back(Q);
-          }
-    if (e == cudaSuccess && !b->queues.empty()) {
-      e = cudaMalloc(&b->d_next, b->queues.size() * sizeof(int));
-      if (e == cudaSuccess) b->owned.push_back(b->d_next);
-    }
+    e = build_queues(b, 0);
   }
   if (e != cudaSuccess) {
     release(b);
@@ -264,6 +288,113 @@ int fc_batch_launch(fc_batch* b, void* stream) {
   e = cudaEventRecord(b->ev_exit, b->origin);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, b->ev_exit, 0);
   return e == cudaSuccess ? FC_OK : cuda_err(e, "batch exit");
+}
+
+int fc_batch_autotune(fc_batch* b, int32_t reps, void* stream) {
+  FcRange nvtx_range(__func__);
+  if (!b) return fc_internal_fail(FC_ERR_INVALID, "batch is NULL");
+  if (reps < 1) return fc_internal_fail(FC_ERR_INVALID, "reps must be >= 1");
+  DevGuard dg(b->device);
+  if (!dg.ok) return fc_internal_fail(FC_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t caller = (cudaStream_t)stream;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaError_t e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_enter, caller);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->ev_enter, 0);
+  // one whole pass of the batch per candidate, timed on the batch's own stream
+  auto time_pass = [&](float* ms) -> int {
+    for (int w = 0; w < 2; ++w) {
+      const int rc = issue(b);
+      if (rc != FC_OK) return rc;
+    }
+    cudaError_t x = cudaEventRecord(t0, b->origin);
+    for (int r = 0; r < reps && x == cudaSuccess; ++r) {
+      const int rc = issue(b);
+      if (rc != FC_OK) return rc;
+    }
+    if (x == cudaSuccess) x = cudaEventRecord(t1, b->origin);
+    if (x == cudaSuccess) x = cudaEventSynchronize(t1);
+    if (x == cudaSuccess) x = cudaEventElapsedTime(ms, t0, t1);
+    return x == cudaSuccess ? FC_OK : cuda_err(x, "batch autotune timing");
+  };
+  int rc = e == cudaSuccess ? FC_OK : cuda_err(e, "batch autotune");
+  if (rc == FC_OK && b->persistent) {
+    // the queued items' chunk count, for the mix as a whole (each plan's rule, or one
+    // count for every queued item: fewer chunks recompute fewer overlapping symbols,
+    // more chunks balance the launch)
+    float best = 1e30f;
+    int best_want = 0;
+    for (int want : {0, 1, 2, 4, 8, 16, 32, 64}) {
+      e = build_queues(b, want);
+      if (e != cudaSuccess) {
+        rc = cuda_err(e, "batch autotune queues");
+        break;
+      }
+      float ms = 0.f;
+      rc = time_pass(&ms);
+      if (rc != FC_OK) break;
+      if (ms < best) {
+        best = ms;
+        best_want = want;
+      }
+    }
+    if (rc == FC_OK) {
+      cudaStreamSynchronize(b->origin);
+      e = build_queues(b, best_want);
+      if (e != cudaSuccess) rc = cuda_err(e, "batch autotune queues");
+    }
+  } else if (rc == FC_OK) {
+    // lanes: one chunk count for every frame call of the batch (each item's plan keeps it
+    // as its choice for the item's stream count and direction), or the plans' own
+    std::vector<int> counts = {0, 1, 2, 4, 8, 16, 32, 64};
+    float best = 1e30f;
+    int best_c = 0;
+    std::vector<std::pair<int, int>> before(b->items.size(), {0, 0});   // each item's choice on entry
+    for (size_t i = 0; i < b->items.size(); ++i) {
+      const fc_batch_item& it = b->items[i];
+      if (!it.state && it.n_streams > 0)
+        fc_plan_choice(it.plan, it.n_streams, it.direction, &before[i].first, &before[i].second);
+    }
+    for (int c : counts) {
+      bool any = false;
+      for (size_t i = 0; i < b->items.size(); ++i) {
+        const fc_batch_item& it = b->items[i];
+        if (it.state || it.n_streams == 0) continue;
+        fc_plan* pl = const_cast<fc_plan*>(it.plan);
+        if (c > 0 && fc_plan_set_choice(pl, it.n_streams, it.direction, c, before[i].second) == FC_OK) any = true;
+        else fc_plan_set_choice(pl, it.n_streams, it.direction, before[i].first, before[i].second);
+      }
+      if (c > 0 && !any) continue;
+      float ms = 0.f;
+      rc = time_pass(&ms);
+      if (rc != FC_OK) break;
+      if (ms < best) {
+        best = ms;
+        best_c = c;
+      }
+    }
+    for (size_t i = 0; rc == FC_OK && i < b->items.size(); ++i) {
+      const fc_batch_item& it = b->items[i];
+      if (it.state || it.n_streams == 0) continue;
+      fc_plan* pl = const_cast<fc_plan*>(it.plan);
+      if (best_c == 0 || fc_plan_set_choice(pl, it.n_streams, it.direction, best_c, before[i].second) != FC_OK)
+        fc_plan_set_choice(pl, it.n_streams, it.direction, before[i].first, before[i].second);
+    }
+  }
+  cudaStreamSynchronize(b->origin);
+  if (b->exec) {                          // the next launch captures the tuned batch
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  if (rc == FC_OK) {
+    e = cudaEventRecord(b->ev_exit, b->origin);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, b->ev_exit, 0);
+    if (e != cudaSuccess) rc = cuda_err(e, "batch autotune exit");
+  }
+  return rc;
 }
 
 void fc_batch_destroy(fc_batch* b) {

@@ -71,6 +71,52 @@ void radix_plan(int n, unsigned char* radix, int* npass) {
   *npass = k;
 }
 
+// Candidate radix schedules of an n-point transform for the autotuner: the power of two
+// 2^a split into ceil(a/4) or ceil(a/4) + 1 passes of radix 2..16, balanced with the
+// larger radices first or last, or as many radix-16 passes as fit first; the radix-3
+// passes last (as radix_plan) or first. The rule's own schedule comes first.
+std::vector<std::vector<unsigned char>> radix_candidates(int n) {
+  std::vector<std::vector<unsigned char>> out;
+  auto add = [&](const std::vector<unsigned char>& r) {
+    if ((int)r.size() > FC_MAX_PASSES) return;
+    if (std::find(out.begin(), out.end(), r) == out.end()) out.push_back(r);
+  };
+  {
+    unsigned char r[FC_MAX_PASSES];
+    int np = 0;
+    radix_plan(n, r, &np);
+    add(std::vector<unsigned char>(r, r + np));
+  }
+  int a = 0, b = 0, m = n;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  while (m % 3 == 0) { m /= 3; ++b; }
+  std::vector<std::vector<unsigned char>> twos;
+  if (a == 0) twos.push_back({});
+  for (int passes = (a + 3) / 4; a > 0 && passes <= (a + 3) / 4 + 1 && passes <= a; ++passes) {
+    const int base = a / passes, extra = a % passes;
+    std::vector<unsigned char> big_first, big_last;
+    for (int i = 0; i < passes; ++i) big_first.push_back((unsigned char)(1 << (base + (i < extra ? 1 : 0))));
+    big_last.assign(big_first.rbegin(), big_first.rend());
+    twos.push_back(big_first);
+    twos.push_back(big_last);
+  }
+  if (a > 4) {                                         // radix 16 while it fits, then the rest
+    std::vector<unsigned char> r;
+    int left = a;
+    while (left >= 4) { r.push_back(16); left -= 4; }
+    if (left) r.push_back((unsigned char)(1 << left));
+    twos.push_back(r);
+  }
+  for (const auto& t : twos) {
+    std::vector<unsigned char> last = t, first(b, 3);
+    for (int i = 0; i < b; ++i) last.push_back(3);
+    first.insert(first.end(), t.begin(), t.end());
+    add(last);
+    add(first);
+  }
+  return out;
+}
+
 struct SubHost {
   int L = 0, Lo = 0, Lact = 0, c = 0, g = 0;
   int L_O = 0, L_S = 0, L_L = 0, L_T = 0, S_L = 0, n_low = 0, R = 0;
@@ -1000,6 +1046,48 @@ int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* strea
       }
     }
   }
+  // Radix schedules of the generic kernels' transforms (the plan's device table, read by
+  // every generic launch): per transform size in turn, each candidate schedule is timed
+  // on the directions whose best launch shape runs the generic kernels, and the fastest
+  // is kept (the specialised and tensor-core kernels have fixed transforms of their own).
+  bool gen_dir[2];
+  for (int dir = 0; dir < 2; ++dir) {
+    const bool special = dir == FC_TX ? (plan->warp_path || plan->tc_tx) : (plan->warp_path || plan->tc_rx);
+    gen_dir[dir] = !special || best[dir].generic;
+  }
+  for (int i = 0; i < plan->h.n_sizes && e == cudaSuccess && (gen_dir[0] || gen_dir[1]); ++i) {
+    FcSize& z = plan->h.sz[i];
+    const auto cands = radix_candidates(z.n);
+    if (cands.size() < 2) continue;
+    float best_ms = 1e30f;
+    std::vector<unsigned char> keep(z.radix, z.radix + z.npass);
+    for (const auto& r : cands) {
+      if (e != cudaSuccess) break;
+      z.npass = (int)r.size();
+      std::copy(r.begin(), r.end(), z.radix);
+      e = cudaMemcpy(plan->d_plan, &plan->h, sizeof(FcPlanDev), cudaMemcpyHostToDevice);
+      auto run = [&]() {
+        cudaError_t x = cudaSuccess;
+        if (gen_dir[FC_TX]) x = launch_tx(plan, n_streams, grid, wave, ws, st, best[FC_TX], plan->io);
+        if (x == cudaSuccess && gen_dir[FC_RX]) x = launch_rx(plan, n_streams, wave, grid, ws, st, best[FC_RX], plan->io);
+        return x;
+      };
+      for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = run();
+      if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+      for (int r2 = 0; r2 < reps && e == cudaSuccess; ++r2) e = run();
+      if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        keep = r;
+      }
+    }
+    z.npass = (int)keep.size();
+    std::copy(keep.begin(), keep.end(), z.radix);
+    if (e == cudaSuccess) e = cudaMemcpy(plan->d_plan, &plan->h, sizeof(FcPlanDev), cudaMemcpyHostToDevice);
+  }
   for (cudaEvent_t x : ev)
     if (x) cudaEventDestroy(x);
   cudaStreamSynchronize(st);
@@ -1009,6 +1097,18 @@ int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* strea
   plan->tuned[{n_streams, FC_TX}] = best[FC_TX];
   plan->tuned[{n_streams, FC_RX}] = best[FC_RX];
   return FC_OK;
+}
+
+int fc_plan_radices(const fc_plan* plan, int32_t n, int32_t* radices, int32_t* n_passes) {
+  if (!plan || !radices || !n_passes) return fail(FC_ERR_INVALID, "NULL argument");
+  for (int i = 0; i < plan->h.n_sizes; ++i) {
+    const FcSize& z = plan->h.sz[i];
+    if (z.n != n) continue;
+    *n_passes = z.npass;
+    for (int k = 0; k < z.npass; ++k) radices[k] = z.radix[k];
+    return FC_OK;
+  }
+  return fail(FC_ERR_INVALID, "the plan has no transform of that size");
 }
 
 int fc_plan_set_choice(fc_plan* plan, int32_t n_streams, int32_t direction, int32_t chunks_per_stream,

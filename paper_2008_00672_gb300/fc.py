@@ -35,7 +35,8 @@ EXPORTED = ("fc_plan_create", "fc_geometry_check", "fc_query", "fc_tx_synthesize
             "fc_state_destroy", "fc_tx_synthesize_stream", "fc_rx_analyze_stream", "fc_plan_autotune",
             "fc_plan_choice", "fc_batch_create", "fc_batch_launch", "fc_batch_destroy", "fc_server_create",
             "fc_server_add_carrier", "fc_server_carrier_sizes", "fc_server_run", "fc_server_destroy",
-            "fc_server_serve", "fc_server_set_limits", "fc_plan_set_first_wait_limit",
+            "fc_server_serve", "fc_server_set_limits", "fc_plan_set_first_wait_limit", "fc_batch_autotune",
+            "fc_plan_radices",
             "fc_plan_device_status", "fc_plan_set_choice", "fc_pipeline_create", "fc_pipeline_destroy",
             "fc_tx_synthesize_host", "fc_rx_analyze_host")
 
@@ -145,6 +146,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.fc_server_carrier_sizes.restype = ctypes.c_int
         lib.fc_server_run.argtypes = [vp, ctypes.POINTER(FcServeRequest), i32, ctypes.POINTER(ctypes.c_double)]
         lib.fc_server_run.restype = ctypes.c_int
+        lib.fc_plan_radices.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        lib.fc_plan_radices.restype = ctypes.c_int
+        lib.fc_batch_autotune.argtypes = [vp, i32, vp]
+        lib.fc_batch_autotune.restype = ctypes.c_int
         lib.fc_plan_set_first_wait_limit.argtypes = [vp, ctypes.c_uint32]
         lib.fc_plan_set_first_wait_limit.restype = ctypes.c_int
         lib.fc_server_serve.argtypes = [vp, ctypes.POINTER(FcServeRequest), i32, ctypes.POINTER(FcServeRecord)]
@@ -449,6 +454,13 @@ class Plan:
     def set_choice(self, n_streams: int, direction: int, chunks_per_stream: int, generic_kernels: int = 0):
         fc_plan_set_choice(self.handle, n_streams, direction, chunks_per_stream, generic_kernels)
 
+    def radices(self, n: int) -> list:
+        """The generic kernels' radix schedule of the plan's n-point transform."""
+        r = (ctypes.c_int32 * 8)()
+        k = ctypes.c_int32(0)
+        _check(load_library().fc_plan_radices(self.handle, int(n), r, ctypes.byref(k)), "fc_plan_radices")
+        return [int(r[i]) for i in range(k.value)]
+
     def choice(self, n_streams: int, direction: int):
         return fc_plan_choice(self.handle, n_streams, direction)
 
@@ -590,6 +602,11 @@ class Batch:
 
     def launch(self, stream=None):
         fc_batch_launch(self.handle, Plan._stream_handle(stream))
+
+    def autotune(self, reps: int = 5, stream=None):
+        """Time the whole batch under each candidate launch shape; keep the fastest."""
+        _check(load_library().fc_batch_autotune(self.handle, int(reps), Plan._stream_handle(stream)),
+               "fc_batch_autotune")
 
     def close(self):
         if self.handle:

@@ -174,3 +174,68 @@ def test_cta_sizes_give_identical_results(torch_cuda, name):
         assert torch.equal(wb, wave[:2]) and torch.equal(eb, est[:2])
         b.close()
     plan.close()
+
+
+@pytest.mark.parametrize("persistent", [True, False])
+def test_batch_autotune_keeps_results(torch_cuda, persistent):
+    """fc_batch_autotune times the whole batch under each candidate chunk count and keeps
+    the fastest; the replayed graph still matches the oracle."""
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import FC_RX, FC_TX, Batch
+    carriers = wl.config_uneven_carriers(seed=1402, n_carriers=8, n_slots=1)
+    S = 2
+    cs = setup(torch, carriers, S, 700)
+    for j, c in enumerate(cs):
+        c["ref_tx"] = [fo.tx_frame(c["geom"], c["grid_np"][s]) for s in range(S)]
+        x = np.stack([c64(wl.awgn(c["ref_tx"][s], 30.0, 91 + 13 * j + s)).astype(np.complex128) for s in range(S)])
+        c["rx_np"] = x
+        c["rx_in"] = torch.from_numpy(c64(x)).cuda()
+    items = [(c["plan"], FC_TX, c["grid"], c["wave"]) for c in cs] + \
+            [(c["plan"], FC_RX, c["rx_in"], c["est"]) for c in cs]
+    b = Batch(items, n_lanes=4, use_graph=True, persistent=persistent)
+    b.launch()
+    b.autotune(reps=2)
+    for c in cs:
+        c["wave"].zero_()
+        c["est"].zero_()
+    b.launch()
+    torch.cuda.synchronize()
+    for c in cs:
+        w, e = c["wave"].cpu().numpy(), c["est"].cpu().numpy()
+        ww, gw = parity.wave_windows(c["geom"]), parity.grid_windows(c["geom"])
+        for s in range(S):
+            parity.check(w[s], c["ref_tx"][s], TOL, ww, (c["geom"].name, "tx", s))
+            parity.check(e[s], fo.rx_frame(c["geom"], c["rx_np"][s]), TOL, gw, (c["geom"].name, "rx", s))
+    b.close()
+    for c in cs:
+        c["plan"].close()
+
+
+def test_autotune_radix_schedules(torch_cuda):
+    """On the generic kernels the autotuner also picks a radix schedule per transform size
+    (written into the plan's tables); every schedule multiplies out to its size, uses the
+    kernels' radices, and the tuned plan still matches the oracle."""
+    torch = torch_cuda
+    import dataclasses
+    from paper_2008_00672_gb300 import Plan
+    geom = dataclasses.replace(wl.config_mixed_20mhz(), flags=1)         # generic kernels
+    plan = Plan(geom)
+    before = {n: plan.radices(n) for n in (512, 1024, 2048)}
+    assert before[1024] == [16, 8, 8] and before[2048] == [16, 16, 8] and before[512] == [8, 8, 8]
+    S = 24
+    plan.autotune(S, reps=2)
+    for n in (512, 1024, 2048):
+        r = plan.radices(n)
+        assert int(np.prod(r)) == n and set(r) <= {2, 4, 8, 16}, (n, r)
+    grid = c64(wl.qam_grid(geom, S, 9))
+    w = torch.empty((S, plan.wave_len), dtype=torch.complex64, device="cuda")
+    plan.tx_synthesize(torch.from_numpy(grid).cuda(), w)
+    est = torch.empty((S, plan.grid_len), dtype=torch.complex64, device="cuda")
+    plan.rx_analyze(w, est)
+    torch.cuda.synchronize()
+    for s in (0, S - 1):
+        ref = fo.tx_frame(geom, grid[s].astype(np.complex128))
+        parity.check(w[s].cpu().numpy(), ref, TOL, parity.wave_windows(geom), s)
+        parity.check(est[s].cpu().numpy(), fo.rx_frame(geom, w[s].cpu().numpy().astype(np.complex128)), TOL,
+                     parity.grid_windows(geom), s)
+    plan.close()
