@@ -67,8 +67,8 @@ def transform_flops(geom) -> float:
 
 
 KERNEL_SOURCES = {
-    "k_tx_sync_warp": ("fc_warp.cu", "fc_internal.cuh", "fc_device.cuh"),
-    "k_rx_sync_warp": ("fc_warp.cu", "fc_internal.cuh", "fc_device.cuh"),
+    "k_tx_sync_warp": ("fc_warp.cu", "fc_warp_fft.cuh", "fc_internal.cuh", "fc_device.cuh"),
+    "k_rx_sync_warp": ("fc_warp.cu", "fc_warp_fft.cuh", "fc_internal.cuh", "fc_device.cuh"),
     "k_tc_fc": ("fc_tensor.cu", "fc_tc.cuh", "fc_internal.cuh", "fc_device.cuh"),
 }
 

@@ -16,11 +16,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfcofdm.so")
-SOURCES = ["fc_kernels.cu", "fc_kernels_256.cu", "fc_kernels_128.cu", "fc_warp.cu", "fc_plan.cu", "fc_static.cu", "fc_stream.cu", "fc_exec.cu",
+SOURCES = ["fc_kernels.cu", "fc_kernels_256.cu", "fc_kernels_128.cu", "fc_warp.cu", "fc_warp_cont.cu", "fc_plan.cu", "fc_static.cu", "fc_stream.cu", "fc_exec.cu",
            "fc_server.cu", "fc_tensor.cu", "fc_host.cu"]
 # sources that include another source (fc_kernels.cu compiled for 256- and 128-thread CTAs)
 INCLUDES = {"fc_kernels_256.cu": ["fc_kernels.cu"], "fc_kernels_128.cu": ["fc_kernels.cu"]}
-HEADERS = ["fc_internal.cuh", "fc_device.cuh", "fc_tc.cuh", "fc_trace.h", os.path.join("..", "..", "include", "fcofdm.h")]
+HEADERS = ["fc_internal.cuh", "fc_device.cuh", "fc_tc.cuh", "fc_trace.h", "fc_warp_fft.cuh", os.path.join("..", "..", "include", "fcofdm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -27,6 +27,9 @@
 #ifndef FC_WARP_RX_MIN_BLOCKS
 #define FC_WARP_RX_MIN_BLOCKS 3  // resident CTAs per SM the warp RX kernel is compiled for
 #endif
+#ifndef FC_WARP_CONT_MIN_BLOCKS
+#define FC_WARP_CONT_MIN_BLOCKS 4  // resident CTAs per SM the continuous warp kernels are compiled for
+#endif
 #define FC_MAX_SIZES 12       // distinct transform sizes in one plan
 #define FC_MAX_PASSES 8
 #define FC_MAX_ELEMS_PER_THREAD 16   // in-place FFT: batch*n <= threads*16
@@ -165,6 +168,13 @@ cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n
 cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams,
                                    const float2* wave, float2* grid, int num_sms, cudaStream_t st);
 cudaError_t fc_set_warp_smem_limits();
+// Continuous mode, one subband with L = L_OFDM = 384, N = 512, 50 % overlap, overlap-save
+// (fc_warp_cont.cu): OFDM modulation into the workspace then FC blocks (TX), FC blocks into
+// the workspace then OFDM demodulation (RX), one warp per pair of symbols or blocks.
+cudaError_t fc_launch_tx_cont_warp(const FcPlanDev* dP, int n_streams, int n_symbols, int n_blocks, const float2* grid,
+                                   float2* ws, float2* wave, int num_sms, cudaStream_t st);
+cudaError_t fc_launch_rx_cont_warp(const FcPlanDev* dP, int n_streams, int n_symbols, int n_blocks, const float2* wave,
+                                   float2* ws, float2* grid, int num_sms, cudaStream_t st);
 
 // helpers for entry points defined outside fc_plan.cu
 int fc_internal_fail(int code, const char* msg);     // records fc_last_error() and returns code

@@ -160,6 +160,7 @@ struct fc_plan {
   std::vector<int> tx_nchunks, rx_nchunks;
   int io = 0;                               // FC_IO_* bits of the frame calls (FC_FLAG_IO_BF16)
   bool warp_path = false;                   // warp-specialised symbol-sync kernels apply
+  bool cont_warp_tx = false, cont_warp_rx = false;   // warp-specialised continuous kernels apply (per direction)
   bool tc_tx = false, tc_rx = false;        // tensor-core FC passes apply (FC_FLAG_TENSOR_DFT)
   bool tc_ofdm = false;                     // and the OFDM (I)DFT too (L_OFDM = 4096)
   const unsigned char* d_dft64 = nullptr;   // DFT-64 B operand images (hi, lo)
@@ -471,6 +472,12 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     const bool shape = (o.L == 1024 && gh[g].N == 2048) || (o.L == 512 && gh[g].N == 1024);
     if (!shape) warp_ok = false;
   }
+  // warp-specialised continuous path: one group, one subband, L = L_OFDM = 384, N = 512,
+  // 50 % overlap, the group at the frame's start; per direction when that side is
+  // overlap-save (its outputs are disjoint and written once)
+  bool cont_warp = !sync && G == 1 && M == 1 && !io_time && !io_bf16 && !(geo->flags & FC_FLAG_GENERIC_KERNELS) &&
+                   sh[0].L == 384 && sh[0].Lo == 384 && gh[0].N == 512 && 2 * gh[0].N_O == gh[0].N &&
+                   gh[0].offset == 0;
   size_t off_wjobs = 0;
   if (warp_ok) {
     // one stream's jobs, most expensive first (N = 2048 before N = 1024): the warp
@@ -696,6 +703,8 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   pl->tx_nchunks = ntx;
   pl->rx_nchunks = nrx;
   pl->warp_path = warp_ok;
+  pl->cont_warp_tx = cont_warp && geo->scheme_tx == FC_OLS;
+  pl->cont_warp_rx = cont_warp && geo->scheme_rx == FC_OLS;
   pl->tc_tx = tc_tx;
   pl->tc_rx = tc_rx;
   pl->tc_ofdm = tc_tx && sh[0].Lo == 4096 && !io_time;
@@ -785,6 +794,9 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* 
   if (plan->h.mode == FC_SYMBOL_SYNC)
     return gen.tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, in,
                               out, io, plan->smem_tx, st);
+  if (plan->cont_warp_tx && !c.generic && io == 0)
+    return fc_launch_tx_cont_warp(plan->d_plan, n_streams, plan->h.g[0].B, plan->h.g[0].R, grid, workspace, wave,
+                                  plan->num_sms, st);
   if (plan->tc_tx && !c.generic && io == 0) {
     const int R = plan->h.g[0].R;
     cudaError_t e = plan->tc_ofdm ? fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_OFDM_MOD, n_streams,
@@ -822,6 +834,9 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* 
   if (plan->h.mode == FC_SYMBOL_SYNC)
     return gen.rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, in,
                               out, io, plan->smem_rx, st);
+  if (plan->cont_warp_rx && !c.generic && io == 0)
+    return fc_launch_rx_cont_warp(plan->d_plan, n_streams, plan->h.g[0].B, plan->h.g[0].R, wave, workspace, grid,
+                                  plan->num_sms, st);
   if (plan->tc_rx && !c.generic && io == 0) {
     const int R = plan->h.g[0].R;
     cudaError_t e = fc_launch_tc(plan->d_plan, plan->d_dft64, FC_TC_RX_FFT, n_streams, R, wave, nullptr, workspace,
@@ -1016,7 +1031,8 @@ int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* strea
   Choice best[2];
   for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir) {
     float best_ms = 1e30f;
-    const bool special = dir == FC_TX ? (plan->warp_path || plan->tc_tx) : (plan->warp_path || plan->tc_rx);
+    const bool special = dir == FC_TX ? (plan->warp_path || plan->tc_tx || plan->cont_warp_tx)
+                                      : (plan->warp_path || plan->tc_rx || plan->cont_warp_rx);
     // candidates: every split with the specialised kernels (where they apply), and every
     // split on every generic-kernel set that fits
     std::vector<Choice> cand;
@@ -1052,7 +1068,8 @@ int fc_plan_autotune(fc_plan* plan, int32_t n_streams, int32_t reps, void* strea
   // is kept (the specialised and tensor-core kernels have fixed transforms of their own).
   bool gen_dir[2];
   for (int dir = 0; dir < 2; ++dir) {
-    const bool special = dir == FC_TX ? (plan->warp_path || plan->tc_tx) : (plan->warp_path || plan->tc_rx);
+    const bool special = dir == FC_TX ? (plan->warp_path || plan->tc_tx || plan->cont_warp_tx)
+                                      : (plan->warp_path || plan->tc_rx || plan->cont_warp_rx);
     gen_dir[dir] = !special || best[dir].generic;
   }
   for (int i = 0; i < plan->h.n_sizes && e == cudaSuccess && (gen_dir[0] || gen_dir[1]); ++i) {
@@ -1129,7 +1146,8 @@ int fc_plan_choice(const fc_plan* plan, int32_t n_streams, int32_t direction, in
     return fail(FC_ERR_INVALID, "bad plan, direction or n_streams");
   const Choice c = choose(plan, n_streams, direction);
   if (chunks_per_stream) *chunks_per_stream = plan->splits[c.split];
-  const bool special = direction == FC_TX ? (plan->warp_path || plan->tc_tx) : (plan->warp_path || plan->tc_rx);
+  const bool special = direction == FC_TX ? (plan->warp_path || plan->tc_tx || plan->cont_warp_tx)
+                                            : (plan->warp_path || plan->tc_rx || plan->cont_warp_rx);
   if (generic_kernels) *generic_kernels = (special && !c.generic) ? 0 : 1;
   return FC_OK;
 }

@@ -22,83 +22,15 @@
 // dealt to as many CTAs as the GPU holds at once.
 #include "fc_device.cuh"
 #include "fc_internal.cuh"
+#include "fc_warp_fft.cuh"
 
 namespace {
 using namespace fcdev;
+using namespace fcwarp;
 
-constexpr int kPad = 33;                       // transpose row stride in float2
-constexpr int kTrans = 32 * kPad;              // per-warp transpose buffer (float2)
 constexpr int kMap = 1024;                     // per-warp spectrum / re-layout buffer (float2)
 constexpr int kScratch = kTrans + kMap;
 constexpr int kWarps = FC_WARP_THREADS / 32;
-
-__device__ __forceinline__ void load_plan_w(FcPlanDev& P, const FcPlanDev* __restrict__ gP) {
-  const int words = (int)(sizeof(FcPlanDev) / 4);
-  const int* src = reinterpret_cast<const int*>(gP);
-  int* dst = reinterpret_cast<int*>(&P);
-  for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = __ldg(src + i);
-}
-
-// exp(+j 2 pi e / n) from the forward twiddle table of size n (power of two)
-__device__ __forceinline__ float2 root_pos(const float2* __restrict__ tw, int n, long long e) {
-  const float2 w = __ldg(tw + (int)(e & (long long)(n - 1)));
-  return make_float2(w.x, -w.y);
-}
-
-// Compiler-only fence: keeps the scheduler from hoisting every load of a stage
-// ahead of its first use (which would need twice the registers of the data).
-__device__ __forceinline__ void sched_fence() { asm volatile("" ::: "memory"); }
-
-// v[k] *= W^{lane e(k)} for k = 1..31 with e(k) = 4 (m & mmask) + j, k = 4 m + j.
-// One 1024-point transform: tw = W_1024 table, mmask = 7 (e = k). Two 512-point
-// transforms: tw = W_512 table, mmask = 3 (e = k mod 16, the same twiddles for both).
-// W^{lane e} = W^{4 (m & mmask) lane} W^{j lane}: 11 table loads and one complex
-// multiply per twiddle (one rounding away from the FP64-generated table; the
-// table's entry 0 is exactly 1).
-__device__ __forceinline__ void step_twiddles(float2 (&v)[32], const float2* __restrict__ tw, int lane, int mmask) {
-  float2 tj[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) tj[j] = __ldg(tw + lane * j);
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    sched_fence();
-    const float2 tm = __ldg(tw + lane * 4 * (m & mmask));
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int k = 4 * m + j;
-      if (k == 0) continue;
-      v[k] = cmul(v[k], j ? cmul(tm, tj[j]) : tm);
-    }
-  }
-}
-
-// Forward four-step FFT of one warp.
-//  two512 = false: one 1024-point transform; in: lane b holds x[32 a + b] in v[a];
-//                  out: lane k1 holds X[k1 + 32 k2] in v[k2].
-//  two512 = true:  two 512-point transforms; in: lane b holds x_T[32 a + b] in
-//                  v[16 T + a] (a < 16); out: lane k1 + 16 T holds X_T[k1 + 16 k2] in v[k2].
-__device__ __forceinline__ void warp_fft(float2 (&v)[32], float2* scr, const float2* __restrict__ tw1024,
-                                         const float2* __restrict__ tw512, int lane, bool two512) {
-  if (!two512) {
-    Dft<32, false>::run(v);
-  } else {
-    Dft<16, false>::run(v);
-    Dft<16, false>::run(v + 16);
-  }
-  step_twiddles(v, two512 ? tw512 : tw1024, lane, two512 ? 3 : 7);
-#pragma unroll
-  for (int k = 0; k < 32; ++k) scr[k * kPad + lane] = v[k];
-  __syncwarp();
-#pragma unroll
-  for (int b = 0; b < 32; ++b) v[b] = scr[lane * kPad + b];
-  __syncwarp();
-  Dft<32, false>::run(v);
-}
-
-__device__ __forceinline__ void conj32(float2 (&v)[32]) {
-#pragma unroll
-  for (int k = 0; k < 32; ++k) v[k].y = -v[k].y;
-}
 
 __device__ __forceinline__ float weight(const FcSubDev& S, const float* __restrict__ d, int p) {
   return (p >= S.p_lo && p < S.p_hi) ? __ldg(d + p) : 0.f;
