@@ -325,3 +325,56 @@ def test_abi_errors_and_noop(torch_cuda):
     with pytest.raises(fc.FcError):
         fc.fc_tx_synthesize(p.handle, 1, None, w.data_ptr())
     p.close()
+
+
+# ---------------------------------------------------------------------------
+# the one-warp-per-pair continuous kernels (L = 384, N = 512, overlap-save side)
+# ---------------------------------------------------------------------------
+
+W384_CASES = [
+    # n_cp (multiples of 4: L_CP = 3 N_CP / 4), c, active, TX, RX, lead pad (high rate)
+    ((40, 36, 36, 36, 36, 36, 36), 0, 288, fo.OLS, fo.OLS, -1),
+    ((40, 36, 36), -100, 200, fo.OLS, fo.OLA, -1),        # warp TX, generic RX
+    ((36, 36, 40, 36, 36), 150, 300, fo.OLA, fo.OLS, -1),  # generic TX, warp RX
+    ((40,), 7, 100, fo.OLS, fo.OLS, 384),                  # one symbol, longer lead pad
+    ((0, 4, 8, 12), 255, 360, fo.OLS, fo.OLS, -1),         # band edge at the Nyquist bin
+]
+
+
+@pytest.mark.parametrize("case", W384_CASES)
+def test_warp_continuous_384_512(torch_cuda, case):
+    n_cp, c, act, stx, srx, lead = case
+    D = wl.rc_transition_weights(384, act, min(8, (384 - act) // 2))
+    geom = geom1(fo.CONTINUOUS, stx, srx, 512, 256, 384, 384, act, c, n_cp, D=D, lead=lead)
+    from paper_2008_00672_gb300 import FC_RX, FC_TX, Plan
+    plan = Plan(geom)
+    for d, side in ((FC_TX, stx), (FC_RX, srx)):
+        assert plan.choice(3, d)[1] == (0 if side == fo.OLS else 1), (d, plan.choice(3, d))
+    plan.close()
+    check_geometry(torch_cuda, geom, 3, 43)
+
+
+def test_nr5mhz_bench_size_sampled(torch_cuda):
+    """The 5 MHz slot workload at the bench's launch (2^16 slots, one per stream) on the
+    warp continuous kernels: three sampled streams, the last included, TX against the
+    oracle and RX (on the TX output) against the oracle."""
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import Plan
+    geom = wl.config_single_5mhz()
+    S = 1 << 16
+    plan = Plan(geom)
+    base = c64(wl.qam_grid(geom, 64, wl.default_seed(1)))
+    grid = torch.from_numpy(base).cuda().repeat(S // 64, 1).contiguous()
+    wave = torch.empty((S, plan.wave_len), dtype=torch.complex64, device="cuda")
+    est = torch.empty_like(grid)
+    ws = plan.workspace(S)
+    plan.tx_synthesize(grid, wave, ws)
+    plan.rx_analyze(wave, est, ws)
+    torch.cuda.synchronize()
+    for s in (0, S // 2 + 5, S - 1):
+        g = base[s % 64].astype(np.complex128)
+        w = wave[s].cpu().numpy()
+        parity.check(w, fo.tx_frame(geom, g), TOL, parity.wave_windows(geom), ("tx", s))
+        parity.check(est[s].cpu().numpy(), fo.rx_frame(geom, w.astype(np.complex128)), TOL,
+                     parity.grid_windows(geom), ("rx", s))
+    plan.close()
