@@ -181,8 +181,10 @@ def _oracle_worker(args):
     import numpy as np
     import workloads as wl
     from oracle import fc_oracle as fo
-    seed, n_frames = args
-    geom = wl.config_mixed_20mhz()
+    seed, n_frames = args[:2]
+    geom = wl.NAMED[args[2]]() if len(args) > 2 else wl.config_mixed_20mhz()
+    if len(args) > 3:                                   # a shorter frame of a multi-slot workload
+        geom = wl.NAMED[args[2]](args[3])
     grid = wl.qam_grid(geom, n_frames, seed)
     t0 = time.perf_counter()
     for s in range(n_frames):
@@ -201,13 +203,16 @@ def oracle_pool(cores: int):
     return pool
 
 
-def oracle_throughput(pool, frames_per_core: int, cores: int, seed: int = 4242):
-    """Time the oracle (TX + RX of whole 1 ms subframes) on the pool's `cores`
-    workers. Returns (Msamples/s, seconds, frames)."""
+def oracle_throughput(pool, frames_per_core: int, cores: int, seed: int = 4242, name: str = "mixed20", arg=None):
+    """Time the oracle (TX + RX of whole frames of the named workload; by default 1 ms
+    subframes of the 20 MHz workload) on the pool's `cores` workers. Returns
+    (Msamples/s, seconds, frames)."""
     import workloads as wl
-    nominal = wl.config_mixed_20mhz().nominal_samples()
+    geom = wl.NAMED[name]() if arg is None else wl.NAMED[name](arg)
+    nominal = geom.nominal_samples()
+    extra = (name,) if arg is None else (name, arg)
     t0 = time.perf_counter()
-    res = pool.map(_oracle_worker, [(seed + i, frames_per_core) for i in range(cores)])
+    res = pool.map(_oracle_worker, [(seed + i, frames_per_core) + extra for i in range(cores)])
     wall = time.perf_counter() - t0
     frames = sum(r[1] for r in res)
     return 2 * nominal * frames / wall / 1e6, wall, frames
@@ -549,7 +554,62 @@ def method_roofline(geom, plan, n_streams: int, ms: float, peaks: dict, n_sms: i
     return {"bound": bound, "frac": max(alu["frac"], hbm["frac"]), "ms": round(ms, 4), "hbm": hbm, "alu": alu}
 
 
-def nr5mhz_bench(torch, dev, st, peaks: dict, n_sms: int, sm_mhz: float, n_slots: int = 65536) -> dict:
+def host_e2e(torch, dev, plan, grid, rx_in, chunk: int, depth: int = 4, reps: int = 5) -> dict:
+    """The workload end to end through the host-buffer calls (fc_tx_synthesize_host and
+    fc_rx_analyze_host side by side on their own CUDA streams, pinned host buffers, the
+    copies inside the timed region): Msamples/s of TX + RX."""
+    from paper_2008_00672_gb300 import Pipeline
+    S = grid.shape[0]
+    h_grid = grid.cpu().pin_memory()
+    h_rx = rx_in.cpu().pin_memory()
+    h_wave = torch.empty((S, plan.wave_len), dtype=torch.complex64).pin_memory()
+    h_est = torch.empty(tuple(grid.shape), dtype=grid.dtype).pin_memory()
+    p_tx, p_rx = Pipeline(plan, chunk, depth), Pipeline(plan, chunk, depth)
+    s_tx, s_rx = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    st = torch.cuda.current_stream(dev)
+
+    def step():
+        s_tx.wait_stream(st)
+        s_rx.wait_stream(st)
+        p_tx.tx(h_grid, h_wave, stream=s_tx)
+        p_rx.rx(h_rx, h_est, stream=s_rx)
+        st.wait_stream(s_tx)
+        st.wait_stream(s_rx)
+
+    step()
+    torch.cuda.synchronize(dev)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        step()
+    b.record(st)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / reps
+    p_tx.close()
+    p_rx.close()
+    return {"value": round(2 * plan.nominal_len * S / ms / 1e3, 1), "unit": "Msamples/s",
+            "h2d_bytes_per_step": (grid.numel() + rx_in.numel()) * 8, "d2h_bytes_per_step": (S * plan.wave_len
+                                                                                            + grid.numel()) * 8,
+            "streams": S, "path": f"fc_tx_synthesize_host + fc_rx_analyze_host side by side, {chunk} streams per "
+                                  f"chunk, {depth} slots each"}
+
+
+def oracle_leg(name: str, frames_per_core: int, arg=None, what: str = "") -> dict:
+    """The oracle on the host cores (one single-threaded process per core) on a bounded
+    sample of a workload's frames."""
+    cores = os.cpu_count() or 1
+    pool = oracle_pool(cores)
+    try:
+        v, wall, frames = oracle_throughput(pool, frames_per_core, cores, seed=6000, name=name, arg=arg)
+    finally:
+        pool.close()
+    return {"value": round(v, 4), "unit": "Msamples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{frames} {what} ({frames_per_core} per core), TX+RX, {wall:.1f} s wall"}
+
+
+def nr5mhz_bench(torch, dev, st, peaks: dict, n_sms: int, sm_mhz: float, n_slots: int = 65536,
+                 cpu_leg: bool = True) -> dict:
     """5 MHz / 24 PRB, 15 kHz, one slot per stream (L = 384, N = 512, continuous OLS TX
     and RX, QPSK): 2^16 independent slots in one TX call and one RX call, each call
     against the HBM and FP32 rooflines of the method's work."""
@@ -588,11 +648,18 @@ def nr5mhz_bench(torch, dev, st, peaks: dict, n_sms: int, sm_mhz: float, n_slots
            "launches_per_call": {"tx": plan.tx_kernels, "rx": plan.rx_kernels},
            "roofline": {"tx": method_roofline(geom, plan, n_slots, tx, peaks, n_sms, sm_mhz),
                         "rx": method_roofline(geom, plan, n_slots, rx, peaks, n_sms, sm_mhz)}}
+    del est, ws
+    e2e_slots = 8192
+    out["e2e"] = host_e2e(torch, dev, plan, grid[:e2e_slots], wave[:e2e_slots], chunk=1024)
+    out["e2e"]["note"] = f"{e2e_slots} of the slots (a smaller set of pinned host buffers)"
+    if cpu_leg:
+        out["cpu_baseline"] = oracle_leg("single5", 256, what="5 MHz slots")
     plan.close()
     return out
 
 
-def nr100_paths_bench(torch, dev, st, peaks: dict, n_sms: int, sm_mhz: float, n_streams: int = 32) -> dict:
+def nr100_paths_bench(torch, dev, st, peaks: dict, n_sms: int, sm_mhz: float, n_streams: int = 32,
+                      cpu_leg: bool = True) -> dict:
     """100 MHz / 273 PRB carrier (N = L = 4096, 10 slots): the FP32 shared-memory FFT
     kernels against the tensor-core four-step GEMM-DFT path (FC_FLAG_TENSOR_DFT), same
     inputs. Each path's calls against the rooflines of the method's work (algorithmic
@@ -635,6 +702,7 @@ def nr100_paths_bench(torch, dev, st, peaks: dict, n_sms: int, sm_mhz: float, n_
                      "roofline": {"tx": method_roofline(base, plan, n_streams, tx, peaks, n_sms, sm_mhz),
                                   "rx": method_roofline(base, plan, n_streams, rx, peaks, n_sms, sm_mhz)}}
         waves[name] = wave[0].cpu().numpy()
+        out[name]["e2e"] = host_e2e(torch, dev, plan, grid, wave, chunk=8)
         if flags:
             d = base.groups[0]
             n_sym = len(d.n_cp)
@@ -652,6 +720,8 @@ def nr100_paths_bench(torch, dev, st, peaks: dict, n_sms: int, sm_mhz: float, n_
                            (out["tensor"]["tx_ms"] + out["tensor"]["rx_ms"]), 3)
     out["tx_rel_diff_tensor_vs_fp32"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
     out["workload"] = f"nr100mhz_30khz_273prb_N4096 x 10 slots, {n_streams} streams, continuous OLA TX / OLS RX"
+    if cpu_leg:
+        out["cpu_baseline"] = oracle_leg("nr100", 1, arg=1, what="one-slot frames of the 100 MHz carrier")
     return out
 
 
@@ -877,8 +947,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     uneven = uneven_carriers_bench(torch, dev, st, args.steps)
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = float(load_peaks()[0].get("sm_max_mhz", 2070.0))
-    nr100 = nr100_paths_bench(torch, dev, st, load_peaks()[0], n_sms, sm_mhz)
-    nr5 = nr5mhz_bench(torch, dev, st, load_peaks()[0], n_sms, sm_mhz)
+    side_cpu = world == 1 and not args.no_cpu_baseline
+    nr100 = nr100_paths_bench(torch, dev, st, load_peaks()[0], n_sms, sm_mhz, cpu_leg=side_cpu)
+    nr5 = nr5mhz_bench(torch, dev, st, load_peaks()[0], n_sms, sm_mhz, cpu_leg=side_cpu)
     serving = serving_bench(torch, dev, args.serve_requests) if args.serve_requests > 0 else None
 
     # ---- one sampled stream of the timed path, kept for the oracle check of the CPU leg ----
