@@ -163,8 +163,10 @@ size_t fc_tc_dft64_image_bytes();
 // one-warp-per-symbol symbol-synchronized kernels (fc_warp.cu): the job-major item list
 // of all streams (jobs: one stream's jobs in cost order) dealt to the resident CTAs; TX
 // zeroes the waveform first
+// weight_floats: the sum over groups of the group's subband length L (the TX weights the
+// kernel stages in shared memory)
 cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, int frame_len,
-                                   const float2* grid, float2* wave, int num_sms, cudaStream_t st);
+                                   int weight_floats, const float2* grid, float2* wave, int num_sms, cudaStream_t st);
 cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams,
                                    const float2* wave, float2* grid, int num_sms, cudaStream_t st);
 cudaError_t fc_set_warp_smem_limits();

@@ -167,6 +167,7 @@ struct fc_plan {
   int* d_err = nullptr;                     // device error word of the tensor-core kernels
   unsigned tc_first_wait = 1u << 22;        // poll limit of the tensor-core kernels' first GEMM wait
   FcJob* d_wjobs = nullptr;                 // one stream's jobs in cost order (warp kernels)
+  int warp_weight_floats = 0;               // sum over groups of the subband length (warp TX weights)
   size_t smem_tx = 0, smem_rx = 0, smem_ofdm = 0;
   int syms_per_stream = 0;
   fc_sizes sizes{};
@@ -703,6 +704,9 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   pl->tx_nchunks = ntx;
   pl->rx_nchunks = nrx;
   pl->warp_path = warp_ok;
+  pl->warp_weight_floats = 0;
+  if (warp_ok)
+    for (int g = 0; g < G; ++g) pl->warp_weight_floats += sh[gh[g].subs[0]].L;
   pl->cont_warp_tx = cont_warp && geo->scheme_tx == FC_OLS;
   pl->cont_warp_rx = cont_warp && geo->scheme_rx == FC_OLS;
   pl->tc_tx = tc_tx;
@@ -789,7 +793,8 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* 
   float2* wave = (float2*)out;
   // float4 reductions of the warp kernel need a 16-byte aligned waveform
   if (plan->warp_path && !c.generic && io == 0 && ((uintptr_t)wave & 15) == 0)
-    return fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, plan->h.frame_len, grid, wave,
+    return fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, plan->h.frame_len,
+                                  plan->warp_weight_floats, grid, wave,
                                   plan->num_sms, st);
   if (plan->h.mode == FC_SYMBOL_SYNC)
     return gen.tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, in,

@@ -46,6 +46,27 @@ struct JobTables {
   const float2* t2048;
 };
 
+// The TX kernel's tables staged in shared memory once per CTA: the forward twiddles of
+// 512, 1024 and 2048 points (the transforms, phi_r theta_n and the odd-sample rotation)
+// and each group's TX weights (the bin loops read them at data-dependent positions, and
+// from shared memory they cost less than from the L1 cache).
+constexpr int kTxTwiddles = 512 + 1024 + 2048;   // float2
+struct TxTables {
+  const float2* t1024;
+  const float2* t512;
+  const float2* t2048;
+};
+
+__device__ __forceinline__ float weight_staged(const FcSubDev& S, const float* d, int p) {
+  return (p >= S.p_lo && p < S.p_hi) ? d[p] : 0.f;
+}
+
+// exp(+j 2 pi e / n) from a staged forward twiddle table of size n (power of two)
+__device__ __forceinline__ float2 root_pos_staged(const float2* tw, int n, long long e) {
+  const float2 w = tw[(int)(e & (long long)(n - 1))];
+  return make_float2(w.x, -w.y);
+}
+
 __device__ __forceinline__ JobTables job_tables(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S) {
   JobTables t;
   if (S.L == 1024) {
@@ -74,9 +95,9 @@ __device__ __forceinline__ JobTables job_tables(const FcPlanDev& P, const FcGrou
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                        const float2* __restrict__ gsrc, float2* __restrict__ wdst, float2* scr,
-                                       float2* map, int lane) {
+                                       float2* map, int lane, const TxTables& tt, const float* wt) {
   const bool big = S.L == 1024;
-  const JobTables tb = job_tables(P, G, S);
+  const JobTables tb{tt.t1024, tt.t512, tt.t2048};
   const int n = jb.index;
   const int hl = S.Lact / 2, hu = S.Lact - hl;
   const float2* __restrict__ row = gsrc + S.grid_off + (long long)n * S.Lact;
@@ -85,8 +106,8 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
   const bool v4 = ((jb.start & 1) == 0);
   const float2* __restrict__ twN = big ? tb.t2048 : tb.t1024;
   const int nN = big ? 2048 : 1024;
-  const float2 ph0 = root_pos(twN, nN, (long long)S.c * G.cps[n]);                  // phi_0 theta_n
-  const float2 ph1 = root_pos(twN, nN, (long long)S.c * (G.cps[n] + G.N_S));       // phi_1 theta_n
+  const float2 ph0 = root_pos_staged(twN, nN, (long long)S.c * G.cps[n]);            // phi_0 theta_n
+  const float2 ph1 = root_pos_staged(twN, nN, (long long)S.c * (G.cps[n] + G.N_S)); // phi_1 theta_n
   const int nst = big ? 7 : 4;
   float2 v[32], keep[32];
 #pragma unroll 1
@@ -122,7 +143,7 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
           int kt = (qp - S.c) & 1023;
           if (kt >= 512) kt -= 1024;
           v[a] = y;
-          map[qp] = cmulc(y, __ldg(tb.t2048 + ((S.c + kt) & 2047)));   // y exp(+j 2 pi q / 2048)
+          map[qp] = cmulc(y, tb.t2048[(S.c + kt) & 2047]);            // y exp(+j 2 pi q / 2048)
         }
         inv = true;
       } else {                                          // T6: odd samples; the even outputs move from
@@ -170,7 +191,7 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
 #pragma unroll
           for (int k2 = 0; k2 < 32; ++k2) {
             const int kt = signed_bin((lane & 15) + 16 * k2, 512);
-            map[(S.c + kt) & 1023] = cscale(cmul(keep[k2], ph), weight(S, S.dtx, kt + 256));
+            map[(S.c + kt) & 1023] = cscale(cmul(keep[k2], ph), weight_staged(S, wt, kt + 256));
             if ((k2 & 7) == 7) sched_fence();
           }
         }
@@ -184,7 +205,7 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
     }
     // ---------------- transform ----------------
     if (inv) conj32(v);
-    warp_fft(v, scr, tb.t1024, tb.t512, lane, two512);
+    warp_fft<true>(v, scr, tb.t1024, tb.t512, lane, two512);
     if (inv) conj32(v);
     // ---------------- consume ----------------
     if (big) {
@@ -196,7 +217,7 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
 #pragma unroll
         for (int k2 = 0; k2 < 32; ++k2) {
           const int kt = signed_bin(lane + 32 * k2, 1024);
-          map[(S.c + kt) & 1023] = cscale(cmul(v[k2], ph), weight(S, S.dtx, kt + 512));
+          map[(S.c + kt) & 1023] = cscale(cmul(v[k2], ph), weight_staged(S, wt, kt + 512));
           if ((k2 & 7) == 7) sched_fence();
         }
         __syncwarp();
@@ -653,10 +674,31 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
                      const float2* __restrict__ grid, float2* __restrict__ wave) {
   __shared__ FcPlanDev P;
   __shared__ int next_item;
+  __shared__ int wt_off[FC_MAX_GROUPS];
   extern __shared__ __align__(16) float2 wscr[];
   load_plan_w(P, gP);
   if (threadIdx.x == 0) next_item = 0;
   __syncthreads();                                  // the plan copy is complete before any use
+  // stage the tables: twiddles [512 | 1024 | 2048], then every group's weights
+  float2* tabs = wscr + kWarps * kScratch;
+  float* wts = reinterpret_cast<float*>(tabs + kTxTwiddles);
+  for (int i = 0; i < P.n_sizes; ++i) {
+    const int n = P.sz[i].n;
+    const int at = n == 512 ? 0 : (n == 1024 ? 512 : (n == 2048 ? 1536 : -1));
+    if (at < 0) continue;
+    for (int m = threadIdx.x; m < n; m += blockDim.x) tabs[at + m] = __ldg(P.sz[i].tw + m);
+  }
+  {
+    int off = 0;
+    for (int g = 0; g < P.n_groups; ++g) {
+      const FcSubDev& S = P.s[P.g[g].first_sub];
+      if (threadIdx.x == 0) wt_off[g] = off;
+      for (int p = threadIdx.x; p < S.L; p += blockDim.x) wts[off + p] = __ldg(S.dtx + p);
+      off += S.L;
+    }
+  }
+  __syncthreads();
+  const TxTables tt{tabs + 512, tabs, tabs + 1536};
   const long long total = (long long)n_jobs * n_streams;
   const int lane = threadIdx.x & 31;
   float2* scr = wscr + (threadIdx.x >> 5) * kScratch;
@@ -682,7 +724,7 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     const FcJob jb = jobs[j];
     const FcGroupDev& G = P.g[jb.group];
     tx_job(P, G, P.s[G.first_sub], jb, grid + (size_t)stream * P.grid_len, wave + (size_t)stream * P.frame_len, scr,
-           map, lane);
+           map, lane, tt, wts + wt_off[jb.group]);
   }
 }
 
@@ -691,20 +733,24 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
 
 size_t fc_warp_smem_bytes() { return (size_t)kWarps * kScratch * sizeof(float2); }
 
+// the TX kernel's dynamic shared memory: per-warp scratch + staged twiddles + weights
+static size_t tx_smem_bytes(int weight_floats) {
+  return fc_warp_smem_bytes() + (size_t)kTxTwiddles * sizeof(float2) + (((size_t)weight_floats * 4 + 15) & ~(size_t)15);
+}
+
 cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, int frame_len,
-                                   const float2* grid, float2* wave, int num_sms, cudaStream_t st) {
+                                   int weight_floats, const float2* grid, float2* wave, int num_sms, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(wave, 0, (size_t)n_streams * frame_len * sizeof(float2), st);
   if (e != cudaSuccess) return e;
+  const size_t smem = tx_smem_bytes(weight_floats);
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tx_sync_warp, FC_WARP_THREADS,
-                                                    fc_warp_smem_bytes());
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tx_sync_warp, FC_WARP_THREADS, smem);
   if (e != cudaSuccess) return e;
   const long long total = (long long)n_jobs * n_streams;
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  k_tx_sync_warp<<<dim3((unsigned)ctas), FC_WARP_THREADS, fc_warp_smem_bytes(), st>>>(dP, jobs, n_jobs, n_streams,
-                                                                                   grid, wave);
+  k_tx_sync_warp<<<dim3((unsigned)ctas), FC_WARP_THREADS, smem, st>>>(dP, jobs, n_jobs, n_streams, grid, wave);
   return cudaGetLastError();
 }
 
@@ -726,7 +772,7 @@ cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n
 cudaError_t fc_set_warp_smem_limits() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_tx_sync_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)fc_warp_smem_bytes())))
+                                (int)tx_smem_bytes(FC_MAX_GROUPS * 1024))))
     return e;
   return cudaFuncSetAttribute(k_rx_sync_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)fc_warp_smem_bytes());

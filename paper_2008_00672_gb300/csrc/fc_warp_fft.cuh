@@ -30,20 +30,29 @@ __device__ __forceinline__ float2 root_pos(const float2* __restrict__ tw, int n,
 // ahead of its first use (which would need twice the registers of the data).
 __device__ __forceinline__ void sched_fence() { asm volatile("" ::: "memory"); }
 
+// Table read: through the read-only data path for a table in global memory, a plain
+// load for one staged in shared memory (STAGED).
+template <bool STAGED>
+__device__ __forceinline__ float2 tw_ld(const float2* __restrict__ p) {
+  if constexpr (STAGED) return *p;
+  else return __ldg(p);
+}
+
 // v[k] *= W^{lane e(k)} for k = 1..31 with e(k) = 4 (m & mmask) + j, k = 4 m + j.
 // One 1024-point transform: tw = W_1024 table, mmask = 7 (e = k). Two 512-point
 // transforms: tw = W_512 table, mmask = 3 (e = k mod 16, the same twiddles for both).
 // W^{lane e} = W^{4 (m & mmask) lane} W^{j lane}: 11 table loads and one complex
 // multiply per twiddle (one rounding away from the FP64-generated table; the
 // table's entry 0 is exactly 1).
+template <bool STAGED = false>
 __device__ __forceinline__ void step_twiddles(float2 (&v)[32], const float2* __restrict__ tw, int lane, int mmask) {
   float2 tj[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) tj[j] = __ldg(tw + lane * j);
+  for (int j = 0; j < 4; ++j) tj[j] = tw_ld<STAGED>(tw + lane * j);
 #pragma unroll
   for (int m = 0; m < 8; ++m) {
     sched_fence();
-    const float2 tm = __ldg(tw + lane * 4 * (m & mmask));
+    const float2 tm = tw_ld<STAGED>(tw + lane * 4 * (m & mmask));
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int k = 4 * m + j;
@@ -58,6 +67,8 @@ __device__ __forceinline__ void step_twiddles(float2 (&v)[32], const float2* __r
 //                  out: lane k1 holds X[k1 + 32 k2] in v[k2].
 //  two512 = true:  two 512-point transforms; in: lane b holds x_T[32 a + b] in
 //                  v[16 T + a] (a < 16); out: lane k1 + 16 T holds X_T[k1 + 16 k2] in v[k2].
+// STAGED: the twiddle tables are in shared memory.
+template <bool STAGED = false>
 __device__ __forceinline__ void warp_fft(float2 (&v)[32], float2* scr, const float2* __restrict__ tw1024,
                                          const float2* __restrict__ tw512, int lane, bool two512) {
   if (!two512) {
@@ -66,7 +77,7 @@ __device__ __forceinline__ void warp_fft(float2 (&v)[32], float2* scr, const flo
     Dft<16, false>::run(v);
     Dft<16, false>::run(v + 16);
   }
-  step_twiddles(v, two512 ? tw512 : tw1024, lane, two512 ? 3 : 7);
+  step_twiddles<STAGED>(v, two512 ? tw512 : tw1024, lane, two512 ? 3 : 7);
 #pragma unroll
   for (int k = 0; k < 32; ++k) scr[k * kPad + lane] = v[k];
   __syncwarp();
