@@ -114,14 +114,15 @@ constexpr int kL = 384, kN = 512, kH = kL / 2;
 // Two 384-point DFTs (INV: inverse without 1/n) of one warp, four-step 12 x 32.
 // In: lane l holds x_b[32 a + l] in v[12 b + a] (a < 12, b < 2).
 // Out: lane 12 b + k1 (< 24) holds X_b[k1 + 12 k2] in v[k2]; lanes 24..31 hold nothing.
-// scr: the warp's transpose buffer (32 x kPad float2); tw = forward table of size 384.
-template <bool INV>
+// scr: the warp's transpose buffer (32 x kPad float2); tw = forward table of size 384
+// (in shared memory if STAGED).
+template <bool INV, bool STAGED = false>
 __device__ __forceinline__ void dft384x2(float2 (&v)[32], float2* scr, const float2* __restrict__ tw, int lane) {
   Dft<12, INV>::run(v);
   Dft<12, INV>::run(v + 12);
 #pragma unroll
   for (int k1 = 1; k1 < 12; ++k1) {              // W_384^(lane k1), the same for both items
-    float2 w = __ldg(tw + lane * k1);
+    float2 w = tw_ld<STAGED>(tw + lane * k1);
     if (INV) w.y = -w.y;
     v[k1] = cmul(v[k1], w);
     v[12 + k1] = cmul(v[12 + k1], w);
@@ -136,6 +137,38 @@ __device__ __forceinline__ void dft384x2(float2 (&v)[32], float2* scr, const flo
 }
 
 __device__ __forceinline__ int signed_bin384(int k) { return k < kH ? k : k - kL; }
+
+// The block kernels' tables staged in shared memory once per CTA, after the warps'
+// transpose buffers: the forward twiddles of 384 and 512 points, then the subband's
+// weights (TX or RX); the bin loops read the weights at positions that depend on the
+// carrier, and shared memory serves them in fewer cycles than the L1 cache.
+constexpr int kContTables = kL + kN;                 // float2, then kL floats of weights
+constexpr size_t kContTableBytes = kContTables * sizeof(float2) + kL * sizeof(float);
+
+struct ContTables {
+  const float2* twL;
+  const float2* twN;
+  const float* w;
+};
+
+__device__ __forceinline__ ContTables stage_cont_tables(const FcPlanDev& P, float2* base, const float* weights) {
+  const FcSubDev& S = P.s[0];
+  const FcGroupDev& G = P.g[0];
+  float* w = reinterpret_cast<float*>(base + kContTables);
+  for (int m = threadIdx.x; m < kL; m += blockDim.x) {
+    base[m] = __ldg(P.sz[S.size_L].tw + m);
+    w[m] = __ldg(weights + m);
+  }
+  for (int m = threadIdx.x; m < kN; m += blockDim.x) base[kL + m] = __ldg(P.sz[G.size_N].tw + m);
+  __syncthreads();
+  return ContTables{base, base + kL, w};
+}
+
+// exp(+j 2 pi e / n) from a staged forward twiddle table of size n (power of two)
+__device__ __forceinline__ float2 root_pos_staged(const float2* tw, int n, long long e) {
+  const float2 w = tw[(int)(e & (long long)(n - 1))];
+  return make_float2(w.x, -w.y);
+}
 
 // warp-level persistent item loop: items [0, total), warp w of the grid takes w, w + W, ...
 struct WarpItems {
@@ -211,8 +244,7 @@ k_tx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
   const FcGroupDev& G = P.g[0];
   const FcSubDev& S = P.s[0];
   const int R = G.R, pairs = (R + 1) / 2;
-  const float2* __restrict__ twL = P.sz[S.size_L].tw;
-  const float2* __restrict__ twN = P.sz[G.size_N].tw;
+  const ContTables T = stage_cont_tables(P, wscr + kWarps * kTrans, S.dtx);
   const long long total = (long long)n_streams * pairs;
   for (long long item = WarpItems().first; item < total; item += WarpItems().step) {
     const int stream = (int)(item / pairs), r0 = 2 * (int)(item - (long long)stream * pairs);
@@ -231,7 +263,7 @@ k_tx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
 #pragma unroll
     for (int a = 24; a < 32; ++a) v[a] = czero();
     // T4: short DFTs
-    dft384x2<false>(v, scr, twL, lane);
+    dft384x2<false, true>(v, scr, T.twL, lane);
     // T5: shift P^(L/2), D_m and phi_r, bin map into the two 512-bin spectra
     float2* map = scr;
 #pragma unroll
@@ -240,14 +272,14 @@ k_tx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
     if (lane < 24) {
       const int b = lane >= 12, k1 = lane - 12 * b;
       if (b < nb) {
-        const float2 ph = root_pos(twN, kN, (long long)S.c * (r0 + b) * G.N_S);
+        const float2 ph = root_pos_staged(T.twN, kN, (long long)S.c * (r0 + b) * G.N_S);
 #pragma unroll
         for (int k2 = 0; k2 < 32; ++k2) {
           const int k = k1 + 12 * k2;
           int p = k + kH;
           if (p >= kL) p -= kL;
           if (p >= S.p_lo && p < S.p_hi)
-            map[kN * b + ((S.c + p - kH) & (kN - 1))] = cscale(cmul(v[k2], ph), __ldg(S.dtx + p));
+            map[kN * b + ((S.c + p - kH) & (kN - 1))] = cscale(cmul(v[k2], ph), T.w[p]);
         }
       }
     }
@@ -259,7 +291,7 @@ k_tx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
     __syncwarp();
     // T6: long IDFTs (1/N and sqrt(I) folded into D)
     conj32(v);
-    warp_fft(v, scr, twN, twN, lane, true);
+    warp_fft<true>(v, scr, T.twN, T.twN, lane, true);
     conj32(v);
     // T7: S window [N_L, N_L + N_S) of block r at r N_S; the frame's first N_L and last
     // N_T samples, which no window covers, are zeros
@@ -293,8 +325,7 @@ k_rx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
   const FcGroupDev& G = P.g[0];
   const FcSubDev& S = P.s[0];
   const int R = G.R, pairs = (R + 1) / 2;
-  const float2* __restrict__ twL = P.sz[S.size_L].tw;
-  const float2* __restrict__ twN = P.sz[G.size_N].tw;
+  const ContTables T = stage_cont_tables(P, wscr + kWarps * kTrans, S.drx);
   const long long total = (long long)n_streams * pairs;
   for (long long item = WarpItems().first; item < total; item += WarpItems().step) {
     const int stream = (int)(item / pairs), r0 = 2 * (int)(item - (long long)stream * pairs);
@@ -308,18 +339,18 @@ k_rx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
       for (int a = 0; a < 16; ++a)
         v[16 * b + a] = b < nb ? __ldg(x + (long long)(r0 + b) * G.N_S + 32 * a + lane) : czero();
     // R2: long DFTs; lane k1 + 16 T holds Y_T[k1 + 16 k2] in v[k2]
-    warp_fft(v, scr, twN, twN, lane, true);
+    warp_fft<true>(v, scr, T.twN, T.twN, lane, true);
     float2* map = scr;
     {
-      const int T = lane >> 4, k1 = lane & 15;
+      const int half = lane >> 4, k1 = lane & 15;
 #pragma unroll
-      for (int k2 = 0; k2 < 32; ++k2) map[kN * T + k1 + 16 * k2] = v[k2];
+      for (int k2 = 0; k2 < 32; ++k2) map[kN * half + k1 + 16 * k2] = v[k2];
     }
     __syncwarp();
     // R3: gather with conj(phi_r), D_m, inverse shift, into the short IDFTs' input layout
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-      const float2 ph = root_pos(twN, kN, (long long)S.c * (r0 + b) * G.N_S);
+      const float2 ph = root_pos_staged(T.twN, kN, (long long)S.c * (r0 + b) * G.N_S);
 #pragma unroll
       for (int a = 0; a < 12; ++a) {
         const int k = 32 * a + lane;
@@ -327,7 +358,7 @@ k_rx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
         if (p >= kL) p -= kL;
         float2 u = czero();
         if (b < nb && p >= S.p_lo && p < S.p_hi)
-          u = cscale(cmulc(map[kN * b + ((S.c + p - kH) & (kN - 1))], ph), __ldg(S.drx + p));
+          u = cscale(cmulc(map[kN * b + ((S.c + p - kH) & (kN - 1))], ph), T.w[p]);
         v[12 * b + a] = u;
       }
     }
@@ -335,7 +366,7 @@ k_rx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
     for (int a = 24; a < 32; ++a) v[a] = czero();
     __syncwarp();
     // R4: short IDFTs
-    dft384x2<true>(v, scr, twL, lane);
+    dft384x2<true, true>(v, scr, T.twL, lane);
     // R5: keep [L_L, L_L + L_S) of block r at low-rate position r L_S + L_L - S_L
     if (lane < 24) {
       const int b = lane >= 12, k1 = lane - 12 * b;
@@ -399,8 +430,8 @@ k_ofdm_demod_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2*
 
 template <class K>
 cudaError_t launch_w(K kern, long long items, int num_sms, cudaStream_t st, const FcPlanDev* dP, int n_streams,
-                     const float2* in, float2* out) {
-  const size_t smem = (size_t)kWarps * kTrans * sizeof(float2);
+                     const float2* in, float2* out, size_t tables = 0) {
+  const size_t smem = (size_t)kWarps * kTrans * sizeof(float2) + tables;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FC_WARP_THREADS, smem);
   if (e != cudaSuccess) return e;
@@ -419,13 +450,14 @@ cudaError_t fc_launch_tx_cont_warp(const FcPlanDev* dP, int n_streams, int n_sym
   cudaError_t e = launch_w(k_ofdm_mod_w384, (long long)n_streams * ((n_symbols + 1) / 2), num_sms, st, dP, n_streams,
                            grid, ws);
   if (e != cudaSuccess) return e;
-  return launch_w(k_tx_cont_w384, (long long)n_streams * ((n_blocks + 1) / 2), num_sms, st, dP, n_streams, ws, wave);
+  return launch_w(k_tx_cont_w384, (long long)n_streams * ((n_blocks + 1) / 2), num_sms, st, dP, n_streams, ws, wave,
+                  kContTableBytes);
 }
 
 cudaError_t fc_launch_rx_cont_warp(const FcPlanDev* dP, int n_streams, int n_symbols, int n_blocks, const float2* wave,
                                    float2* ws, float2* grid, int num_sms, cudaStream_t st) {
   cudaError_t e = launch_w(k_rx_cont_w384, (long long)n_streams * ((n_blocks + 1) / 2), num_sms, st, dP, n_streams,
-                           wave, ws);
+                           wave, ws, kContTableBytes);
   if (e != cudaSuccess) return e;
   return launch_w(k_ofdm_demod_w384, (long long)n_streams * ((n_symbols + 1) / 2), num_sms, st, dP, n_streams, ws, grid);
 }
