@@ -46,25 +46,20 @@ struct JobTables {
   const float2* t2048;
 };
 
-// The TX kernel's tables staged in shared memory once per CTA: the forward twiddles of
-// 512, 1024 and 2048 points (the transforms, phi_r theta_n and the odd-sample rotation)
-// and each group's TX weights (the bin loops read them at data-dependent positions, and
-// from shared memory they cost less than from the L1 cache).
-constexpr int kTxTwiddles = 512 + 1024 + 2048;   // float2
+// The TX kernel's tables staged in shared memory once per CTA: the per-lane step
+// twiddles of the 512-point (16 rows) and 1024-point (32 rows) transforms, the full
+// 2048-point forward table (the odd-sample rotation) and each group's TX weights (the bin
+// loops read them at data-dependent positions; from shared memory they cost less than
+// from the L1 cache).
+constexpr int kTxTwiddles = 16 * 32 + 32 * 32 + 2048;   // float2
 struct TxTables {
-  const float2* t1024;
-  const float2* t512;
-  const float2* t2048;
+  const float2* t1024;    // per-lane step table, 1024 points
+  const float2* t512;     // per-lane step table, 512 points
+  const float2* t2048;    // full forward table, 2048 points
 };
 
 __device__ __forceinline__ float weight_staged(const FcSubDev& S, const float* d, int p) {
   return (p >= S.p_lo && p < S.p_hi) ? d[p] : 0.f;
-}
-
-// exp(+j 2 pi e / n) from a staged forward twiddle table of size n (power of two)
-__device__ __forceinline__ float2 root_pos_staged(const float2* tw, int n, long long e) {
-  const float2 w = tw[(int)(e & (long long)(n - 1))];
-  return make_float2(w.x, -w.y);
 }
 
 __device__ __forceinline__ JobTables job_tables(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S) {
@@ -104,10 +99,10 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
   const int lcp = S.lcp[n], ncp = G.ncp[n];
   const bool ols = P.scheme_tx == FC_OLS;
   const bool v4 = ((jb.start & 1) == 0);
-  const float2* __restrict__ twN = big ? tb.t2048 : tb.t1024;
   const int nN = big ? 2048 : 1024;
-  const float2 ph0 = root_pos_staged(twN, nN, (long long)S.c * G.cps[n]);            // phi_0 theta_n
-  const float2 ph1 = root_pos_staged(twN, nN, (long long)S.c * (G.cps[n] + G.N_S)); // phi_1 theta_n
+  const float2* __restrict__ twNg = P.sz[G.size_N].tw;                              // the plan's full table
+  const float2 ph0 = root_pos(twNg, nN, (long long)S.c * G.cps[n]);                  // phi_0 theta_n
+  const float2 ph1 = root_pos(twNg, nN, (long long)S.c * (G.cps[n] + G.N_S));       // phi_1 theta_n
   const int nst = big ? 7 : 4;
   float2 v[32], keep[32];
 #pragma unroll 1
@@ -684,9 +679,10 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
   float* wts = reinterpret_cast<float*>(tabs + kTxTwiddles);
   for (int i = 0; i < P.n_sizes; ++i) {
     const int n = P.sz[i].n;
-    const int at = n == 512 ? 0 : (n == 1024 ? 512 : (n == 2048 ? 1536 : -1));
-    if (at < 0) continue;
-    for (int m = threadIdx.x; m < n; m += blockDim.x) tabs[at + m] = __ldg(P.sz[i].tw + m);
+    if (n == 512) stage_lane_twiddles(tabs, P.sz[i].tw, 512, 16);
+    if (n == 1024) stage_lane_twiddles(tabs + 512, P.sz[i].tw, 1024, 32);
+    if (n == 2048)
+      for (int m = threadIdx.x; m < n; m += blockDim.x) tabs[1536 + m] = __ldg(P.sz[i].tw + m);
   }
   {
     int off = 0;

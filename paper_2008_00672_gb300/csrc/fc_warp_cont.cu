@@ -114,15 +114,15 @@ constexpr int kL = 384, kN = 512, kH = kL / 2;
 // Two 384-point DFTs (INV: inverse without 1/n) of one warp, four-step 12 x 32.
 // In: lane l holds x_b[32 a + l] in v[12 b + a] (a < 12, b < 2).
 // Out: lane 12 b + k1 (< 24) holds X_b[k1 + 12 k2] in v[k2]; lanes 24..31 hold nothing.
-// scr: the warp's transpose buffer (32 x kPad float2); tw = forward table of size 384
-// (in shared memory if STAGED).
+// scr: the warp's transpose buffer (32 x kPad float2); tw = forward table of size 384,
+// or with STAGED a per-lane step table in shared memory (row k1 holds W_384^(k1 lane)).
 template <bool INV, bool STAGED = false>
 __device__ __forceinline__ void dft384x2(float2 (&v)[32], float2* scr, const float2* __restrict__ tw, int lane) {
   Dft<12, INV>::run(v);
   Dft<12, INV>::run(v + 12);
 #pragma unroll
   for (int k1 = 1; k1 < 12; ++k1) {              // W_384^(lane k1), the same for both items
-    float2 w = tw_ld<STAGED>(tw + lane * k1);
+    float2 w = STAGED ? tw[k1 * 32 + lane] : __ldg(tw + lane * k1);
     if (INV) w.y = -w.y;
     v[k1] = cmul(v[k1], w);
     v[12 + k1] = cmul(v[12 + k1], w);
@@ -139,15 +139,16 @@ __device__ __forceinline__ void dft384x2(float2 (&v)[32], float2* scr, const flo
 __device__ __forceinline__ int signed_bin384(int k) { return k < kH ? k : k - kL; }
 
 // The block kernels' tables staged in shared memory once per CTA, after the warps'
-// transpose buffers: the forward twiddles of 384 and 512 points, then the subband's
-// weights (TX or RX); the bin loops read the weights at positions that depend on the
-// carrier, and shared memory serves them in fewer cycles than the L1 cache.
-constexpr int kContTables = kL + kN;                 // float2, then kL floats of weights
+// transpose buffers: per-lane step twiddles (row e holds W^(e lane), lane = 0..31; one
+// conflict-free read per twiddle) of the 384-point four-step (12 rows) and of the
+// two 512-point transforms (16 rows), then the subband's weights (TX or RX), which the bin
+// loops read at positions that depend on the carrier.
+constexpr int kContTables = 12 * 32 + 16 * 32;       // float2, then kL floats of weights
 constexpr size_t kContTableBytes = kContTables * sizeof(float2) + kL * sizeof(float);
 
 struct ContTables {
-  const float2* twL;
-  const float2* twN;
+  const float2* twL;      // per-lane step table, 384 points
+  const float2* twN;      // per-lane step table, 512 points
   const float* w;
 };
 
@@ -155,19 +156,11 @@ __device__ __forceinline__ ContTables stage_cont_tables(const FcPlanDev& P, floa
   const FcSubDev& S = P.s[0];
   const FcGroupDev& G = P.g[0];
   float* w = reinterpret_cast<float*>(base + kContTables);
-  for (int m = threadIdx.x; m < kL; m += blockDim.x) {
-    base[m] = __ldg(P.sz[S.size_L].tw + m);
-    w[m] = __ldg(weights + m);
-  }
-  for (int m = threadIdx.x; m < kN; m += blockDim.x) base[kL + m] = __ldg(P.sz[G.size_N].tw + m);
+  stage_lane_twiddles(base, P.sz[S.size_L].tw, kL, 12);
+  stage_lane_twiddles(base + 12 * 32, P.sz[G.size_N].tw, kN, 16);
+  for (int m = threadIdx.x; m < kL; m += blockDim.x) w[m] = __ldg(weights + m);
   __syncthreads();
-  return ContTables{base, base + kL, w};
-}
-
-// exp(+j 2 pi e / n) from a staged forward twiddle table of size n (power of two)
-__device__ __forceinline__ float2 root_pos_staged(const float2* tw, int n, long long e) {
-  const float2 w = tw[(int)(e & (long long)(n - 1))];
-  return make_float2(w.x, -w.y);
+  return ContTables{base, base + 12 * 32, w};
 }
 
 // warp-level persistent item loop: items [0, total), warp w of the grid takes w, w + W, ...
@@ -272,7 +265,7 @@ k_tx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
     if (lane < 24) {
       const int b = lane >= 12, k1 = lane - 12 * b;
       if (b < nb) {
-        const float2 ph = root_pos_staged(T.twN, kN, (long long)S.c * (r0 + b) * G.N_S);
+        const float2 ph = root_pos(P.sz[G.size_N].tw, kN, (long long)S.c * (r0 + b) * G.N_S);
 #pragma unroll
         for (int k2 = 0; k2 < 32; ++k2) {
           const int k = k1 + 12 * k2;
@@ -350,7 +343,7 @@ k_rx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
     // R3: gather with conj(phi_r), D_m, inverse shift, into the short IDFTs' input layout
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-      const float2 ph = root_pos_staged(T.twN, kN, (long long)S.c * (r0 + b) * G.N_S);
+      const float2 ph = root_pos(P.sz[G.size_N].tw, kN, (long long)S.c * (r0 + b) * G.N_S);
 #pragma unroll
       for (int a = 0; a < 12; ++a) {
         const int k = 32 * a + lane;

@@ -30,36 +30,43 @@ __device__ __forceinline__ float2 root_pos(const float2* __restrict__ tw, int n,
 // ahead of its first use (which would need twice the registers of the data).
 __device__ __forceinline__ void sched_fence() { asm volatile("" ::: "memory"); }
 
-// Table read: through the read-only data path for a table in global memory, a plain
-// load for one staged in shared memory (STAGED).
-template <bool STAGED>
-__device__ __forceinline__ float2 tw_ld(const float2* __restrict__ p) {
-  if constexpr (STAGED) return *p;
-  else return __ldg(p);
-}
-
 // v[k] *= W^{lane e(k)} for k = 1..31 with e(k) = 4 (m & mmask) + j, k = 4 m + j.
 // One 1024-point transform: tw = W_1024 table, mmask = 7 (e = k). Two 512-point
 // transforms: tw = W_512 table, mmask = 3 (e = k mod 16, the same twiddles for both).
 // W^{lane e} = W^{4 (m & mmask) lane} W^{j lane}: 11 table loads and one complex
 // multiply per twiddle (one rounding away from the FP64-generated table; the
 // table's entry 0 is exactly 1).
+// STAGED: tw is instead a per-lane table in shared memory whose row e (32 float2) holds
+// W^(e lane) for lane = 0..31 (rows 0..31 for 1024 points, 0..15 for 512), so that each
+// twiddle is one conflict-free shared-memory read and no multiply composes it (strided
+// reads tw[lane 4 m] of a plain table would hit one bank from every lane).
 template <bool STAGED = false>
 __device__ __forceinline__ void step_twiddles(float2 (&v)[32], const float2* __restrict__ tw, int lane, int mmask) {
-  float2 tj[4];
+  if constexpr (STAGED) {
 #pragma unroll
-  for (int j = 0; j < 4; ++j) tj[j] = tw_ld<STAGED>(tw + lane * j);
+    for (int k = 1; k < 32; ++k) v[k] = cmul(v[k], tw[((k & (4 * mmask + 3))) * 32 + lane]);
+  } else {
+    float2 tj[4];
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    sched_fence();
-    const float2 tm = tw_ld<STAGED>(tw + lane * 4 * (m & mmask));
+    for (int j = 0; j < 4; ++j) tj[j] = __ldg(tw + lane * j);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int k = 4 * m + j;
-      if (k == 0) continue;
-      v[k] = cmul(v[k], j ? cmul(tm, tj[j]) : tm);
+    for (int m = 0; m < 8; ++m) {
+      sched_fence();
+      const float2 tm = __ldg(tw + lane * 4 * (m & mmask));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = 4 * m + j;
+        if (k == 0) continue;
+        v[k] = cmul(v[k], j ? cmul(tm, tj[j]) : tm);
+      }
     }
   }
+}
+
+// Fill a per-lane step table for step_twiddles<true>: row e, lane l = W_n^(e l) from the
+// forward table of size n (all threads of the CTA; the caller synchronises).
+__device__ __forceinline__ void stage_lane_twiddles(float2* dst, const float2* __restrict__ tw, int n, int rows) {
+  for (int i = threadIdx.x; i < rows * 32; i += blockDim.x) dst[i] = __ldg(tw + ((i >> 5) * (i & 31)) % n);
 }
 
 // Forward four-step FFT of one warp.
@@ -67,7 +74,7 @@ __device__ __forceinline__ void step_twiddles(float2 (&v)[32], const float2* __r
 //                  out: lane k1 holds X[k1 + 32 k2] in v[k2].
 //  two512 = true:  two 512-point transforms; in: lane b holds x_T[32 a + b] in
 //                  v[16 T + a] (a < 16); out: lane k1 + 16 T holds X_T[k1 + 16 k2] in v[k2].
-// STAGED: the twiddle tables are in shared memory.
+// STAGED: tw1024 / tw512 are per-lane step tables in shared memory (step_twiddles).
 template <bool STAGED = false>
 __device__ __forceinline__ void warp_fft(float2 (&v)[32], float2* scr, const float2* __restrict__ tw1024,
                                          const float2* __restrict__ tw512, int lane, bool two512) {
