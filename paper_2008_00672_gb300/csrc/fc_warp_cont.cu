@@ -282,9 +282,10 @@ k_tx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
 #pragma unroll
       for (int a = 0; a < 16; ++a) v[16 * b + a] = map[kN * b + 32 * a + lane];
     __syncwarp();
-    // T6: long IDFTs (1/N and sqrt(I) folded into D)
+    // T6: long IDFTs (1/N and sqrt(I) folded into D); step twiddles from the global table
+    // (measured faster here than the staged per-lane table, which the RX kernel uses)
     conj32(v);
-    warp_fft<true>(v, scr, T.twN, T.twN, lane, true);
+    warp_fft(v, scr, P.sz[G.size_N].tw, P.sz[G.size_N].tw, lane, true);
     conj32(v);
     // T7: S window [N_L, N_L + N_S) of block r at r N_S; the frame's first N_L and last
     // N_T samples, which no window covers, are zeros
