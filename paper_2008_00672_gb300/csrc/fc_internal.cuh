@@ -168,7 +168,7 @@ size_t fc_tc_dft64_image_bytes();
 cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, int frame_len,
                                    int weight_floats, const float2* grid, float2* wave, int num_sms, cudaStream_t st);
 cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams,
-                                   const float2* wave, float2* grid, int num_sms, cudaStream_t st);
+                                   int weight_floats, const float2* wave, float2* grid, int num_sms, cudaStream_t st);
 cudaError_t fc_set_warp_smem_limits();
 // Continuous mode, one subband with L = L_OFDM = 384, N = 512, 50 % overlap, overlap-save
 // (fc_warp_cont.cu): OFDM modulation into the workspace then FC blocks (TX), FC blocks into

@@ -834,7 +834,8 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* 
   const float2* wave = (const float2*)in;
   float2* grid = (float2*)out;
   if (plan->warp_path && !c.generic && io == 0)
-    return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, wave, grid, plan->num_sms,
+    return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, plan->warp_weight_floats, wave,
+                                  grid, plan->num_sms,
                                   st);
   if (plan->h.mode == FC_SYMBOL_SYNC)
     return gen.rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, in,

@@ -31,6 +31,11 @@ using namespace fcwarp;
 constexpr int kMap = 1024;                     // per-warp spectrum / re-layout buffer (float2)
 constexpr int kScratch = kTrans + kMap;
 constexpr int kWarps = FC_WARP_THREADS / 32;
+// RX: one CTA of 12 warps per SM (the register file's limit at 168 registers), sharing the
+// staged tables: per-lane step twiddles of 1024 points (32 rows) and 512 points (16 rows)
+constexpr int kRxThreads = 384;
+constexpr int kRxWarps = kRxThreads / 32;
+constexpr int kRxTwiddles = 32 * 32 + 16 * 32;   // float2
 
 __device__ __forceinline__ float weight(const FcSubDev& S, const float* __restrict__ d, int p) {
   return (p >= S.p_lo && p < S.p_hi) ? __ldg(d + p) : 0.f;
@@ -275,8 +280,17 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
 // hundred bytes of spills included). The L = 1024 block loop carries only block 0's part
 // of the symbol body into the block-1 iteration, which assembles and demodulates it.
 // ---------------------------------------------------------------------------
-template <int K, bool INV>
+template <int K, bool INV, bool STAGED = false>
 __device__ __forceinline__ void step_twiddles_k(float2* v, const float2* __restrict__ tw, int lane) {
+  if constexpr (STAGED) {             // per-lane step table in shared memory: row k holds W^(k lane)
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+      float2 w = tw[k * 32 + lane];
+      if (INV) w.y = -w.y;
+      v[k] = cmul(v[k], w);
+    }
+    return;
+  }
   float2 tj[4];
   tj[0] = make_float2(1.f, 0.f);
 #pragma unroll
@@ -297,10 +311,10 @@ __device__ __forceinline__ void step_twiddles_k(float2* v, const float2* __restr
 
 // Four-step 1024-point FFT. In: lane b holds x[32 a + b] in v[a].
 // Out: lane k1 holds X[k1 + 32 k2] in v[k2]. tw = forward table of size 1024.
-template <bool INV>
+template <bool INV, bool STAGED = false>
 __device__ __forceinline__ void warp_fft1024_d(float2 (&v)[32], float2* scr, const float2* __restrict__ tw, int lane) {
   Dft<32, INV>::run(v);
-  step_twiddles_k<32, INV>(v, tw, lane);
+  step_twiddles_k<32, INV, STAGED>(v, tw, lane);
 #pragma unroll
   for (int k = 0; k < 32; ++k) scr[k * kPad + lane] = v[k];
   __syncwarp();
@@ -313,7 +327,7 @@ __device__ __forceinline__ void warp_fft1024_d(float2 (&v)[32], float2* scr, con
 // Two four-step 512-point FFTs (16 x 32). In: lane b holds x_T[32 a + b] in
 // v[16 T + a], a < 16. Out: lane L = k1 + 16 T holds X_T[k1 + 16 k2] in v[k2].
 // tw = forward table of size 512.
-template <bool INV>
+template <bool INV, bool STAGED = false>
 __device__ __forceinline__ void warp_fft512x2_d(float2 (&v)[32], float2* scr, const float2* __restrict__ tw, int lane) {
   Dft<16, INV>::run(v);
   Dft<16, INV>::run(v + 16);
@@ -321,7 +335,7 @@ __device__ __forceinline__ void warp_fft512x2_d(float2 (&v)[32], float2* scr, co
     float2 t[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) t[k] = make_float2(1.f, 0.f);
-    step_twiddles_k<16, INV>(t, tw, lane);       // t[k] = W_512^{+-lane k}
+    step_twiddles_k<16, INV, STAGED>(t, tw, lane);       // t[k] = W_512^{+-lane k}
 #pragma unroll
     for (int k = 1; k < 16; ++k) {
       v[k] = cmul(v[k], t[k]);
@@ -336,6 +350,15 @@ __device__ __forceinline__ void warp_fft512x2_d(float2 (&v)[32], float2* scr, co
   __syncwarp();
   Dft<32, INV>::run(v);
 }
+
+// The RX kernel's tables staged in shared memory once per CTA: per-lane step twiddles of
+// the 1024-point and 512-point transforms (rows of 32: row k holds W^(k lane)) and the
+// job's group's RX weights.
+struct RxStaged {
+  const float2* s1024;
+  const float2* s512;
+  const float* w;
+};
 
 // ---------------------------------------------------------------------------
 // RX, N = 2048, L = 1024
@@ -356,7 +379,7 @@ __device__ __forceinline__ float2 mul_jpow(float2 x, int e) {
 // store j^k (g_r[k] - (-1)^k map[k]) (the bracket of eq:reduc, map holding g_1).
 __device__ __forceinline__ void rx_block_gather_1024(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S,
                                                      const FcJob& jb, const float2* __restrict__ src, float2* scr,
-                                                     float2* map, int lane, int r, bool combine) {
+                                                     float2* map, int lane, int r, bool combine, const RxStaged& st) {
   constexpr int L = 1024;
   const float2* __restrict__ twL = P.sz[S.size_L].tw;
   const float2* __restrict__ twN = P.sz[G.size_N].tw;
@@ -372,7 +395,7 @@ __device__ __forceinline__ void rx_block_gather_1024(const FcPlanDev& P, const F
       const float2 x0 = __ldg(x + tp), x1 = __ldg(x + tp + 1024);
       X[a] = s ? cmul(csub(x0, x1), __ldg(twN + tp)) : cadd(x0, x1);
     }
-    warp_fft1024_d<false>(X, scr, twL, lane);     // bin 2 (k1 + 32 k2) + s
+    warp_fft1024_d<false, true>(X, scr, st.s1024, lane);     // bin 2 (k1 + 32 k2) + s
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) {
       const int q = 2 * (lane + 32 * k2) + s;
@@ -380,7 +403,7 @@ __device__ __forceinline__ void rx_block_gather_1024(const FcPlanDev& P, const F
       if (kt >= 1024) kt -= 2048;
       if (kt >= -L / 2 && kt < L / 2) {
         const int k = kt & (L - 1);
-        const float2 g = cscale(cmulc(X[k2], ph), weight(S, S.drx, kt + L / 2));
+        const float2 g = cscale(cmulc(X[k2], ph), weight_staged(S, st.w, kt + L / 2));
         if (!combine) {
           map[k] = g;
         } else {
@@ -399,14 +422,14 @@ __device__ __forceinline__ void rx_block_gather_1024(const FcPlanDev& P, const F
 // 1024 points per symbol instead of 7), at the cost of a second pass over the output row.
 __device__ __noinline__ void rx_job_1024_reduced(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                             const float2* __restrict__ src, float2* __restrict__ gdst, float2* scr,
-                                            float2* map, int lane) {
+                                            float2* map, int lane, const RxStaged& st) {
   constexpr int L = 1024;
   const float2* __restrict__ twL = P.sz[S.size_L].tw;
   const int n = jb.index;
   const int hl = S.Lact / 2, hu = S.Lact - hl;
   float2* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
   float2 u[32];
-  rx_block_gather_1024(P, G, S, jb, src, scr, map, lane, 1, false);    // map = g_1
+  rx_block_gather_1024(P, G, S, jb, src, scr, map, lane, 1, false, st);    // map = g_1
   __syncwarp();
   // L (-j)^k g_1[k] goes straight to the output row; the same thread adds the
   // transform result to it at the end (no register copy across the next stages)
@@ -417,15 +440,15 @@ __device__ __noinline__ void rx_job_1024_reduced(const FcPlanDev& P, const FcGro
     if (f >= -hl && f < hu) row[f + hl] = cscale(mul_jpow(map[k], 3 * k), (float)L);
   }
   __syncwarp();
-  rx_block_gather_1024(P, G, S, jb, src, scr, map, lane, 0, true);     // map = j^k (g_0 - (-1)^k g_1)
+  rx_block_gather_1024(P, G, S, jb, src, scr, map, lane, 0, true, st);     // map = j^k (g_0 - (-1)^k g_1)
   __syncwarp();
 #pragma unroll
   for (int a = 0; a < 32; ++a) u[a] = map[32 * a + lane];
   __syncwarp();
-  warp_fft1024_d<true>(u, scr, twL, lane);        // time k1 + 32 k2
+  warp_fft1024_d<true, true>(u, scr, st.s1024, lane);        // time k1 + 32 k2
 #pragma unroll
   for (int k2 = 16; k2 < 32; ++k2) u[k2] = czero();   // S_hat
-  warp_fft1024_d<false>(u, scr, twL, lane);       // bin k1 + 32 k2
+  warp_fft1024_d<false, true>(u, scr, st.s1024, lane);       // bin k1 + 32 k2
 #pragma unroll
   for (int k2 = 0; k2 < 32; ++k2) {
     const int bin = lane + 32 * k2;
@@ -439,7 +462,7 @@ __device__ __noinline__ void rx_job_1024_reduced(const FcPlanDev& P, const FcGro
 template <bool OLA>
 __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                             const float2* __restrict__ src, float2* __restrict__ gdst, float2* scr,
-                                            float2* map, int lane) {
+                                            float2* map, int lane, const RxStaged& st) {
   constexpr int L = 1024;
   constexpr bool ola = OLA;
   constexpr int kCarry = OLA ? 24 : 16;
@@ -483,14 +506,14 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
           u[a] = cmul(csub(x0, x1), __ldg(twN + tp));   // (x0 - x1) exp(-j 2 pi tp / 2048)
         }
       }
-      warp_fft1024_d<false>(u, scr, twL, lane);     // bin 2 (k1 + 32 k2) + s
+      warp_fft1024_d<false, true>(u, scr, st.s1024, lane);     // bin 2 (k1 + 32 k2) + s
 #pragma unroll
       for (int k2 = 0; k2 < 32; ++k2) {
         const int q = 2 * (lane + 32 * k2) + s;
         int kt = (q - S.c) & 2047;
         if (kt >= 1024) kt -= 2048;
         if (kt >= -L / 2 && kt < L / 2) {
-          const float wt = weight(S, S.drx, kt + L / 2);
+          const float wt = weight_staged(S, st.w, kt + L / 2);
           map[kt & (L - 1)] = cscale(cmulc(u[k2], ph), wt);
         }
       }
@@ -500,7 +523,7 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
     for (int a = 0; a < 32; ++a) u[a] = map[32 * a + lane];
     __syncwarp();
     // R4: short IDFT
-    warp_fft1024_d<true>(u, scr, twL, lane);        // z_r[k1 + 32 k2] in u[k2]
+    warp_fft1024_d<true, true>(u, scr, st.s1024, lane);        // z_r[k1 + 32 k2] in u[k2]
     // R5: S window + concatenation (eq:concat2), or OLA of both blocks; x_ofdm[t], t = lane + 32 k
     if (r == 0) {
 #pragma unroll
@@ -514,7 +537,7 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
       else h[k] = k < 8 ? h0[k] : (k < kCarry ? cadd(h0[k], u[k - 8]) : u[k - 8]);
     }
     // R6: OFDM demodulation and active-bin output
-    warp_fft1024_d<false>(h, scr, twL, lane);
+    warp_fft1024_d<false, true>(h, scr, st.s1024, lane);
     const int hl = S.Lact / 2, hu = S.Lact - hl;
     float2* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
 #pragma unroll
@@ -531,7 +554,7 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
 // ---------------------------------------------------------------------------
 __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                            const float2* __restrict__ src, float2* __restrict__ gdst, float2* scr,
-                                           float2* map, int lane) {
+                                           float2* map, int lane, const RxStaged& st) {
   constexpr int L = 512;
   const float2* __restrict__ twL = P.sz[S.size_L].tw;
   const float2* __restrict__ twN = P.sz[G.size_N].tw;
@@ -548,7 +571,7 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
       if (ola && !(t >= G.N_L && t < G.N_L + G.N_S)) xv = czero();
       u[a] = xv;
     }
-    warp_fft1024_d<false>(u, scr, twN, lane);       // bin k1 + 32 k2
+    warp_fft1024_d<false, true>(u, scr, st.s1024, lane);       // bin k1 + 32 k2
     const float2 ph = root_pos(twN, 1024, (long long)S.c * (G.cps[n] + r * G.N_S));
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) {
@@ -556,7 +579,7 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
       int kt = (q - S.c) & 1023;
       if (kt >= 512) kt -= 1024;
       if (kt >= -L / 2 && kt < L / 2) {
-        const float wt = weight(S, S.drx, kt + L / 2);
+        const float wt = weight_staged(S, st.w, kt + L / 2);
         map[r * L + (kt & (L - 1))] = cscale(cmulc(u[k2], ph), wt);
       }
     }
@@ -569,7 +592,7 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
     v[16 + a] = map[L + 32 * a + lane];
   }
   __syncwarp();
-  warp_fft512x2_d<true>(v, scr, twL, lane);         // lane k1 + 16 r: z_r[k1 + 16 k2]
+  warp_fft512x2_d<true, true>(v, scr, st.s512, lane);         // lane k1 + 16 r: z_r[k1 + 16 k2]
   {
     const int r = lane >> 4, k1 = lane & 15;
 #pragma unroll
@@ -591,7 +614,7 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
     v[16 + a] = czero();
   }
   __syncwarp();
-  warp_fft512x2_d<false>(v, scr, twL, lane);        // lanes 0..15: X[k1 + 16 k2]
+  warp_fft512x2_d<false, true>(v, scr, st.s512, lane);        // lanes 0..15: X[k1 + 16 k2]
   if (lane < 16) {
     const int hl = S.Lact / 2, hu = S.Lact - hl;
     float2* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
@@ -618,25 +641,44 @@ __device__ __forceinline__ void prefetch_l2(const float2* p, int n, int lane) {
 
 // RX jobs of different streams share nothing, so no item waits for another.
 __device__ __forceinline__ void rx_dispatch(const FcPlanDev& P, const FcJob& jb, const float2* __restrict__ src,
-                                            float2* __restrict__ gdst, float2* scr, float2* map, int lane) {
+                                            float2* __restrict__ gdst, float2* scr, float2* map, int lane,
+                                            const RxStaged& st) {
   const FcGroupDev& G = P.g[jb.group];
   const FcSubDev& S = P.s[G.first_sub];
   if (S.L == 1024 && (P.flags & FC_FLAG_REDUCED_RX) && P.scheme_rx == FC_OLS)
-    rx_job_1024_reduced(P, G, S, jb, src, gdst, scr, map, lane);
-  else if (S.L == 1024 && P.scheme_rx == FC_OLA) rx_job_1024<true>(P, G, S, jb, src, gdst, scr, map, lane);
-  else if (S.L == 1024) rx_job_1024<false>(P, G, S, jb, src, gdst, scr, map, lane);
-  else rx_job_512(P, G, S, jb, src, gdst, scr, map, lane);
+    rx_job_1024_reduced(P, G, S, jb, src, gdst, scr, map, lane, st);
+  else if (S.L == 1024 && P.scheme_rx == FC_OLA) rx_job_1024<true>(P, G, S, jb, src, gdst, scr, map, lane, st);
+  else if (S.L == 1024) rx_job_1024<false>(P, G, S, jb, src, gdst, scr, map, lane, st);
+  else rx_job_512(P, G, S, jb, src, gdst, scr, map, lane, st);
 }
 
-__global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_RX_MIN_BLOCKS)
+__global__ void __launch_bounds__(kRxThreads, 1)
 k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, int n_jobs, int n_streams,
                      const float2* __restrict__ wave, float2* __restrict__ grid) {
   __shared__ FcPlanDev P;
   __shared__ int next_item;
+  __shared__ int wt_off[FC_MAX_GROUPS];
   extern __shared__ __align__(16) float2 wscr[];
   load_plan_w(P, gP);
   if (threadIdx.x == 0) next_item = 0;
   __syncthreads();                                  // the plan copy is complete before any use
+  // stage the per-lane step twiddles [1024: 32 rows | 512: 16 rows] and every group's weights
+  float2* tabs = wscr + kRxWarps * kScratch;
+  float* wts = reinterpret_cast<float*>(tabs + kRxTwiddles);
+  for (int i = 0; i < P.n_sizes; ++i) {
+    if (P.sz[i].n == 1024) stage_lane_twiddles(tabs, P.sz[i].tw, 1024, 32);
+    if (P.sz[i].n == 512) stage_lane_twiddles(tabs + 1024, P.sz[i].tw, 512, 16);
+  }
+  {
+    int off = 0;
+    for (int g = 0; g < P.n_groups; ++g) {
+      const FcSubDev& S = P.s[P.g[g].first_sub];
+      if (threadIdx.x == 0) wt_off[g] = off;
+      for (int p = threadIdx.x; p < S.L; p += blockDim.x) wts[off + p] = __ldg(S.drx + p);
+      off += S.L;
+    }
+  }
+  __syncthreads();
   const long long total = (long long)n_jobs * n_streams;
   const int lane = threadIdx.x & 31;
   float2* scr = wscr + (threadIdx.x >> 5) * kScratch;
@@ -658,7 +700,9 @@ k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
       const int Nn = P.g[jbn.group].N;
       prefetch_l2(wave + (size_t)(nx - (long long)jn * n_streams) * P.frame_len + jbn.start, Nn + Nn / 2, lane);
     }
-    rx_dispatch(P, jobs[j], wave + (size_t)stream * P.frame_len, grid + (size_t)stream * P.grid_len, scr, map, lane);
+    const FcJob jb = jobs[j];
+    const RxStaged st{tabs, tabs + 1024, wts + wt_off[jb.group]};
+    rx_dispatch(P, jb, wave + (size_t)stream * P.frame_len, grid + (size_t)stream * P.grid_len, scr, map, lane, st);
   }
 }
 
@@ -750,18 +794,22 @@ cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n
   return cudaGetLastError();
 }
 
+static size_t rx_smem_bytes(int weight_floats) {
+  return (size_t)kRxWarps * kScratch * sizeof(float2) + (size_t)kRxTwiddles * sizeof(float2) +
+         (((size_t)weight_floats * 4 + 15) & ~(size_t)15);
+}
+
 cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams,
-                                   const float2* wave, float2* grid, int num_sms, cudaStream_t st) {
+                                   int weight_floats, const float2* wave, float2* grid, int num_sms, cudaStream_t st) {
+  const size_t smem = rx_smem_bytes(weight_floats);
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rx_sync_warp, FC_WARP_THREADS,
-                                                                fc_warp_smem_bytes());
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rx_sync_warp, kRxThreads, smem);
   if (e != cudaSuccess) return e;
   const long long total = (long long)n_jobs * n_streams;
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  k_rx_sync_warp<<<dim3((unsigned)ctas), FC_WARP_THREADS, fc_warp_smem_bytes(), st>>>(dP, jobs, n_jobs, n_streams,
-                                                                                   wave, grid);
+  k_rx_sync_warp<<<dim3((unsigned)ctas), kRxThreads, smem, st>>>(dP, jobs, n_jobs, n_streams, wave, grid);
   return cudaGetLastError();
 }
 
@@ -771,5 +819,5 @@ cudaError_t fc_set_warp_smem_limits() {
                                 (int)tx_smem_bytes(FC_MAX_GROUPS * 1024))))
     return e;
   return cudaFuncSetAttribute(k_rx_sync_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)fc_warp_smem_bytes());
+                              (int)rx_smem_bytes(FC_MAX_GROUPS * 1024));
 }
