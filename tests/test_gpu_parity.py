@@ -190,7 +190,8 @@ WARP_CASES = [
     (2048, 1024, 600, 700, (144, 0, 512, 16), fo.OLS, fo.OLA),     # band wraps past N/2; CP 0 and N/4
     (2048, 1024, 1000, -1, (8, 9, 7), fo.OLA, fo.OLA),             # odd starts: float2 reductions
     (1024, 512, 288, 159, (88, 72, 72, 72), fo.OLA, fo.OLS),
-    (1024, 512, 500, -400, (0, 256, 30, 72, 72), fo.OLS, fo.OLS),
+    (1024, 512, 500, -400, (0, 256, 30, 72, 72), fo.OLS, fo.OLS),   # two TX pairs and a single
+    (1024, 512, 400, 3, (40,), fo.OLA, fo.OLA),                       # one symbol: no TX pair
 ]
 
 
