@@ -1054,7 +1054,8 @@ def profile_case(args):
     import numpy as np
     import torch
     import workloads as wl
-    from paper_2008_00672_gb300 import FC_FLAG_GENERIC_KERNELS, FC_FLAG_TENSOR_DFT, FC_RX, FC_TX, Plan, build
+    from paper_2008_00672_gb300 import (FC_FLAG_GENERIC_KERNELS, FC_FLAG_IO_BF16, FC_FLAG_TENSOR_DFT, FC_RX, FC_TX,
+                                        Plan, build)
 
     name = args.profile_case
     shape = {}
@@ -1071,6 +1072,8 @@ def profile_case(args):
     for d, k in ((FC_TX, args.tx_chunks), (FC_RX, args.rx_chunks)):
         if k:
             shape[d] = (k, 0)
+    if args.io_bf16:
+        geom = dataclasses.replace(geom, flags=geom.flags | FC_FLAG_IO_BF16)
     build.build()
     plan = Plan(geom)
     S = args.streams
@@ -1079,6 +1082,9 @@ def profile_case(args):
     base = wl.qam_grid(geom, min(S, 64), wl.default_seed(2)).astype(np.complex64)
     grid = torch.from_numpy(base).cuda().repeat(-(-S // base.shape[0]), 1)[:S].contiguous()
     wave = torch.empty((S, plan.wave_len), dtype=torch.complex64, device="cuda")
+    if args.io_bf16:
+        grid = torch.view_as_real(grid).to(torch.bfloat16).contiguous()
+        wave = torch.empty((S, plan.wave_len, 2), dtype=torch.bfloat16, device="cuda")
     est = torch.empty_like(grid)
     for _ in range(args.warmup + 1):
         plan.tx_synthesize(grid, wave)
@@ -1098,7 +1104,7 @@ def profile_case(args):
         timed = (f"; mean of {args.time}: TX {ev[0].elapsed_time(ev[1]) / args.time:.4f} ms, "
                  f"RX {ev[1].elapsed_time(ev[2]) / args.time:.4f} ms")
     plan.close()
-    print(f"{name}: {S} streams, {args.warmup} warm-up passes + 1, launches per pass "
+    print(f"{name}{' (complex-BF16 I/O)' if args.io_bf16 else ''}: {S} streams, {args.warmup} warm-up passes + 1, launches per pass "
           f"TX {plan.tx_kernels} RX {plan.rx_kernels}{timed}", flush=True)
 
 
@@ -1119,6 +1125,7 @@ def main():
     ap.add_argument("--tx-chunks", type=int, default=0, help="profile case: chunks per stream of the TX launch")
     ap.add_argument("--rx-chunks", type=int, default=0, help="profile case: chunks per stream of the RX launch")
     ap.add_argument("--time", type=int, default=0, help="profile case: then time this many TX and RX calls")
+    ap.add_argument("--io-bf16", action="store_true", help="profile case: complex-BF16 grid and waveform")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args)

@@ -106,7 +106,8 @@ typedef struct fc_geometry {
    joint form of eq:reduc (Sec. V-A): x_hat = C Omega(g_0 - Omega g_1) + Omega Omega g_1
    with C = W S_hat W^-1, instead of the two block IDFTs, the S window, eq:concat2 and
    the OFDM DFT. Same result up to rounding. It applies to the specialised one-warp-per-
-   symbol kernels only; other RX work (OLA, other sizes, FC_FLAG_GENERIC_KERNELS) ignores it. */
+   symbol kernels with complex64 output only; other RX work (OLA, other sizes,
+   FC_FLAG_GENERIC_KERNELS, complex-BF16 output) ignores it. */
 #define FC_FLAG_REDUCED_RX 2
 /* Continuous FC with one subband and L_m = N = 4096 (the 100 MHz NR carrier): run the
    FC block transforms on the tensor cores as a four-step GEMM-DFT (4096 = 64 x 64,
@@ -131,9 +132,11 @@ typedef struct fc_geometry {
    as without the flag, and round each output sample once to the nearest BF16 (ties to
    even): the result is the complex64 result rounded to BF16, up to the FP32 path's own
    error at rounding boundaries. Stream calls keep their TX tail and RX look-behind in
-   FP32, so a streamed slot is rounded once too. Runs on the generic kernels; the
-   specialised and tensor-core kernels (FC_FLAG_TENSOR_DFT) do not apply. Combines with
-   FC_FLAG_IO_TIME. */
+   FP32, so a streamed slot is rounded once too. Runs on the generic kernels and on the
+   specialised one-warp kernels; the symbol-synchronised TX of the latter adds its
+   overlapping blocks into a complex64 frame in the workspace (workspace_per_stream then
+   holds one frame) and rounds it into the output in a second pass (tx_kernels = 2). The
+   tensor-core kernels (FC_FLAG_TENSOR_DFT) do not apply. Combines with FC_FLAG_IO_TIME. */
 #define FC_FLAG_IO_BF16 16
 
 #define FC_MAX_GROUPS 4

@@ -165,18 +165,24 @@ size_t fc_tc_dft64_image_bytes();
 // zeroes the waveform first
 // weight_floats: the sum over groups of the group's subband length L (the TX weights the
 // kernel stages in shared memory)
+// grid_bf16 / io (FC_IO_* bits): complex-BF16 caller samples; the TX kernel accumulates
+// into a complex64 waveform (zeroed here), which fc_launch_to_bf16 rounds into a BF16
+// output.
 cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, int frame_len,
-                                   int weight_floats, const float2* grid, float2* wave, int num_sms, cudaStream_t st);
+                                   int weight_floats, const void* grid, int grid_bf16, float2* wave, int num_sms,
+                                   cudaStream_t st);
 cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams,
-                                   int weight_floats, const float2* wave, float2* grid, int num_sms, cudaStream_t st);
+                                   int weight_floats, const void* wave, void* grid, int io, int num_sms,
+                                   cudaStream_t st);
+cudaError_t fc_launch_to_bf16(const float2* src, void* dst, long long n, int num_sms, cudaStream_t st);
 cudaError_t fc_set_warp_smem_limits();
 // Continuous mode, one subband with L = L_OFDM = 384, N = 512, 50 % overlap, overlap-save
 // (fc_warp_cont.cu): OFDM modulation into the workspace then FC blocks (TX), FC blocks into
 // the workspace then OFDM demodulation (RX), one warp per pair of symbols or blocks.
-cudaError_t fc_launch_tx_cont_warp(const FcPlanDev* dP, int n_streams, int n_symbols, int n_blocks, const float2* grid,
-                                   float2* ws, float2* wave, int num_sms, cudaStream_t st);
-cudaError_t fc_launch_rx_cont_warp(const FcPlanDev* dP, int n_streams, int n_symbols, int n_blocks, const float2* wave,
-                                   float2* ws, float2* grid, int num_sms, cudaStream_t st);
+cudaError_t fc_launch_tx_cont_warp(const FcPlanDev* dP, int n_streams, int n_symbols, int n_blocks, const void* grid,
+                                   float2* ws, void* wave, int io, int num_sms, cudaStream_t st);
+cudaError_t fc_launch_rx_cont_warp(const FcPlanDev* dP, int n_streams, int n_symbols, int n_blocks, const void* wave,
+                                   float2* ws, void* grid, int io, int num_sms, cudaStream_t st);
 
 // helpers for entry points defined outside fc_plan.cu
 int fc_internal_fail(int code, const char* msg);     // records fc_last_error() and returns code

@@ -462,11 +462,11 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   }
 
   // warp-specialised path: symbol-sync, one subband per group, I = 2, L in {512, 1024}
-  // (complex-BF16 I/O runs on the generic kernels: their outputs are written once, from
-  // FP32 values, where the specialised kernels accumulate into the output buffer)
+  // (complex-BF16 I/O: the TX kernel accumulates into a complex64 waveform in the
+  // workspace, rounded once into the BF16 output afterwards)
   const bool io_time = (geo->flags & FC_FLAG_IO_TIME) != 0;
   const bool io_bf16 = (geo->flags & FC_FLAG_IO_BF16) != 0;
-  bool warp_ok = sync && !(geo->flags & FC_FLAG_GENERIC_KERNELS) && !io_time && !io_bf16 && (frame_len % 2 == 0);
+  bool warp_ok = sync && !(geo->flags & FC_FLAG_GENERIC_KERNELS) && !io_time && (frame_len % 2 == 0);
   for (int g = 0; g < G && warp_ok; ++g) {
     if (gh[g].subs.size() != 1) { warp_ok = false; break; }
     const SubHost& o = sh[gh[g].subs[0]];
@@ -476,7 +476,7 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   // warp-specialised continuous path: one group, one subband, L = L_OFDM = 384, N = 512,
   // 50 % overlap, the group at the frame's start; per direction when that side is
   // overlap-save (its outputs are disjoint and written once)
-  bool cont_warp = !sync && G == 1 && M == 1 && !io_time && !io_bf16 && !(geo->flags & FC_FLAG_GENERIC_KERNELS) &&
+  bool cont_warp = !sync && G == 1 && M == 1 && !io_time && !(geo->flags & FC_FLAG_GENERIC_KERNELS) &&
                    sh[0].L == 384 && sh[0].Lo == 384 && gh[0].N == 512 && 2 * gh[0].N_O == gh[0].N &&
                    gh[0].offset == 0;
   size_t off_wjobs = 0;
@@ -558,6 +558,8 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     tc_off = ws_len;
     ws_len += (long long)sh[0].R * 4096;
   }
+  // the warp TX kernel's complex64 accumulator of a BF16 frame output
+  if (warp_ok && io_bf16) ws_len = std::max(ws_len, ((long long)frame_len + 1) / 2 * 2);
 
   // grid offsets in the caller's subband order
   std::vector<long long> grid_off(M);
@@ -603,7 +605,7 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   pl->io = io_bf16 ? (FC_IO_IN_BF16 | FC_IO_OUT_BF16) : 0;
   z.slot_len = streamable ? slot_len : 0;
   z.stream_delay = streamable ? stream_delay : 0;
-  z.tx_kernels = sync ? 1 : (tc_tx ? 3 : 2);
+  z.tx_kernels = sync ? ((warp_ok && io_bf16) ? 2 : 1) : (tc_tx ? 3 : 2);   // + the BF16 rounding pass
   z.rx_kernels = sync ? 1 : (tc_rx ? 3 : 2);
   size_t off_dft = 0, off_err = 0;
   if (tc_tx) {
@@ -783,24 +785,34 @@ const FcGenKernels& gen_for(const fc_plan* pl, long long n_ctas, int set) {
   return *pl->gen[0];
 }
 
-// io: FC_IO_* bits of this call's input and output; the specialised and tensor-core
-// kernels take complex64 only (a plan with FC_FLAG_IO_BF16 never selects them)
+// io: FC_IO_* bits of this call's input and output; the one-warp kernels take complex64
+// and complex BF16, the tensor-core kernels complex64 only (a plan with FC_FLAG_IO_BF16
+// never selects them)
 cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* out, float2* workspace,
                       cudaStream_t st, Choice c, int io) {
   const size_t k = (size_t)c.split;
   const FcGenKernels& gen = gen_for(plan, (long long)n_streams * plan->tx_nchunks[k], c.set);
   const float2* grid = (const float2*)in;
   float2* wave = (float2*)out;
-  // float4 reductions of the warp kernel need a 16-byte aligned waveform
-  if (plan->warp_path && !c.generic && io == 0 && ((uintptr_t)wave & 15) == 0)
-    return fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, plan->h.frame_len,
-                                  plan->warp_weight_floats, grid, wave,
-                                  plan->num_sms, st);
+  if (plan->warp_path && !c.generic) {
+    // float4 reductions of the warp kernel need a 16-byte aligned complex64 waveform: the
+    // output itself, or for a BF16 output the workspace (frame_len samples a stream)
+    const bool out16 = (io & FC_IO_OUT_BF16) != 0;
+    float2* acc = out16 ? workspace : wave;
+    if (acc && ((uintptr_t)acc & 15) == 0) {
+      cudaError_t e = fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, plan->h.frame_len,
+                                             plan->warp_weight_floats, in, (io & FC_IO_IN_BF16) != 0, acc,
+                                             plan->num_sms, st);
+      if (e == cudaSuccess && out16)
+        e = fc_launch_to_bf16(acc, out, (long long)n_streams * plan->h.frame_len, plan->num_sms, st);
+      return e;
+    }
+  }
   if (plan->h.mode == FC_SYMBOL_SYNC)
     return gen.tx_sync(plan->d_plan, plan->d_jobs, plan->tx_chunks[k], plan->tx_nchunks[k], n_streams, in,
                               out, io, plan->smem_tx, st);
-  if (plan->cont_warp_tx && !c.generic && io == 0)
-    return fc_launch_tx_cont_warp(plan->d_plan, n_streams, plan->h.g[0].B, plan->h.g[0].R, grid, workspace, wave,
+  if (plan->cont_warp_tx && !c.generic)
+    return fc_launch_tx_cont_warp(plan->d_plan, n_streams, plan->h.g[0].B, plan->h.g[0].R, in, workspace, out, io,
                                   plan->num_sms, st);
   if (plan->tc_tx && !c.generic && io == 0) {
     const int R = plan->h.g[0].R;
@@ -833,15 +845,14 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* 
   const FcGenKernels& gen = gen_for(plan, (long long)n_streams * plan->rx_nchunks[k], c.set);
   const float2* wave = (const float2*)in;
   float2* grid = (float2*)out;
-  if (plan->warp_path && !c.generic && io == 0)
-    return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, plan->warp_weight_floats, wave,
-                                  grid, plan->num_sms,
-                                  st);
+  if (plan->warp_path && !c.generic)
+    return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, plan->warp_weight_floats, in,
+                                  out, io, plan->num_sms, st);
   if (plan->h.mode == FC_SYMBOL_SYNC)
     return gen.rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, in,
                               out, io, plan->smem_rx, st);
-  if (plan->cont_warp_rx && !c.generic && io == 0)
-    return fc_launch_rx_cont_warp(plan->d_plan, n_streams, plan->h.g[0].B, plan->h.g[0].R, wave, workspace, grid,
+  if (plan->cont_warp_rx && !c.generic)
+    return fc_launch_rx_cont_warp(plan->d_plan, n_streams, plan->h.g[0].B, plan->h.g[0].R, in, workspace, out, io,
                                   plan->num_sms, st);
   if (plan->tc_rx && !c.generic && io == 0) {
     const int R = plan->h.g[0].R;

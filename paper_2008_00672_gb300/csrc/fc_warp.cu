@@ -37,10 +37,6 @@ constexpr int kRxThreads = 384;
 constexpr int kRxWarps = kRxThreads / 32;
 constexpr int kRxTwiddles = 32 * 32 + 16 * 32;   // float2
 
-__device__ __forceinline__ float weight(const FcSubDev& S, const float* __restrict__ d, int p) {
-  return (p >= S.p_lo && p < S.p_hi) ? __ldg(d + p) : 0.f;
-}
-
 // signed short-transform frequency of natural bin k (even L)
 __device__ __forceinline__ int signed_bin(int k, int L) { return k < L / 2 ? k : k - L; }
 
@@ -67,20 +63,6 @@ __device__ __forceinline__ float weight_staged(const FcSubDev& S, const float* d
   return (p >= S.p_lo && p < S.p_hi) ? d[p] : 0.f;
 }
 
-__device__ __forceinline__ JobTables job_tables(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S) {
-  JobTables t;
-  if (S.L == 1024) {
-    t.t1024 = P.sz[S.size_L].tw;
-    t.t2048 = P.sz[G.size_N].tw;
-    t.t512 = nullptr;
-  } else {
-    t.t512 = P.sz[S.size_L].tw;
-    t.t1024 = P.sz[G.size_N].tw;
-    t.t2048 = nullptr;
-  }
-  return t;
-}
-
 // ---------------------------------------------------------------------------
 // TX job. L = 1024 (N = 2048), stages:
 //   0   OFDM IDFT of the grid row -> body (kept in registers)
@@ -93,14 +75,15 @@ __device__ __forceinline__ JobTables job_tables(const FcPlanDev& P, const FcGrou
 //   1   both blocks segmented from the body, two 512-point DFTs (kept in registers)
 //   2/3 block r = 0/1: map into the 1024-bin spectrum, IDFT, reduce into the waveform
 // ---------------------------------------------------------------------------
+template <typename TI>
 __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
-                                       const float2* __restrict__ gsrc, float2* __restrict__ wdst, float2* scr,
+                                       const TI* __restrict__ gsrc, float2* __restrict__ wdst, float2* scr,
                                        float2* map, int lane, const TxTables& tt, const float* wt) {
   const bool big = S.L == 1024;
   const JobTables tb{tt.t1024, tt.t512, tt.t2048};
   const int n = jb.index;
   const int hl = S.Lact / 2, hu = S.Lact - hl;
-  const float2* __restrict__ row = gsrc + S.grid_off + (long long)n * S.Lact;
+  const TI* __restrict__ row = gsrc + S.grid_off + (long long)n * S.Lact;
   const int lcp = S.lcp[n], ncp = G.ncp[n];
   const bool ols = P.scheme_tx == FC_OLS;
   const bool v4 = ((jb.start & 1) == 0);
@@ -120,7 +103,7 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
 #pragma unroll
         for (int a = 0; a < 32; ++a) {
           const int f = signed_bin(32 * a + lane, 1024);
-          v[a] = (f >= -hl && f < hu) ? __ldg(row + f + hl) : czero();
+          v[a] = (f >= -hl && f < hu) ? ld_io(row + f + hl) : czero();
         }
         inv = true;
       } else if (st == 1 || st == 4) {                  // T2-T3: block r from the body
@@ -161,7 +144,7 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
 #pragma unroll
         for (int a = 0; a < 16; ++a) {
           const int f = signed_bin(32 * a + lane, 512);
-          v[a] = (f >= -hl && f < hu) ? __ldg(row + f + hl) : czero();
+          v[a] = (f >= -hl && f < hu) ? ld_io(row + f + hl) : czero();
           v[16 + a] = czero();
         }
         inv = true;
@@ -377,13 +360,13 @@ __device__ __forceinline__ float2 mul_jpow(float2 x, int e) {
 // then the subband's 1024 bins gathered with conj(phi_r theta_n) and D_m into map
 // at their natural short-transform index k. combine: instead of storing g_r[k],
 // store j^k (g_r[k] - (-1)^k map[k]) (the bracket of eq:reduc, map holding g_1).
+template <typename TI>
 __device__ __forceinline__ void rx_block_gather_1024(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S,
-                                                     const FcJob& jb, const float2* __restrict__ src, float2* scr,
+                                                     const FcJob& jb, const TI* __restrict__ src, float2* scr,
                                                      float2* map, int lane, int r, bool combine, const RxStaged& st) {
   constexpr int L = 1024;
-  const float2* __restrict__ twL = P.sz[S.size_L].tw;
   const float2* __restrict__ twN = P.sz[G.size_N].tw;
-  const float2* __restrict__ x = src + jb.start + r * (2048 / 2);
+  const TI* __restrict__ x = src + jb.start + r * (2048 / 2);
   const float2 ph = root_pos(twN, 2048, (long long)S.c * (G.cps[jb.index] + r * G.N_S));
 #pragma unroll
   for (int s = 0; s < 2; ++s) {
@@ -392,7 +375,7 @@ __device__ __forceinline__ void rx_block_gather_1024(const FcPlanDev& P, const F
 #pragma unroll
     for (int a = 0; a < 32; ++a) {
       const int tp = 32 * a + lane;
-      const float2 x0 = __ldg(x + tp), x1 = __ldg(x + tp + 1024);
+      const float2 x0 = ld_io(x + tp), x1 = ld_io(x + tp + 1024);
       X[a] = s ? cmul(csub(x0, x1), __ldg(twN + tp)) : cadd(x0, x1);
     }
     warp_fft1024_d<false, true>(X, scr, st.s1024, lane);     // bin 2 (k1 + 32 k2) + s
@@ -420,11 +403,11 @@ __device__ __forceinline__ void rx_block_gather_1024(const FcPlanDev& P, const F
 // where g_r are the gathered block spectra and S_hat keeps time samples [0, L/2).
 // One IDFT and one DFT replace the two block IDFTs and the OFDM DFT (6 transforms of
 // 1024 points per symbol instead of 7), at the cost of a second pass over the output row.
+template <typename TI>
 __device__ __noinline__ void rx_job_1024_reduced(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
-                                            const float2* __restrict__ src, float2* __restrict__ gdst, float2* scr,
+                                            const TI* __restrict__ src, float2* __restrict__ gdst, float2* scr,
                                             float2* map, int lane, const RxStaged& st) {
   constexpr int L = 1024;
-  const float2* __restrict__ twL = P.sz[S.size_L].tw;
   const int n = jb.index;
   const int hl = S.Lact / 2, hu = S.Lact - hl;
   float2* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
@@ -459,14 +442,13 @@ __device__ __noinline__ void rx_job_1024_reduced(const FcPlanDev& P, const FcGro
 
 // OLA: the scheme (a template parameter, so that the overlap-save form carries only the
 // 16 values per lane it needs across the block loop)
-template <bool OLA>
+template <bool OLA, typename TI, typename TO>
 __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
-                                            const float2* __restrict__ src, float2* __restrict__ gdst, float2* scr,
+                                            const TI* __restrict__ src, TO* __restrict__ gdst, float2* scr,
                                             float2* map, int lane, const RxStaged& st) {
   constexpr int L = 1024;
   constexpr bool ola = OLA;
   constexpr int kCarry = OLA ? 24 : 16;
-  const float2* __restrict__ twL = P.sz[S.size_L].tw;
   const float2* __restrict__ twN = P.sz[G.size_N].tw;
   const int n = jb.index;
   // the part of the symbol body that block 0 contributes, x_ofdm[lane + 32 k] for k < 16
@@ -476,7 +458,7 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
 #pragma unroll 1
   for (int r = 0; r < 2; ++r) {
     // R1-R2: block r, radix-2 split of the 2048-point DFT into even (s = 0) and odd bins
-    const float2* __restrict__ x = src + jb.start + r * (2048 / 2);
+    const TI* __restrict__ x = src + jb.start + r * (2048 / 2);
     float2 u[32];
     // R3: gather the subband's 1024 bins with conj(phi_r theta_n), D_m, inverse shift; the even
     // bins right after their transform, so only one half-spectrum is live in registers
@@ -487,7 +469,7 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
 #pragma unroll
         for (int a = 0; a < 32; ++a) {
           const int tp = 32 * a + lane;
-          float2 x0 = __ldg(x + tp), x1 = __ldg(x + tp + 1024);
+          float2 x0 = ld_io(x + tp), x1 = ld_io(x + tp + 1024);
           if (ola) {                               // A window [N_L, N_L + N_S) = [512, 1536)
             if (tp < 512) x0 = czero();
             if (tp >= 512) x1 = czero();
@@ -498,7 +480,7 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
 #pragma unroll
         for (int a = 0; a < 32; ++a) {
           const int tp = 32 * a + lane;
-          float2 x0 = __ldg(x + tp), x1 = __ldg(x + tp + 1024);
+          float2 x0 = ld_io(x + tp), x1 = ld_io(x + tp + 1024);
           if (ola) {
             if (tp < 512) x0 = czero();
             if (tp >= 512) x1 = czero();
@@ -539,12 +521,12 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
     // R6: OFDM demodulation and active-bin output
     warp_fft1024_d<false, true>(h, scr, st.s1024, lane);
     const int hl = S.Lact / 2, hu = S.Lact - hl;
-    float2* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
+    TO* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) {
       const int bin = lane + 32 * k2;
       const int f = bin < L / 2 ? bin : bin - L;
-      if (f >= -hl && f < hu) row[f + hl] = h[k2];
+      if (f >= -hl && f < hu) st_io(row + f + hl, h[k2]);
     }
   }
 }
@@ -552,22 +534,22 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
 // ---------------------------------------------------------------------------
 // RX, N = 1024, L = 512
 // ---------------------------------------------------------------------------
+template <typename TI, typename TO>
 __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
-                                           const float2* __restrict__ src, float2* __restrict__ gdst, float2* scr,
+                                           const TI* __restrict__ src, TO* __restrict__ gdst, float2* scr,
                                            float2* map, int lane, const RxStaged& st) {
   constexpr int L = 512;
-  const float2* __restrict__ twL = P.sz[S.size_L].tw;
   const float2* __restrict__ twN = P.sz[G.size_N].tw;
   const int n = jb.index;
   const bool ola = P.scheme_rx == FC_OLA;
 #pragma unroll 1
   for (int r = 0; r < 2; ++r) {                      // one copy of the block DFT in the code
-    const float2* __restrict__ x = src + jb.start + r * (1024 / 2);
+    const TI* __restrict__ x = src + jb.start + r * (1024 / 2);
     float2 u[32];
 #pragma unroll
     for (int a = 0; a < 32; ++a) {
       const int t = 32 * a + lane;
-      float2 xv = __ldg(x + t);
+      float2 xv = ld_io(x + t);
       if (ola && !(t >= G.N_L && t < G.N_L + G.N_S)) xv = czero();
       u[a] = xv;
     }
@@ -617,12 +599,12 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
   warp_fft512x2_d<false, true>(v, scr, st.s512, lane);        // lanes 0..15: X[k1 + 16 k2]
   if (lane < 16) {
     const int hl = S.Lact / 2, hu = S.Lact - hl;
-    float2* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
+    TO* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) {
       const int bin = lane + 16 * k2;
       const int f = bin < L / 2 ? bin : bin - L;
-      if (f >= -hl && f < hu) row[f + hl] = v[k2];
+      if (f >= -hl && f < hu) st_io(row + f + hl, v[k2]);
     }
   }
 }
@@ -635,26 +617,36 @@ __device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G,
 // same mix of job shapes and the launch has no partial last wave.
 // ---------------------------------------------------------------------------
 // Ask L2 for [p, p + n): one 128-byte line per lane and step (p + n within the buffer).
-__device__ __forceinline__ void prefetch_l2(const float2* p, int n, int lane) {
-  for (int i = 16 * lane; i < n; i += 16 * 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + i));
+template <typename T>
+__device__ __forceinline__ void prefetch_l2(const T* p, int n, int lane) {
+  constexpr int kLine = 128 / (int)sizeof(T);
+  for (int i = kLine * lane; i < n; i += kLine * 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + i));
 }
 
-// RX jobs of different streams share nothing, so no item waits for another.
-__device__ __forceinline__ void rx_dispatch(const FcPlanDev& P, const FcJob& jb, const float2* __restrict__ src,
-                                            float2* __restrict__ gdst, float2* scr, float2* map, int lane,
+// RX jobs of different streams share nothing, so no item waits for another. The eq:reduc
+// form adds into its output row after storing to it, so it runs for complex64 output
+// only; a BF16 output (rounded once per sample) takes the direct form.
+template <typename TI, typename TO>
+__device__ __forceinline__ void rx_dispatch(const FcPlanDev& P, const FcJob& jb, const TI* __restrict__ src,
+                                            TO* __restrict__ gdst, float2* scr, float2* map, int lane,
                                             const RxStaged& st) {
   const FcGroupDev& G = P.g[jb.group];
   const FcSubDev& S = P.s[G.first_sub];
-  if (S.L == 1024 && (P.flags & FC_FLAG_REDUCED_RX) && P.scheme_rx == FC_OLS)
-    rx_job_1024_reduced(P, G, S, jb, src, gdst, scr, map, lane, st);
-  else if (S.L == 1024 && P.scheme_rx == FC_OLA) rx_job_1024<true>(P, G, S, jb, src, gdst, scr, map, lane, st);
+  if constexpr (std::is_same<TO, float2>::value) {
+    if (S.L == 1024 && (P.flags & FC_FLAG_REDUCED_RX) && P.scheme_rx == FC_OLS) {
+      rx_job_1024_reduced(P, G, S, jb, src, gdst, scr, map, lane, st);
+      return;
+    }
+  }
+  if (S.L == 1024 && P.scheme_rx == FC_OLA) rx_job_1024<true>(P, G, S, jb, src, gdst, scr, map, lane, st);
   else if (S.L == 1024) rx_job_1024<false>(P, G, S, jb, src, gdst, scr, map, lane, st);
   else rx_job_512(P, G, S, jb, src, gdst, scr, map, lane, st);
 }
 
+template <typename TI, typename TO>
 __global__ void __launch_bounds__(kRxThreads, 1)
 k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, int n_jobs, int n_streams,
-                     const float2* __restrict__ wave, float2* __restrict__ grid) {
+                     const TI* __restrict__ wave, TO* __restrict__ grid) {
   __shared__ FcPlanDev P;
   __shared__ int next_item;
   __shared__ int wt_off[FC_MAX_GROUPS];
@@ -708,9 +700,10 @@ k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
 
 // TX: jobs of one stream run on several CTAs and reduce into the same waveform, which
 // is zeroed beforehand.
+template <typename TI>
 __global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_TX_MIN_BLOCKS)
 k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, int n_jobs, int n_streams,
-                     const float2* __restrict__ grid, float2* __restrict__ wave) {
+                     const TI* __restrict__ grid, float2* __restrict__ wave) {
   __shared__ FcPlanDev P;
   __shared__ int next_item;
   __shared__ int wt_off[FC_MAX_GROUPS];
@@ -778,20 +771,28 @@ static size_t tx_smem_bytes(int weight_floats) {
   return fc_warp_smem_bytes() + (size_t)kTxTwiddles * sizeof(float2) + (((size_t)weight_floats * 4 + 15) & ~(size_t)15);
 }
 
-cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, int frame_len,
-                                   int weight_floats, const float2* grid, float2* wave, int num_sms, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(wave, 0, (size_t)n_streams * frame_len * sizeof(float2), st);
-  if (e != cudaSuccess) return e;
-  const size_t smem = tx_smem_bytes(weight_floats);
+template <typename TI>
+static cudaError_t launch_tx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, size_t smem,
+                                  const TI* grid, float2* wave, int num_sms, cudaStream_t st) {
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tx_sync_warp, FC_WARP_THREADS, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tx_sync_warp<TI>, FC_WARP_THREADS, smem);
   if (e != cudaSuccess) return e;
   const long long total = (long long)n_jobs * n_streams;
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  k_tx_sync_warp<<<dim3((unsigned)ctas), FC_WARP_THREADS, smem, st>>>(dP, jobs, n_jobs, n_streams, grid, wave);
+  k_tx_sync_warp<TI><<<dim3((unsigned)ctas), FC_WARP_THREADS, smem, st>>>(dP, jobs, n_jobs, n_streams, grid, wave);
   return cudaGetLastError();
+}
+
+cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, int frame_len,
+                                   int weight_floats, const void* grid, int grid_bf16, float2* wave, int num_sms,
+                                   cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(wave, 0, (size_t)n_streams * frame_len * sizeof(float2), st);
+  if (e != cudaSuccess) return e;
+  const size_t smem = tx_smem_bytes(weight_floats);
+  return grid_bf16 ? launch_tx_warp(dP, jobs, n_jobs, n_streams, smem, (const bf2*)grid, wave, num_sms, st)
+                   : launch_tx_warp(dP, jobs, n_jobs, n_streams, smem, (const float2*)grid, wave, num_sms, st);
 }
 
 static size_t rx_smem_bytes(int weight_floats) {
@@ -799,25 +800,60 @@ static size_t rx_smem_bytes(int weight_floats) {
          (((size_t)weight_floats * 4 + 15) & ~(size_t)15);
 }
 
-cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams,
-                                   int weight_floats, const float2* wave, float2* grid, int num_sms, cudaStream_t st) {
-  const size_t smem = rx_smem_bytes(weight_floats);
+template <typename TI, typename TO>
+static cudaError_t launch_rx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, size_t smem,
+                                  const void* wave, void* grid, int num_sms, cudaStream_t st) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rx_sync_warp, kRxThreads, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rx_sync_warp<TI, TO>, kRxThreads, smem);
   if (e != cudaSuccess) return e;
   const long long total = (long long)n_jobs * n_streams;
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  k_rx_sync_warp<<<dim3((unsigned)ctas), kRxThreads, smem, st>>>(dP, jobs, n_jobs, n_streams, wave, grid);
+  k_rx_sync_warp<TI, TO><<<dim3((unsigned)ctas), kRxThreads, smem, st>>>(dP, jobs, n_jobs, n_streams,
+                                                                        (const TI*)wave, (TO*)grid);
+  return cudaGetLastError();
+}
+
+cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams,
+                                   int weight_floats, const void* wave, void* grid, int io, int num_sms,
+                                   cudaStream_t st) {
+  const size_t smem = rx_smem_bytes(weight_floats);
+  // the calls' I/O: complex64, BF16 frame calls, BF16 stream calls (complex64 frame in)
+  switch (io & (FC_IO_IN_BF16 | FC_IO_OUT_BF16)) {
+    case 0: return launch_rx_warp<float2, float2>(dP, jobs, n_jobs, n_streams, smem, wave, grid, num_sms, st);
+    case FC_IO_IN_BF16 | FC_IO_OUT_BF16:
+      return launch_rx_warp<bf2, bf2>(dP, jobs, n_jobs, n_streams, smem, wave, grid, num_sms, st);
+    case FC_IO_OUT_BF16: return launch_rx_warp<float2, bf2>(dP, jobs, n_jobs, n_streams, smem, wave, grid, num_sms, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+namespace {
+// A complex64 buffer rounded once to complex BF16 (the warp TX kernel's accumulated
+// waveform into a BF16 output).
+__global__ void k_to_bf16(const float2* __restrict__ src, bf2* __restrict__ dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    st_io(dst + i, __ldg(src + i));
+}
+}  // namespace
+
+cudaError_t fc_launch_to_bf16(const float2* src, void* dst, long long n, int num_sms, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  long long ctas = (n + 255) / 256;
+  if (ctas > 8LL * num_sms) ctas = 8LL * num_sms;
+  k_to_bf16<<<dim3((unsigned)ctas), 256, 0, st>>>(src, (bf2*)dst, n);
   return cudaGetLastError();
 }
 
 cudaError_t fc_set_warp_smem_limits() {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_tx_sync_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)tx_smem_bytes(FC_MAX_GROUPS * 1024))))
+  const int tx = (int)tx_smem_bytes(FC_MAX_GROUPS * 1024), rx = (int)rx_smem_bytes(FC_MAX_GROUPS * 1024);
+  if ((e = cudaFuncSetAttribute(k_tx_sync_warp<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tx))) return e;
+  if ((e = cudaFuncSetAttribute(k_tx_sync_warp<bf2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tx))) return e;
+  if ((e = cudaFuncSetAttribute(k_rx_sync_warp<float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rx)))
     return e;
-  return cudaFuncSetAttribute(k_rx_sync_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)rx_smem_bytes(FC_MAX_GROUPS * 1024));
+  if ((e = cudaFuncSetAttribute(k_rx_sync_warp<float2, bf2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rx)))
+    return e;
+  return cudaFuncSetAttribute(k_rx_sync_warp<bf2, bf2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rx);
 }

@@ -175,8 +175,9 @@ struct WarpItems {
 // ---------------------------------------------------------------------------
 // T1-T2: OFDM IDFT and CP insertion of symbols 2p, 2p + 1 into the low-rate stream
 // ---------------------------------------------------------------------------
+template <typename TI>
 __global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_CONT_MIN_BLOCKS)
-k_ofdm_mod_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __restrict__ grid,
+k_ofdm_mod_w384(const FcPlanDev* __restrict__ gP, int n_streams, const TI* __restrict__ grid,
                 float2* __restrict__ ws) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) float2 wscr[];
@@ -191,7 +192,7 @@ k_ofdm_mod_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* _
   const long long total = (long long)n_streams * pairs;
   for (long long item = WarpItems().first; item < total; item += WarpItems().step) {
     const int stream = (int)(item / pairs), n0 = 2 * (int)(item - (long long)stream * pairs);
-    const float2* __restrict__ rows = grid + (size_t)stream * P.grid_len + S.grid_off;
+    const TI* __restrict__ rows = grid + (size_t)stream * P.grid_len + S.grid_off;
     float2 v[32];
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
@@ -199,7 +200,7 @@ k_ofdm_mod_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* _
 #pragma unroll
       for (int a = 0; a < 12; ++a) {
         const int f = signed_bin384(32 * a + lane);
-        v[12 * b + a] = (live && f >= -hl && f < hu) ? __ldg(rows + (long long)(n0 + b) * S.Lact + f + hl) : czero();
+        v[12 * b + a] = (live && f >= -hl && f < hu) ? ld_io(rows + (long long)(n0 + b) * S.Lact + f + hl) : czero();
       }
     }
 #pragma unroll
@@ -225,9 +226,10 @@ k_ofdm_mod_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* _
 // ---------------------------------------------------------------------------
 // T3-T7, overlap-save: FC blocks 2p, 2p + 1 of the low-rate stream -> waveform
 // ---------------------------------------------------------------------------
+template <typename TO>
 __global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_CONT_MIN_BLOCKS)
 k_tx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __restrict__ ws,
-               float2* __restrict__ wave) {
+               TO* __restrict__ wave) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) float2 wscr[];
   load_plan_w(P, gP);
@@ -292,13 +294,13 @@ k_tx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
     const int b = lane >> 4, k1 = lane & 15;
     if (b < nb) {
       const int r = r0 + b;
-      float2* __restrict__ out = wave + (size_t)stream * P.frame_len + (long long)r * G.N_S;
+      TO* __restrict__ out = wave + (size_t)stream * P.frame_len + (long long)r * G.N_S;
 #pragma unroll
       for (int k2 = 0; k2 < 32; ++k2) {
         const int tau = k1 + 16 * k2;
         const bool keep = tau >= G.N_L && tau < G.N_L + G.N_S;
-        if (keep) out[tau] = v[k2];
-        else if ((r == 0 && tau < G.N_L) || (r == R - 1 && tau >= G.N_L + G.N_S)) out[tau] = czero();
+        if (keep) st_io(out + tau, v[k2]);
+        else if ((r == 0 && tau < G.N_L) || (r == R - 1 && tau >= G.N_L + G.N_S)) st_io(out + tau, czero());
       }
     }
   }
@@ -307,8 +309,9 @@ k_tx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
 // ---------------------------------------------------------------------------
 // R1-R5, overlap-save: FC blocks 2p, 2p + 1 of the waveform -> low-rate stream
 // ---------------------------------------------------------------------------
+template <typename TI>
 __global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_CONT_MIN_BLOCKS)
-k_rx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __restrict__ wave,
+k_rx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const TI* __restrict__ wave,
                float2* __restrict__ ws) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) float2 wscr[];
@@ -324,14 +327,14 @@ k_rx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
   for (long long item = WarpItems().first; item < total; item += WarpItems().step) {
     const int stream = (int)(item / pairs), r0 = 2 * (int)(item - (long long)stream * pairs);
     const int nb = R - r0 < 2 ? R - r0 : 2;
-    const float2* __restrict__ x = wave + (size_t)stream * P.frame_len;
+    const TI* __restrict__ x = wave + (size_t)stream * P.frame_len;
     float2 v[32];
     // R1: block r is the N samples from r N_S (overlap-save: no window)
 #pragma unroll
     for (int b = 0; b < 2; ++b)
 #pragma unroll
       for (int a = 0; a < 16; ++a)
-        v[16 * b + a] = b < nb ? __ldg(x + (long long)(r0 + b) * G.N_S + 32 * a + lane) : czero();
+        v[16 * b + a] = b < nb ? ld_io(x + (long long)(r0 + b) * G.N_S + 32 * a + lane) : czero();
     // R2: long DFTs; lane k1 + 16 T holds Y_T[k1 + 16 k2] in v[k2]
     warp_fft<true>(v, scr, T.twN, T.twN, lane, true);
     float2* map = scr;
@@ -380,9 +383,10 @@ k_rx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
 // ---------------------------------------------------------------------------
 // R5-R6: CP removal and OFDM DFT of symbols 2p, 2p + 1, active bins to the grid
 // ---------------------------------------------------------------------------
+template <typename TO>
 __global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_CONT_MIN_BLOCKS)
 k_ofdm_demod_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __restrict__ ws,
-                  float2* __restrict__ grid) {
+                  TO* __restrict__ grid) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) float2 wscr[];
   load_plan_w(P, gP);
@@ -411,20 +415,20 @@ k_ofdm_demod_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2*
     if (lane < 24) {
       const int b = lane >= 12, k1 = lane - 12 * b, n = n0 + b;
       if (n < B) {
-        float2* __restrict__ row = grid + (size_t)stream * P.grid_len + S.grid_off + (long long)n * S.Lact;
+        TO* __restrict__ row = grid + (size_t)stream * P.grid_len + S.grid_off + (long long)n * S.Lact;
 #pragma unroll
         for (int k2 = 0; k2 < 32; ++k2) {
           const int f = signed_bin384(k1 + 12 * k2);
-          if (f >= -hl && f < hu) row[f + hl] = v[k2];
+          if (f >= -hl && f < hu) st_io(row + f + hl, v[k2]);
         }
       }
     }
   }
 }
 
-template <class K>
+template <class K, class TI, class TO>
 cudaError_t launch_w(K kern, long long items, int num_sms, cudaStream_t st, const FcPlanDev* dP, int n_streams,
-                     const float2* in, float2* out, size_t tables = 0) {
+                     const TI* in, TO* out, size_t tables = 0) {
   const size_t smem = (size_t)kWarps * kTrans * sizeof(float2) + tables;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FC_WARP_THREADS, smem);
@@ -439,19 +443,31 @@ cudaError_t launch_w(K kern, long long items, int num_sms, cudaStream_t st, cons
 
 }  // namespace
 
-cudaError_t fc_launch_tx_cont_warp(const FcPlanDev* dP, int n_streams, int n_symbols, int n_blocks, const float2* grid,
-                                   float2* ws, float2* wave, int num_sms, cudaStream_t st) {
-  cudaError_t e = launch_w(k_ofdm_mod_w384, (long long)n_streams * ((n_symbols + 1) / 2), num_sms, st, dP, n_streams,
-                           grid, ws);
+// io: FC_IO_* bits (complex-BF16 grid / waveform; the workspace stays complex64)
+cudaError_t fc_launch_tx_cont_warp(const FcPlanDev* dP, int n_streams, int n_symbols, int n_blocks, const void* grid,
+                                   float2* ws, void* wave, int io, int num_sms, cudaStream_t st) {
+  const long long syms = (long long)n_streams * ((n_symbols + 1) / 2), blks = (long long)n_streams * ((n_blocks + 1) / 2);
+  cudaError_t e = (io & FC_IO_IN_BF16)
+                      ? launch_w(k_ofdm_mod_w384<bf2>, syms, num_sms, st, dP, n_streams, (const bf2*)grid, ws)
+                      : launch_w(k_ofdm_mod_w384<float2>, syms, num_sms, st, dP, n_streams, (const float2*)grid, ws);
   if (e != cudaSuccess) return e;
-  return launch_w(k_tx_cont_w384, (long long)n_streams * ((n_blocks + 1) / 2), num_sms, st, dP, n_streams, ws, wave,
-                  kContTableBytes);
+  return (io & FC_IO_OUT_BF16)
+             ? launch_w(k_tx_cont_w384<bf2>, blks, num_sms, st, dP, n_streams, (const float2*)ws, (bf2*)wave,
+                        kContTableBytes)
+             : launch_w(k_tx_cont_w384<float2>, blks, num_sms, st, dP, n_streams, (const float2*)ws, (float2*)wave,
+                        kContTableBytes);
 }
 
-cudaError_t fc_launch_rx_cont_warp(const FcPlanDev* dP, int n_streams, int n_symbols, int n_blocks, const float2* wave,
-                                   float2* ws, float2* grid, int num_sms, cudaStream_t st) {
-  cudaError_t e = launch_w(k_rx_cont_w384, (long long)n_streams * ((n_blocks + 1) / 2), num_sms, st, dP, n_streams,
-                           wave, ws, kContTableBytes);
+cudaError_t fc_launch_rx_cont_warp(const FcPlanDev* dP, int n_streams, int n_symbols, int n_blocks, const void* wave,
+                                   float2* ws, void* grid, int io, int num_sms, cudaStream_t st) {
+  const long long syms = (long long)n_streams * ((n_symbols + 1) / 2), blks = (long long)n_streams * ((n_blocks + 1) / 2);
+  cudaError_t e = (io & FC_IO_IN_BF16)
+                      ? launch_w(k_rx_cont_w384<bf2>, blks, num_sms, st, dP, n_streams, (const bf2*)wave, ws,
+                                 kContTableBytes)
+                      : launch_w(k_rx_cont_w384<float2>, blks, num_sms, st, dP, n_streams, (const float2*)wave, ws,
+                                 kContTableBytes);
   if (e != cudaSuccess) return e;
-  return launch_w(k_ofdm_demod_w384, (long long)n_streams * ((n_symbols + 1) / 2), num_sms, st, dP, n_streams, ws, grid);
+  return (io & FC_IO_OUT_BF16)
+             ? launch_w(k_ofdm_demod_w384<bf2>, syms, num_sms, st, dP, n_streams, (const float2*)ws, (bf2*)grid)
+             : launch_w(k_ofdm_demod_w384<float2>, syms, num_sms, st, dP, n_streams, (const float2*)ws, (float2*)grid);
 }

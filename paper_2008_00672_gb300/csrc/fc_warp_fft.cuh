@@ -4,6 +4,8 @@
 // transpose through a padded per-warp shared-memory buffer.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "fc_device.cuh"
 #include "fc_internal.cuh"
 
@@ -12,6 +14,15 @@ using namespace fcdev;
 
 constexpr int kPad = 33;                       // transpose row stride in float2
 constexpr int kTrans = 32 * kPad;              // per-warp transpose buffer (float2)
+
+// Caller sample I/O: complex64, or complex BF16 ({bf16 re, bf16 im}, FC_FLAG_IO_BF16).
+// The kernels compute in FP32; a BF16 output sample is rounded once, to nearest, ties
+// to even, when it is stored.
+using bf2 = __nv_bfloat162;
+__device__ __forceinline__ float2 ld_io(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ld_io(const bf2* p) { return __bfloat1622float2(__ldg(p)); }
+__device__ __forceinline__ void st_io(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void st_io(bf2* p, float2 v) { *p = __float22bfloat162_rn(v); }
 
 __device__ __forceinline__ void load_plan_w(FcPlanDev& P, const FcPlanDev* __restrict__ gP) {
   const int words = (int)(sizeof(FcPlanDev) / 4);

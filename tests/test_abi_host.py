@@ -222,7 +222,9 @@ def test_time_io_sizes(fc):
 def test_bf16_io_sizes(fc):
     """FC_FLAG_IO_BF16 halves the bytes of a sample and nothing else: the lengths stay,
     the workspace stays FP32, and the tensor-core passes (which accumulate into the
-    output) give way to the generic kernels."""
+    output) give way to the generic kernels. A symbol-sync plan of the one-warp kernels
+    adds its TX blocks into a complex64 frame in the workspace (one frame a stream) and
+    rounds it into the BF16 output in a second launch."""
     import dataclasses
     for geom in (wl.config_single_5mhz(), wl.config_mixed_20mhz(), wl.config_100mhz(2)):
         a = fc.fc_geometry_check(geom)
@@ -230,7 +232,12 @@ def test_bf16_io_sizes(fc):
         assert (a.sample_bytes, b.sample_bytes) == (8, 4)
         for f in ("grid_len", "wave_len", "slot_len", "stream_delay", "tx_in_len", "rx_out_len"):
             assert getattr(a, f) == getattr(b, f), f
-        assert b.workspace_per_stream == a.workspace_per_stream
+        if geom.mode == fo.SYMBOL_SYNC:
+            assert a.workspace_per_stream == 0
+            assert b.workspace_per_stream == 8 * (b.wave_len + b.wave_len % 2)
+            assert (b.tx_kernels, b.rx_kernels) == (2, 1)
+        else:
+            assert b.workspace_per_stream == a.workspace_per_stream
     g = wl.config_100mhz(2)
     t = fc.fc_geometry_check(dataclasses.replace(g, flags=4 | 16))
     assert (t.tx_kernels, t.rx_kernels) == (2, 2)
