@@ -135,7 +135,8 @@ typedef struct fc_geometry {
    FP32, so a streamed slot is rounded once too. Runs on the generic kernels and on the
    specialised one-warp kernels; the symbol-synchronised TX of the latter adds its
    overlapping blocks into a complex64 frame in the workspace (workspace_per_stream then
-   holds one frame) and rounds it into the output in a second pass (tx_kernels = 2). The
+   holds one frame) and rounds it into the output in a second pass (tx_kernels = 2), and
+   its RX widens the BF16 waveform into that frame first (rx_kernels = 2). The
    tensor-core kernels (FC_FLAG_TENSOR_DFT) do not apply. Combines with FC_FLAG_IO_TIME. */
 #define FC_FLAG_IO_BF16 16
 

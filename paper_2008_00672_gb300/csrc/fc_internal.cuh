@@ -167,7 +167,8 @@ size_t fc_tc_dft64_image_bytes();
 // kernel stages in shared memory)
 // grid_bf16 / io (FC_IO_* bits): complex-BF16 caller samples; the TX kernel accumulates
 // into a complex64 waveform (zeroed here), which fc_launch_to_bf16 rounds into a BF16
-// output.
+// output; the RX kernel takes a complex64 waveform (fc_launch_from_bf16 widens a BF16
+// one) and writes complex64 or BF16 estimates.
 cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, int frame_len,
                                    int weight_floats, const void* grid, int grid_bf16, float2* wave, int num_sms,
                                    cudaStream_t st);
@@ -175,6 +176,7 @@ cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n
                                    int weight_floats, const void* wave, void* grid, int io, int num_sms,
                                    cudaStream_t st);
 cudaError_t fc_launch_to_bf16(const float2* src, void* dst, long long n, int num_sms, cudaStream_t st);
+cudaError_t fc_launch_from_bf16(const void* src, float2* dst, long long n, int num_sms, cudaStream_t st);
 cudaError_t fc_set_warp_smem_limits();
 // Continuous mode, one subband with L = L_OFDM = 384, N = 512, 50 % overlap, overlap-save
 // (fc_warp_cont.cu): OFDM modulation into the workspace then FC blocks (TX), FC blocks into

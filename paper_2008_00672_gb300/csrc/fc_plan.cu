@@ -558,7 +558,8 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     tc_off = ws_len;
     ws_len += (long long)sh[0].R * 4096;
   }
-  // the warp TX kernel's complex64 accumulator of a BF16 frame output
+  // the warp kernels' complex64 frame: the TX accumulator of a BF16 output, the RX copy
+  // of a BF16 input
   if (warp_ok && io_bf16) ws_len = std::max(ws_len, ((long long)frame_len + 1) / 2 * 2);
 
   // grid offsets in the caller's subband order
@@ -606,7 +607,7 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   z.slot_len = streamable ? slot_len : 0;
   z.stream_delay = streamable ? stream_delay : 0;
   z.tx_kernels = sync ? ((warp_ok && io_bf16) ? 2 : 1) : (tc_tx ? 3 : 2);   // + the BF16 rounding pass
-  z.rx_kernels = sync ? 1 : (tc_rx ? 3 : 2);
+  z.rx_kernels = sync ? ((warp_ok && io_bf16) ? 2 : 1) : (tc_rx ? 3 : 2);   // + the BF16 widening pass
   size_t off_dft = 0, off_err = 0;
   if (tc_tx) {
     std::vector<unsigned char> img(fc_tc_dft64_image_bytes());
@@ -845,9 +846,18 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* 
   const FcGenKernels& gen = gen_for(plan, (long long)n_streams * plan->rx_nchunks[k], c.set);
   const float2* wave = (const float2*)in;
   float2* grid = (float2*)out;
-  if (plan->warp_path && !c.generic)
-    return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, plan->warp_weight_floats, in,
-                                  out, io, plan->num_sms, st);
+  if (plan->warp_path && !c.generic) {
+    // a BF16 waveform is widened into the workspace (frame_len samples a stream) first
+    const void* x = in;
+    if ((io & FC_IO_IN_BF16) && workspace && ((uintptr_t)workspace & 15) == 0) {
+      cudaError_t e = fc_launch_from_bf16(in, workspace, (long long)n_streams * plan->h.frame_len, plan->num_sms, st);
+      if (e != cudaSuccess) return e;
+      x = workspace;
+    }
+    if (!(io & FC_IO_IN_BF16) || x != in)
+      return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, plan->warp_weight_floats, x,
+                                    out, io & FC_IO_OUT_BF16, plan->num_sms, st);
+  }
   if (plan->h.mode == FC_SYMBOL_SYNC)
     return gen.rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, in,
                               out, io, plan->smem_rx, st);

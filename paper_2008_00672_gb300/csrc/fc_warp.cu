@@ -819,31 +819,41 @@ cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n
                                    int weight_floats, const void* wave, void* grid, int io, int num_sms,
                                    cudaStream_t st) {
   const size_t smem = rx_smem_bytes(weight_floats);
-  // the calls' I/O: complex64, BF16 frame calls, BF16 stream calls (complex64 frame in)
+  // complex64 input (a BF16 waveform is widened beforehand: the BF16 loads would grow
+  // the L = 1024 job past what the instruction cache holds, which doubled its time)
   switch (io & (FC_IO_IN_BF16 | FC_IO_OUT_BF16)) {
     case 0: return launch_rx_warp<float2, float2>(dP, jobs, n_jobs, n_streams, smem, wave, grid, num_sms, st);
-    case FC_IO_IN_BF16 | FC_IO_OUT_BF16:
-      return launch_rx_warp<bf2, bf2>(dP, jobs, n_jobs, n_streams, smem, wave, grid, num_sms, st);
     case FC_IO_OUT_BF16: return launch_rx_warp<float2, bf2>(dP, jobs, n_jobs, n_streams, smem, wave, grid, num_sms, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 namespace {
-// A complex64 buffer rounded once to complex BF16 (the warp TX kernel's accumulated
-// waveform into a BF16 output).
-__global__ void k_to_bf16(const float2* __restrict__ src, bf2* __restrict__ dst, long long n) {
+// Sample-type conversion of a buffer: complex64 rounded once to complex BF16 (the warp TX
+// kernel's accumulated waveform into a BF16 output), or complex BF16 widened exactly to
+// complex64 (a BF16 waveform into the warp RX kernel).
+template <typename TI, typename TO>
+__global__ void k_convert(const TI* __restrict__ src, TO* __restrict__ dst, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    st_io(dst + i, __ldg(src + i));
+    st_io(dst + i, ld_io(src + i));
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_convert(const TI* src, TO* dst, long long n, int num_sms, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  long long ctas = (n + 255) / 256;
+  if (ctas > 8LL * num_sms) ctas = 8LL * num_sms;
+  k_convert<<<dim3((unsigned)ctas), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t fc_launch_to_bf16(const float2* src, void* dst, long long n, int num_sms, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  long long ctas = (n + 255) / 256;
-  if (ctas > 8LL * num_sms) ctas = 8LL * num_sms;
-  k_to_bf16<<<dim3((unsigned)ctas), 256, 0, st>>>(src, (bf2*)dst, n);
-  return cudaGetLastError();
+  return launch_convert(src, (bf2*)dst, n, num_sms, st);
+}
+
+cudaError_t fc_launch_from_bf16(const void* src, float2* dst, long long n, int num_sms, cudaStream_t st) {
+  return launch_convert((const bf2*)src, dst, n, num_sms, st);
 }
 
 cudaError_t fc_set_warp_smem_limits() {
@@ -853,7 +863,5 @@ cudaError_t fc_set_warp_smem_limits() {
   if ((e = cudaFuncSetAttribute(k_tx_sync_warp<bf2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tx))) return e;
   if ((e = cudaFuncSetAttribute(k_rx_sync_warp<float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rx)))
     return e;
-  if ((e = cudaFuncSetAttribute(k_rx_sync_warp<float2, bf2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rx)))
-    return e;
-  return cudaFuncSetAttribute(k_rx_sync_warp<bf2, bf2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rx);
+  return cudaFuncSetAttribute(k_rx_sync_warp<float2, bf2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rx);
 }

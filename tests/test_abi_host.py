@@ -224,7 +224,8 @@ def test_bf16_io_sizes(fc):
     the workspace stays FP32, and the tensor-core passes (which accumulate into the
     output) give way to the generic kernels. A symbol-sync plan of the one-warp kernels
     adds its TX blocks into a complex64 frame in the workspace (one frame a stream) and
-    rounds it into the BF16 output in a second launch."""
+    rounds it into the BF16 output in a second launch; its RX widens the BF16 waveform
+    into that frame first."""
     import dataclasses
     for geom in (wl.config_single_5mhz(), wl.config_mixed_20mhz(), wl.config_100mhz(2)):
         a = fc.fc_geometry_check(geom)
@@ -235,7 +236,7 @@ def test_bf16_io_sizes(fc):
         if geom.mode == fo.SYMBOL_SYNC:
             assert a.workspace_per_stream == 0
             assert b.workspace_per_stream == 8 * (b.wave_len + b.wave_len % 2)
-            assert (b.tx_kernels, b.rx_kernels) == (2, 1)
+            assert (b.tx_kernels, b.rx_kernels) == (2, 2)
         else:
             assert b.workspace_per_stream == a.workspace_per_stream
     g = wl.config_100mhz(2)

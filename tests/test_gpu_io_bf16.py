@@ -157,11 +157,11 @@ def test_bf16_nr5mhz_continuous(torch_cuda):
 
 def test_bf16_nr20mhz_mixed_numerology(torch_cuda):
     """The one-warp-per-symbol kernels with BF16 I/O (TX into a complex64 frame in the
-    workspace, then one rounding pass)."""
+    workspace, then one rounding pass; RX from the waveform widened into that frame)."""
     geom = dataclasses.replace(wl.config_mixed_20mhz(), flags=BF16)
     from paper_2008_00672_gb300 import Plan
     p = Plan(geom)
-    assert (p.tx_kernels, p.rx_kernels) == (2, 1) and p.workspace_per_stream >= 8 * p.wave_len
+    assert (p.tx_kernels, p.rx_kernels) == (2, 2) and p.workspace_per_stream >= 8 * p.wave_len
     p.close()
     tx_rx_case(torch_cuda, geom, 2, 24)
 
