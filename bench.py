@@ -658,6 +658,54 @@ def nr5mhz_bench(torch, dev, st, peaks: dict, n_sms: int, sm_mhz: float, n_slots
     return out
 
 
+def bf16_io_bench(torch, dev, st, reps: int = 10) -> dict:
+    """Complex-BF16 I/O (FC_FLAG_IO_BF16) on the one-warp kernels against complex64 I/O
+    on the same calls: the 20 MHz subframe at 2048 streams and the 5 MHz slot at 8192
+    slots, TX and RX call times by CUDA events on the launching stream."""
+    import numpy as np
+    import workloads as wl
+    from paper_2008_00672_gb300 import FC_FLAG_IO_BF16, Plan
+
+    out = {}
+    for name, geom0, S in (("nr20mhz_mixed", wl.config_mixed_20mhz(), 2048),
+                           ("nr5mhz_continuous", wl.config_single_5mhz(), 8192)):
+        row = {}
+        for io in ("complex64", "bf16"):
+            geom = dataclasses.replace(geom0, flags=FC_FLAG_IO_BF16) if io == "bf16" else geom0
+            plan = Plan(geom, device=dev.index or 0)
+            base = torch.from_numpy(wl.qam_grid(geom, 64, wl.default_seed(3)).astype(np.complex64)).to(dev)
+            grid = base.repeat(S // 64, 1).contiguous()
+            wave = torch.empty((S, plan.wave_len), dtype=torch.complex64, device=dev)
+            if io == "bf16":
+                grid = torch.view_as_real(grid).to(torch.bfloat16).contiguous()
+                wave = torch.empty((S, plan.wave_len, 2), dtype=torch.bfloat16, device=dev)
+            est = torch.empty_like(grid)
+            ws = plan.workspace(S)
+            for _ in range(3):
+                plan.tx_synthesize(grid, wave, ws)
+                plan.rx_analyze(wave, est, ws)
+            torch.cuda.synchronize(dev)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev[0].record(st)
+            for _ in range(reps):
+                plan.tx_synthesize(grid, wave, ws)
+            ev[1].record(st)
+            for _ in range(reps):
+                plan.rx_analyze(wave, est, ws)
+            ev[2].record(st)
+            torch.cuda.synchronize(dev)
+            tx, rx = ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps
+            row[io] = {"tx_ms": round(tx, 4), "rx_ms": round(rx, 4),
+                       "msamples_per_s": round(2 * plan.nominal_len * S / (tx + rx) / 1e3, 1),
+                       "launches_per_call": {"tx": plan.tx_kernels, "rx": plan.rx_kernels},
+                       "io_bytes_per_step": 2 * S * (plan.grid_len + plan.wave_len) * plan.sample_bytes}
+            del grid, wave, est, ws
+            plan.close()
+        row["streams"] = S
+        out[name] = row
+    return out
+
+
 def nr100_paths_bench(torch, dev, st, peaks: dict, n_sms: int, sm_mhz: float, n_streams: int = 32,
                       cpu_leg: bool = True) -> dict:
     """100 MHz / 273 PRB carrier (N = L = 4096, 10 slots): the FP32 shared-memory FFT
@@ -950,6 +998,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     side_cpu = world == 1 and not args.no_cpu_baseline
     nr100 = nr100_paths_bench(torch, dev, st, load_peaks()[0], n_sms, sm_mhz, cpu_leg=side_cpu)
     nr5 = nr5mhz_bench(torch, dev, st, load_peaks()[0], n_sms, sm_mhz, cpu_leg=side_cpu)
+    bf16_io = bf16_io_bench(torch, dev, st)
     serving = serving_bench(torch, dev, args.serve_requests) if args.serve_requests > 0 else None
 
     # ---- one sampled stream of the timed path, kept for the oracle check of the CPU leg ----
@@ -1030,7 +1079,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
            "accuracy": accuracy,
            "fc_distortion": fc_distortion_bench(torch, dev), "fc_spectrum": fc_spectrum_bench(torch, dev),
            "rx_variants": rx_variants, "uneven_carriers": uneven, "serving": serving, "nr100mhz_paths": nr100,
-           "nr5mhz_continuous": nr5,
+           "nr5mhz_continuous": nr5, "bf16_io": bf16_io,
            "clocks": clk, "gpu_launches": args.steps * (plan.tx_kernels + plan.rx_kernels)}
     print(json.dumps(out), flush=True)
 
