@@ -167,6 +167,7 @@ struct fc_plan {
   int* d_err = nullptr;                     // device error word of the tensor-core kernels
   unsigned tc_first_wait = 1u << 22;        // poll limit of the tensor-core kernels' first GEMM wait
   FcJob* d_wjobs = nullptr;                 // one stream's jobs in cost order (warp kernels)
+  int n_wjobs_big = 0;                      // the first n_wjobs_big of them belong to N = 2048 groups
   int warp_weight_floats = 0;               // sum over groups of the subband length (warp TX weights)
   size_t smem_tx = 0, smem_rx = 0, smem_ofdm = 0;
   int syms_per_stream = 0;
@@ -480,6 +481,7 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
                    sh[0].L == 384 && sh[0].Lo == 384 && gh[0].N == 512 && 2 * gh[0].N_O == gh[0].N &&
                    gh[0].offset == 0;
   size_t off_wjobs = 0;
+  int n_big = 0;
   if (warp_ok) {
     // one stream's jobs, most expensive first (N = 2048 before N = 1024): the warp
     // kernels deal the job-major list of all streams to their CTAs in this order
@@ -487,6 +489,7 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     std::stable_sort(by_cost.begin(), by_cost.end(),
                      [&](const FcJob& a, const FcJob& b) { return gh[a.group].N > gh[b.group].N; });
     off_wjobs = blob.add_vec(by_cost);
+    for (const FcJob& jb : by_cost) n_big += gh[jb.group].N == 2048;
   }
 
   // ---- buffers and shared memory -------------------------------------------
@@ -606,8 +609,15 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   pl->io = io_bf16 ? (FC_IO_IN_BF16 | FC_IO_OUT_BF16) : 0;
   z.slot_len = streamable ? slot_len : 0;
   z.stream_delay = streamable ? stream_delay : 0;
-  z.tx_kernels = sync ? ((warp_ok && io_bf16) ? 2 : 1) : (tc_tx ? 3 : 2);   // + the BF16 rounding pass
-  z.rx_kernels = sync ? ((warp_ok && io_bf16) ? 2 : 1) : (tc_rx ? 3 : 2);   // + the BF16 widening pass
+  // the one-warp kernels: one launch per job shape present, + the BF16 rounding / widening pass
+  int warp_shapes = 0;
+  if (warp_ok) {
+    bool big = false, small = false;
+    for (const GroupHost& o : gh) (o.N == 2048 ? big : small) = true;
+    warp_shapes = (int)big + (int)small;
+  }
+  z.tx_kernels = sync ? (warp_ok ? warp_shapes + (int)io_bf16 : 1) : (tc_tx ? 3 : 2);
+  z.rx_kernels = sync ? (warp_ok ? warp_shapes + (int)io_bf16 : 1) : (tc_rx ? 3 : 2);
   size_t off_dft = 0, off_err = 0;
   if (tc_tx) {
     std::vector<unsigned char> img(fc_tc_dft64_image_bytes());
@@ -719,7 +729,10 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
     pl->d_dft64 = base + off_dft;
     pl->d_err = reinterpret_cast<int*>(base + off_err);
   }
-  if (warp_ok) pl->d_wjobs = reinterpret_cast<FcJob*>(base + off_wjobs);
+  if (warp_ok) {
+    pl->d_wjobs = reinterpret_cast<FcJob*>(base + off_wjobs);
+    pl->n_wjobs_big = n_big;
+  }
   return FC_OK;
 }
 
@@ -801,9 +814,9 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* 
     const bool out16 = (io & FC_IO_OUT_BF16) != 0;
     float2* acc = out16 ? workspace : wave;
     if (acc && ((uintptr_t)acc & 15) == 0) {
-      cudaError_t e = fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, plan->h.frame_len,
-                                             plan->warp_weight_floats, in, (io & FC_IO_IN_BF16) != 0, acc,
-                                             plan->num_sms, st);
+      cudaError_t e = fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, plan->n_wjobs_big, n_streams,
+                                             plan->h.frame_len, plan->warp_weight_floats, in,
+                                             (io & FC_IO_IN_BF16) != 0, acc, plan->num_sms, st);
       if (e == cudaSuccess && out16)
         e = fc_launch_to_bf16(acc, out, (long long)n_streams * plan->h.frame_len, plan->num_sms, st);
       return e;
@@ -855,8 +868,9 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* 
       x = workspace;
     }
     if (!(io & FC_IO_IN_BF16) || x != in)
-      return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, n_streams, plan->warp_weight_floats, x,
-                                    out, io & FC_IO_OUT_BF16, plan->num_sms, st);
+      return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, plan->n_wjobs_big, n_streams,
+                                    plan->warp_weight_floats, plan->h.scheme_rx, plan->h.flags, x, out,
+                                    io & FC_IO_OUT_BF16, plan->num_sms, st);
   }
   if (plan->h.mode == FC_SYMBOL_SYNC)
     return gen.rx_sync(plan->d_plan, plan->d_jobs, plan->rx_chunks[k], plan->rx_nchunks[k], n_streams, in,

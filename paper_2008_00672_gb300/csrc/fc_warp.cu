@@ -75,11 +75,11 @@ __device__ __forceinline__ float weight_staged(const FcSubDev& S, const float* d
 //   1   both blocks segmented from the body, two 512-point DFTs (kept in registers)
 //   2/3 block r = 0/1: map into the 1024-bin spectrum, IDFT, reduce into the waveform
 // ---------------------------------------------------------------------------
-template <typename TI>
+template <bool BIG, typename TI>
 __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                        const TI* __restrict__ gsrc, float2* __restrict__ wdst, float2* scr,
                                        float2* map, int lane, const TxTables& tt, const float* wt) {
-  const bool big = S.L == 1024;
+  constexpr bool big = BIG;                        // L = 1024 (N = 2048), else L = 512
   const JobTables tb{tt.t1024, tt.t512, tt.t2048};
   const int n = jb.index;
   const int hl = S.Lact / 2, hu = S.Lact - hl;
@@ -404,7 +404,7 @@ __device__ __forceinline__ void rx_block_gather_1024(const FcPlanDev& P, const F
 // One IDFT and one DFT replace the two block IDFTs and the OFDM DFT (6 transforms of
 // 1024 points per symbol instead of 7), at the cost of a second pass over the output row.
 template <typename TI>
-__device__ __noinline__ void rx_job_1024_reduced(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
+__device__ __forceinline__ void rx_job_1024_reduced(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                             const TI* __restrict__ src, float2* __restrict__ gdst, float2* scr,
                                             float2* map, int lane, const RxStaged& st) {
   constexpr int L = 1024;
@@ -443,7 +443,7 @@ __device__ __noinline__ void rx_job_1024_reduced(const FcPlanDev& P, const FcGro
 // OLA: the scheme (a template parameter, so that the overlap-save form carries only the
 // 16 values per lane it needs across the block loop)
 template <bool OLA, typename TI, typename TO>
-__device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
+__device__ __forceinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                             const TI* __restrict__ src, TO* __restrict__ gdst, float2* scr,
                                             float2* map, int lane, const RxStaged& st) {
   constexpr int L = 1024;
@@ -535,7 +535,7 @@ __device__ __noinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev& G
 // RX, N = 1024, L = 512
 // ---------------------------------------------------------------------------
 template <typename TI, typename TO>
-__device__ __noinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
+__device__ __forceinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                            const TI* __restrict__ src, TO* __restrict__ gdst, float2* scr,
                                            float2* map, int lane, const RxStaged& st) {
   constexpr int L = 512;
@@ -623,27 +623,29 @@ __device__ __forceinline__ void prefetch_l2(const T* p, int n, int lane) {
   for (int i = kLine * lane; i < n; i += kLine * 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + i));
 }
 
-// RX jobs of different streams share nothing, so no item waits for another. The eq:reduc
-// form adds into its output row after storing to it, so it runs for complex64 output
-// only; a BF16 output (rounded once per sample) takes the direct form.
-template <typename TI, typename TO>
-__device__ __forceinline__ void rx_dispatch(const FcPlanDev& P, const FcJob& jb, const TI* __restrict__ src,
-                                            TO* __restrict__ gdst, float2* scr, float2* map, int lane,
-                                            const RxStaged& st) {
+// RX job shapes: each runs in a kernel of its own, with its job function inlined (one
+// shape's code per kernel, no calls). The eq:reduc form adds into its output row after
+// storing to it, so it runs for complex64 output only; a BF16 output (rounded once per
+// sample) takes the direct form.
+enum RxShape { kRx1024Ols = 0, kRx1024Ola = 1, kRx512 = 2, kRx1024Reduced = 3 };
+
+template <int SHAPE, typename TI, typename TO>
+__device__ __forceinline__ void rx_run(const FcPlanDev& P, const FcJob& jb, const TI* __restrict__ src,
+                                       TO* __restrict__ gdst, float2* scr, float2* map, int lane, const RxStaged& st) {
   const FcGroupDev& G = P.g[jb.group];
   const FcSubDev& S = P.s[G.first_sub];
-  if constexpr (std::is_same<TO, float2>::value) {
-    if (S.L == 1024 && (P.flags & FC_FLAG_REDUCED_RX) && P.scheme_rx == FC_OLS) {
-      rx_job_1024_reduced(P, G, S, jb, src, gdst, scr, map, lane, st);
-      return;
-    }
+  if constexpr (SHAPE == kRx1024Reduced) {
+    if constexpr (std::is_same<TO, float2>::value) rx_job_1024_reduced(P, G, S, jb, src, gdst, scr, map, lane, st);
+  } else if constexpr (SHAPE == kRx1024Ola) {
+    rx_job_1024<true>(P, G, S, jb, src, gdst, scr, map, lane, st);
+  } else if constexpr (SHAPE == kRx1024Ols) {
+    rx_job_1024<false>(P, G, S, jb, src, gdst, scr, map, lane, st);
+  } else {
+    rx_job_512(P, G, S, jb, src, gdst, scr, map, lane, st);
   }
-  if (S.L == 1024 && P.scheme_rx == FC_OLA) rx_job_1024<true>(P, G, S, jb, src, gdst, scr, map, lane, st);
-  else if (S.L == 1024) rx_job_1024<false>(P, G, S, jb, src, gdst, scr, map, lane, st);
-  else rx_job_512(P, G, S, jb, src, gdst, scr, map, lane, st);
 }
 
-template <typename TI, typename TO>
+template <int SHAPE, typename TI, typename TO>
 __global__ void __launch_bounds__(kRxThreads, 1)
 k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, int n_jobs, int n_streams,
                      const TI* __restrict__ wave, TO* __restrict__ grid) {
@@ -694,13 +696,14 @@ k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     }
     const FcJob jb = jobs[j];
     const RxStaged st{tabs, tabs + 1024, wts + wt_off[jb.group]};
-    rx_dispatch(P, jb, wave + (size_t)stream * P.frame_len, grid + (size_t)stream * P.grid_len, scr, map, lane, st);
+    rx_run<SHAPE>(P, jb, wave + (size_t)stream * P.frame_len, grid + (size_t)stream * P.grid_len, scr, map, lane, st);
   }
 }
 
 // TX: jobs of one stream run on several CTAs and reduce into the same waveform, which
-// is zeroed beforehand.
-template <typename TI>
+// is zeroed beforehand. One kernel per job shape (BIG: the N = 2048 groups' jobs), so that
+// each holds one shape's code.
+template <bool BIG, typename TI>
 __global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_TX_MIN_BLOCKS)
 k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, int n_jobs, int n_streams,
                      const TI* __restrict__ grid, float2* __restrict__ wave) {
@@ -756,7 +759,7 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     }
     const FcJob jb = jobs[j];
     const FcGroupDev& G = P.g[jb.group];
-    tx_job(P, G, P.s[G.first_sub], jb, grid + (size_t)stream * P.grid_len, wave + (size_t)stream * P.frame_len, scr,
+    tx_job<BIG>(P, G, P.s[G.first_sub], jb, grid + (size_t)stream * P.grid_len, wave + (size_t)stream * P.frame_len, scr,
            map, lane, tt, wts + wt_off[jb.group]);
   }
 }
@@ -771,28 +774,39 @@ static size_t tx_smem_bytes(int weight_floats) {
   return fc_warp_smem_bytes() + (size_t)kTxTwiddles * sizeof(float2) + (((size_t)weight_floats * 4 + 15) & ~(size_t)15);
 }
 
-template <typename TI>
+template <bool BIG, typename TI>
 static cudaError_t launch_tx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, size_t smem,
                                   const TI* grid, float2* wave, int num_sms, cudaStream_t st) {
+  if (n_jobs < 1) return cudaSuccess;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tx_sync_warp<TI>, FC_WARP_THREADS, smem);
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tx_sync_warp<BIG, TI>, FC_WARP_THREADS, smem);
   if (e != cudaSuccess) return e;
   const long long total = (long long)n_jobs * n_streams;
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  k_tx_sync_warp<TI><<<dim3((unsigned)ctas), FC_WARP_THREADS, smem, st>>>(dP, jobs, n_jobs, n_streams, grid, wave);
+  k_tx_sync_warp<BIG, TI><<<dim3((unsigned)ctas), FC_WARP_THREADS, smem, st>>>(dP, jobs, n_jobs, n_streams, grid,
+                                                                              wave);
   return cudaGetLastError();
 }
 
-cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, int frame_len,
-                                   int weight_floats, const void* grid, int grid_bf16, float2* wave, int num_sms,
-                                   cudaStream_t st) {
+template <typename TI>
+static cudaError_t launch_tx_shapes(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,
+                                    size_t smem, const TI* grid, float2* wave, int num_sms, cudaStream_t st) {
+  cudaError_t e = launch_tx_warp<true>(dP, jobs, n_big, n_streams, smem, grid, wave, num_sms, st);
+  if (e != cudaSuccess) return e;
+  return launch_tx_warp<false>(dP, jobs + n_big, n_jobs - n_big, n_streams, smem, grid, wave, num_sms, st);
+}
+
+cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,
+                                   int frame_len, int weight_floats, const void* grid, int grid_bf16, float2* wave,
+                                   int num_sms, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(wave, 0, (size_t)n_streams * frame_len * sizeof(float2), st);
   if (e != cudaSuccess) return e;
   const size_t smem = tx_smem_bytes(weight_floats);
-  return grid_bf16 ? launch_tx_warp(dP, jobs, n_jobs, n_streams, smem, (const bf2*)grid, wave, num_sms, st)
-                   : launch_tx_warp(dP, jobs, n_jobs, n_streams, smem, (const float2*)grid, wave, num_sms, st);
+  return grid_bf16 ? launch_tx_shapes(dP, jobs, n_jobs, n_big, n_streams, smem, (const bf2*)grid, wave, num_sms, st)
+                   : launch_tx_shapes(dP, jobs, n_jobs, n_big, n_streams, smem, (const float2*)grid, wave, num_sms, st);
 }
 
 static size_t rx_smem_bytes(int weight_floats) {
@@ -800,30 +814,59 @@ static size_t rx_smem_bytes(int weight_floats) {
          (((size_t)weight_floats * 4 + 15) & ~(size_t)15);
 }
 
-template <typename TI, typename TO>
+template <int SHAPE, typename TI, typename TO>
 static cudaError_t launch_rx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, size_t smem,
                                   const void* wave, void* grid, int num_sms, cudaStream_t st) {
+  if (n_jobs < 1) return cudaSuccess;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rx_sync_warp<TI, TO>, kRxThreads, smem);
+  cudaError_t e =
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rx_sync_warp<SHAPE, TI, TO>, kRxThreads, smem);
   if (e != cudaSuccess) return e;
   const long long total = (long long)n_jobs * n_streams;
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  k_rx_sync_warp<TI, TO><<<dim3((unsigned)ctas), kRxThreads, smem, st>>>(dP, jobs, n_jobs, n_streams,
-                                                                        (const TI*)wave, (TO*)grid);
+  k_rx_sync_warp<SHAPE, TI, TO><<<dim3((unsigned)ctas), kRxThreads, smem, st>>>(dP, jobs, n_jobs, n_streams,
+                                                                               (const TI*)wave, (TO*)grid);
   return cudaGetLastError();
 }
 
-cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams,
-                                   int weight_floats, const void* wave, void* grid, int io, int num_sms,
-                                   cudaStream_t st) {
+template <typename TO>
+static cudaError_t launch_rx_shapes(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,
+                                    size_t smem, const void* wave, void* grid, int big_shape, int num_sms,
+                                    cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (big_shape == kRx1024Ola) {
+    e = launch_rx_warp<kRx1024Ola, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st);
+  } else {
+    bool done = false;
+    if constexpr (std::is_same<TO, float2>::value) {
+      if (big_shape == kRx1024Reduced) {
+        e = launch_rx_warp<kRx1024Reduced, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st);
+        done = true;
+      }
+    }
+    if (!done) e = launch_rx_warp<kRx1024Ols, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st);
+  }
+  if (e != cudaSuccess) return e;
+  return launch_rx_warp<kRx512, float2, TO>(dP, jobs + n_big, n_jobs - n_big, n_streams, smem, wave, grid, num_sms,
+                                            st);
+}
+
+cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,
+                                   int weight_floats, int scheme_rx, int flags, const void* wave, void* grid, int io,
+                                   int num_sms, cudaStream_t st) {
   const size_t smem = rx_smem_bytes(weight_floats);
+  const int big_shape = scheme_rx == FC_OLA ? kRx1024Ola
+                        : ((flags & FC_FLAG_REDUCED_RX) && !(io & FC_IO_OUT_BF16)) ? kRx1024Reduced
+                                                                                   : kRx1024Ols;
   // complex64 input (a BF16 waveform is widened beforehand: the BF16 loads would grow
   // the L = 1024 job past what the instruction cache holds, which doubled its time)
   switch (io & (FC_IO_IN_BF16 | FC_IO_OUT_BF16)) {
-    case 0: return launch_rx_warp<float2, float2>(dP, jobs, n_jobs, n_streams, smem, wave, grid, num_sms, st);
-    case FC_IO_OUT_BF16: return launch_rx_warp<float2, bf2>(dP, jobs, n_jobs, n_streams, smem, wave, grid, num_sms, st);
+    case 0:
+      return launch_rx_shapes<float2>(dP, jobs, n_jobs, n_big, n_streams, smem, wave, grid, big_shape, num_sms, st);
+    case FC_IO_OUT_BF16:
+      return launch_rx_shapes<bf2>(dP, jobs, n_jobs, n_big, n_streams, smem, wave, grid, big_shape, num_sms, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -859,9 +902,16 @@ cudaError_t fc_launch_from_bf16(const void* src, float2* dst, long long n, int n
 cudaError_t fc_set_warp_smem_limits() {
   cudaError_t e;
   const int tx = (int)tx_smem_bytes(FC_MAX_GROUPS * 1024), rx = (int)rx_smem_bytes(FC_MAX_GROUPS * 1024);
-  if ((e = cudaFuncSetAttribute(k_tx_sync_warp<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tx))) return e;
-  if ((e = cudaFuncSetAttribute(k_tx_sync_warp<bf2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tx))) return e;
-  if ((e = cudaFuncSetAttribute(k_rx_sync_warp<float2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rx)))
-    return e;
-  return cudaFuncSetAttribute(k_rx_sync_warp<float2, bf2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rx);
+  const void* tx_kernels[] = {(const void*)k_tx_sync_warp<true, float2>, (const void*)k_tx_sync_warp<false, float2>,
+                              (const void*)k_tx_sync_warp<true, bf2>, (const void*)k_tx_sync_warp<false, bf2>};
+  for (const void* k : tx_kernels)
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tx))) return e;
+  const void* rx_kernels[] = {
+      (const void*)k_rx_sync_warp<kRx1024Ols, float2, float2>, (const void*)k_rx_sync_warp<kRx1024Ola, float2, float2>,
+      (const void*)k_rx_sync_warp<kRx512, float2, float2>, (const void*)k_rx_sync_warp<kRx1024Reduced, float2, float2>,
+      (const void*)k_rx_sync_warp<kRx1024Ols, float2, bf2>, (const void*)k_rx_sync_warp<kRx1024Ola, float2, bf2>,
+      (const void*)k_rx_sync_warp<kRx512, float2, bf2>};
+  for (const void* k : rx_kernels)
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, rx))) return e;
+  return cudaSuccess;
 }
