@@ -168,6 +168,8 @@ struct fc_plan {
   unsigned tc_first_wait = 1u << 22;        // poll limit of the tensor-core kernels' first GEMM wait
   FcJob* d_wjobs = nullptr;                 // one stream's jobs in cost order (warp kernels)
   int n_wjobs_big = 0;                      // the first n_wjobs_big of them belong to N = 2048 groups
+  FcJob* d_wtxjobs = nullptr;               // the TX list: the same, N = 1024 symbols in pairs
+  int n_wtxjobs = 0;
   int warp_weight_floats = 0;               // sum over groups of the subband length (warp TX weights)
   size_t smem_tx = 0, smem_rx = 0, smem_ofdm = 0;
   int syms_per_stream = 0;
@@ -480,8 +482,8 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   bool cont_warp = !sync && G == 1 && M == 1 && !io_time && !(geo->flags & FC_FLAG_GENERIC_KERNELS) &&
                    sh[0].L == 384 && sh[0].Lo == 384 && gh[0].N == 512 && 2 * gh[0].N_O == gh[0].N &&
                    gh[0].offset == 0;
-  size_t off_wjobs = 0;
-  int n_big = 0;
+  size_t off_wjobs = 0, off_wtx = 0;
+  int n_big = 0, n_wtx = 0;
   if (warp_ok) {
     // one stream's jobs, most expensive first (N = 2048 before N = 1024): the warp
     // kernels deal the job-major list of all streams to their CTAs in this order
@@ -490,6 +492,19 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
                      [&](const FcJob& a, const FcJob& b) { return gh[a.group].N > gh[b.group].N; });
     off_wjobs = blob.add_vec(by_cost);
     for (const FcJob& jb : by_cost) n_big += gh[jb.group].N == 2048;
+    // TX: the N = 1024 groups' symbols in pairs (n, n + 1) (nblk = 4), whose OFDM IDFTs
+    // share one two-transform FFT (a group's odd last symbol alone), by time
+    std::vector<FcJob> tx(by_cost.begin(), by_cost.begin() + n_big);
+    std::vector<FcJob> pairs;
+    for (int g = 0; g < G; ++g) {
+      const GroupHost& o = gh[g];
+      if (o.N == 2048) continue;
+      for (int n = 0; n < o.B; n += 2) pairs.push_back(FcJob{g, n, n + 1 < o.B ? 4 : 2, o.offset + o.sigma[n]});
+    }
+    std::stable_sort(pairs.begin(), pairs.end(), [](const FcJob& a, const FcJob& b) { return a.start < b.start; });
+    tx.insert(tx.end(), pairs.begin(), pairs.end());
+    off_wtx = blob.add_vec(tx);
+    n_wtx = (int)tx.size();
   }
 
   // ---- buffers and shared memory -------------------------------------------
@@ -732,6 +747,8 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   if (warp_ok) {
     pl->d_wjobs = reinterpret_cast<FcJob*>(base + off_wjobs);
     pl->n_wjobs_big = n_big;
+    pl->d_wtxjobs = reinterpret_cast<FcJob*>(base + off_wtx);
+    pl->n_wtxjobs = n_wtx;
   }
   return FC_OK;
 }
@@ -814,9 +831,12 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* 
     const bool out16 = (io & FC_IO_OUT_BF16) != 0;
     float2* acc = out16 ? workspace : wave;
     if (acc && ((uintptr_t)acc & 15) == 0) {
-      cudaError_t e = fc_launch_tx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, plan->n_wjobs_big, n_streams,
-                                             plan->h.frame_len, plan->warp_weight_floats, in,
-                                             (io & FC_IO_IN_BF16) != 0, acc, plan->num_sms, st);
+      // complex64 input: the N = 1024 symbols in pairs; BF16 input: one symbol a job
+      const bool in16 = (io & FC_IO_IN_BF16) != 0;
+      cudaError_t e = fc_launch_tx_sync_warp(plan->d_plan, in16 ? plan->d_wjobs : plan->d_wtxjobs,
+                                             in16 ? plan->n_jobs : plan->n_wtxjobs, plan->n_wjobs_big, n_streams,
+                                             plan->h.frame_len, plan->warp_weight_floats, in, in16, acc,
+                                             plan->num_sms, st);
       if (e == cudaSuccess && out16)
         e = fc_launch_to_bf16(acc, out, (long long)n_streams * plan->h.frame_len, plan->num_sms, st);
       return e;

@@ -18,8 +18,14 @@
 // A TX job is a short program of stages "prepare -> forward FFT -> consume" (inverse
 // transforms as conj(FFT(conj(x)))), so the TX kernel holds a single copy of the
 // unrolled FFT; RX jobs keep direction-specialised transforms in rolled loops (one copy
-// of each per job shape). Both kernels take the job-major list of all streams' jobs,
-// dealt to as many CTAs as the GPU holds at once.
+// of each per job shape). Each direction launches one kernel per job shape (the
+// N = 2048 groups' jobs, then the N = 1024 groups'), with the job inlined: a kernel then
+// holds one shape's code, which the instruction cache keeps, and no calls (TX 1.395 ->
+// 1.347 ms, RX 1.202 -> 1.066 ms at 2048 streams against one kernel for both shapes).
+// Each launch takes the job-major list of its jobs over all streams, dealt to as many
+// CTAs as the GPU holds at once.
+#include <algorithm>
+
 #include "fc_device.cuh"
 #include "fc_internal.cuh"
 #include "fc_warp_fft.cuh"
@@ -53,6 +59,11 @@ struct JobTables {
 // loops read them at data-dependent positions; from shared memory they cost less than
 // from the L1 cache).
 constexpr int kTxTwiddles = 16 * 32 + 32 * 32 + 2048;   // float2
+// The L = 512 kernel needs no 2048-point table; its warps hold a pair buffer (the second
+// body of a pair of symbols) after their scratch instead.
+constexpr int kPairBuf = 512;                              // float2
+template <bool BIG> constexpr int kTxWarpScratch = BIG ? kScratch : kScratch + kPairBuf;
+template <bool BIG> constexpr int kTxTables = BIG ? kTxTwiddles : kTxTwiddles - 2048;
 struct TxTables {
   const float2* t1024;    // per-lane step table, 1024 points
   const float2* t512;     // per-lane step table, 512 points
@@ -70,31 +81,46 @@ __device__ __forceinline__ float weight_staged(const FcSubDev& S, const float* d
 //   2/5 even output samples of block r (IDFT of the folded spectrum), kept in registers
 //   3/6 odd output samples (IDFT of the spectrum times exp(+j 2 pi q / 2048)); both
 //       parities reduced into the waveform as float4
-// L = 512 (N = 1024), stages:
-//   0   OFDM IDFT -> body to the map buffer
-//   1   both blocks segmented from the body, two 512-point DFTs (kept in registers)
-//   2/3 block r = 0/1: map into the 1024-bin spectrum, IDFT, reduce into the waveform
+// L = 512 (N = 1024), a pair of symbols n, n + 1 (jb.nblk == 4) or a single symbol:
+//   0   OFDM IDFT of both rows in one two-transform FFT (a single symbol: the second
+//       transform's input is zero) -> body of n to the map buffer, body of n + 1 to the
+//       warp's pair buffer
+//   1   symbol s: both blocks segmented from its body, two 512-point DFTs (kept in registers)
+//   2/3 symbol s, block r = 0/1: map into the 1024-bin spectrum, IDFT, reduce into the waveform
+//   4-6 stages 1-3 for symbol n + 1 (pairs: the seven stages of an N = 2048 symbol)
 // ---------------------------------------------------------------------------
 template <bool BIG, typename TI>
 __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                        const TI* __restrict__ gsrc, float2* __restrict__ wdst, float2* scr,
-                                       float2* map, int lane, const TxTables& tt, const float* wt) {
+                                       float2* map, float2* pbuf, int lane, const TxTables& tt, const float* wt) {
   constexpr bool big = BIG;                        // L = 1024 (N = 2048), else L = 512
+  // pairs for complex64 input only: with BF16 loads the pair code grew the kernel past
+  // what the instruction cache holds (1.49 -> 1.65 ms at 2048 streams)
+  const bool pair = !big && std::is_same<TI, float2>::value && jb.nblk == 4;
   const JobTables tb{tt.t1024, tt.t512, tt.t2048};
-  const int n = jb.index;
   const int hl = S.Lact / 2, hu = S.Lact - hl;
-  const TI* __restrict__ row = gsrc + S.grid_off + (long long)n * S.Lact;
-  const int lcp = S.lcp[n], ncp = G.ncp[n];
+  const TI* __restrict__ row = gsrc + S.grid_off + (long long)jb.index * S.Lact;
   const bool ols = P.scheme_tx == FC_OLS;
-  const bool v4 = ((jb.start & 1) == 0);
   const int nN = big ? 2048 : 1024;
   const float2* __restrict__ twNg = P.sz[G.size_N].tw;                              // the plan's full table
-  const float2 ph0 = root_pos(twNg, nN, (long long)S.c * G.cps[n]);                  // phi_0 theta_n
-  const float2 ph1 = root_pos(twNg, nN, (long long)S.c * (G.cps[n] + G.N_S));       // phi_1 theta_n
-  const int nst = big ? 7 : 4;
+  // the current symbol's CP lengths, position and phases (the second symbol of a pair
+  // takes them over at stage 4)
+  int lcp, ncp, start;
+  float2 ph0, ph1;
+  auto symbol = [&](int n) {
+    lcp = S.lcp[n];
+    ncp = G.ncp[n];
+    start = G.offset + G.sigma[n];
+    ph0 = root_pos(twNg, nN, (long long)S.c * G.cps[n]);                            // phi_0 theta_n
+    ph1 = root_pos(twNg, nN, (long long)S.c * (G.cps[n] + G.N_S));                 // phi_1 theta_n
+  };
+  symbol(jb.index);
+  const bool v4 = ((start & 1) == 0);
+  const int nst = (big || pair) ? 7 : 4;
   float2 v[32], keep[32];
 #pragma unroll 1
   for (int st = 0; st < nst; ++st) {
+    if (pair && st == 4) symbol(jb.index + 1);
     // ---------------- prepare ----------------
     bool inv, two512;
     if (big) {
@@ -140,16 +166,19 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
         inv = true;
       }
     } else {
+      const int ss = (pair && st >= 4) ? st - 3 : st;   // stage of the current symbol
       if (st == 0) {
 #pragma unroll
         for (int a = 0; a < 16; ++a) {
           const int f = signed_bin(32 * a + lane, 512);
-          v[a] = (f >= -hl && f < hu) ? ld_io(row + f + hl) : czero();
-          v[16 + a] = czero();
+          const bool in = f >= -hl && f < hu;
+          v[a] = in ? ld_io(row + f + hl) : czero();
+          v[16 + a] = (pair && in) ? ld_io(row + S.Lact + f + hl) : czero();
         }
         inv = true;
         two512 = true;
-      } else if (st == 1) {
+      } else if (ss == 1) {
+        const float2* body = (st >= 4) ? pbuf : map;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
 #pragma unroll
@@ -158,14 +187,14 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
             bool k;
             if (!ols) k = (r == 0) ? (t >= 128 - lcp && t < 384) : (t >= 128 && t < 384);
             else k = (r == 0) ? (t >= 128 - lcp) : (t < 384);
-            v[16 * r + a] = k ? map[(t - 128 + 256 * r) & 511] : czero();
+            v[16 * r + a] = k ? body[(t - 128 + 256 * r) & 511] : czero();
           }
         }
         __syncwarp();
         inv = false;
         two512 = true;
-      } else {                                          // block r = st - 2 into the 1024-bin spectrum
-        const int r = st - 2;
+      } else {                                          // block r = ss - 2 into the 1024-bin spectrum
+        const int r = ss - 2;
 #pragma unroll
         for (int a = 0; a < 32; ++a) map[32 * a + lane] = czero();
         __syncwarp();
@@ -218,7 +247,7 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
             if (!(tau >= lo && tau < hi)) a0 = czero();
             if (!(tau + 1 >= lo && tau + 1 < hi)) a1 = czero();
           }
-          float2* dst = wdst + jb.start + r * 1024 + tau;
+          float2* dst = wdst + start + r * 1024 + tau;
           if (v4) {
             atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a0.x, a0.y, a1.x, a1.y));
           } else {
@@ -229,24 +258,26 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
         __syncwarp();
       }
     } else {
-      if (st == 0) {                                    // body[k1 + 16 k2] in lanes 0..15
-        if (lane < 16) {
+      const int ss = (pair && st >= 4) ? st - 3 : st;
+      if (st == 0) {                                    // body of n [k1 + 16 k2] from lanes 0..15 to
+        if (lane < 16 || pair) {                        // the map buffer, body of n + 1 from lanes
+          float2* body = (lane < 16) ? map : pbuf;      // 16..31 to the pair buffer
 #pragma unroll
-          for (int k2 = 0; k2 < 32; ++k2) map[lane + 16 * k2] = v[k2];
+          for (int k2 = 0; k2 < 32; ++k2) body[(lane & 15) + 16 * k2] = v[k2];
         }
         __syncwarp();
-      } else if (st == 1) {
+      } else if (ss == 1) {
 #pragma unroll
         for (int k = 0; k < 32; ++k) keep[k] = v[k];   // U_r[k1 + 16 k2], r = lane >> 4
       } else {
-        const int r = st - 2;
+        const int r = ss - 2;
         const int lo = r ? G.N_L : G.N_L - ncp, hi = G.N_L + G.N_S;
 #pragma unroll
         for (int k2 = 0; k2 < 32; ++k2) {
           const int tau = lane + 32 * k2;
           float2 a0 = v[k2];
           if (ols && !(tau >= lo && tau < hi)) a0 = czero();
-          atomicAdd(wdst + jb.start + r * 512 + tau, a0);
+          atomicAdd(wdst + start + r * 512 + tau, a0);
         }
       }
     }
@@ -714,14 +745,14 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
   load_plan_w(P, gP);
   if (threadIdx.x == 0) next_item = 0;
   __syncthreads();                                  // the plan copy is complete before any use
-  // stage the tables: twiddles [512 | 1024 | 2048], then every group's weights
-  float2* tabs = wscr + kWarps * kScratch;
-  float* wts = reinterpret_cast<float*>(tabs + kTxTwiddles);
+  // stage the tables: twiddles [512 | 1024 | 2048 (BIG only)], then every group's weights
+  float2* tabs = wscr + kWarps * kTxWarpScratch<BIG>;
+  float* wts = reinterpret_cast<float*>(tabs + kTxTables<BIG>);
   for (int i = 0; i < P.n_sizes; ++i) {
     const int n = P.sz[i].n;
     if (n == 512) stage_lane_twiddles(tabs, P.sz[i].tw, 512, 16);
     if (n == 1024) stage_lane_twiddles(tabs + 512, P.sz[i].tw, 1024, 32);
-    if (n == 2048)
+    if (BIG && n == 2048)                             // the odd-sample rotation of the N = 2048 jobs
       for (int m = threadIdx.x; m < n; m += blockDim.x) tabs[1536 + m] = __ldg(P.sz[i].tw + m);
   }
   {
@@ -734,11 +765,12 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     }
   }
   __syncthreads();
-  const TxTables tt{tabs + 512, tabs, tabs + 1536};
+  const TxTables tt{tabs + 512, tabs, BIG ? tabs + 1536 : nullptr};
   const long long total = (long long)n_jobs * n_streams;
   const int lane = threadIdx.x & 31;
-  float2* scr = wscr + (threadIdx.x >> 5) * kScratch;
+  float2* scr = wscr + (threadIdx.x >> 5) * kTxWarpScratch<BIG>;
   float2* map = scr + kTrans;
+  float2* pbuf = BIG ? nullptr : map + kMap;
   while (true) {
     int u = 0;
     if (lane == 0) u = atomicAdd(&next_item, 1);
@@ -755,23 +787,23 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
       const FcSubDev& Sn = P.s[P.g[jbn.group].first_sub];
       prefetch_l2(grid + (size_t)(nx - (long long)jn * n_streams) * P.grid_len + Sn.grid_off +
                       (long long)jbn.index * Sn.Lact,
-                  Sn.Lact, lane);
+                  (jbn.nblk == 4 ? 2 : 1) * Sn.Lact, lane);
     }
     const FcJob jb = jobs[j];
     const FcGroupDev& G = P.g[jb.group];
     tx_job<BIG>(P, G, P.s[G.first_sub], jb, grid + (size_t)stream * P.grid_len, wave + (size_t)stream * P.frame_len, scr,
-           map, lane, tt, wts + wt_off[jb.group]);
+           map, pbuf, lane, tt, wts + wt_off[jb.group]);
   }
 }
 
 
 }  // namespace
 
-size_t fc_warp_smem_bytes() { return (size_t)kWarps * kScratch * sizeof(float2); }
-
-// the TX kernel's dynamic shared memory: per-warp scratch + staged twiddles + weights
-static size_t tx_smem_bytes(int weight_floats) {
-  return fc_warp_smem_bytes() + (size_t)kTxTwiddles * sizeof(float2) + (((size_t)weight_floats * 4 + 15) & ~(size_t)15);
+// the TX kernels' dynamic shared memory: per-warp scratch + staged twiddles + weights
+static size_t tx_smem_bytes(bool big, int weight_floats) {
+  const int scratch = big ? kTxWarpScratch<true> : kTxWarpScratch<false>;
+  const int twiddles = big ? kTxTables<true> : kTxTables<false>;
+  return ((size_t)kWarps * scratch + twiddles) * sizeof(float2) + (((size_t)weight_floats * 4 + 15) & ~(size_t)15);
 }
 
 template <bool BIG, typename TI>
@@ -793,10 +825,12 @@ static cudaError_t launch_tx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_
 
 template <typename TI>
 static cudaError_t launch_tx_shapes(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,
-                                    size_t smem, const TI* grid, float2* wave, int num_sms, cudaStream_t st) {
-  cudaError_t e = launch_tx_warp<true>(dP, jobs, n_big, n_streams, smem, grid, wave, num_sms, st);
+                                    int weight_floats, const TI* grid, float2* wave, int num_sms, cudaStream_t st) {
+  cudaError_t e = launch_tx_warp<true>(dP, jobs, n_big, n_streams, tx_smem_bytes(true, weight_floats), grid, wave,
+                                       num_sms, st);
   if (e != cudaSuccess) return e;
-  return launch_tx_warp<false>(dP, jobs + n_big, n_jobs - n_big, n_streams, smem, grid, wave, num_sms, st);
+  return launch_tx_warp<false>(dP, jobs + n_big, n_jobs - n_big, n_streams, tx_smem_bytes(false, weight_floats), grid,
+                               wave, num_sms, st);
 }
 
 cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,
@@ -804,9 +838,10 @@ cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n
                                    int num_sms, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(wave, 0, (size_t)n_streams * frame_len * sizeof(float2), st);
   if (e != cudaSuccess) return e;
-  const size_t smem = tx_smem_bytes(weight_floats);
-  return grid_bf16 ? launch_tx_shapes(dP, jobs, n_jobs, n_big, n_streams, smem, (const bf2*)grid, wave, num_sms, st)
-                   : launch_tx_shapes(dP, jobs, n_jobs, n_big, n_streams, smem, (const float2*)grid, wave, num_sms, st);
+  return grid_bf16
+             ? launch_tx_shapes(dP, jobs, n_jobs, n_big, n_streams, weight_floats, (const bf2*)grid, wave, num_sms, st)
+             : launch_tx_shapes(dP, jobs, n_jobs, n_big, n_streams, weight_floats, (const float2*)grid, wave, num_sms,
+                                st);
 }
 
 static size_t rx_smem_bytes(int weight_floats) {
@@ -901,7 +936,8 @@ cudaError_t fc_launch_from_bf16(const void* src, float2* dst, long long n, int n
 
 cudaError_t fc_set_warp_smem_limits() {
   cudaError_t e;
-  const int tx = (int)tx_smem_bytes(FC_MAX_GROUPS * 1024), rx = (int)rx_smem_bytes(FC_MAX_GROUPS * 1024);
+  const int tx = (int)std::max(tx_smem_bytes(true, FC_MAX_GROUPS * 1024), tx_smem_bytes(false, FC_MAX_GROUPS * 1024));
+  const int rx = (int)rx_smem_bytes(FC_MAX_GROUPS * 1024);
   const void* tx_kernels[] = {(const void*)k_tx_sync_warp<true, float2>, (const void*)k_tx_sync_warp<false, float2>,
                               (const void*)k_tx_sync_warp<true, bf2>, (const void*)k_tx_sync_warp<false, bf2>};
   for (const void* k : tx_kernels)
