@@ -168,8 +168,8 @@ struct fc_plan {
   unsigned tc_first_wait = 1u << 22;        // poll limit of the tensor-core kernels' first GEMM wait
   FcJob* d_wjobs = nullptr;                 // one stream's jobs in cost order (warp kernels)
   int n_wjobs_big = 0;                      // the first n_wjobs_big of them belong to N = 2048 groups
-  FcJob* d_wtxjobs = nullptr;               // the TX list: the same, N = 1024 symbols in pairs
-  int n_wtxjobs = 0;
+  FcJob* d_wpjobs = nullptr;                // the same list with the N = 1024 symbols in pairs
+  int n_wpjobs = 0;
   int warp_weight_floats = 0;               // sum over groups of the subband length (warp TX weights)
   size_t smem_tx = 0, smem_rx = 0, smem_ofdm = 0;
   int syms_per_stream = 0;
@@ -492,8 +492,8 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
                      [&](const FcJob& a, const FcJob& b) { return gh[a.group].N > gh[b.group].N; });
     off_wjobs = blob.add_vec(by_cost);
     for (const FcJob& jb : by_cost) n_big += gh[jb.group].N == 2048;
-    // TX: the N = 1024 groups' symbols in pairs (n, n + 1) (nblk = 4), whose OFDM IDFTs
-    // share one two-transform FFT (a group's odd last symbol alone), by time
+    // the N = 1024 groups' symbols in pairs (n, n + 1) (nblk = 4), whose OFDM IDFTs (TX)
+    // or DFTs (RX) share one two-transform FFT (a group's odd last symbol alone), by time
     std::vector<FcJob> tx(by_cost.begin(), by_cost.begin() + n_big);
     std::vector<FcJob> pairs;
     for (int g = 0; g < G; ++g) {
@@ -747,8 +747,8 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   if (warp_ok) {
     pl->d_wjobs = reinterpret_cast<FcJob*>(base + off_wjobs);
     pl->n_wjobs_big = n_big;
-    pl->d_wtxjobs = reinterpret_cast<FcJob*>(base + off_wtx);
-    pl->n_wtxjobs = n_wtx;
+    pl->d_wpjobs = reinterpret_cast<FcJob*>(base + off_wtx);
+    pl->n_wpjobs = n_wtx;
   }
   return FC_OK;
 }
@@ -833,8 +833,8 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* 
     if (acc && ((uintptr_t)acc & 15) == 0) {
       // complex64 input: the N = 1024 symbols in pairs; BF16 input: one symbol a job
       const bool in16 = (io & FC_IO_IN_BF16) != 0;
-      cudaError_t e = fc_launch_tx_sync_warp(plan->d_plan, in16 ? plan->d_wjobs : plan->d_wtxjobs,
-                                             in16 ? plan->n_jobs : plan->n_wtxjobs, plan->n_wjobs_big, n_streams,
+      cudaError_t e = fc_launch_tx_sync_warp(plan->d_plan, in16 ? plan->d_wjobs : plan->d_wpjobs,
+                                             in16 ? plan->n_jobs : plan->n_wpjobs, plan->n_wjobs_big, n_streams,
                                              plan->h.frame_len, plan->warp_weight_floats, in, in16, acc,
                                              plan->num_sms, st);
       if (e == cudaSuccess && out16)
@@ -888,7 +888,7 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* 
       x = workspace;
     }
     if (!(io & FC_IO_IN_BF16) || x != in)
-      return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wjobs, plan->n_jobs, plan->n_wjobs_big, n_streams,
+      return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wpjobs, plan->n_wpjobs, plan->n_wjobs_big, n_streams,
                                     plan->warp_weight_floats, plan->h.scheme_rx, plan->h.flags, x, out,
                                     io & FC_IO_OUT_BF16, plan->num_sms, st);
   }

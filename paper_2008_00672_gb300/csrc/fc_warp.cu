@@ -565,75 +565,90 @@ __device__ __forceinline__ void rx_job_1024(const FcPlanDev& P, const FcGroupDev
 // ---------------------------------------------------------------------------
 // RX, N = 1024, L = 512
 // ---------------------------------------------------------------------------
+// A job is one symbol or a pair of symbols n, n + 1 (jb.nblk == 4): each symbol's two
+// block DFTs, gather and short IDFTs, then the OFDM DFTs of both bodies as one
+// two-transform FFT (a single symbol's second transform has a zero input). The first
+// body waits in registers while the second symbol's blocks run.
 template <typename TI, typename TO>
 __device__ __forceinline__ void rx_job_512(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                            const TI* __restrict__ src, TO* __restrict__ gdst, float2* scr,
                                            float2* map, int lane, const RxStaged& st) {
   constexpr int L = 512;
   const float2* __restrict__ twN = P.sz[G.size_N].tw;
-  const int n = jb.index;
   const bool ola = P.scheme_rx == FC_OLA;
+  const bool pair = jb.nblk == 4;
+  float2 b0[16], v[32];
 #pragma unroll 1
-  for (int r = 0; r < 2; ++r) {                      // one copy of the block DFT in the code
-    const TI* __restrict__ x = src + jb.start + r * (1024 / 2);
-    float2 u[32];
+  for (int s = 0; s < (pair ? 2 : 1); ++s) {
+    const int n = jb.index + s;
+    const int start = G.offset + G.sigma[n];
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {                    // one copy of the block DFT in the code
+      const TI* __restrict__ x = src + start + r * (1024 / 2);
+      float2 u[32];
 #pragma unroll
-    for (int a = 0; a < 32; ++a) {
-      const int t = 32 * a + lane;
-      float2 xv = ld_io(x + t);
-      if (ola && !(t >= G.N_L && t < G.N_L + G.N_S)) xv = czero();
-      u[a] = xv;
-    }
-    warp_fft1024_d<false, true>(u, scr, st.s1024, lane);       // bin k1 + 32 k2
-    const float2 ph = root_pos(twN, 1024, (long long)S.c * (G.cps[n] + r * G.N_S));
+      for (int a = 0; a < 32; ++a) {
+        const int t = 32 * a + lane;
+        float2 xv = ld_io(x + t);
+        if (ola && !(t >= G.N_L && t < G.N_L + G.N_S)) xv = czero();
+        u[a] = xv;
+      }
+      warp_fft1024_d<false, true>(u, scr, st.s1024, lane);     // bin k1 + 32 k2
+      const float2 ph = root_pos(twN, 1024, (long long)S.c * (G.cps[n] + r * G.N_S));
 #pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) {
-      const int q = lane + 32 * k2;
-      int kt = (q - S.c) & 1023;
-      if (kt >= 512) kt -= 1024;
-      if (kt >= -L / 2 && kt < L / 2) {
-        const float wt = weight_staged(S, st.w, kt + L / 2);
-        map[r * L + (kt & (L - 1))] = cscale(cmulc(u[k2], ph), wt);
+      for (int k2 = 0; k2 < 32; ++k2) {
+        const int q = lane + 32 * k2;
+        int kt = (q - S.c) & 1023;
+        if (kt >= 512) kt -= 1024;
+        if (kt >= -L / 2 && kt < L / 2) {
+          const float wt = weight_staged(S, st.w, kt + L / 2);
+          map[r * L + (kt & (L - 1))] = cscale(cmulc(u[k2], ph), wt);
+        }
       }
     }
-  }
-  __syncwarp();
-  float2 v[32];
+    __syncwarp();
 #pragma unroll
-  for (int a = 0; a < 16; ++a) {
-    v[a] = map[32 * a + lane];
-    v[16 + a] = map[L + 32 * a + lane];
-  }
-  __syncwarp();
-  warp_fft512x2_d<true, true>(v, scr, st.s512, lane);         // lane k1 + 16 r: z_r[k1 + 16 k2]
-  {
-    const int r = lane >> 4, k1 = lane & 15;
-#pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) map[r * L + k1 + 16 * k2] = v[k2];
-  }
-  __syncwarp();
-#pragma unroll
-  for (int a = 0; a < 16; ++a) {
-    const int t = 32 * a + lane;
-    float2 val;
-    if (!ola) {
-      val = t < L / 2 ? map[L / 4 + t] : map[L + t - L / 4];
-    } else {
-      val = czero();
-      if (L / 4 + t < L) val = map[L / 4 + t];
-      if (t >= L / 4) val = cadd(val, map[L + t - L / 4]);
+    for (int a = 0; a < 16; ++a) {
+      v[a] = map[32 * a + lane];
+      v[16 + a] = map[L + 32 * a + lane];
     }
-    v[a] = val;
-    v[16 + a] = czero();
+    __syncwarp();
+    warp_fft512x2_d<true, true>(v, scr, st.s512, lane);       // lane k1 + 16 r: z_r[k1 + 16 k2]
+    {
+      const int r = lane >> 4, k1 = lane & 15;
+#pragma unroll
+      for (int k2 = 0; k2 < 32; ++k2) map[r * L + k1 + 16 * k2] = v[k2];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int a = 0; a < 16; ++a) {                   // the body of symbol n: x_T[32 a + lane]
+      const int t = 32 * a + lane;
+      float2 val;
+      if (!ola) {
+        val = t < L / 2 ? map[L / 4 + t] : map[L + t - L / 4];
+      } else {
+        val = czero();
+        if (L / 4 + t < L) val = map[L / 4 + t];
+        if (t >= L / 4) val = cadd(val, map[L + t - L / 4]);
+      }
+      if (s == 0) b0[a] = val;
+      else v[16 + a] = val;
+    }
+    __syncwarp();
   }
-  __syncwarp();
-  warp_fft512x2_d<false, true>(v, scr, st.s512, lane);        // lanes 0..15: X[k1 + 16 k2]
-  if (lane < 16) {
+#pragma unroll
+  for (int a = 0; a < 16; ++a) {
+    v[a] = b0[a];
+    if (!pair) v[16 + a] = czero();
+  }
+  warp_fft512x2_d<false, true>(v, scr, st.s512, lane);        // lane k1 + 16 T: X_T[k1 + 16 k2]
+  const int sym = lane >> 4;
+  if (sym == 0 || pair) {
     const int hl = S.Lact / 2, hu = S.Lact - hl;
-    TO* __restrict__ row = gdst + S.grid_off + (long long)n * S.Lact;
+    TO* __restrict__ row = gdst + S.grid_off + (long long)(jb.index + sym) * S.Lact;
 #pragma unroll
     for (int k2 = 0; k2 < 32; ++k2) {
-      const int bin = lane + 16 * k2;
+      const int bin = (lane & 15) + 16 * k2;
       const int f = bin < L / 2 ? bin : bin - L;
       if (f >= -hl && f < hu) st_io(row + f + hl, v[k2]);
     }
@@ -722,8 +737,9 @@ k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     if (nx < total) {
       const int jn = (int)(nx / n_streams);
       const FcJob jbn = jobs[jn];
-      const int Nn = P.g[jbn.group].N;
-      prefetch_l2(wave + (size_t)(nx - (long long)jn * n_streams) * P.frame_len + jbn.start, Nn + Nn / 2, lane);
+      const FcGroupDev& Gn = P.g[jbn.group];
+      const int span = Gn.N + Gn.N / 2 + (jbn.nblk == 4 ? Gn.sigma[jbn.index + 1] - Gn.sigma[jbn.index] : 0);
+      prefetch_l2(wave + (size_t)(nx - (long long)jn * n_streams) * P.frame_len + jbn.start, span, lane);
     }
     const FcJob jb = jobs[j];
     const RxStaged st{tabs, tabs + 1024, wts + wt_off[jb.group]};
