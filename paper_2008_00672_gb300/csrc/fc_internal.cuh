@@ -24,9 +24,6 @@
 #ifndef FC_WARP_TX_MIN_BLOCKS
 #define FC_WARP_TX_MIN_BLOCKS 2  // resident CTAs per SM the warp TX kernel is compiled for
 #endif
-#ifndef FC_WARP_RX_MIN_BLOCKS
-#define FC_WARP_RX_MIN_BLOCKS 3  // resident CTAs per SM the warp RX kernel is compiled for
-#endif
 #ifndef FC_WARP_CONT_MIN_BLOCKS
 #define FC_WARP_CONT_MIN_BLOCKS 4  // resident CTAs per SM the continuous warp kernels are compiled for
 #endif
