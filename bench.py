@@ -232,6 +232,7 @@ def run_reference(args, rank: int, world: int):
                 times.append(wall)
     finally:
         pool.close()
+        pool.join()           # the workers gone before the next GPU measurement
     value = statistics.median(vals)
     sample = f"{cores} frames (1 per core) of the 1 ms subframe, TX+RX, per step"
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Msamples/s",
@@ -604,6 +605,7 @@ def oracle_leg(name: str, frames_per_core: int, arg=None, what: str = "") -> dic
         v, wall, frames = oracle_throughput(pool, frames_per_core, cores, seed=6000, name=name, arg=arg)
     finally:
         pool.close()
+        pool.join()           # the workers gone before the next GPU measurement
     return {"value": round(v, 4), "unit": "Msamples/s", "cores": cores, "kind": "oracle",
             "sample": f"{frames} {what} ({frames_per_core} per core), TX+RX, {wall:.1f} s wall"}
 
@@ -1061,6 +1063,7 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
             v, wall, frames = oracle_throughput(pool, 12, cores)   # ~10-20 s of host work
         finally:
             pool.close()
+            pool.join()
         cpu = {"value": round(v, 4), "unit": "Msamples/s", "cores": cores, "kind": "oracle",
                "sample": f"{frames} subframes of the 20 MHz workload ({frames // cores} per core, one "
                          f"single-threaded process per core), TX+RX, {wall:.1f} s wall"}
