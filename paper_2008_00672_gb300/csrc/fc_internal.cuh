@@ -166,9 +166,11 @@ size_t fc_tc_dft64_image_bytes();
 // into a complex64 waveform (zeroed here), which fc_launch_to_bf16 rounds into a BF16
 // output; the RX kernel takes a complex64 waveform (fc_launch_from_bf16 widens a BF16
 // one) and writes complex64 or BF16 estimates.
-cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,
-                                   int frame_len, int weight_floats, const void* grid, int grid_bf16, float2* wave,
-                                   int num_sms, cudaStream_t st);
+// TX: jobs [0, n_init) (even symbols of the only N = 2048 group, or none) initialise the
+// waveform in a launch of their own; otherwise the waveform is zeroed first.
+cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_init, int n_big,
+                                   int n_streams, int frame_len, int weight_floats, const void* grid, int grid_bf16,
+                                   float2* wave, int num_sms, cudaStream_t st);
 // Jobs [0, n_big) are the N = 2048 groups' (one kernel), the rest the N = 1024 groups'
 // (a second kernel, launched after the first)
 cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,

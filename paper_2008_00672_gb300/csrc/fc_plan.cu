@@ -166,10 +166,13 @@ struct fc_plan {
   const unsigned char* d_dft64 = nullptr;   // DFT-64 B operand images (hi, lo)
   int* d_err = nullptr;                     // device error word of the tensor-core kernels
   unsigned tc_first_wait = 1u << 22;        // poll limit of the tensor-core kernels' first GEMM wait
-  FcJob* d_wjobs = nullptr;                 // one stream's jobs in cost order (warp kernels)
+  FcJob* d_wjobs = nullptr;                 // one stream's TX jobs in dealing order (warp kernels, BF16 input)
   int n_wjobs_big = 0;                      // the first n_wjobs_big of them belong to N = 2048 groups
+  int n_wjobs_init = 0;                     // of which the first n_wjobs_init initialise the TX waveform
   FcJob* d_wpjobs = nullptr;                // the same list with the N = 1024 symbols in pairs
   int n_wpjobs = 0;
+  FcJob* d_wrxjobs = nullptr;               // the RX list: by time, N = 1024 symbols in pairs
+  int n_wrxjobs = 0;
   int warp_weight_floats = 0;               // sum over groups of the subband length (warp TX weights)
   size_t smem_tx = 0, smem_rx = 0, smem_ofdm = 0;
   int syms_per_stream = 0;
@@ -482,29 +485,48 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   bool cont_warp = !sync && G == 1 && M == 1 && !io_time && !(geo->flags & FC_FLAG_GENERIC_KERNELS) &&
                    sh[0].L == 384 && sh[0].Lo == 384 && gh[0].N == 512 && 2 * gh[0].N_O == gh[0].N &&
                    gh[0].offset == 0;
-  size_t off_wjobs = 0, off_wtx = 0;
-  int n_big = 0, n_wtx = 0;
+  size_t off_wjobs = 0, off_wtx = 0, off_wrx = 0;
+  int n_big = 0, n_wtx = 0, n_init = 0, n_wrx = 0;
   if (warp_ok) {
-    // one stream's jobs, most expensive first (N = 2048 before N = 1024): the warp
-    // kernels deal the job-major list of all streams to their CTAs in this order
-    std::vector<FcJob> by_cost = jobs;
-    std::stable_sort(by_cost.begin(), by_cost.end(),
-                     [&](const FcJob& a, const FcJob& b) { return gh[a.group].N > gh[b.group].N; });
-    off_wjobs = blob.add_vec(by_cost);
-    for (const FcJob& jb : by_cost) n_big += gh[jb.group].N == 2048;
-    // the N = 1024 groups' symbols in pairs (n, n + 1) (nblk = 4), whose OFDM IDFTs (TX)
-    // or DFTs (RX) share one two-transform FFT (a group's odd last symbol alone), by time
-    std::vector<FcJob> tx(by_cost.begin(), by_cost.begin() + n_big);
-    std::vector<FcJob> pairs;
+    // One stream's jobs in the order the warp kernels deal them (the job-major list of
+    // all streams), most expensive first: the N = 2048 groups' symbols, then the N = 1024
+    // groups'. RX takes them by time, the N = 1024 symbols in pairs (n, n + 1) (nblk = 4)
+    // whose OFDM DFTs share one two-transform FFT (a group's odd last symbol alone). TX
+    // takes the same pairs (their OFDM IDFTs; with complex64 input, else single symbols)
+    // and, with one N = 2048 group, that group's even symbols first: their launch
+    // initialises the waveform (stores, and zeros between their disjoint spans) instead
+    // of a memset.
+    int big_groups = 0;
+    for (const GroupHost& o : gh) big_groups += o.N == 2048;
+    std::vector<FcJob> big, init, rest, singles, pairs;
+    for (const FcJob& jb : jobs) {                   // jobs are sorted by time
+      if (gh[jb.group].N != 2048) {
+        singles.push_back(jb);
+        continue;
+      }
+      big.push_back(jb);
+      (big_groups == 1 && jb.index % 2 == 0 ? init : rest).push_back(jb);
+    }
     for (int g = 0; g < G; ++g) {
       const GroupHost& o = gh[g];
       if (o.N == 2048) continue;
       for (int n = 0; n < o.B; n += 2) pairs.push_back(FcJob{g, n, n + 1 < o.B ? 4 : 2, o.offset + o.sigma[n]});
     }
     std::stable_sort(pairs.begin(), pairs.end(), [](const FcJob& a, const FcJob& b) { return a.start < b.start; });
-    tx.insert(tx.end(), pairs.begin(), pairs.end());
-    off_wtx = blob.add_vec(tx);
-    n_wtx = (int)tx.size();
+    n_big = (int)big.size();
+    n_init = (int)init.size();
+    auto cat = [](std::vector<FcJob> a, const std::vector<FcJob>& b, const std::vector<FcJob>& c) {
+      a.insert(a.end(), b.begin(), b.end());
+      a.insert(a.end(), c.begin(), c.end());
+      return a;
+    };
+    const std::vector<FcJob> tx_singles = cat(init, rest, singles), tx_pairs = cat(init, rest, pairs);
+    const std::vector<FcJob> rx = cat(big, {}, pairs);
+    off_wjobs = blob.add_vec(tx_singles);
+    off_wtx = blob.add_vec(tx_pairs);
+    off_wrx = blob.add_vec(rx);
+    n_wtx = (int)tx_pairs.size();
+    n_wrx = (int)rx.size();
   }
 
   // ---- buffers and shared memory -------------------------------------------
@@ -624,14 +646,15 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   pl->io = io_bf16 ? (FC_IO_IN_BF16 | FC_IO_OUT_BF16) : 0;
   z.slot_len = streamable ? slot_len : 0;
   z.stream_delay = streamable ? stream_delay : 0;
-  // the one-warp kernels: one launch per job shape present, + the BF16 rounding / widening pass
+  // the one-warp kernels: one launch per job shape present (TX: the N = 2048 jobs in two
+  // launches where the first initialises the waveform), + the BF16 rounding / widening pass
   int warp_shapes = 0;
   if (warp_ok) {
     bool big = false, small = false;
     for (const GroupHost& o : gh) (o.N == 2048 ? big : small) = true;
     warp_shapes = (int)big + (int)small;
   }
-  z.tx_kernels = sync ? (warp_ok ? warp_shapes + (int)io_bf16 : 1) : (tc_tx ? 3 : 2);
+  z.tx_kernels = sync ? (warp_ok ? warp_shapes + (n_init > 0 && n_init < n_big) + (int)io_bf16 : 1) : (tc_tx ? 3 : 2);
   z.rx_kernels = sync ? (warp_ok ? warp_shapes + (int)io_bf16 : 1) : (tc_rx ? 3 : 2);
   size_t off_dft = 0, off_err = 0;
   if (tc_tx) {
@@ -747,8 +770,11 @@ int build_plan(fc_plan* pl, const fc_geometry* geo, bool upload) {
   if (warp_ok) {
     pl->d_wjobs = reinterpret_cast<FcJob*>(base + off_wjobs);
     pl->n_wjobs_big = n_big;
+    pl->n_wjobs_init = n_init;
     pl->d_wpjobs = reinterpret_cast<FcJob*>(base + off_wtx);
     pl->n_wpjobs = n_wtx;
+    pl->d_wrxjobs = reinterpret_cast<FcJob*>(base + off_wrx);
+    pl->n_wrxjobs = n_wrx;
   }
   return FC_OK;
 }
@@ -834,7 +860,8 @@ cudaError_t launch_tx(const fc_plan* plan, int n_streams, const void* in, void* 
       // complex64 input: the N = 1024 symbols in pairs; BF16 input: one symbol a job
       const bool in16 = (io & FC_IO_IN_BF16) != 0;
       cudaError_t e = fc_launch_tx_sync_warp(plan->d_plan, in16 ? plan->d_wjobs : plan->d_wpjobs,
-                                             in16 ? plan->n_jobs : plan->n_wpjobs, plan->n_wjobs_big, n_streams,
+                                             in16 ? plan->n_jobs : plan->n_wpjobs, plan->n_wjobs_init,
+                                             plan->n_wjobs_big, n_streams,
                                              plan->h.frame_len, plan->warp_weight_floats, in, in16, acc,
                                              plan->num_sms, st);
       if (e == cudaSuccess && out16)
@@ -888,7 +915,7 @@ cudaError_t launch_rx(const fc_plan* plan, int n_streams, const void* in, void* 
       x = workspace;
     }
     if (!(io & FC_IO_IN_BF16) || x != in)
-      return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wpjobs, plan->n_wpjobs, plan->n_wjobs_big, n_streams,
+      return fc_launch_rx_sync_warp(plan->d_plan, plan->d_wrxjobs, plan->n_wrxjobs, plan->n_wjobs_big, n_streams,
                                     plan->warp_weight_floats, plan->h.scheme_rx, plan->h.flags, x, out,
                                     io & FC_IO_OUT_BF16, plan->num_sms, st);
   }

@@ -89,7 +89,13 @@ __device__ __forceinline__ float weight_staged(const FcSubDev& S, const float* d
 //   2/3 symbol s, block r = 0/1: map into the 1024-bin spectrum, IDFT, reduce into the waveform
 //   4-6 stages 1-3 for symbol n + 1 (pairs: the seven stages of an N = 2048 symbol)
 // ---------------------------------------------------------------------------
-template <bool BIG, typename TI>
+// INIT (N = 2048 jobs of even n, one such group in the plan): the job writes its span
+// [sigma_n, sigma_n + 3N/2) with stores instead of reductions (block 1 adds block 0's
+// overlapping half, written by the same lane, before storing) and zeroes the samples up
+// to the next even symbol (or the frame's end; the first one also those before it):
+// this launch then initialises the whole waveform, which needs no memset, and the later
+// launches reduce into it. Even symbols' spans are disjoint (2N + CPs > 3N/2 apart).
+template <bool BIG, bool INIT, typename TI>
 __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                        const TI* __restrict__ gsrc, float2* __restrict__ wdst, float2* scr,
                                        float2* map, float2* pbuf, int lane, const TxTables& tt, const float* wt) {
@@ -248,7 +254,18 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
             if (!(tau + 1 >= lo && tau + 1 < hi)) a1 = czero();
           }
           float2* dst = wdst + start + r * 1024 + tau;
-          if (v4) {
+          if constexpr (INIT) {
+            if (r && tau < 1024) {                      // block 0's second half, this lane's
+              a0 = cadd(a0, dst[0]);
+              a1 = cadd(a1, dst[1]);
+            }
+            if (v4) {
+              *reinterpret_cast<float4*>(dst) = make_float4(a0.x, a0.y, a1.x, a1.y);
+            } else {
+              dst[0] = a0;
+              dst[1] = a1;
+            }
+          } else if (v4) {
             atomicAdd(reinterpret_cast<float4*>(dst), make_float4(a0.x, a0.y, a1.x, a1.y));
           } else {
             atomicAdd(dst, a0);
@@ -281,6 +298,13 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
         }
       }
     }
+  }
+  if constexpr (INIT) {
+    const int n = jb.index;
+    const int end = n + 2 < G.B ? G.offset + G.sigma[n + 2] : P.frame_len;
+    for (int t = start + 3 * G.N / 2 + lane; t < end; t += 32) wdst[t] = czero();
+    if (n == 0)
+      for (int t = lane; t < start; t += 32) wdst[t] = czero();
   }
 }
 
@@ -750,7 +774,7 @@ k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
 // TX: jobs of one stream run on several CTAs and reduce into the same waveform, which
 // is zeroed beforehand. One kernel per job shape (BIG: the N = 2048 groups' jobs), so that
 // each holds one shape's code.
-template <bool BIG, typename TI>
+template <bool BIG, bool INIT, typename TI>
 __global__ void __launch_bounds__(FC_WARP_THREADS, FC_WARP_TX_MIN_BLOCKS)
 k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs, int n_jobs, int n_streams,
                      const TI* __restrict__ grid, float2* __restrict__ wave) {
@@ -807,7 +831,7 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     }
     const FcJob jb = jobs[j];
     const FcGroupDev& G = P.g[jb.group];
-    tx_job<BIG>(P, G, P.s[G.first_sub], jb, grid + (size_t)stream * P.grid_len, wave + (size_t)stream * P.frame_len, scr,
+    tx_job<BIG, INIT>(P, G, P.s[G.first_sub], jb, grid + (size_t)stream * P.grid_len, wave + (size_t)stream * P.frame_len, scr,
            map, pbuf, lane, tt, wts + wt_off[jb.group]);
   }
 }
@@ -822,42 +846,47 @@ static size_t tx_smem_bytes(bool big, int weight_floats) {
   return ((size_t)kWarps * scratch + twiddles) * sizeof(float2) + (((size_t)weight_floats * 4 + 15) & ~(size_t)15);
 }
 
-template <bool BIG, typename TI>
+template <bool BIG, bool INIT, typename TI>
 static cudaError_t launch_tx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, size_t smem,
                                   const TI* grid, float2* wave, int num_sms, cudaStream_t st) {
   if (n_jobs < 1) return cudaSuccess;
   int per_sm = 0;
   cudaError_t e =
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tx_sync_warp<BIG, TI>, FC_WARP_THREADS, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tx_sync_warp<BIG, INIT, TI>, FC_WARP_THREADS, smem);
   if (e != cudaSuccess) return e;
   const long long total = (long long)n_jobs * n_streams;
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  k_tx_sync_warp<BIG, TI><<<dim3((unsigned)ctas), FC_WARP_THREADS, smem, st>>>(dP, jobs, n_jobs, n_streams, grid,
-                                                                              wave);
+  k_tx_sync_warp<BIG, INIT, TI><<<dim3((unsigned)ctas), FC_WARP_THREADS, smem, st>>>(dP, jobs, n_jobs, n_streams,
+                                                                                    grid, wave);
   return cudaGetLastError();
 }
 
 template <typename TI>
-static cudaError_t launch_tx_shapes(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,
-                                    int weight_floats, const TI* grid, float2* wave, int num_sms, cudaStream_t st) {
-  cudaError_t e = launch_tx_warp<true>(dP, jobs, n_big, n_streams, tx_smem_bytes(true, weight_floats), grid, wave,
-                                       num_sms, st);
+static cudaError_t launch_tx_shapes(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_init, int n_big,
+                                    int n_streams, int weight_floats, const TI* grid, float2* wave, int num_sms,
+                                    cudaStream_t st) {
+  const size_t big = tx_smem_bytes(true, weight_floats);
+  cudaError_t e = launch_tx_warp<true, true>(dP, jobs, n_init, n_streams, big, grid, wave, num_sms, st);
   if (e != cudaSuccess) return e;
-  return launch_tx_warp<false>(dP, jobs + n_big, n_jobs - n_big, n_streams, tx_smem_bytes(false, weight_floats), grid,
-                               wave, num_sms, st);
+  e = launch_tx_warp<true, false>(dP, jobs + n_init, n_big - n_init, n_streams, big, grid, wave, num_sms, st);
+  if (e != cudaSuccess) return e;
+  return launch_tx_warp<false, false>(dP, jobs + n_big, n_jobs - n_big, n_streams, tx_smem_bytes(false, weight_floats),
+                                      grid, wave, num_sms, st);
 }
 
-cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,
-                                   int frame_len, int weight_floats, const void* grid, int grid_bf16, float2* wave,
-                                   int num_sms, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(wave, 0, (size_t)n_streams * frame_len * sizeof(float2), st);
-  if (e != cudaSuccess) return e;
-  return grid_bf16
-             ? launch_tx_shapes(dP, jobs, n_jobs, n_big, n_streams, weight_floats, (const bf2*)grid, wave, num_sms, st)
-             : launch_tx_shapes(dP, jobs, n_jobs, n_big, n_streams, weight_floats, (const float2*)grid, wave, num_sms,
-                                st);
+cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_init, int n_big,
+                                   int n_streams, int frame_len, int weight_floats, const void* grid, int grid_bf16,
+                                   float2* wave, int num_sms, cudaStream_t st) {
+  if (n_init == 0) {                                // no initialising launch: zero the waveform
+    cudaError_t e = cudaMemsetAsync(wave, 0, (size_t)n_streams * frame_len * sizeof(float2), st);
+    if (e != cudaSuccess) return e;
+  }
+  return grid_bf16 ? launch_tx_shapes(dP, jobs, n_jobs, n_init, n_big, n_streams, weight_floats, (const bf2*)grid,
+                                      wave, num_sms, st)
+                   : launch_tx_shapes(dP, jobs, n_jobs, n_init, n_big, n_streams, weight_floats, (const float2*)grid,
+                                      wave, num_sms, st);
 }
 
 static size_t rx_smem_bytes(int weight_floats) {
@@ -954,8 +983,10 @@ cudaError_t fc_set_warp_smem_limits() {
   cudaError_t e;
   const int tx = (int)std::max(tx_smem_bytes(true, FC_MAX_GROUPS * 1024), tx_smem_bytes(false, FC_MAX_GROUPS * 1024));
   const int rx = (int)rx_smem_bytes(FC_MAX_GROUPS * 1024);
-  const void* tx_kernels[] = {(const void*)k_tx_sync_warp<true, float2>, (const void*)k_tx_sync_warp<false, float2>,
-                              (const void*)k_tx_sync_warp<true, bf2>, (const void*)k_tx_sync_warp<false, bf2>};
+  const void* tx_kernels[] = {
+      (const void*)k_tx_sync_warp<true, true, float2>, (const void*)k_tx_sync_warp<true, false, float2>,
+      (const void*)k_tx_sync_warp<false, false, float2>, (const void*)k_tx_sync_warp<true, true, bf2>,
+      (const void*)k_tx_sync_warp<true, false, bf2>, (const void*)k_tx_sync_warp<false, false, bf2>};
   for (const void* k : tx_kernels)
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tx))) return e;
   const void* rx_kernels[] = {

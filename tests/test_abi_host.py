@@ -236,9 +236,10 @@ def test_bf16_io_sizes(fc):
         if geom.mode == fo.SYMBOL_SYNC:
             assert a.workspace_per_stream == 0
             assert b.workspace_per_stream == 8 * (b.wave_len + b.wave_len % 2)
-            # one launch per numerology group's job shape (two here), + the BF16 pass
-            assert (a.tx_kernels, a.rx_kernels) == (2, 2)
-            assert (b.tx_kernels, b.rx_kernels) == (3, 3)
+            # one launch per numerology group's job shape (two here; TX: the N = 2048
+            # jobs in two, the even symbols' initialising the waveform), + the BF16 pass
+            assert (a.tx_kernels, a.rx_kernels) == (3, 2)
+            assert (b.tx_kernels, b.rx_kernels) == (4, 3)
         else:
             assert b.workspace_per_stream == a.workspace_per_stream
     g = wl.config_100mhz(2)

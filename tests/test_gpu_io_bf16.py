@@ -161,8 +161,9 @@ def test_bf16_nr20mhz_mixed_numerology(torch_cuda):
     geom = dataclasses.replace(wl.config_mixed_20mhz(), flags=BF16)
     from paper_2008_00672_gb300 import Plan
     p = Plan(geom)
-    # one launch per numerology group's job shape, + the rounding (TX) / widening (RX) pass
-    assert (p.tx_kernels, p.rx_kernels) == (3, 3) and p.workspace_per_stream >= 8 * p.wave_len
+    # one launch per numerology group's job shape (TX: the N = 2048 jobs in two), + the
+    # rounding (TX) / widening (RX) pass
+    assert (p.tx_kernels, p.rx_kernels) == (4, 3) and p.workspace_per_stream >= 8 * p.wave_len
     p.close()
     tx_rx_case(torch_cuda, geom, 2, 24)
 
@@ -322,7 +323,7 @@ def test_bf16_host_pipeline_equals_device_calls(torch_cuda):
     plan.tx_synthesize(h_grid.cuda(), d_wave)
     plan.rx_analyze(d_wave, d_est)
     torch.cuda.synchronize()
-    assert plan.tx_kernels == 3                       # the one-warp TX (two job shapes), rounding pass
+    assert plan.tx_kernels == 4                       # the one-warp TX (three launches), rounding pass
     assert_bf16_match(h_wave, d_wave, "pipeline tx")
     # RX writes every output once: the same bytes (its input is the pipeline's waveform)
     plan.rx_analyze(h_wave.cuda(), d_est)
