@@ -98,7 +98,8 @@ __device__ __forceinline__ float weight_staged(const FcSubDev& S, const float* d
 template <bool BIG, bool INIT, typename TI>
 __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, const FcSubDev& S, const FcJob& jb,
                                        const TI* __restrict__ gsrc, float2* __restrict__ wdst, float2* scr,
-                                       float2* map, float2* pbuf, int lane, const TxTables& tt, const float* wt) {
+                                       float2* map, float2* pbuf, int lane, const TxTables& tt, const float* wt,
+                                       bool& waited) {
   constexpr bool big = BIG;                        // L = 1024 (N = 2048), else L = 512
   // pairs for complex64 input only: with BF16 loads the pair code grew the kernel past
   // what the instruction cache holds (1.49 -> 1.65 ms at 2048 streams)
@@ -245,6 +246,10 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
       } else {                                          // T7: OLS window, R_N^{(r)}, Gamma_sigma
         const int r = (st == 6);
         const int lo = r ? G.N_L : G.N_L - ncp, hi = G.N_L + G.N_S;
+        if (!waited) {                                  // the previous launch's waveform writes
+          pdl_wait();
+          waited = true;
+        }
 #pragma unroll
         for (int k2 = 0; k2 < 32; ++k2) {
           const int tau = 2 * (lane + 32 * k2);
@@ -289,6 +294,10 @@ __device__ __forceinline__ void tx_job(const FcPlanDev& P, const FcGroupDev& G, 
       } else {
         const int r = ss - 2;
         const int lo = r ? G.N_L : G.N_L - ncp, hi = G.N_L + G.N_S;
+        if (!waited) {
+          pdl_wait();
+          waited = true;
+        }
 #pragma unroll
         for (int k2 = 0; k2 < 32; ++k2) {
           const int tau = lane + 32 * k2;
@@ -723,6 +732,7 @@ k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
   __shared__ int next_item;
   __shared__ int wt_off[FC_MAX_GROUPS];
   extern __shared__ __align__(16) float2 wscr[];
+  pdl_trigger();
   load_plan_w(P, gP);
   if (threadIdx.x == 0) next_item = 0;
   __syncthreads();                                  // the plan copy is complete before any use
@@ -769,6 +779,7 @@ k_rx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     const RxStaged st{tabs, tabs + 1024, wts + wt_off[jb.group]};
     rx_run<SHAPE>(P, jb, wave + (size_t)stream * P.frame_len, grid + (size_t)stream * P.grid_len, scr, map, lane, st);
   }
+  pdl_wait();               // a dependent launch completes after the launch before it
 }
 
 // TX: jobs of one stream run on several CTAs and reduce into the same waveform, which
@@ -782,6 +793,7 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
   __shared__ int next_item;
   __shared__ int wt_off[FC_MAX_GROUPS];
   extern __shared__ __align__(16) float2 wscr[];
+  pdl_trigger();
   load_plan_w(P, gP);
   if (threadIdx.x == 0) next_item = 0;
   __syncthreads();                                  // the plan copy is complete before any use
@@ -811,6 +823,7 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
   float2* scr = wscr + (threadIdx.x >> 5) * kTxWarpScratch<BIG>;
   float2* map = scr + kTrans;
   float2* pbuf = BIG ? nullptr : map + kMap;
+  bool waited = false;
   while (true) {
     int u = 0;
     if (lane == 0) u = atomicAdd(&next_item, 1);
@@ -832,7 +845,7 @@ k_tx_sync_warp(const FcPlanDev* __restrict__ gP, const FcJob* __restrict__ jobs,
     const FcJob jb = jobs[j];
     const FcGroupDev& G = P.g[jb.group];
     tx_job<BIG, INIT>(P, G, P.s[G.first_sub], jb, grid + (size_t)stream * P.grid_len, wave + (size_t)stream * P.frame_len, scr,
-           map, pbuf, lane, tt, wts + wt_off[jb.group]);
+           map, pbuf, lane, tt, wts + wt_off[jb.group], waited);
   }
 }
 
@@ -846,9 +859,28 @@ static size_t tx_smem_bytes(bool big, int weight_floats) {
   return ((size_t)kWarps * scratch + twiddles) * sizeof(float2) + (((size_t)weight_floats * 4 + 15) & ~(size_t)15);
 }
 
+// A launch, as a programmatic dependent of the stream's previous kernel when pdl is set
+// (the kernels trigger their dependents at their start and wait for their
+// prerequisites where they need them).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(void (*kern)(KArgs...), unsigned ctas, unsigned threads, size_t smem, cudaStream_t st,
+                            bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <bool BIG, bool INIT, typename TI>
 static cudaError_t launch_tx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, size_t smem,
-                                  const TI* grid, float2* wave, int num_sms, cudaStream_t st) {
+                                  const TI* grid, float2* wave, int num_sms, cudaStream_t st, bool& pdl) {
   if (n_jobs < 1) return cudaSuccess;
   int per_sm = 0;
   cudaError_t e =
@@ -858,9 +890,10 @@ static cudaError_t launch_tx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  k_tx_sync_warp<BIG, INIT, TI><<<dim3((unsigned)ctas), FC_WARP_THREADS, smem, st>>>(dP, jobs, n_jobs, n_streams,
-                                                                                    grid, wave);
-  return cudaGetLastError();
+  e = launch_k(k_tx_sync_warp<BIG, INIT, TI>, (unsigned)ctas, FC_WARP_THREADS, smem, st, pdl, dP, jobs, n_jobs,
+               n_streams, grid, wave);
+  pdl = true;                                        // the call's next launch may overlap this one's tail
+  return e;
 }
 
 template <typename TI>
@@ -868,12 +901,13 @@ static cudaError_t launch_tx_shapes(const FcPlanDev* dP, const FcJob* jobs, int 
                                     int n_streams, int weight_floats, const TI* grid, float2* wave, int num_sms,
                                     cudaStream_t st) {
   const size_t big = tx_smem_bytes(true, weight_floats);
-  cudaError_t e = launch_tx_warp<true, true>(dP, jobs, n_init, n_streams, big, grid, wave, num_sms, st);
+  bool pdl = false;                                  // the first launch follows the stream's earlier work
+  cudaError_t e = launch_tx_warp<true, true>(dP, jobs, n_init, n_streams, big, grid, wave, num_sms, st, pdl);
   if (e != cudaSuccess) return e;
-  e = launch_tx_warp<true, false>(dP, jobs + n_init, n_big - n_init, n_streams, big, grid, wave, num_sms, st);
+  e = launch_tx_warp<true, false>(dP, jobs + n_init, n_big - n_init, n_streams, big, grid, wave, num_sms, st, pdl);
   if (e != cudaSuccess) return e;
   return launch_tx_warp<false, false>(dP, jobs + n_big, n_jobs - n_big, n_streams, tx_smem_bytes(false, weight_floats),
-                                      grid, wave, num_sms, st);
+                                      grid, wave, num_sms, st, pdl);
 }
 
 cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_init, int n_big,
@@ -896,7 +930,7 @@ static size_t rx_smem_bytes(int weight_floats) {
 
 template <int SHAPE, typename TI, typename TO>
 static cudaError_t launch_rx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, size_t smem,
-                                  const void* wave, void* grid, int num_sms, cudaStream_t st) {
+                                  const void* wave, void* grid, int num_sms, cudaStream_t st, bool& pdl) {
   if (n_jobs < 1) return cudaSuccess;
   int per_sm = 0;
   cudaError_t e =
@@ -906,9 +940,10 @@ static cudaError_t launch_rx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  k_rx_sync_warp<SHAPE, TI, TO><<<dim3((unsigned)ctas), kRxThreads, smem, st>>>(dP, jobs, n_jobs, n_streams,
-                                                                               (const TI*)wave, (TO*)grid);
-  return cudaGetLastError();
+  e = launch_k(k_rx_sync_warp<SHAPE, TI, TO>, (unsigned)ctas, kRxThreads, smem, st, pdl, dP, jobs, n_jobs, n_streams,
+               (const TI*)wave, (TO*)grid);
+  pdl = true;
+  return e;
 }
 
 template <typename TO>
@@ -916,21 +951,22 @@ static cudaError_t launch_rx_shapes(const FcPlanDev* dP, const FcJob* jobs, int 
                                     size_t smem, const void* wave, void* grid, int big_shape, int num_sms,
                                     cudaStream_t st) {
   cudaError_t e = cudaSuccess;
+  bool pdl = false;                                  // the first launch follows the stream's earlier work
   if (big_shape == kRx1024Ola) {
-    e = launch_rx_warp<kRx1024Ola, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st);
+    e = launch_rx_warp<kRx1024Ola, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st, pdl);
   } else {
     bool done = false;
     if constexpr (std::is_same<TO, float2>::value) {
       if (big_shape == kRx1024Reduced) {
-        e = launch_rx_warp<kRx1024Reduced, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st);
+        e = launch_rx_warp<kRx1024Reduced, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st, pdl);
         done = true;
       }
     }
-    if (!done) e = launch_rx_warp<kRx1024Ols, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st);
+    if (!done) e = launch_rx_warp<kRx1024Ols, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st, pdl);
   }
   if (e != cudaSuccess) return e;
   return launch_rx_warp<kRx512, float2, TO>(dP, jobs + n_big, n_jobs - n_big, n_streams, smem, wave, grid, num_sms,
-                                            st);
+                                            st, pdl);
 }
 
 cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,

@@ -37,6 +37,13 @@ __device__ __forceinline__ float2 root_pos(const float2* __restrict__ tw, int n,
   return make_float2(w.x, -w.y);
 }
 
+// Programmatic dependent launch: a kernel lets the next launch of its stream start its
+// CTAs once all of its own CTAs are running (they are sized to be resident together);
+// the next one waits for this grid's completion and memory before it touches what this
+// grid writes. Without a dependent launch both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Compiler-only fence: keeps the scheduler from hoisting every load of a stage
 // ahead of its first use (which would need twice the registers of the data).
 __device__ __forceinline__ void sched_fence() { asm volatile("" ::: "memory"); }
