@@ -859,25 +859,6 @@ static size_t tx_smem_bytes(bool big, int weight_floats) {
   return ((size_t)kWarps * scratch + twiddles) * sizeof(float2) + (((size_t)weight_floats * 4 + 15) & ~(size_t)15);
 }
 
-// A launch, as a programmatic dependent of the stream's previous kernel when pdl is set
-// (the kernels trigger their dependents at their start and wait for their
-// prerequisites where they need them).
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_k(void (*kern)(KArgs...), unsigned ctas, unsigned threads, size_t smem, cudaStream_t st,
-                            bool pdl, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(ctas);
-  cfg.blockDim = dim3(threads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kern, args...);
-}
-
 template <bool BIG, bool INIT, typename TI>
 static cudaError_t launch_tx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_streams, size_t smem,
                                   const TI* grid, float2* wave, int num_sms, cudaStream_t st, bool& pdl) {
@@ -890,7 +871,7 @@ static cudaError_t launch_tx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  e = launch_k(k_tx_sync_warp<BIG, INIT, TI>, (unsigned)ctas, FC_WARP_THREADS, smem, st, pdl, dP, jobs, n_jobs,
+  e = fcwarp::launch_k(k_tx_sync_warp<BIG, INIT, TI>, (unsigned)ctas, FC_WARP_THREADS, smem, st, pdl, dP, jobs, n_jobs,
                n_streams, grid, wave);
   pdl = true;                                        // the call's next launch may overlap this one's tail
   return e;
@@ -940,7 +921,7 @@ static cudaError_t launch_rx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  e = launch_k(k_rx_sync_warp<SHAPE, TI, TO>, (unsigned)ctas, kRxThreads, smem, st, pdl, dP, jobs, n_jobs, n_streams,
+  e = fcwarp::launch_k(k_rx_sync_warp<SHAPE, TI, TO>, (unsigned)ctas, kRxThreads, smem, st, pdl, dP, jobs, n_jobs, n_streams,
                (const TI*)wave, (TO*)grid);
   pdl = true;
   return e;

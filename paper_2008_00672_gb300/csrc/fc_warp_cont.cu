@@ -181,6 +181,7 @@ k_ofdm_mod_w384(const FcPlanDev* __restrict__ gP, int n_streams, const TI* __res
                 float2* __restrict__ ws) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) float2 wscr[];
+  pdl_trigger();                                    // the block kernel may stage its tables meanwhile
   load_plan_w(P, gP);
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -240,6 +241,7 @@ k_tx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2* __
   const FcSubDev& S = P.s[0];
   const int R = G.R, pairs = (R + 1) / 2;
   const ContTables T = stage_cont_tables(P, wscr + kWarps * kTrans, S.dtx);
+  pdl_wait();                                       // the low-rate stream of the OFDM kernel
   const long long total = (long long)n_streams * pairs;
   for (long long item = WarpItems().first; item < total; item += WarpItems().step) {
     const int stream = (int)(item / pairs), r0 = 2 * (int)(item - (long long)stream * pairs);
@@ -315,6 +317,7 @@ k_rx_cont_w384(const FcPlanDev* __restrict__ gP, int n_streams, const TI* __rest
                float2* __restrict__ ws) {
   __shared__ FcPlanDev P;
   extern __shared__ __align__(16) float2 wscr[];
+  pdl_trigger();                                    // the OFDM kernel may start meanwhile
   load_plan_w(P, gP);
   __syncthreads();
   const int lane = threadIdx.x & 31;
@@ -391,6 +394,7 @@ k_ofdm_demod_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2*
   extern __shared__ __align__(16) float2 wscr[];
   load_plan_w(P, gP);
   __syncthreads();
+  pdl_wait();                                       // the low-rate stream of the block kernel
   const int lane = threadIdx.x & 31;
   float2* scr = wscr + (threadIdx.x >> 5) * kTrans;
   const FcSubDev& S = P.s[0];
@@ -426,9 +430,11 @@ k_ofdm_demod_w384(const FcPlanDev* __restrict__ gP, int n_streams, const float2*
   }
 }
 
+// pdl: a programmatic dependent of the call's first kernel (which triggers at its start;
+// the dependent waits before it reads the workspace)
 template <class K, class TI, class TO>
 cudaError_t launch_w(K kern, long long items, int num_sms, cudaStream_t st, const FcPlanDev* dP, int n_streams,
-                     const TI* in, TO* out, size_t tables = 0) {
+                     const TI* in, TO* out, size_t tables = 0, bool pdl = false) {
   const size_t smem = (size_t)kWarps * kTrans * sizeof(float2) + tables;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FC_WARP_THREADS, smem);
@@ -437,8 +443,7 @@ cudaError_t launch_w(K kern, long long items, int num_sms, cudaStream_t st, cons
   const long long need = (items + kWarps - 1) / kWarps;
   if (ctas > need) ctas = need;
   if (ctas < 1) return cudaSuccess;
-  kern<<<dim3((unsigned)ctas), FC_WARP_THREADS, smem, st>>>(dP, n_streams, in, out);
-  return cudaGetLastError();
+  return fcwarp::launch_k(kern, (unsigned)ctas, FC_WARP_THREADS, smem, st, pdl, dP, n_streams, in, out);
 }
 
 }  // namespace
@@ -453,9 +458,9 @@ cudaError_t fc_launch_tx_cont_warp(const FcPlanDev* dP, int n_streams, int n_sym
   if (e != cudaSuccess) return e;
   return (io & FC_IO_OUT_BF16)
              ? launch_w(k_tx_cont_w384<bf2>, blks, num_sms, st, dP, n_streams, (const float2*)ws, (bf2*)wave,
-                        kContTableBytes)
+                        kContTableBytes, true)
              : launch_w(k_tx_cont_w384<float2>, blks, num_sms, st, dP, n_streams, (const float2*)ws, (float2*)wave,
-                        kContTableBytes);
+                        kContTableBytes, true);
 }
 
 cudaError_t fc_launch_rx_cont_warp(const FcPlanDev* dP, int n_streams, int n_symbols, int n_blocks, const void* wave,
@@ -468,6 +473,8 @@ cudaError_t fc_launch_rx_cont_warp(const FcPlanDev* dP, int n_streams, int n_sym
                                  kContTableBytes);
   if (e != cudaSuccess) return e;
   return (io & FC_IO_OUT_BF16)
-             ? launch_w(k_ofdm_demod_w384<bf2>, syms, num_sms, st, dP, n_streams, (const float2*)ws, (bf2*)grid)
-             : launch_w(k_ofdm_demod_w384<float2>, syms, num_sms, st, dP, n_streams, (const float2*)ws, (float2*)grid);
+             ? launch_w(k_ofdm_demod_w384<bf2>, syms, num_sms, st, dP, n_streams, (const float2*)ws, (bf2*)grid, 0,
+                        true)
+             : launch_w(k_ofdm_demod_w384<float2>, syms, num_sms, st, dP, n_streams, (const float2*)ws, (float2*)grid, 0,
+                        true);
 }

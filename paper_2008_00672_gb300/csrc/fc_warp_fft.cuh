@@ -44,6 +44,25 @@ __device__ __forceinline__ float2 root_pos(const float2* __restrict__ tw, int n,
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// A launch, as a programmatic dependent of the stream's previous kernel when pdl is set
+// (the kernels trigger their dependents at their start and wait for their
+// prerequisites where they need them).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), unsigned ctas, unsigned threads, size_t smem, cudaStream_t st,
+                            bool pdl, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Compiler-only fence: keeps the scheduler from hoisting every load of a stage
 // ahead of its first use (which would need twice the registers of the data).
 __device__ __forceinline__ void sched_fence() { asm volatile("" ::: "memory"); }

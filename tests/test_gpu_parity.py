@@ -224,6 +224,20 @@ def test_warp_path_two_groups_odd_offsets(torch_cuda, flags):
     check_geometry(torch_cuda, geom, 2, 37)
 
 
+@pytest.mark.parametrize("N,L,cps", [(2048, 1024, ((160, 144, 144, 144), (150, 144, 144, 154))),
+                                      (1024, 512, ((72, 72, 88), (80, 72, 80)))])
+def test_warp_path_two_groups_same_numerology(torch_cuda, N, L, cps):
+    """Two groups of one numerology (one subband each, both halves of the band): with two
+    N = 2048 groups no launch initialises the waveform (a memset zeroes it); with two
+    N = 1024 groups both groups' symbol pairs share one launch."""
+    act = 12 * (L // 48)
+    ga, gb = wl.Group(N, N // 2, cps[0]), wl.Group(N, N // 2, cps[1])
+    sa = wl.Subband(L, L, act, -N // 4, 0, wl.rc_transition_weights(L, act, 8))
+    sb = wl.Subband(L, L, act, N // 4 + 1, 1, wl.rc_transition_weights(L, act, 8))
+    geom = wl.Geometry(fo.SYMBOL_SYNC, fo.OLA, fo.OLS, (ga, gb), (sa, sb))
+    check_geometry(torch_cuda, geom, 2, 43)
+
+
 def test_nr100mhz_two_slots(torch_cuda):
     check_geometry(torch_cuda, wl.config_100mhz(2), 1, wl.default_seed(3))
 
