@@ -89,6 +89,42 @@ def test_batch_uneven_carriers_match_oracle(torch_cuda, use_graph, persistent):
         c["plan"].close()
 
 
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_warp_carriers_match_oracle(torch_cuda, use_graph):
+    """One-warp carriers in a batch, captured into a CUDA graph (their calls are chains of
+    programmatic dependent launches: the symbol-sync TX initialising launch, the
+    per-shape launches, the continuous kernels' second launch) or run on lanes."""
+    torch = torch_cuda
+    from paper_2008_00672_gb300 import FC_RX, FC_TX, Batch
+    carriers = [wl.config_mixed_20mhz(), wl.config_single_5mhz(), wl.config_mixed_20mhz()]
+    S = 2
+    cs = setup(torch, carriers, S, 700)
+    for j, c in enumerate(cs):
+        ref = [fo.tx_frame(c["geom"], c["grid_np"][s]) for s in range(S)]
+        c["ref_tx"] = ref
+        x = np.stack([c64(wl.awgn(ref[s], 30.0, 91 + 13 * j + s)).astype(np.complex128) for s in range(S)])
+        c["rx_np"] = x
+        c["rx_in"] = torch.from_numpy(c64(x)).cuda()
+    items = [(c["plan"], FC_TX, c["grid"], c["wave"]) for c in cs] + \
+            [(c["plan"], FC_RX, c["rx_in"], c["est"]) for c in cs]
+    b = Batch(items, n_lanes=3, use_graph=use_graph)
+    for _ in range(2):                       # the second launch replays the graph
+        for c in cs:
+            c["wave"].fill_(1.0)             # the TX calls initialise their waveforms themselves
+            c["est"].zero_()
+        b.launch()
+        torch.cuda.synchronize()
+        for c in cs:
+            w, e = c["wave"].cpu().numpy(), c["est"].cpu().numpy()
+            ww, gw = parity.wave_windows(c["geom"]), parity.grid_windows(c["geom"])
+            for s in range(S):
+                parity.check(w[s], c["ref_tx"][s], TOL, ww, (c["geom"].name, "tx", s))
+                parity.check(e[s], fo.rx_frame(c["geom"], c["rx_np"][s]), TOL, gw, (c["geom"].name, "rx", s))
+    b.close()
+    for c in cs:
+        c["plan"].close()
+
+
 def test_batch_equals_single_calls(torch_cuda):
     torch = torch_cuda
     from paper_2008_00672_gb300 import FC_TX, Batch

@@ -192,6 +192,7 @@ WARP_CASES = [
     (1024, 512, 288, 159, (88, 72, 72, 72), fo.OLA, fo.OLS),
     (1024, 512, 500, -400, (0, 256, 30, 72, 72), fo.OLS, fo.OLS),   # two TX pairs and a single
     (1024, 512, 400, 3, (40,), fo.OLA, fo.OLA),                       # one symbol: no TX pair
+    (2048, 1024, 500, 100, (144,), fo.OLS, fo.OLS),                   # one symbol: only the initialising TX launch
 ]
 
 
