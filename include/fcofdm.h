@@ -50,7 +50,7 @@ extern "C" {
 /* status codes */
 #define FC_OK 0
 #define FC_ERR_INVALID 1      /* geometry or argument violates a documented constraint */
-#define FC_ERR_UNSUPPORTED 2  /* valid for the paper, but a size this build has no kernel for */
+#define FC_ERR_UNSUPPORTED 2  /* valid for the paper, but a size the library has no kernel for */
 #define FC_ERR_NOMEM 3        /* device allocation failed (plan creation only) */
 #define FC_ERR_CUDA 4         /* a CUDA runtime call or kernel launch failed */
 #define FC_ERR_TIMEOUT 5      /* a bounded device-side wait gave up */
@@ -142,7 +142,7 @@ typedef struct fc_geometry {
 
 #define FC_MAX_GROUPS 4
 #define FC_MAX_SUBBANDS 16
-#define FC_MAX_TRANSFORM 4096  /* largest N, L_m or L_OFDM,m this build has kernels for */
+#define FC_MAX_TRANSFORM 4096  /* largest N, L_m or L_OFDM,m the library has kernels for */
 
 typedef struct fc_sizes {
   int64_t grid_len;        /* complex QAM symbols per stream                           */

@@ -1271,7 +1271,7 @@ const char* fc_status_string(int status) {
   switch (status) {
     case FC_OK: return "FC_OK";
     case FC_ERR_INVALID: return "FC_ERR_INVALID: invalid geometry or argument";
-    case FC_ERR_UNSUPPORTED: return "FC_ERR_UNSUPPORTED: size or layout this build has no kernel for";
+    case FC_ERR_UNSUPPORTED: return "FC_ERR_UNSUPPORTED: size or layout the library has no kernel for";
     case FC_ERR_NOMEM: return "FC_ERR_NOMEM: device allocation failed";
     case FC_ERR_CUDA: return "FC_ERR_CUDA: CUDA runtime error";
     case FC_ERR_TIMEOUT: return "FC_ERR_TIMEOUT: bounded device wait expired";
