@@ -871,8 +871,8 @@ static cudaError_t launch_tx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  e = fcwarp::launch_k(k_tx_sync_warp<BIG, INIT, TI>, (unsigned)ctas, FC_WARP_THREADS, smem, st, pdl, dP, jobs, n_jobs,
-               n_streams, grid, wave);
+  e = fcwarp::launch_k(k_tx_sync_warp<BIG, INIT, TI>, (unsigned)ctas, FC_WARP_THREADS, smem, st, pdl, dP, jobs,
+                       n_jobs, n_streams, grid, wave);
   pdl = true;                                        // the call's next launch may overlap this one's tail
   return e;
 }
@@ -921,8 +921,8 @@ static cudaError_t launch_rx_warp(const FcPlanDev* dP, const FcJob* jobs, int n_
   long long ctas = (long long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (ctas > total) ctas = total;
   if (ctas < 1) return cudaSuccess;
-  e = fcwarp::launch_k(k_rx_sync_warp<SHAPE, TI, TO>, (unsigned)ctas, kRxThreads, smem, st, pdl, dP, jobs, n_jobs, n_streams,
-               (const TI*)wave, (TO*)grid);
+  e = fcwarp::launch_k(k_rx_sync_warp<SHAPE, TI, TO>, (unsigned)ctas, kRxThreads, smem, st, pdl, dP, jobs, n_jobs,
+                       n_streams, (const TI*)wave, (TO*)grid);
   pdl = true;
   return e;
 }
@@ -939,11 +939,13 @@ static cudaError_t launch_rx_shapes(const FcPlanDev* dP, const FcJob* jobs, int 
     bool done = false;
     if constexpr (std::is_same<TO, float2>::value) {
       if (big_shape == kRx1024Reduced) {
-        e = launch_rx_warp<kRx1024Reduced, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st, pdl);
+        e = launch_rx_warp<kRx1024Reduced, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st,
+                                                       pdl);
         done = true;
       }
     }
-    if (!done) e = launch_rx_warp<kRx1024Ols, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st, pdl);
+    if (!done)
+      e = launch_rx_warp<kRx1024Ols, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st, pdl);
   }
   if (e != cudaSuccess) return e;
   return launch_rx_warp<kRx512, float2, TO>(dP, jobs + n_big, n_jobs - n_big, n_streams, smem, wave, grid, num_sms,
