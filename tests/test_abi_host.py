@@ -250,6 +250,36 @@ def test_bf16_io_sizes(fc):
     assert it.sample_bytes == 4 and it.tx_in_len == it.time_tx_len
 
 
+def test_warp_launch_counts(fc):
+    """Symbol-sync plans of the one-warp kernels launch one kernel per numerology job shape
+    and direction; TX adds one where the plan's only N = 2048 group's even symbols
+    initialise the waveform (two N = 2048 groups: a memset instead); complex-BF16 I/O
+    adds its rounding / widening pass. Plans outside the one-warp shapes: one launch."""
+    import dataclasses
+
+    def sync(groups, subs):
+        return wl.Geometry(fo.SYMBOL_SYNC, fo.OLA, fo.OLS, tuple(groups), tuple(subs))
+
+    A = lambda cps: wl.Group(2048, 1024, cps)                      # noqa: E731
+    B = lambda cps: wl.Group(1024, 512, cps)                       # noqa: E731
+    sa = lambda c, g: wl.Subband(1024, 1024, 480, c, g, wl.rc_transition_weights(1024, 480, 8))   # noqa: E731
+    sb = lambda c, g: wl.Subband(512, 512, 240, c, g, wl.rc_transition_weights(512, 240, 8))      # noqa: E731
+    cases = [
+        (sync([A((144, 144, 144))], [sa(0, 0)]), (2, 1)),          # init + odd symbols
+        (sync([A((144,))], [sa(0, 0)]), (1, 1)),                   # one symbol: the init launch alone
+        (sync([B((72, 72, 72))], [sb(0, 0)]), (1, 1)),             # memset + pairs
+        (sync([A((160, 144, 144, 144)), A((150, 144, 144, 154))], [sa(-512, 0), sa(513, 1)]), (1, 1)),
+        (wl.config_mixed_20mhz(), (3, 2)),
+    ]
+    for geom, (tx, rx) in cases:
+        z = fc.fc_geometry_check(geom)
+        assert (z.tx_kernels, z.rx_kernels) == (tx, rx), (geom.name, z.tx_kernels, z.rx_kernels)
+        b = fc.fc_geometry_check(dataclasses.replace(geom, flags=16))
+        assert (b.tx_kernels, b.rx_kernels) == (tx + 1, rx + 1)
+    g = fc.fc_geometry_check(dataclasses.replace(wl.config_mixed_20mhz(), flags=1))   # generic kernels
+    assert (g.tx_kernels, g.rx_kernels) == (1, 1)
+
+
 def test_no_gpu_fails_loudly(fc):
     """There is no CPU path: without a usable GPU, creating a plan or a server returns
     FC_ERR_CUDA (and the binding raises) instead of computing anything on the host."""
