@@ -172,7 +172,7 @@ cudaError_t fc_launch_tx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n
                                    int n_streams, int frame_len, int weight_floats, const void* grid, int grid_bf16,
                                    float2* wave, int num_sms, cudaStream_t st);
 // Jobs [0, n_big) are the N = 2048 groups' (one kernel), the rest the N = 1024 groups'
-// (a second kernel, launched after the first)
+// (a second kernel: TX launches it after the first, RX before)
 cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,
                                    int weight_floats, int scheme_rx, int flags, const void* wave, void* grid, int io,
                                    int num_sms, cudaStream_t st);

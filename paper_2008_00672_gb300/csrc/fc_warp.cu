@@ -19,7 +19,7 @@
 // transforms as conj(FFT(conj(x)))), so the TX kernel holds a single copy of the
 // unrolled FFT; RX jobs keep direction-specialised transforms in rolled loops (one copy
 // of each per job shape). Each direction launches one kernel per job shape (the
-// N = 2048 groups' jobs, then the N = 1024 groups'), with the job inlined: a kernel then
+// N = 2048 groups' jobs and the N = 1024 groups'), with the job inlined: a kernel then
 // holds one shape's code, which the instruction cache keeps, and no calls (TX 1.395 ->
 // 1.347 ms, RX 1.202 -> 1.066 ms at 2048 streams against one kernel for both shapes).
 // Each launch takes the job-major list of its jobs over all streams, dealt to as many
@@ -933,6 +933,11 @@ static cudaError_t launch_rx_shapes(const FcPlanDev* dP, const FcJob* jobs, int 
                                     cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   bool pdl = false;                                  // the first launch follows the stream's earlier work
+  // the N = 1024 jobs first: measured 1 % faster than the other order (the N = 2048
+  // kernel's longer jobs then start under the first kernel's tail)
+  e = launch_rx_warp<kRx512, float2, TO>(dP, jobs + n_big, n_jobs - n_big, n_streams, smem, wave, grid, num_sms, st,
+                                         pdl);
+  if (e != cudaSuccess) return e;
   if (big_shape == kRx1024Ola) {
     e = launch_rx_warp<kRx1024Ola, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st, pdl);
   } else {
@@ -947,9 +952,7 @@ static cudaError_t launch_rx_shapes(const FcPlanDev* dP, const FcJob* jobs, int 
     if (!done)
       e = launch_rx_warp<kRx1024Ols, float2, TO>(dP, jobs, n_big, n_streams, smem, wave, grid, num_sms, st, pdl);
   }
-  if (e != cudaSuccess) return e;
-  return launch_rx_warp<kRx512, float2, TO>(dP, jobs + n_big, n_jobs - n_big, n_streams, smem, wave, grid, num_sms,
-                                            st, pdl);
+  return e;
 }
 
 cudaError_t fc_launch_rx_sync_warp(const FcPlanDev* dP, const FcJob* jobs, int n_jobs, int n_big, int n_streams,
