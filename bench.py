@@ -999,9 +999,11 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
     uneven = uneven_carriers_bench(torch, dev, st, args.steps)
     n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = float(load_peaks()[0].get("sm_max_mhz", 2070.0))
+    # the side sections' oracle legs run after every GPU measurement: the oracle workers'
+    # memory traffic on the host slowed later pinned-buffer copies
     side_cpu = world == 1 and not args.no_cpu_baseline
-    nr100 = nr100_paths_bench(torch, dev, st, load_peaks()[0], n_sms, sm_mhz, cpu_leg=side_cpu)
-    nr5 = nr5mhz_bench(torch, dev, st, load_peaks()[0], n_sms, sm_mhz, cpu_leg=side_cpu)
+    nr100 = nr100_paths_bench(torch, dev, st, load_peaks()[0], n_sms, sm_mhz, cpu_leg=False)
+    nr5 = nr5mhz_bench(torch, dev, st, load_peaks()[0], n_sms, sm_mhz, cpu_leg=False)
     bf16_io = bf16_io_bench(torch, dev, st)
     serving = serving_bench(torch, dev, args.serve_requests) if args.serve_requests > 0 else None
 
@@ -1067,6 +1069,9 @@ def run_gpu(args, rank: int, world: int, local_rank: int):
         cpu = {"value": round(v, 4), "unit": "Msamples/s", "cores": cores, "kind": "oracle",
                "sample": f"{frames} subframes of the 20 MHz workload ({frames // cores} per core, one "
                          f"single-threaded process per core), TX+RX, {wall:.1f} s wall"}
+    if side_cpu:
+        nr100["cpu_baseline"] = oracle_leg("nr100", 1, arg=1, what="one-slot frames of the 100 MHz carrier")
+        nr5["cpu_baseline"] = oracle_leg("single5", 256, what="5 MHz slots")
 
     out = {"metric": METRIC, "value": round(value, 2), "unit": "Msamples/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 4), "higher_is_better": True,
